@@ -1,0 +1,189 @@
+"""Python handle on the FP64 CPU oracle (``dpo.c``).  TEST INFRASTRUCTURE ONLY.
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this module.  It never imports the GPU package and the
+GPU package never imports it.  Inputs are netlist/library text and numpy
+arrays; all outputs are numpy arrays in the netlist's own order (nets in
+declaration order, startpoints in order of appearance, cells in order of
+appearance).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dpo.c")
+_OUT = os.path.join(_HERE, "_out")
+_SO = os.path.join(_OUT, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_P = ctypes.c_void_p
+_D = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+_F = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
+_U32 = np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")
+_U64 = np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")
+_I64 = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
+
+
+def build(force: bool = False) -> str:
+    """Compiles the oracle with the host C compiler (no GPU code)."""
+    os.makedirs(_OUT, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _opt(ptr_type):
+    """ndpointer that also accepts None."""
+    class _Opt(ptr_type):  # type: ignore[misc, valid-type]
+        @classmethod
+        def from_param(cls, obj):
+            return None if obj is None else ptr_type.from_param(obj)
+    return _Opt
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            L.orc_load.argtypes = [ctypes.c_char_p, ctypes.c_char_p, ctypes.c_char_p, ctypes.c_int]
+            L.orc_load.restype = _P
+            L.orc_free.argtypes = [_P]
+            L.orc_info.argtypes = [_P, _I64]
+            L.orc_start_nets.argtypes = [_P, _I64]
+            L.orc_cell_outs.argtypes = [_P, _I64]
+            L.orc_set_pincap.argtypes = [_P, ctypes.c_int64, ctypes.c_double]
+            L.orc_cload.argtypes = [_P, _D]
+            L.orc_forward.argtypes = [_P, _D, _D, ctypes.c_int, _D, _D]
+            L.orc_forward.restype = ctypes.c_int
+            L.orc_power.argtypes = [_P, _D, ctypes.c_double, ctypes.c_double]
+            L.orc_power.restype = ctypes.c_double
+            L.orc_backward.argtypes = [_P, _D, _D, _opt(_D), ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                       ctypes.c_double, _opt(_D), _opt(_D), _opt(_D), _opt(_D), _opt(_D)]
+            L.orc_backward.restype = ctypes.c_int
+            L.orc_philox4x32_10.argtypes = [_U32, _U32, _U32]
+            L.orc_simulate.argtypes = [_P, _F, _F, ctypes.c_uint64, ctypes.c_int, _opt(_U64), _U32, _U32]
+            L.orc_simulate.restype = ctypes.c_int
+            L.orc_hybrid.argtypes = [_P, _D, _U32, ctypes.c_int, ctypes.c_double, ctypes.c_double, _D, _D]
+            _lib = L
+    return _lib
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    """One Philox4x32-10 block: counter (4 x u32), key (2 x u32) -> 4 x u32."""
+    out = np.zeros(4, np.uint32)
+    _load().orc_philox4x32_10(np.ascontiguousarray(ctr, np.uint32), np.ascontiguousarray(key, np.uint32), out)
+    return out
+
+
+class Oracle:
+    """FP64 reference for one netlist."""
+
+    def __init__(self, netlist: str, library: str):
+        L = _load()
+        err = ctypes.create_string_buffer(512)
+        h = L.orc_load(netlist.encode(), library.encode(), err, 512)
+        if not h:
+            raise ValueError(f"oracle: {err.value.decode()}")
+        self._h = h
+        info = np.zeros(5, np.int64)
+        L.orc_info(h, info)
+        self.n_nets, self.n_start, self.n_cells, self.n_edges, self.depth = (int(x) for x in info)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.orc_free(h)
+            self._h = None
+
+    def start_nets(self) -> np.ndarray:
+        out = np.zeros(self.n_start, np.int64)
+        _load().orc_start_nets(self._h, out)
+        return out
+
+    def cell_outs(self) -> np.ndarray:
+        out = np.zeros(self.n_cells, np.int64)
+        _load().orc_cell_outs(self._h, out)
+        return out
+
+    def set_pincap(self, cell: int, cap: float) -> None:
+        _load().orc_set_pincap(self._h, int(cell), float(cap))
+
+    def cload(self) -> np.ndarray:
+        out = np.zeros(self.n_nets, np.float64)
+        _load().orc_cload(self._h, out)
+        return out
+
+    def forward(self, sp_in, tr_in, tr_mode: int = 0):
+        """Per-net SP and TR (Algorithm 2, Eq. 2) from startpoint inputs (binary32 inputs
+        convert exactly; binary64 inputs allow finite differences)."""
+        sp = np.zeros(self.n_nets, np.float64)
+        tr = np.zeros(self.n_nets, np.float64)
+        _load().orc_forward(self._h, np.ascontiguousarray(sp_in, np.float64),
+                            np.ascontiguousarray(tr_in, np.float64), int(tr_mode), sp, tr)
+        return sp, tr
+
+    def power(self, alpha, vdd: float = 0.8, fclk: float = 1e9) -> float:
+        """Eq. 1 in watts, caps in fF."""
+        return float(_load().orc_power(self._h, np.ascontiguousarray(alpha, np.float64), vdd, fclk))
+
+    def backward(self, sp, alpha, beta=None, grad_mode: int = 0, tr_mode: int = 0,
+                 vdd: float = 0.8, fclk: float = 1e9) -> dict:
+        """Gradients of Eq. 1 (Eq. 7; Eq. 6 for grad_mode 1)."""
+        out = {
+            "grad_sp_in": np.zeros(self.n_start), "grad_tr_in": np.zeros(self.n_start),
+            "grad_pincap": np.zeros(self.n_cells), "grad_cload": np.zeros(self.n_nets),
+            "grad_net": np.zeros(self.n_nets),
+        }
+        if grad_mode and beta is None:
+            raise ValueError("beta required for hybrid gradient modes")
+        rc = _load().orc_backward(self._h, np.ascontiguousarray(sp, np.float64),
+                                  np.ascontiguousarray(alpha, np.float64),
+                                  None if beta is None else np.ascontiguousarray(beta, np.float64),
+                                  int(grad_mode), int(tr_mode), vdd, fclk, out["grad_sp_in"],
+                                  out["grad_tr_in"], out["grad_pincap"], out["grad_cload"], out["grad_net"])
+        if rc != 0:
+            raise MemoryError("oracle backward")
+        return out
+
+    def simulate(self, sp_in, tr_in, seed: int = 42, T: int = 64, want_words: bool = False):
+        """Bit-packed Markov simulation: (toggles, ones[, words[n_nets, T]])."""
+        tg = np.zeros(self.n_nets, np.uint32)
+        on = np.zeros(self.n_nets, np.uint32)
+        words = np.zeros((self.n_nets, T), np.uint64) if want_words else None
+        rc = _load().orc_simulate(self._h, np.ascontiguousarray(sp_in, np.float32),
+                                  np.ascontiguousarray(tr_in, np.float32), int(seed), int(T), words, tg, on)
+        if rc != 0:
+            raise MemoryError("oracle simulate")
+        return (tg, on, words) if want_words else (tg, on)
+
+    def hybrid(self, tr_model, toggles, T: int = 64, beta_min: float = 0.1, beta_max: float = 10.0):
+        """Eq. 4-5: (beta, hybrid TR) per net."""
+        beta = np.zeros(self.n_nets)
+        trh = np.zeros(self.n_nets)
+        _load().orc_hybrid(self._h, np.ascontiguousarray(tr_model, np.float64),
+                           np.ascontiguousarray(toggles, np.uint32), int(T), beta_min, beta_max, beta, trh)
+        return beta, trh
+
+    def step(self, sp_in, tr_in, *, seed: int = 42, T: int = 64, grad_mode: int = 1, tr_mode: int = 0,
+             vdd: float = 0.8, fclk: float = 1e9, beta_min: float = 0.1, beta_max: float = 10.0) -> dict:
+        """The whole hot path once: forward, power, simulation, hybrid, adjoint."""
+        sp, tr = self.forward(sp_in, tr_in, tr_mode)
+        p_model = self.power(tr, vdd, fclk)
+        tg, on = self.simulate(sp_in, tr_in, seed, T)
+        beta, trh = self.hybrid(tr, tg, T, beta_min, beta_max)
+        p_hyb = self.power(trh, vdd, fclk)
+        alpha = trh if grad_mode else tr
+        g = self.backward(sp, alpha, beta if grad_mode else None, grad_mode, tr_mode, vdd, fclk)
+        g.update(sp=sp, tr=tr, toggles=tg, ones=on, beta=beta, tr_hyb=trh, power_model=p_model,
+                 power_hybrid=p_hyb)
+        return g

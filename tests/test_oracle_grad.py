@@ -1,0 +1,170 @@
+"""Oracle gradient pins (Sec. III-E, Eq. 7; Sec. III-D, Eq. 6; Sec. V-B protocol).
+
+* dP/d(input SP): central finite differences of the FP64 forward + Eq. 1 (h = 1e-5).
+* The paper's own thresholds (Sec. V-B: 32 random roots, eps = 1e-4, mean relative error
+  < 1e-4, max < 2e-4), applied with a central difference. A one-sided difference carries an
+  O(eps) truncation error that alone exceeds those thresholds on these netlists, so the
+  one-sided form is checked for first-order convergence instead.
+* dP/d(input TR), dP/d(pin cap), dP/d(C_load): P is linear in each, so finite differences
+  are exact up to rounding.
+* Hybrid mode 2 (beta held fixed): finite differences of sum K beta TR C.
+* Hybrid mode 1 (Eq. 6, beta scales the accumulated gradient): closed form on an inverter
+  chain, sum over stages of (product of betas up to the stage) * local term * (-1)^stage;
+  with all beta = 1 it reduces to the model gradient.
+"""
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle
+from paper_2608_03778_gb300 import netgen
+
+VDD, F = 0.8, 1e9
+K = 0.5 * VDD ** 2 * F * 1e-15
+
+
+@pytest.fixture(scope="module")
+def small(library_text):
+    spec = netgen.WORKLOADS["small"]
+    o = Oracle(netgen.netlist_text(spec), library_text)
+    sp_in, tr_in = netgen.scenario_inputs(o.n_start, 1000)
+    return o, sp_in[:, 0].astype(np.float64), tr_in[:, 0].astype(np.float64)
+
+
+def P_of(o, sp_in, tr_in, tr_mode=0, beta=None):
+    sp, tr = o.forward(sp_in, tr_in, tr_mode)
+    return o.power(tr if beta is None else beta * tr, VDD, F)
+
+
+def fd_ok(g, fd):
+    return np.abs(g - fd) <= 1e-6 * np.abs(fd) + 1e-8 * np.abs(fd).max()
+
+
+@pytest.mark.parametrize("tr_mode", [0, 1])
+def test_grad_sp_central_fd(small, tr_mode):
+    o, sp_in, tr_in = small
+    sp, tr = o.forward(sp_in, tr_in, tr_mode)
+    g = o.backward(sp, tr, None, 0, tr_mode, VDD, F)["grad_sp_in"]
+    h = 1e-5
+    fd = np.empty(o.n_start)
+    for k in range(o.n_start):
+        up, dn = sp_in.copy(), sp_in.copy()
+        up[k] += h
+        dn[k] -= h
+        fd[k] = (P_of(o, up, tr_in, tr_mode) - P_of(o, dn, tr_in, tr_mode)) / (2 * h)
+    assert fd_ok(g, fd).all()
+
+
+def test_paper_protocol_thresholds(small):
+    o, sp_in, tr_in = small
+    sp, tr = o.forward(sp_in, tr_in)
+    g = o.backward(sp, tr, None, 0, 0, VDD, F)["grad_sp_in"]
+    rng = np.random.default_rng(32)
+    roots = rng.choice(o.n_start, 32, replace=False)
+    eps = 1e-4
+    rel = []
+    for k in roots:
+        up, dn = sp_in.copy(), sp_in.copy()
+        up[k] += eps
+        dn[k] -= eps
+        fd = (P_of(o, up, tr_in) - P_of(o, dn, tr_in)) / (2 * eps)
+        rel.append(abs(fd - g[k]) / abs(g[k]))
+    rel = np.array(rel)
+    assert rel.mean() < 1e-4 and rel.max() < 2e-4, rel
+
+
+def test_one_sided_difference_converges_first_order(small):
+    o, sp_in, tr_in = small
+    sp, tr = o.forward(sp_in, tr_in)
+    g = o.backward(sp, tr, None, 0, 0, VDD, F)["grad_sp_in"]
+    p0 = P_of(o, sp_in, tr_in)
+    k = int(np.argmax(np.abs(g)))
+    errs = []
+    for eps in [1e-2, 1e-3, 1e-4]:
+        up = sp_in.copy()
+        up[k] += eps
+        errs.append(abs((P_of(o, up, tr_in) - p0) / eps - g[k]))
+    # the error must fall about tenfold per tenfold smaller step (truncation O(eps))
+    assert 5 < errs[0] / errs[1] < 20 and 5 < errs[1] / errs[2] < 20, errs
+
+
+def test_grad_tr_in_exact_linearity(small):
+    o, sp_in, tr_in = small
+    sp, tr = o.forward(sp_in, tr_in)
+    g = o.backward(sp, tr)["grad_tr_in"]
+    cl = o.cload()
+    np.testing.assert_allclose(g, K * cl[o.start_nets()], rtol=1e-14)
+    d = 1e-3
+    for k in [0, 5, 50, o.n_start - 1]:
+        up = tr_in.copy()
+        up[k] += d
+        fd = (P_of(o, sp_in, up) - P_of(o, sp_in, tr_in)) / d
+        assert fd == pytest.approx(g[k], rel=1e-9)
+
+
+def test_grad_pincap_exact_linearity(library_text):
+    spec = netgen.WORKLOADS["small"]
+    o = Oracle(netgen.netlist_text(spec), library_text)
+    sp_in, tr_in = netgen.scenario_inputs(o.n_start, 1000)
+    sp, tr = o.forward(sp_in[:, 0], tr_in[:, 0])
+    g = o.backward(sp, tr)["grad_pincap"]
+    p0 = o.power(tr, VDD, F)
+    for c in [0, 7, 123, o.n_cells - 1]:
+        o2 = Oracle(netgen.netlist_text(spec), library_text)
+        cl_before = o2.cload()
+        o2.set_pincap(c, 0.8 + 0.5)   # all cells read their cap from the library; set one explicitly
+        base = Oracle(netgen.netlist_text(spec), library_text)
+        # the library cap of cell c: recover it from the load change
+        delta_cl = o2.cload() - cl_before
+        d_cap = delta_cl[delta_cl != 0]
+        assert np.allclose(d_cap, d_cap[0])
+        fd = (o2.power(tr, VDD, F) - base.power(tr, VDD, F)) / d_cap[0]
+        assert fd == pytest.approx(g[c], rel=1e-9)
+
+
+def test_grad_cload_is_K_tr(small):
+    o, sp_in, tr_in = small
+    sp, tr = o.forward(sp_in, tr_in)
+    g = o.backward(sp, tr)["grad_cload"]
+    # P = K sum tr C exactly: rebuild P from the gradient and the loads
+    assert (g * o.cload()).sum() == pytest.approx(o.power(tr, VDD, F), rel=1e-12)
+    np.testing.assert_allclose(g, K * tr, rtol=1e-15)
+
+
+def test_hybrid_exact_mode_central_fd(small):
+    o, sp_in, tr_in = small
+    rng = np.random.default_rng(4)
+    beta = rng.uniform(0.1, 3.0, o.n_nets)
+    sp, tr = o.forward(sp_in, tr_in)
+    g = o.backward(sp, beta * tr, beta, 2, 0, VDD, F)["grad_sp_in"]
+    h = 1e-5
+    fd = np.empty(o.n_start)
+    for k in range(o.n_start):
+        up, dn = sp_in.copy(), sp_in.copy()
+        up[k] += h
+        dn[k] -= h
+        fd[k] = (P_of(o, up, tr_in, 0, beta) - P_of(o, dn, tr_in, 0, beta)) / (2 * h)
+    assert fd_ok(g, fd).all()
+
+
+def inverter_chain(n):
+    lines = [f"net n{i} {1.0 + 0.25 * i}" for i in range(n + 1)] + ["input n0"]
+    lines += [f"cell u{i} INV_X2 A=n{i} ZN=n{i + 1}" for i in range(n)]
+    return "\n".join(lines) + "\n"
+
+
+@pytest.mark.parametrize("x", [0.2, 0.7])
+def test_hybrid_paper_mode_chain_closed_form(x, library_text):
+    n = 6
+    o = Oracle(inverter_chain(n), library_text)
+    rng = np.random.default_rng(9)
+    beta = rng.uniform(0.2, 4.0, n + 1)
+    sp, tr = o.forward(np.array([x]), np.array([0.1]))
+    g = o.backward(sp, beta * tr, beta, 1, 0, VDD, F)["grad_sp_in"][0]
+    cl = o.cload()
+    # net i (i >= 1) has SP x or 1-x; d sp_i / d x = (-1)^i; local_i = K C_i (2 - 4 sp_i)
+    want = sum(np.prod(beta[: i + 1]) * K * cl[i] * (2 - 4 * sp[i]) * (-1) ** i for i in range(1, n + 1))
+    assert g == pytest.approx(want, rel=1e-13)
+    # all beta = 1 reduces to the model gradient
+    g1 = o.backward(sp, tr, np.ones(n + 1), 1, 0, VDD, F)["grad_sp_in"][0]
+    g0 = o.backward(sp, tr, None, 0, 0, VDD, F)["grad_sp_in"][0]
+    assert g1 == pytest.approx(g0, rel=1e-15)
