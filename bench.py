@@ -1,0 +1,334 @@
+#!/usr/bin/env python
+"""Benchmark of the DiffPower hot path on GB300.
+
+One step = the whole hot path once on the roofline-scale synthetic netlist
+(2,000,000 cells, 147,456 startpoints, depth 80, fanout cap 32):
+forward SP/TR + model power, 4,096-vector Markov simulation with PopCount
+toggles, hybrid beta + hybrid power, and the full adjoint (paper's beta rule),
+with gradients w.r.t. input SP/TR, pin caps and net loads written out.
+
+value = cells x ranks / (max over ranks of the device time per step) in
+cell-evals/s; e2e = the same through the C-ABI with host (pinned) buffers,
+host<->device copies included.  Multi-GPU runs are independent replicas.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd cell-evals/s vs HBM roofline; served p50/p99 latency vs plain loop"
+UNIT = "cell-evals/s"
+L2_FLUSH_BYTES = 256 << 20   # > 2x the 126 MB L2
+
+
+def peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def algorithmic_bytes(nn: int, ns: int, nc: int, ne: int, T: int) -> dict:
+    """Compulsory bytes per phase: every structure or value array read or written once,
+    int32 indices, binary32 values, compact CSR (4(nc+1) + 4E + nc bytes of fanin structure);
+    repeated gathers and intermediates (edge adjoints) not counted."""
+    fanin = 4 * (nc + 1) + 4 * ne + nc
+    fanout = 4 * (nn + 1) + 4 * ne
+    return {
+        # inputs, fanin structure, C_load, SP and TR out
+        "forward": fanin + 8 * ns + 4 * nn + 8 * nn,
+        # inputs, fanin structure, every net's words written once and read once, toggles + ones,
+        # beta and hybrid TR out (TR_model read)
+        "simulation": 8 * ns + fanin + 2 * 8 * T * nn + 8 * nn + 12 * nn,
+        # fanin + fanout structure, SP, C_load, beta read; adjoint per net written
+        "backward": fanin + fanout + 4 * nn * 3 + 4 * nn,
+        # outputs: grad_cload (TR, beta in, out), grad_pincap (structure, out), grad_tr_in, grad_sp_in
+        "outputs": 12 * nn + fanin + 4 * nc + 8 * ns + 8 * ns,
+    }
+
+
+class Clocks:
+    """Samples nvidia-smi during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(gpu)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.p = None
+
+    def stop(self) -> dict | None:
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as g:
+            for line in g:
+                c = [x.strip() for x in line.split(",")]
+                if len(c) >= 9:
+                    rows.append(c)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(world: int):
+    import torch
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return dist if world > 1 else None
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int) -> None:
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def workload(name: str):
+    from paper_2608_03778_gb300 import netgen
+    spec = netgen.WORKLOADS[name]
+    lib = netgen.library_text()
+    text = netgen.netlist_text(spec)
+    sp, tr = netgen.scenario_inputs(spec.n_start, 1000)
+    return spec, lib, text, np.ascontiguousarray(sp[:, 0]), np.ascontiguousarray(tr[:, 0])
+
+
+def cpu_baseline(text: str, lib: str, sp, tr, n_cells: int, T: int) -> dict:
+    """The FP64 oracle, as it stands, single-threaded, on one full step of the same workload."""
+    from oracle.oracle import Oracle
+    o = Oracle(text, lib)
+    t0 = time.perf_counter()
+    o.step(sp, tr, seed=42, T=T, grad_mode=1)
+    dt = time.perf_counter() - t0
+    return {"value": n_cells / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one full step (forward, power, {64 * T}-vector simulation, hybrid, adjoint) of the same "
+                      f"netlist, {dt:.1f} s, single thread"}
+
+
+def run_reference(args, rank: int, world: int) -> None:
+    """Reference arm: the FP64 CPU oracle on the host cores, rank 0 only."""
+    if rank != 0:
+        return
+    from oracle.oracle import Oracle
+    spec, lib, text, sp, tr = workload(args.workload)
+    o = Oracle(text, lib)
+    T, T_sample = 64, 8
+
+    def one():
+        t0 = time.perf_counter()
+        s, t = o.forward(sp, tr, 0)
+        o.power(t)
+        t1 = time.perf_counter()
+        tg, _ = o.simulate(sp, tr, 42, T_sample)
+        beta, trh = o.hybrid(t, tg, T_sample)
+        o.power(trh)
+        t2 = time.perf_counter()
+        o.backward(s, trh, beta, 1, 0)
+        t3 = time.perf_counter()
+        return (t1 - t0) + (t3 - t2) + (t2 - t1) * (T / T_sample)
+
+    for _ in range(args.warmup):
+        one()
+    ts = [one() for _ in range(args.steps)]
+    ms = 1e3 * sum(ts) / len(ts)
+    val = spec.n_cells / (ms / 1e3)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {spec.n_cells} cells, {spec.n_start} startpoints, depth "
+                               f"{spec.depth}", "sim_vectors": 64 * T},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"per step: forward, power and adjoint of the full netlist plus the simulation "
+                                   f"at {64 * T_sample} vectors, its time scaled by {T // T_sample} to "
+                                   f"{64 * T} vectors; single thread"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="roofline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    args.warmup = max(3, args.warmup)
+
+    import torch
+    torch.cuda.set_device(local)
+    dist_setup(world)
+    from paper_2608_03778_gb300 import dp
+
+    spec, lib, text, sp, tr = workload(args.workload)
+    stream = torch.cuda.current_stream()
+    ctx = dp.dp_create(local, stream.cuda_stream)
+    d = dp.dp_design_load(ctx, text, lib)
+    info = dp.dp_design_info(d)
+    nn, ns, nc, ne = info.n_nets, info.n_start, info.n_cells, info.n_edges
+    cfg = dp.config()   # grad_mode 1 (paper's beta rule), 64 words, tr_mode 0
+    dev = torch.device("cuda", local)
+    sp_d, tr_d = torch.from_numpy(sp).to(dev), torch.from_numpy(tr).to(dev)
+    g = {k: torch.zeros(n, device=dev) for k, n in [("sp", ns), ("tr", ns), ("pin", nc), ("cl", nn)]}
+    watts = np.zeros(2)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        dp.dp_set_inputs(ctx, d, sp_d, tr_d, 1, 1)
+        dp.dp_step(ctx, d, cfg, g["sp"], g["tr"], g["pin"], g["cl"], None, 1)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- device-timed steps, L2 flushed before each (outside the events)
+    clk = Clocks(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    phases = []
+    barrier(world)
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+        phases.append(dp.dp_phase_times(ctx, d))   # library events around each phase of this step
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = clk.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = max_over_ranks(sum(step_ms) / len(step_ms), world)
+    ph = np.median(np.stack(phases), axis=0)
+    kernels = dp.dp_step_kernels(d)
+    dp.dp_step(ctx, d, cfg, g["sp"], g["tr"], g["pin"], g["cl"], watts, 1)
+
+    # ---- end to end through the C-ABI with pinned host buffers
+    pin = lambda n, dt: torch.empty(n, dtype=dt, pin_memory=True).numpy()  # noqa: E731
+    sp_h, tr_h = pin(ns, torch.float32), pin(ns, torch.float32)
+    sp_h[:], tr_h[:] = sp, tr
+    hg = {k: pin(n, torch.float32) for k, n in [("sp", ns), ("tr", ns), ("pin", nc), ("cl", nn)]}
+    w_h = pin(2, torch.float64)
+    for _ in range(2):
+        dp.dp_set_inputs(ctx, d, sp_h, tr_h, 1, 0)
+        dp.dp_step(ctx, d, cfg, hg["sp"], hg["tr"], hg["pin"], hg["cl"], w_h, 0)
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        dp.dp_set_inputs(ctx, d, sp_h, tr_h, 1, 0)
+        dp.dp_step(ctx, d, cfg, hg["sp"], hg["tr"], hg["pin"], hg["cl"], w_h, 0)
+    e2e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0) / args.steps, world)
+    barrier(world)
+    h2d = 8 * ns
+    d2h = 4 * (2 * ns + nc + nn) + 16
+
+    # ---- roofline of the dominant phase
+    pk = peaks()
+    ab = algorithmic_bytes(nn, ns, nc, ne, cfg.sim_words)
+    names = ["forward", "simulation", "backward", "outputs"]
+    per_phase = {}
+    for i, n in enumerate(names):
+        t = float(ph[i]) * 1e-3
+        ach = ab[n] / t / 1e9 if t > 0 else 0.0
+        per_phase[n] = {"ms": float(ph[i]), "algorithmic_bytes": ab[n], "achieved_gbs": ach,
+                        "frac": ach / pk["hbm_gbs"]}
+    dom = max(names[:3], key=lambda n: per_phase[n]["ms"])
+    fb_ms = per_phase["forward"]["ms"] + per_phase["backward"]["ms"]
+    line = {
+        "metric": METRIC,
+        "value": nc * world / (ms / 1e3),
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {
+            "workload": f"{args.workload}: {nc} cells, {ns} startpoints ({spec.n_pi} PI + {spec.n_dff} DFF), "
+                        f"depth {info.n_levels}, fanout cap {spec.fanout_cap}, seed {spec.seed}",
+            "step": "forward SP/TR + power, 4,096-vector simulation, hybrid beta + power, adjoint "
+                    "(grad_mode 1) with all gradient outputs",
+            "global_batch": 1, "parallelism": f"replicas x{world}",
+            "l2": "256 MB buffer written before every timed step (outside the step's events)",
+        },
+        "roofline": {"bound": "hbm", "kernel": f"{dom} phase ({info.n_levels} per-level launches)",
+                     "achieved": per_phase[dom]["achieved_gbs"], "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": per_phase[dom]["frac"], "traffic": None, "peak_source": pk["source"]},
+        "phases": per_phase,
+        "fwd_bwd": {"ms": fb_ms, "cell_evals_per_s": nc / (fb_ms / 1e3),
+                    "frac": (ab["forward"] + ab["backward"]) / (fb_ms / 1e3) / 1e9 / pk["hbm_gbs"]},
+        "power_w": {"model": float(watts[0]), "hybrid": float(watts[1])},
+        "e2e": {"value": nc * world / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(kernels),
+        "clocks": clocks,
+        "device_bytes": int(info.device_bytes),
+    }
+    dp.dp_design_free(d)
+    dp.dp_destroy(ctx)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(text, lib, sp, tr, nc, cfg.sim_words)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

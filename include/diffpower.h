@@ -1,0 +1,236 @@
+/*
+ * diffpower.h - C-ABI of the GB300 DiffPower hot path (libdiffpower.so).
+ *
+ * The library keeps a compiled netlist resident on one GPU and runs the
+ * paper's analysis steps on it:
+ *   load a bytecode netlist (Sec. III-A, Algorithm 1), set the startpoint SP/TR
+ *   (Sec. III-A), propagate SP/TR (Sec. III-B, Algorithm 2, Eq. 2), simulate
+ *   (Sec. III-C, Eq. 4), calibrate beta (Sec. III-D, Eq. 5), report switching
+ *   power (Eq. 1) and back-propagate its gradient (Sec. III-E, Eq. 6, Eq. 7).
+ *
+ * Conventions for every entry point:
+ *  - Return value: DP_OK or an error code; after an error, dp_last_error()
+ *    on the context gives a one-line message. Invalid sizes, NULL required
+ *    pointers and calls in the wrong order are rejected before any GPU work.
+ *  - Ownership: the library owns dp_ctx, dp_design and dp_compiled objects
+ *    and their device memory. Caller buffers are borrowed for the duration of
+ *    the call only: inputs are copied in, outputs are written into caller
+ *    memory. `on_device` = 1 means the caller's pointers are device pointers
+ *    on the context's device, 0 means host pointers.
+ *  - Ordering: every per-net array is in net declaration order of the
+ *    netlist text, every per-startpoint array in the order in which
+ *    startpoints appear (`input` and `dff` lines), every per-cell array in the
+ *    order of `cell` lines. The library's internal renumbering never shows.
+ *  - Streams: work is queued on the context's stream (the one given to
+ *    dp_create, e.g. PyTorch's current stream, or a private one). Calls that
+ *    write host memory synchronise that stream before they return; calls
+ *    with device outputs return without synchronising.
+ *  - Threads: one context per host thread.
+ *  - Device waits: no kernel of the library waits without a bound. A wait
+ *    that runs out records an error on the device; the next synchronising
+ *    call returns DP_ETIMEOUT and the design stays usable.
+ *
+ * Text formats (whitespace separated, '#' starts a comment):
+ *   library:  cell <ref> <out_pin> <pin_cap_fF> <function>
+ *             seq  <ref> <d_pin> <q_pin> <d_pin_cap_fF>
+ *     <function> uses identifiers (input pins), 0, 1, parentheses and
+ *     ! ~ (not, prefix), ' (not, postfix), & * (and), ^ (xor), | + (or), with
+ *     precedence NOT > AND > XOR > OR (Sec. III-A).
+ *   netlist:  net <name> <wire_cap_fF>          (declares a net, in order)
+ *             input <net>                        (primary input: startpoint)
+ *             output <net>                       (primary output: no extra load)
+ *             dff <inst> <seq_ref> <d>=<net> <q>=<net>
+ *                 (Q is a pseudo-primary input / startpoint; D is a
+ *                  pseudo-primary output and adds the D pin cap to its net)
+ *             cell <inst> <ref> <pin>=<net> ... (every pin connected once)
+ *   Every net needs exactly one driver; combinational cycles are rejected.
+ *   Limits: at most 4 inputs per cell, fewer than 2^24 nets.
+ */
+#ifndef DIFFPOWER_H
+#define DIFFPOWER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DP_OK = 0,
+    DP_EINVAL = 1,        /* bad argument or size */
+    DP_EPARSE = 2,        /* malformed library or netlist text */
+    DP_ECYCLE = 3,        /* combinational cycle */
+    DP_ENOMEM = 4,        /* host or device allocation failed */
+    DP_ECUDA = 5,         /* a CUDA runtime call failed */
+    DP_ETIMEOUT = 6,      /* a bounded device wait gave up */
+    DP_ESTATE = 7,        /* call out of order (e.g. backward before propagate) */
+    DP_EUNSUPPORTED = 8   /* valid input beyond this library's limits */
+} dp_status;
+
+typedef struct dp_ctx dp_ctx;
+typedef struct dp_design dp_design;
+typedef struct dp_compiled dp_compiled;
+
+/* Analysis settings.  Defaults (dp_config_default): Vdd 0.8 V, f 1 GHz,
+ * beta in [0.1, 10] (Sec. V-B), tr_mode 0, grad_mode 1, 64 words (4,096
+ * vectors), seed 42. */
+typedef struct {
+    double vdd;          /* supply voltage, V (Eq. 1) */
+    double fclk;         /* clock frequency, Hz (Eq. 1) */
+    float beta_min;      /* Eq. 5 clip bounds */
+    float beta_max;
+    int32_t tr_mode;     /* 0: startpoint TR = given input TR, 2P(1-P) elsewhere;
+                            1: TR = 2P(1-P) on every net (Eq. 2, Algorithm 2 kernel 3) */
+    int32_t grad_mode;   /* 0: gradient of the model power (Eq. 7);
+                            1: hybrid, paper rule - each net's accumulated gradient
+                               is multiplied by its beta (Eq. 6);
+                            2: hybrid, exact gradient of sum K beta TR C with beta fixed */
+    int32_t sim_words;   /* T, 64-bit words per net: 64*T vectors, 64*(T-1) transitions (Eq. 4); 2..4096 */
+    int32_t reserved;    /* must be 0 */
+    uint64_t seed;       /* Philox4x32-10 key for the startpoint Markov chains (Sec. III-C) */
+} dp_config;
+
+typedef struct {
+    int64_t n_nets;      /* all nets, startpoints included */
+    int64_t n_start;     /* startpoints: primary inputs + DFF Q pins */
+    int64_t n_cells;     /* combinational cells */
+    int64_t n_edges;     /* cell input pins (fanin edges) */
+    int32_t n_levels;    /* depth: cells sit on levels 1..n_levels (Sec. III-A) */
+    int32_t n_ops;       /* distinct cell functions (logic ids) in use */
+    size_t device_bytes; /* device memory held by the design, bytes */
+} dp_info;
+
+/* Fills *cfg with the defaults above. */
+void dp_config_default(dp_config *cfg);
+
+/* One-line message of the last failing call on this context (never NULL). */
+const char *dp_last_error(const dp_ctx *ctx);
+
+/* ---------------- host-only compilation (no GPU needed) ---------------- */
+
+/* Compiles library + netlist text on the host (Sec. III-A, Algorithm 1):
+ * parses every library function into post-order stack bytecode (IN(k), NOT,
+ * AND, OR, XOR, CONST_0/1), matches common gates to fixed logic ids and
+ * deduplicates the rest by bytecode signature, derives each function's truth
+ * table by running its bytecode, levelizes the netlist, renumbers cells level
+ * by level sorted by logic id, and builds the fanin records and the
+ * transposed fanout CSR.  On failure returns DP_EPARSE / DP_ECYCLE /
+ * DP_EUNSUPPORTED / DP_ENOMEM and writes a message into err (errlen bytes,
+ * may be NULL). *out is owned by the caller and freed with dp_compiled_free. */
+dp_status dp_compile(const char *netlist, size_t netlist_len, const char *library, size_t library_len,
+                     dp_compiled **out, char *err, size_t errlen);
+void dp_compiled_free(dp_compiled *c);
+dp_status dp_compiled_info(const dp_compiled *c, dp_info *info);
+
+/* Read-only views into a compiled netlist, for inspection and tests.  All
+ * pointers are host memory owned by *c and valid until dp_compiled_free.
+ * Internal numbering: nets [0, n_start) are the startpoints in input order;
+ * internal cell i (level-major, sorted by logic id inside a level) drives
+ * internal net n_start + i. */
+typedef struct {
+    const int32_t *lvl_ptr;      /* [n_levels+1]: cells of level l (1-based) are [lvl_ptr[l-1], lvl_ptr[l]) */
+    const uint32_t *fanin;       /* [4*n_cells]: word 4i+j = internal net of input slot j of cell i;
+                                    bits 24..31 of word 4i hold the cell's logic id; unused slots 0xFFFFFF */
+    const int32_t *fout_ptr;     /* [n_nets+1]: fanout edges of internal net n */
+    const int32_t *fout_edge;    /* [n_edges]: edge id 4*cell+slot, ascending within a net */
+    const int32_t *net_of_user;  /* [n_nets]: declaration index -> internal net */
+    const int32_t *cell_of_user; /* [n_cells]: cell line index -> internal cell */
+    const float *base_cap;       /* [n_nets]: wire cap + DFF D pin caps, fF, internal order */
+    const float *pincap;         /* [n_cells]: input pin cap, fF, internal order */
+    const uint8_t *op_arity;     /* [256]: inputs of each logic id */
+    const uint16_t *op_tt;       /* [256]: truth table, bit m = f(m), bit j of m = input slot j */
+    /* Algorithm 1 export: bytecode of every non-common function (logic id >= 32) */
+    const uint8_t *bc_ops;       /* [n_bc]: 0 IN, 1 NOT, 2 AND, 3 OR, 4 XOR, 5 CONST_0, 6 CONST_1 */
+    const int8_t *bc_args;       /* [n_bc]: IN slot, else 0 */
+    const int32_t *bc_offset;    /* [256]: start of a logic id's bytecode, -1 for common gates */
+    const int32_t *bc_length;    /* [256] */
+    int64_t n_bc;
+} dp_compiled_view;
+dp_status dp_compiled_view_get(const dp_compiled *c, dp_compiled_view *view);
+
+/* Logic id and bytecode of one function string under the library rules
+ * (Algorithm 1 for a single expression).  ops/args receive up to cap
+ * instructions; *len the full length; *n_inputs the input count; *tt the
+ * truth table when n_inputs <= 4; *logic_id the common-gate id (< 32), or -1
+ * for a function that would get a generated id. */
+dp_status dp_compile_function(const char *func, uint8_t *ops, int8_t *args, int32_t cap, int32_t *len,
+                              int32_t *n_inputs, uint16_t *tt, int32_t *logic_id);
+
+/* ------------------------------ GPU side ------------------------------- */
+
+/* Creates a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * to queue work on (NULL: the library creates a private non-blocking stream). */
+dp_status dp_create(int device, void *cuda_stream, dp_ctx **out);
+void dp_destroy(dp_ctx *ctx);
+
+/* Waits for all work queued by this context; returns DP_ETIMEOUT if a bounded
+ * device wait gave up since the last synchronisation. */
+dp_status dp_sync(dp_ctx *ctx);
+
+/* Compiles (as dp_compile) and uploads a netlist; the design keeps its whole
+ * graph and per-net state resident in device memory (Sec. III). */
+dp_status dp_design_load(dp_ctx *ctx, const char *netlist, size_t netlist_len, const char *library,
+                         size_t library_len, dp_design **out);
+/* Uploads an already compiled netlist (the compiled object is not consumed). */
+dp_status dp_design_upload(dp_ctx *ctx, const dp_compiled *c, dp_design **out);
+void dp_design_free(dp_design *d);
+dp_status dp_design_info(const dp_design *d, dp_info *info);
+
+/* Startpoint SP and TR (Sec. III-A), n_start values each, binary32.  Only
+ * n_scen = 1 is supported (DP_EUNSUPPORTED otherwise).  SP must lie in [0,1]
+ * and TR in [0,1]; values are not checked on the device path. */
+dp_status dp_set_inputs(dp_design *d, const float *sp, const float *tr, int32_t n_scen, int on_device);
+
+/* Sizing delta: sets the input pin cap (fF) of n cells given by cell-line index
+ * and updates the loads C_load of the nets they read (Eq. 1). Indices must be
+ * in range (checked for host input only). */
+dp_status dp_set_pincap(dp_design *d, const int32_t *cells, const float *pincap, int32_t n, int on_device);
+
+/* Pass 1 (Sec. III-B, Algorithm 2): SP and TR_model (Eq. 2) of every net, and the
+ * model power (Eq. 1).  Needs dp_set_inputs. */
+dp_status dp_propagate(dp_design *d, const dp_config *cfg);
+
+/* Pass 2 and hybrid (Sec. III-C, III-D): Markov-chain startpoint vectors
+ * (Philox4x32-10), bit-packed simulation of cfg->sim_words words per net,
+ * PopCount toggle and ones counts, beta (Eq. 5), hybrid TR = beta TR_model and
+ * the hybrid power.  Needs dp_propagate with the same tr_mode. */
+dp_status dp_simulate(dp_design *d, const dp_config *cfg);
+
+/* Total switching power (Eq. 1) in watts into watts[0] (host):
+ * hybrid = 0 model TR, 1 hybrid TR.  Synchronises. */
+dp_status dp_total_power(dp_design *d, int hybrid, double *watts);
+
+/* Sec. III-E: gradient of the power with respect to the startpoint SP
+ * (grad_sp_in[n_start]), startpoint TR (grad_tr_in[n_start]), the input pin
+ * cap of each cell (grad_pincap[n_cells], W/fF) and each net's load
+ * (grad_cload[n_nets], W/fF).  Any output may be NULL.  cfg->grad_mode picks
+ * the model (needs dp_propagate) or a hybrid objective (needs dp_simulate).
+ * No atomics: results are bitwise reproducible. */
+dp_status dp_backward(dp_design *d, const dp_config *cfg, float *grad_sp_in, float *grad_tr_in,
+                      float *grad_pincap, float *grad_cload, int on_device);
+
+/* Per-net results: SP, TR_model, beta, hybrid TR, toggle and ones counts.
+ * Any output may be NULL; beta/tr_hyb/toggles/ones need dp_simulate. */
+dp_status dp_get_nets(dp_design *d, float *sp, float *tr, float *beta, float *tr_hyb, uint32_t *toggles,
+                      uint32_t *ones, int on_device);
+
+/* The whole hot path in one call: dp_propagate, dp_simulate, dp_backward and
+ * both powers (watts[0] model, watts[1] hybrid; host, may be NULL), replayed
+ * as one CUDA graph per (design, config).  Gradient outputs as dp_backward. */
+dp_status dp_step(dp_design *d, const dp_config *cfg, float *grad_sp_in, float *grad_tr_in, float *grad_pincap,
+                  float *grad_cload, double *watts, int on_device);
+
+/* Device time in milliseconds of the last dp_step / dp_propagate / dp_simulate /
+ * dp_backward per phase (CUDA events on the context stream; synchronises):
+ * ms[0] forward, ms[1] simulation + hybrid, ms[2] backward, ms[3] power + cap gradients. */
+dp_status dp_phase_times(dp_design *d, float *ms4);
+
+/* Number of kernels the last dp_step launched: the kernel nodes of its CUDA
+ * graph plus the output kernels queued after it (0 before the first dp_step). */
+dp_status dp_step_kernels(const dp_design *d, int64_t *kernels);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DIFFPOWER_H */

@@ -1,0 +1,626 @@
+// C-ABI of libdiffpower.so: contexts, resident designs, and the call sequence
+// of the hot path (load, set inputs, propagate, simulate, power, backward).
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "compiled.h"
+#include "diffpower.h"
+#include "kernels.h"
+
+struct dp_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+};
+
+struct dp_design {
+    dp_ctx *ctx = nullptr;
+    dp::DevDesign d{};
+    dp::OpTable ops{};
+    std::vector<int32_t> lvl_ptr;
+    int64_t n_edges = 0;
+    int32_t n_ops = 0;
+    std::vector<void *> allocs;
+    size_t bytes = 0;
+    int words_T = 0;
+    // output staging for host outputs
+    float *st_gsp = nullptr, *st_gtr = nullptr, *st_gpin = nullptr, *st_gcl = nullptr;
+    // state
+    bool inputs_set = false;
+    bool fwd_valid = false;
+    int fwd_tr_mode = -1;
+    bool sim_valid = false;
+    // graph of the whole step for one config
+    cudaGraphExec_t graph = nullptr;
+    dp_config graph_cfg{};
+    cudaStream_t cap_stream = nullptr;
+    int64_t graph_kernels = 0;
+    int64_t step_kernels = 0;
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    bool ev_valid[5] = {false, false, false, false, false};
+};
+
+namespace {
+
+// Host-side fault injection for tests: DP_FAULT=alloc:N fails the N-th
+// device allocation of the process with DP_ENOMEM (no GPU fault involved).
+long g_alloc_count = 0;
+long fault_alloc_at() {
+    static long at = -2;
+    if (at == -2) {
+        at = -1;
+        const char *f = std::getenv("DP_FAULT");
+        if (f && std::strncmp(f, "alloc:", 6) == 0) at = std::atol(f + 6);
+    }
+    return at;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+dp_status set_err(dp_ctx *c, dp_status s, const std::string &m) {
+    if (c) c->err = m;
+    return s;
+}
+
+dp_status cuda_err(dp_ctx *c, cudaError_t e, const char *where) {
+    if (e == cudaSuccess) return DP_OK;
+    dp_status s = e == cudaErrorMemoryAllocation ? DP_ENOMEM : DP_ECUDA;
+    return set_err(c, s, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+dp_status launch_check(dp_ctx *c, const char *where) { return cuda_err(c, cudaGetLastError(), where); }
+
+template <class T>
+dp_status dalloc(dp_design *D, T **p, size_t count) {
+    *p = nullptr;
+    size_t bytes = sizeof(T) * (count ? count : 1);
+    long n = ++g_alloc_count;
+    if (fault_alloc_at() == n) return set_err(D->ctx, DP_ENOMEM, "injected allocation failure (DP_FAULT)");
+    void *v = nullptr;
+    cudaError_t e = cudaMalloc(&v, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_err(D->ctx, e, "cudaMalloc");
+    }
+    D->allocs.push_back(v);
+    D->bytes += bytes;
+    *p = static_cast<T *>(v);
+    return DP_OK;
+}
+
+double power_K(const dp_config &c) { return 0.5 * c.vdd * c.vdd * c.fclk * 1e-15; }
+
+dp_status check_cfg(dp_ctx *ctx, const dp_config *c) {
+    if (!c) return set_err(ctx, DP_EINVAL, "NULL config");
+    if (!(c->vdd > 0) || !(c->fclk > 0) || !std::isfinite(c->vdd) || !std::isfinite(c->fclk))
+        return set_err(ctx, DP_EINVAL, "vdd and fclk must be positive");
+    if (!(c->beta_min > 0) || !(c->beta_max >= c->beta_min) || !std::isfinite(c->beta_max))
+        return set_err(ctx, DP_EINVAL, "need 0 < beta_min <= beta_max");
+    if (c->tr_mode < 0 || c->tr_mode > 1) return set_err(ctx, DP_EINVAL, "tr_mode must be 0 or 1");
+    if (c->grad_mode < 0 || c->grad_mode > 2) return set_err(ctx, DP_EINVAL, "grad_mode must be 0, 1 or 2");
+    if (c->sim_words < 2 || c->sim_words > 4096) return set_err(ctx, DP_EINVAL, "sim_words must be in [2, 4096]");
+    if (c->reserved != 0) return set_err(ctx, DP_EINVAL, "reserved must be 0");
+    return DP_OK;
+}
+
+void free_design(dp_design *D) {
+    if (!D) return;
+    DeviceGuard g(D->ctx ? D->ctx->device : 0);
+    if (D->ctx) cudaStreamSynchronize(D->ctx->stream);
+    if (D->graph) cudaGraphExecDestroy(D->graph);
+    if (D->cap_stream) cudaStreamDestroy(D->cap_stream);
+    for (auto &e : D->ev)
+        if (e) cudaEventDestroy(e);
+    for (void *p : D->allocs) cudaFree(p);
+    delete D;
+}
+
+dp_status ensure_words(dp_design *D, int T) {
+    if (D->words_T >= T && D->d.words) return DP_OK;
+    if (D->d.words) {
+        cudaStreamSynchronize(D->ctx->stream);
+        for (auto it = D->allocs.begin(); it != D->allocs.end(); ++it)
+            if (*it == D->d.words) {
+                cudaFree(*it);
+                D->allocs.erase(it);
+                D->bytes -= sizeof(uint64_t) * (size_t)D->d.n_nets * (size_t)D->words_T;
+                break;
+            }
+        D->d.words = nullptr;
+        D->words_T = 0;
+        if (D->graph) { cudaGraphExecDestroy(D->graph); D->graph = nullptr; }
+    }
+    dp_status s = dalloc(D, &D->d.words, (size_t)D->d.n_nets * (size_t)T);
+    if (s == DP_OK) D->words_T = T;
+    return s;
+}
+
+dp_status ensure_stage(dp_design *D) {
+    if (D->st_gsp) return DP_OK;
+    dp_status s;
+    if ((s = dalloc(D, &D->st_gsp, (size_t)D->d.n_start)) != DP_OK) return s;
+    if ((s = dalloc(D, &D->st_gtr, (size_t)D->d.n_start)) != DP_OK) return s;
+    if ((s = dalloc(D, &D->st_gpin, (size_t)D->d.n_cells)) != DP_OK) return s;
+    return dalloc(D, &D->st_gcl, (size_t)D->d.n_nets);
+}
+
+void rec(dp_design *D, int i, cudaStream_t s) {
+    cudaEventRecord(D->ev[i], s);
+    D->ev_valid[i] = true;
+}
+
+// ---- the phases, queued on stream s (also used under graph capture) ----
+void q_forward(dp_design *D, const dp_config &c, cudaStream_t s) {
+    dp::launch_init_start(D->d, c.tr_mode, s);
+    for (int l = 1; l <= D->d.n_levels; l++) dp::launch_fwd_level(D->d, D->ops, D->lvl_ptr[l - 1], D->lvl_ptr[l], s);
+    dp::launch_power(D->d, false, power_K(c), 0, s);
+}
+
+void q_simulate(dp_design *D, const dp_config &c, cudaStream_t s) {
+    dp::launch_sim_start(D->d, c.sim_words, c.seed, s);
+    for (int l = 1; l <= D->d.n_levels; l++)
+        dp::launch_sim_level(D->d, D->ops, D->lvl_ptr[l - 1], D->lvl_ptr[l], c.sim_words, s);
+    dp::launch_hybrid(D->d, c.sim_words, c.beta_min, c.beta_max, s);
+    dp::launch_power(D->d, true, power_K(c), 1, s);
+}
+
+void q_backward(dp_design *D, const dp_config &c, float *gsp, cudaStream_t s) {
+    const float K = (float)power_K(c);
+    for (int l = D->d.n_levels; l >= 1; l--)
+        dp::launch_bwd_level(D->d, D->ops, D->lvl_ptr[l - 1], D->lvl_ptr[l], c.grad_mode, K, s);
+    dp::launch_bwd_start(D->d, c.grad_mode, c.tr_mode, K, gsp, s);
+}
+
+// gradient outputs (user order) into device pointers, staged when the caller's buffers are host memory
+dp_status q_outputs(dp_design *D, const dp_config &c, float *gsp, float *gtr, float *gpin, float *gcl, int on_device,
+                    bool gsp_done) {
+    cudaStream_t s = D->ctx->stream;
+    const bool hyb = c.grad_mode != 0;
+    if (on_device) {
+        if (gsp && !gsp_done && D->d.n_start)
+            cudaMemcpyAsync(gsp, D->d.gnet, sizeof(float) * (size_t)D->d.n_start, cudaMemcpyDeviceToDevice, s);
+        dp::launch_cap_grads(D->d, D->ops, hyb, c.tr_mode, power_K(c), gcl, gpin, gtr, s);
+        return launch_check(D->ctx, "gradient outputs");
+    }
+    dp_status st = ensure_stage(D);
+    if (st != DP_OK) return st;
+    dp::launch_cap_grads(D->d, D->ops, hyb, c.tr_mode, power_K(c), gcl ? D->st_gcl : nullptr,
+                         gpin ? D->st_gpin : nullptr, gtr ? D->st_gtr : nullptr, s);
+    if ((st = launch_check(D->ctx, "gradient outputs")) != DP_OK) return st;
+    cudaError_t e = cudaSuccess;
+    if (gsp && D->d.n_start)
+        e = cudaMemcpyAsync(gsp, D->d.gnet, sizeof(float) * (size_t)D->d.n_start, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && gtr && D->d.n_start)
+        e = cudaMemcpyAsync(gtr, D->st_gtr, sizeof(float) * (size_t)D->d.n_start, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && gpin && D->d.n_cells)
+        e = cudaMemcpyAsync(gpin, D->st_gpin, sizeof(float) * (size_t)D->d.n_cells, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && gcl && D->d.n_nets)
+        e = cudaMemcpyAsync(gcl, D->st_gcl, sizeof(float) * (size_t)D->d.n_nets, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return cuda_err(D->ctx, e, "gradient copy");
+}
+
+}  // namespace
+
+extern "C" {
+
+void dp_config_default(dp_config *c) {
+    if (!c) return;
+    std::memset(c, 0, sizeof *c);
+    c->vdd = 0.8;
+    c->fclk = 1e9;
+    c->beta_min = 0.1f;
+    c->beta_max = 10.f;
+    c->tr_mode = 0;
+    c->grad_mode = 1;
+    c->sim_words = 64;
+    c->reserved = 0;
+    c->seed = 42;
+}
+
+const char *dp_last_error(const dp_ctx *ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
+
+dp_status dp_create(int device, void *cuda_stream, dp_ctx **out) {
+    if (!out) return DP_EINVAL;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) {
+        cudaGetLastError();
+        return DP_ECUDA;
+    }
+    if (device < 0 || device >= n) return DP_EINVAL;
+    dp_ctx *c = new (std::nothrow) dp_ctx();
+    if (!c) return DP_ENOMEM;
+    c->device = device;
+    DeviceGuard g(device);
+    if (cuda_stream) {
+        c->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            return DP_ECUDA;
+        }
+        c->own_stream = true;
+    }
+    *out = c;
+    return DP_OK;
+}
+
+void dp_destroy(dp_ctx *c) {
+    if (!c) return;
+    DeviceGuard g(c->device);
+    if (c->own_stream) {
+        cudaStreamSynchronize(c->stream);
+        cudaStreamDestroy(c->stream);
+    }
+    delete c;
+}
+
+dp_status dp_sync(dp_ctx *c) {
+    if (!c) return DP_EINVAL;
+    DeviceGuard g(c->device);
+    return cuda_err(c, cudaStreamSynchronize(c->stream), "dp_sync");
+}
+
+dp_status dp_design_upload(dp_ctx *ctx, const dp_compiled *cp, dp_design **out) {
+    if (!ctx || !cp || !out) return set_err(ctx, DP_EINVAL, "NULL argument");
+    *out = nullptr;
+    DeviceGuard g(ctx->device);
+    dp_design *D = new (std::nothrow) dp_design();
+    if (!D) return set_err(ctx, DP_ENOMEM, "out of memory");
+    D->ctx = ctx;
+    auto &d = D->d;
+    d.n_nets = cp->n_nets;
+    d.n_start = cp->n_start;
+    d.n_cells = cp->n_cells;
+    d.n_levels = cp->n_levels;
+    D->n_edges = cp->n_edges;
+    D->n_ops = cp->n_ops;
+    D->lvl_ptr = cp->lvl_ptr;
+    for (int i = 0; i < 256; i++) D->ops.e[i] = (uint32_t)cp->op_tt[i] | ((uint32_t)cp->op_arity[i] << 16);
+    const size_t nn = (size_t)d.n_nets, nc = (size_t)d.n_cells, ns = (size_t)d.n_start;
+    dp_status s = DP_OK;
+    uint4 *fanin = nullptr;
+    int32_t *fptr = nullptr, *fedge = nullptr, *nou = nullptr, *cou = nullptr;
+    float *base = nullptr;
+#define TRY(x) do { if ((s = (x)) != DP_OK) { free_design(D); return s; } } while (0)
+    TRY(dalloc(D, &fanin, nc));
+    TRY(dalloc(D, &fptr, nn + 1));
+    TRY(dalloc(D, &fedge, (size_t)cp->n_edges));
+    TRY(dalloc(D, &nou, nn));
+    TRY(dalloc(D, &cou, nc));
+    TRY(dalloc(D, &base, nn));
+    TRY(dalloc(D, &d.pincap, nc));
+    TRY(dalloc(D, &d.cload, nn));
+    TRY(dalloc(D, &d.sp_in, ns));
+    TRY(dalloc(D, &d.tr_in, ns));
+    TRY(dalloc(D, &d.sp, nn));
+    TRY(dalloc(D, &d.tr, nn));
+    TRY(dalloc(D, &d.beta, nn));
+    TRY(dalloc(D, &d.trh, nn));
+    TRY(dalloc(D, &d.toggles, nn));
+    TRY(dalloc(D, &d.ones, nn));
+    TRY(dalloc(D, &d.gnet, nn));
+    TRY(dalloc(D, &d.gedge, nc));
+    TRY(dalloc(D, &d.partials, (size_t)dp::kPowerBlocks));
+    TRY(dalloc(D, &d.power, 4));
+    d.fanin = fanin;
+    d.fout_ptr = fptr;
+    d.fout_edge = fedge;
+    d.net_of_user = nou;
+    d.cell_of_user = cou;
+    d.base_cap = base;
+    cudaStream_t st = ctx->stream;
+    cudaError_t e = cudaSuccess;
+    auto up = [&](void *dst, const void *src, size_t b) {
+        if (e == cudaSuccess && b) e = cudaMemcpyAsync(dst, src, b, cudaMemcpyHostToDevice, st);
+    };
+    up(fanin, cp->fanin.data(), sizeof(uint32_t) * cp->fanin.size());
+    up(fptr, cp->fout_ptr.data(), sizeof(int32_t) * cp->fout_ptr.size());
+    up(fedge, cp->fout_edge.data(), sizeof(int32_t) * cp->fout_edge.size());
+    up(nou, cp->net_of_user.data(), sizeof(int32_t) * nn);
+    up(cou, cp->cell_of_user.data(), sizeof(int32_t) * nc);
+    up(base, cp->base_cap.data(), sizeof(float) * nn);
+    up(d.pincap, cp->pincap.data(), sizeof(float) * nc);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.power, 0, 4 * sizeof(double), st);
+    if (e != cudaSuccess) { s = cuda_err(ctx, e, "upload"); free_design(D); return s; }
+    dp::launch_cload(d, st);
+    for (auto &ev : D->ev)
+        if (e == cudaSuccess) e = cudaEventCreate(&ev);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&D->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { s = cuda_err(ctx, e, "upload"); free_design(D); return s; }
+#undef TRY
+    *out = D;
+    return DP_OK;
+}
+
+dp_status dp_design_load(dp_ctx *ctx, const char *netlist, size_t netlist_len, const char *library,
+                         size_t library_len, dp_design **out) {
+    if (!ctx || !out) return set_err(ctx, DP_EINVAL, "NULL argument");
+    dp_compiled *cp = nullptr;
+    char msg[512] = {0};
+    dp_status s = dp_compile(netlist, netlist_len, library, library_len, &cp, msg, sizeof msg);
+    if (s != DP_OK) return set_err(ctx, s, std::string("compile: ") + msg);
+    s = dp_design_upload(ctx, cp, out);
+    dp_compiled_free(cp);
+    return s;
+}
+
+void dp_design_free(dp_design *D) { free_design(D); }
+
+dp_status dp_design_info(const dp_design *D, dp_info *info) {
+    if (!D || !info) return DP_EINVAL;
+    info->n_nets = D->d.n_nets;
+    info->n_start = D->d.n_start;
+    info->n_cells = D->d.n_cells;
+    info->n_edges = D->n_edges;
+    info->n_levels = D->d.n_levels;
+    info->n_ops = D->n_ops;
+    info->device_bytes = D->bytes;
+    return DP_OK;
+}
+
+dp_status dp_set_inputs(dp_design *D, const float *sp, const float *tr, int32_t n_scen, int on_device) {
+    if (!D) return DP_EINVAL;
+    dp_ctx *c = D->ctx;
+    if (n_scen != 1) return set_err(c, DP_EUNSUPPORTED, "only one scenario per design is supported");
+    const int64_t ns = D->d.n_start;
+    if (ns && (!sp || !tr)) return set_err(c, DP_EINVAL, "NULL input");
+    if (!on_device)
+        for (int64_t k = 0; k < ns; k++)
+            if (!(sp[k] >= 0.f && sp[k] <= 1.f && tr[k] >= 0.f && tr[k] <= 1.f))
+                return set_err(c, DP_EINVAL, "input SP and TR must lie in [0,1] (startpoint " + std::to_string(k) + ")");
+    DeviceGuard g(c->device);
+    cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    cudaError_t e = cudaSuccess;
+    if (ns) e = cudaMemcpyAsync(D->d.sp_in, sp, sizeof(float) * (size_t)ns, kind, c->stream);
+    if (ns && e == cudaSuccess) e = cudaMemcpyAsync(D->d.tr_in, tr, sizeof(float) * (size_t)ns, kind, c->stream);
+    if (e != cudaSuccess) return cuda_err(c, e, "dp_set_inputs");
+    D->inputs_set = true;
+    D->fwd_valid = false;
+    D->sim_valid = false;
+    return DP_OK;
+}
+
+dp_status dp_set_pincap(dp_design *D, const int32_t *cells, const float *caps, int32_t n, int on_device) {
+    if (!D) return DP_EINVAL;
+    dp_ctx *c = D->ctx;
+    if (n < 0 || (n > 0 && (!cells || !caps))) return set_err(c, DP_EINVAL, "bad sizing delta");
+    if (n == 0) return DP_OK;
+    DeviceGuard g(c->device);
+    int32_t *dc = nullptr;
+    float *dv = nullptr;
+    std::vector<void *> tmp;
+    cudaError_t e = cudaSuccess;
+    if (!on_device) {
+        for (int32_t i = 0; i < n; i++)
+            if (cells[i] < 0 || cells[i] >= D->d.n_cells || !(caps[i] >= 0.f) || !std::isfinite(caps[i]))
+                return set_err(c, DP_EINVAL, "cell index or pin cap out of range");
+        e = cudaMallocAsync((void **)&dc, sizeof(int32_t) * (size_t)n, c->stream);
+        if (e == cudaSuccess) e = cudaMallocAsync((void **)&dv, sizeof(float) * (size_t)n, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dc, cells, sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dv, caps, sizeof(float) * (size_t)n, cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess) {
+            if (dc) cudaFreeAsync(dc, c->stream);
+            if (dv) cudaFreeAsync(dv, c->stream);
+            return cuda_err(c, e, "dp_set_pincap");
+        }
+    } else {
+        dc = const_cast<int32_t *>(cells);
+        dv = const_cast<float *>(caps);
+    }
+    dp::launch_set_pincap(D->d, dc, dv, n, c->stream);
+    dp::launch_cload(D->d, c->stream);
+    dp_status s = launch_check(c, "dp_set_pincap");
+    if (!on_device) {
+        cudaFreeAsync(dc, c->stream);
+        cudaFreeAsync(dv, c->stream);
+    }
+    // loads changed: the powers and gradients must be recomputed (SP and TR stay valid)
+    return s;
+}
+
+dp_status dp_propagate(dp_design *D, const dp_config *cfg) {
+    if (!D) return DP_EINVAL;
+    dp_status s = check_cfg(D->ctx, cfg);
+    if (s != DP_OK) return s;
+    if (!D->inputs_set) return set_err(D->ctx, DP_ESTATE, "dp_propagate before dp_set_inputs");
+    DeviceGuard g(D->ctx->device);
+    cudaStream_t st = D->ctx->stream;
+    rec(D, 0, st);
+    q_forward(D, *cfg, st);
+    rec(D, 1, st);
+    if ((s = launch_check(D->ctx, "dp_propagate")) != DP_OK) return s;
+    D->fwd_valid = true;
+    D->fwd_tr_mode = cfg->tr_mode;
+    D->sim_valid = false;
+    return DP_OK;
+}
+
+dp_status dp_simulate(dp_design *D, const dp_config *cfg) {
+    if (!D) return DP_EINVAL;
+    dp_status s = check_cfg(D->ctx, cfg);
+    if (s != DP_OK) return s;
+    if (!D->fwd_valid || D->fwd_tr_mode != cfg->tr_mode)
+        return set_err(D->ctx, DP_ESTATE, "dp_simulate needs dp_propagate with the same tr_mode");
+    DeviceGuard g(D->ctx->device);
+    if ((s = ensure_words(D, cfg->sim_words)) != DP_OK) return s;
+    cudaStream_t st = D->ctx->stream;
+    rec(D, 1, st);
+    q_simulate(D, *cfg, st);
+    rec(D, 2, st);
+    if ((s = launch_check(D->ctx, "dp_simulate")) != DP_OK) return s;
+    D->sim_valid = true;
+    return DP_OK;
+}
+
+dp_status dp_total_power(dp_design *D, int hybrid, double *watts) {
+    if (!D || !watts) return DP_EINVAL;
+    if (!D->fwd_valid || (hybrid && !D->sim_valid))
+        return set_err(D->ctx, DP_ESTATE, hybrid ? "hybrid power needs dp_simulate" : "power needs dp_propagate");
+    DeviceGuard g(D->ctx->device);
+    cudaError_t e = cudaMemcpyAsync(watts, D->d.power + (hybrid ? 1 : 0), sizeof(double), cudaMemcpyDeviceToHost,
+                                    D->ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(D->ctx->stream);
+    return cuda_err(D->ctx, e, "dp_total_power");
+}
+
+dp_status dp_backward(dp_design *D, const dp_config *cfg, float *gsp, float *gtr, float *gpin, float *gcl,
+                      int on_device) {
+    if (!D) return DP_EINVAL;
+    dp_status s = check_cfg(D->ctx, cfg);
+    if (s != DP_OK) return s;
+    if (!D->fwd_valid || D->fwd_tr_mode != cfg->tr_mode)
+        return set_err(D->ctx, DP_ESTATE, "dp_backward needs dp_propagate with the same tr_mode");
+    if (cfg->grad_mode != 0 && !D->sim_valid)
+        return set_err(D->ctx, DP_ESTATE, "hybrid gradients need dp_simulate");
+    DeviceGuard g(D->ctx->device);
+    cudaStream_t st = D->ctx->stream;
+    rec(D, 2, st);
+    q_backward(D, *cfg, on_device ? gsp : nullptr, st);
+    rec(D, 3, st);
+    if ((s = launch_check(D->ctx, "dp_backward")) != DP_OK) return s;
+    s = q_outputs(D, *cfg, gsp, gtr, gpin, gcl, on_device, on_device != 0);
+    rec(D, 4, st);
+    return s;
+}
+
+dp_status dp_get_nets(dp_design *D, float *sp, float *tr, float *beta, float *trh, uint32_t *tg, uint32_t *on,
+                      int on_device) {
+    if (!D) return DP_EINVAL;
+    dp_ctx *c = D->ctx;
+    if ((sp || tr) && !D->fwd_valid) return set_err(c, DP_ESTATE, "SP/TR need dp_propagate");
+    if ((beta || trh || tg || on) && !D->sim_valid) return set_err(c, DP_ESTATE, "simulation outputs need dp_simulate");
+    DeviceGuard g(c->device);
+    cudaStream_t st = c->stream;
+    const int64_t nn = D->d.n_nets;
+    if (nn == 0) return DP_OK;
+    dp_status s = DP_OK;
+    float *stage = nullptr;
+    if (!on_device) {
+        if ((s = ensure_stage(D)) != DP_OK) return s;
+        stage = D->st_gcl;  // n_nets floats
+    }
+    struct Out { void *dst; int kind; };
+    Out outs[6] = {{sp, 0}, {tr, 1}, {beta, 2}, {trh, 3}, {tg, 4}, {on, 5}};
+    for (auto &o : outs) {
+        if (!o.dst) continue;
+        void *dst = on_device ? o.dst : (void *)stage;
+        switch (o.kind) {
+            case 0: dp::launch_gather_f32(D->d.sp, D->d.net_of_user, (float *)dst, nn, st); break;
+            case 1: dp::launch_gather_f32(D->d.tr, D->d.net_of_user, (float *)dst, nn, st); break;
+            case 2: dp::launch_gather_f32(D->d.beta, D->d.net_of_user, (float *)dst, nn, st); break;
+            case 3: dp::launch_trh_user(D->d, (float *)dst, st); break;
+            case 4: dp::launch_gather_u32(D->d.toggles, D->d.net_of_user, (uint32_t *)dst, nn, st); break;
+            case 5: dp::launch_gather_u32(D->d.ones, D->d.net_of_user, (uint32_t *)dst, nn, st); break;
+        }
+        if ((s = launch_check(c, "dp_get_nets")) != DP_OK) return s;
+        if (!on_device) {
+            cudaError_t e = cudaMemcpyAsync(o.dst, stage, 4 * (size_t)nn, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return cuda_err(c, e, "dp_get_nets");
+        }
+    }
+    return DP_OK;
+}
+
+dp_status dp_step(dp_design *D, const dp_config *cfg, float *gsp, float *gtr, float *gpin, float *gcl, double *watts,
+                  int on_device) {
+    if (!D) return DP_EINVAL;
+    dp_status s = check_cfg(D->ctx, cfg);
+    if (s != DP_OK) return s;
+    if (!D->inputs_set) return set_err(D->ctx, DP_ESTATE, "dp_step before dp_set_inputs");
+    DeviceGuard g(D->ctx->device);
+    if ((s = ensure_words(D, cfg->sim_words)) != DP_OK) return s;
+    cudaStream_t st = D->ctx->stream;
+    if (!D->graph || std::memcmp(&D->graph_cfg, cfg, sizeof *cfg) != 0) {
+        if (D->graph) { cudaGraphExecDestroy(D->graph); D->graph = nullptr; }
+        cudaStream_t cs = D->cap_stream;
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_err(D->ctx, e, "graph capture");
+        cudaEventRecord(D->ev[0], cs);
+        q_forward(D, *cfg, cs);
+        cudaEventRecord(D->ev[1], cs);
+        q_simulate(D, *cfg, cs);
+        cudaEventRecord(D->ev[2], cs);
+        q_backward(D, *cfg, nullptr, cs);
+        cudaEventRecord(D->ev[3], cs);
+        e = cudaStreamEndCapture(cs, &graph);
+        D->graph_kernels = 0;
+        if (e == cudaSuccess) {
+            size_t nn = 0;
+            e = cudaGraphGetNodes(graph, nullptr, &nn);
+            std::vector<cudaGraphNode_t> nodes(nn);
+            if (e == cudaSuccess && nn) e = cudaGraphGetNodes(graph, nodes.data(), &nn);
+            for (size_t i = 0; e == cudaSuccess && i < nn; i++) {
+                cudaGraphNodeType t;
+                if ((e = cudaGraphNodeGetType(nodes[i], &t)) == cudaSuccess && t == cudaGraphNodeTypeKernel)
+                    D->graph_kernels++;
+            }
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&D->graph, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) { D->graph = nullptr; return cuda_err(D->ctx, e, "graph instantiate"); }
+        D->graph_cfg = *cfg;
+    }
+    cudaError_t e = cudaGraphLaunch(D->graph, st);
+    if (e != cudaSuccess) return cuda_err(D->ctx, e, "graph launch");
+    for (int i = 0; i < 4; i++) D->ev_valid[i] = true;
+    D->fwd_valid = true;
+    D->fwd_tr_mode = cfg->tr_mode;
+    D->sim_valid = true;
+    s = q_outputs(D, *cfg, gsp, gtr, gpin, gcl, on_device, false);
+    rec(D, 4, st);
+    D->step_kernels = D->graph_kernels + (gcl && D->d.n_nets ? 1 : 0) + (gpin && D->d.n_cells ? 1 : 0) +
+                      (gtr && D->d.n_start ? 1 : 0);
+    if (s != DP_OK) return s;
+    if (watts) {
+        e = cudaMemcpyAsync(watts, D->d.power, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_err(D->ctx, e, "dp_step power");
+    }
+    return DP_OK;
+}
+
+dp_status dp_step_kernels(const dp_design *D, int64_t *k) {
+    if (!D || !k) return DP_EINVAL;
+    *k = D->step_kernels;
+    return DP_OK;
+}
+
+dp_status dp_phase_times(dp_design *D, float *ms) {
+    if (!D || !ms) return DP_EINVAL;
+    DeviceGuard g(D->ctx->device);
+    cudaError_t e = cudaStreamSynchronize(D->ctx->stream);
+    if (e != cudaSuccess) return cuda_err(D->ctx, e, "dp_phase_times");
+    for (int i = 0; i < 4; i++) {
+        ms[i] = 0.f;
+        if (D->ev_valid[i] && D->ev_valid[i + 1]) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, D->ev[i], D->ev[i + 1]) == cudaSuccess) ms[i] = t;
+            else cudaGetLastError();
+        }
+    }
+    return DP_OK;
+}
+
+}  // extern "C"

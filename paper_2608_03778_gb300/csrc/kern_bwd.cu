@@ -1,0 +1,93 @@
+// Reverse pass (Sec. III-E, Eq. 7; Eq. 6 for the paper's hybrid rule).
+// Nets are visited in reverse level order.  A net's adjoint is the sum of the
+// contributions its fanout cells left on their input edges plus its local
+// term; a cell then writes one contribution per input edge into its own
+// slots.  Every fanout cell of a level-l net sits on a level above l, so the
+// edge contributions are complete when the net is visited: a gather over the
+// transposed fanout CSR replaces atomic scatters, and the result is
+// reproducible bit for bit.
+#include "kern_common.cuh"
+
+namespace dp {
+namespace {
+
+__host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+__device__ __forceinline__ float fanout_sum(const int32_t *__restrict__ fptr, const int32_t *__restrict__ fedge,
+                                            const float *__restrict__ ge, int64_t n) {
+    float acc = 0.f;
+    const int32_t e1 = fptr[n + 1];
+    for (int32_t e = fptr[n]; e < e1; e++) acc += ge[fedge[e]];
+    return acc;
+}
+
+// grad_mode 0: g = acc + local; 1: g = beta (acc + local) (Eq. 6); 2: g = acc + beta local
+__device__ __forceinline__ float combine(int grad_mode, float acc, float local, const float *beta, int64_t n) {
+    if (grad_mode == 1) return beta[n] * (acc + local);
+    if (grad_mode == 2) return acc + beta[n] * local;
+    return acc + local;
+}
+
+__global__ void k_bwd_level(const uint4 *__restrict__ fanin, const int32_t *__restrict__ fptr,
+                            const int32_t *__restrict__ fedge, const float *__restrict__ sp,
+                            const float *__restrict__ cload, const float *__restrict__ beta, float *gnet,
+                            float4 *gedge, int32_t c0, int32_t c1, int64_t ns, int grad_mode, float K, OpTable ops) {
+    int32_t c = c0 + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (c >= c1) return;
+    const int64_t n = ns + c;
+    const float acc = fanout_sum(fptr, fedge, reinterpret_cast<const float *>(gedge), n);
+    const float p = sp[n];
+    // local term: d(K C 2P(1-P))/dP = K C (2 - 4P)
+    const float g = combine(grad_mode, acc, K * cload[n] * (2.f - 4.f * p), beta, n);
+    gnet[n] = g;
+    const uint4 r = fanin[c];
+    const uint32_t op = r.x >> 24;
+    const int k = op_arity(ops, op);
+    float a[4] = {0.f, 0.f, 0.f, 0.f};
+    if (k > 0) a[0] = sp[r.x & kMask24];
+    if (k > 1) a[1] = sp[r.y];
+    if (k > 2) a[2] = sp[r.z];
+    if (k > 3) a[3] = sp[r.w];
+    float d[4];
+    cell_partials(k, op_tt(ops, op), a, d);
+    gedge[c] = make_float4(g * d[0], g * d[1], g * d[2], g * d[3]);
+}
+
+__global__ void k_bwd_start(const int32_t *__restrict__ fptr, const int32_t *__restrict__ fedge,
+                            const float *__restrict__ sp, const float *__restrict__ cload,
+                            const float *__restrict__ beta, float *gnet, const float4 *gedge, int64_t ns,
+                            int grad_mode, int tr_mode, float K, float *out) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ns) return;
+    const float acc = fanout_sum(fptr, fedge, reinterpret_cast<const float *>(gedge), k);
+    // a startpoint has a local SP term only when its TR is derived from its SP (tr_mode 1)
+    const float local = tr_mode ? K * cload[k] * (2.f - 4.f * sp[k]) : 0.f;
+    const float g = combine(grad_mode, acc, local, beta, k);
+    gnet[k] = g;
+    if (out) out[k] = g;
+}
+
+}  // namespace
+
+static inline int level_block(int64_t n) {
+    int b = 256;
+    while (b > 32 && n < (int64_t)b * 304) b >>= 1;
+    return b;
+}
+
+void launch_bwd_level(const DevDesign &d, const OpTable &ops, int32_t c0, int32_t c1, int grad_mode, float K,
+                      cudaStream_t s) {
+    if (c1 <= c0) return;
+    int b = level_block(c1 - c0);
+    k_bwd_level<<<(unsigned)cdiv(c1 - c0, b), b, 0, s>>>(d.fanin, d.fout_ptr, d.fout_edge, d.sp, d.cload, d.beta,
+                                                         d.gnet, d.gedge, c0, c1, d.n_start, grad_mode, K, ops);
+}
+
+void launch_bwd_start(const DevDesign &d, int grad_mode, int tr_mode, float K, float *grad_sp_in, cudaStream_t s) {
+    if (d.n_start == 0) return;
+    int b = level_block(d.n_start);
+    k_bwd_start<<<(unsigned)cdiv(d.n_start, b), b, 0, s>>>(d.fout_ptr, d.fout_edge, d.sp, d.cload, d.beta, d.gnet,
+                                                           d.gedge, d.n_start, grad_mode, tr_mode, K, grad_sp_in);
+}
+
+}  // namespace dp

@@ -1,0 +1,214 @@
+// Forward pass (Sec. III-B, Algorithm 2, Eq. 2), loads and power (Eq. 1),
+// capacitance gradients and output gathers.
+#include "kern_common.cuh"
+
+namespace dp {
+namespace {
+
+__host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// startpoints: SP = input SP; TR = input TR (tr_mode 0) or 2P(1-P) (tr_mode 1)
+__global__ void k_init_start(const float *__restrict__ sp_in, const float *__restrict__ tr_in, float *sp, float *tr,
+                             int64_t ns, int tr_mode) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ns) return;
+    float p = sp_in[k];
+    sp[k] = p;
+    tr[k] = tr_mode ? 2.f * p * (1.f - p) : tr_in[k];
+}
+
+// one thread per cell of one level: gather fanin SPs, evaluate the cell's
+// multilinear extension, write SP and TR_model = 2P(1-P) of its output net
+__global__ void k_fwd_level(const uint4 *__restrict__ fanin, float *sp, float *tr, int32_t c0, int32_t c1,
+                            int64_t ns, OpTable ops) {
+    int32_t c = c0 + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (c >= c1) return;
+    const uint4 r = fanin[c];
+    const uint32_t op = r.x >> 24;
+    const int k = op_arity(ops, op);
+    float a[4] = {0.f, 0.f, 0.f, 0.f};
+    if (k > 0) a[0] = sp[r.x & kMask24];
+    if (k > 1) a[1] = sp[r.y];
+    if (k > 2) a[2] = sp[r.z];
+    if (k > 3) a[3] = sp[r.w];
+    float p = cell_sp(k, op_tt(ops, op), a);
+    p = fminf(fmaxf(p, 0.f), 1.f);  // safety clamp only (values are in [0,1] mathematically)
+    sp[ns + c] = p;
+    tr[ns + c] = 2.f * p * (1.f - p);
+}
+
+// Eq. 1 loads: C_load = wire + DFF D caps + sum of the input pin caps of the driven cells
+__global__ void k_cload(const float *__restrict__ base, const int32_t *__restrict__ fptr,
+                        const int32_t *__restrict__ fedge, const float *__restrict__ pincap, float *cload, int64_t nn) {
+    int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= nn) return;
+    float c = base[n];
+    for (int32_t e = fptr[n]; e < fptr[n + 1]; e++) c += pincap[fedge[e] >> 2];
+    cload[n] = c;
+}
+
+__global__ void k_set_pincap(const int32_t *__restrict__ cells, const float *__restrict__ caps,
+                             const int32_t *__restrict__ cell_of_user, float *pincap, int32_t n, int64_t nc) {
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t u = cells[i];
+    if (u >= 0 && u < nc) pincap[cell_of_user[u]] = caps[i];
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    return v;
+}
+
+// power partials: a fixed grid and a fixed per-thread stride make the FP64
+// summation order independent of timing, so the result is reproducible
+__global__ void __launch_bounds__(kPowerThreads) k_power_partials(const float *__restrict__ tr,
+                                                                  const float *__restrict__ beta,
+                                                                  const float *__restrict__ cload, double *partials,
+                                                                  int64_t nn) {
+    double s = 0.0;
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < nn; n += (int64_t)gridDim.x * blockDim.x) {
+        double a = (double)tr[n];
+        if (beta) a *= (double)beta[n];
+        s += a * (double)cload[n];
+    }
+    __shared__ double sh[kPowerThreads / 32];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double t = threadIdx.x < kPowerThreads / 32 ? sh[threadIdx.x] : 0.0;
+        t = warp_sum(t);
+        if (threadIdx.x == 0) partials[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(kPowerThreads) k_power_final(const double *__restrict__ partials, int nb, double K,
+                                                               double *out) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) s += partials[i];
+    __shared__ double sh[kPowerThreads / 32];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double t = threadIdx.x < kPowerThreads / 32 ? sh[threadIdx.x] : 0.0;
+        t = warp_sum(t);
+        if (threadIdx.x == 0) *out = K * t;
+    }
+}
+
+// d P / d C_load (user net order) = K alpha
+__global__ void k_grad_cload(const float *__restrict__ tr, const float *__restrict__ beta,
+                             const int32_t *__restrict__ net_of_user, float K, float *out, int64_t nn) {
+    int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= nn) return;
+    int32_t n = net_of_user[u];
+    float a = tr[n];
+    if (beta) a *= beta[n];
+    out[u] = K * a;
+}
+
+// d P / d pincap (user cell order) = K * sum over the cell's inputs of alpha
+__global__ void k_grad_pincap(const uint4 *__restrict__ fanin, const float *__restrict__ tr,
+                              const float *__restrict__ beta, const int32_t *__restrict__ cell_of_user, float K,
+                              float *out, int64_t nc, OpTable ops) {
+    int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= nc) return;
+    const uint4 r = fanin[cell_of_user[u]];
+    const int k = op_arity(ops, r.x >> 24);
+    const uint32_t n[4] = {r.x & kMask24, r.y, r.z, r.w};
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < 4; j++)
+        if (j < k) s += beta ? beta[n[j]] * tr[n[j]] : tr[n[j]];
+    out[u] = K * s;
+}
+
+// d P / d TR_in (startpoint order) = K beta C_load when the startpoint TR is an input (tr_mode 0)
+__global__ void k_grad_tr_in(const float *__restrict__ beta, const float *__restrict__ cload, float K, int tr_mode,
+                             float *out, int64_t ns) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ns) return;
+    out[k] = tr_mode ? 0.f : K * (beta ? beta[k] : 1.f) * cload[k];
+}
+
+__global__ void k_gather_f32(const float *__restrict__ src, const int32_t *__restrict__ idx, float *dst, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = src[idx[i]];
+}
+__global__ void k_gather_u32(const uint32_t *__restrict__ src, const int32_t *__restrict__ idx, uint32_t *dst,
+                             int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = src[idx[i]];
+}
+__global__ void k_trh_user(const float *__restrict__ tr, const float *__restrict__ beta,
+                           const int32_t *__restrict__ idx, float *dst, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) { int32_t m = idx[i]; dst[i] = beta[m] * tr[m]; }
+}
+
+}  // namespace
+
+// 1-D grids for per-level kernels: blocks small enough that a level spreads
+// over all SMs (the level, not the GPU, is the unit of parallel work)
+static inline int level_block(int64_t n) {
+    int b = 256;
+    while (b > 32 && n < (int64_t)b * 304) b >>= 1;
+    return b;
+}
+
+void launch_init_start(const DevDesign &d, int tr_mode, cudaStream_t s) {
+    if (d.n_start == 0) return;
+    k_init_start<<<(unsigned)cdiv(d.n_start, 256), 256, 0, s>>>(d.sp_in, d.tr_in, d.sp, d.tr, d.n_start, tr_mode);
+}
+
+void launch_fwd_level(const DevDesign &d, const OpTable &ops, int32_t c0, int32_t c1, cudaStream_t s) {
+    if (c1 <= c0) return;
+    int b = level_block(c1 - c0);
+    k_fwd_level<<<(unsigned)cdiv(c1 - c0, b), b, 0, s>>>(d.fanin, d.sp, d.tr, c0, c1, d.n_start, ops);
+}
+
+void launch_cload(const DevDesign &d, cudaStream_t s) {
+    if (d.n_nets == 0) return;
+    k_cload<<<(unsigned)cdiv(d.n_nets, 256), 256, 0, s>>>(d.base_cap, d.fout_ptr, d.fout_edge, d.pincap, d.cload,
+                                                          d.n_nets);
+}
+
+void launch_set_pincap(const DevDesign &d, const int32_t *cells, const float *caps, int32_t n, cudaStream_t s) {
+    if (n <= 0) return;
+    k_set_pincap<<<(unsigned)cdiv(n, 256), 256, 0, s>>>(cells, caps, d.cell_of_user, d.pincap, n, d.n_cells);
+}
+
+void launch_power(const DevDesign &d, bool hybrid, double K, int slot, cudaStream_t s) {
+    k_power_partials<<<kPowerBlocks, kPowerThreads, 0, s>>>(d.tr, hybrid ? d.beta : nullptr, d.cload, d.partials,
+                                                            d.n_nets);
+    k_power_final<<<1, kPowerThreads, 0, s>>>(d.partials, kPowerBlocks, K, d.power + slot);
+}
+
+void launch_cap_grads(const DevDesign &d, const OpTable &ops, bool hybrid, int tr_mode, double K,
+                          float *grad_cload, float *grad_pincap, float *grad_tr_in, cudaStream_t s) {
+    const float *beta = hybrid ? d.beta : nullptr;
+    if (grad_cload && d.n_nets)
+        k_grad_cload<<<(unsigned)cdiv(d.n_nets, 256), 256, 0, s>>>(d.tr, beta, d.net_of_user, (float)K, grad_cload,
+                                                                   d.n_nets);
+    if (grad_pincap && d.n_cells)
+        k_grad_pincap<<<(unsigned)cdiv(d.n_cells, 256), 256, 0, s>>>(d.fanin, d.tr, beta, d.cell_of_user, (float)K,
+                                                                     grad_pincap, d.n_cells, ops);
+    if (grad_tr_in && d.n_start)
+        k_grad_tr_in<<<(unsigned)cdiv(d.n_start, 256), 256, 0, s>>>(beta, d.cload, (float)K, tr_mode, grad_tr_in,
+                                                                     d.n_start);
+}
+
+void launch_gather_f32(const float *src, const int32_t *idx, float *dst, int64_t n, cudaStream_t s) {
+    if (n) k_gather_f32<<<(unsigned)cdiv(n, 256), 256, 0, s>>>(src, idx, dst, n);
+}
+void launch_gather_u32(const uint32_t *src, const int32_t *idx, uint32_t *dst, int64_t n, cudaStream_t s) {
+    if (n) k_gather_u32<<<(unsigned)cdiv(n, 256), 256, 0, s>>>(src, idx, dst, n);
+}
+void launch_trh_user(const DevDesign &d, float *dst, cudaStream_t s) {
+    if (d.n_nets) k_trh_user<<<(unsigned)cdiv(d.n_nets, 256), 256, 0, s>>>(d.tr, d.beta, d.net_of_user, dst, d.n_nets);
+}
+
+}  // namespace dp

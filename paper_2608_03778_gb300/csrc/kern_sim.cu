@@ -1,0 +1,172 @@
+// Pass 2 (Sec. III-C): Markov-chain startpoint vectors, bit-packed level-by-
+// level simulation with PopCount toggle counting (Eq. 4), and the hybrid
+// calibration beta = clip(TR_acc / TR_model) (Sec. III-D, Eq. 5).
+//
+// Layout: words[n * T + t], bit b of word t = lane b (an independent chain)
+// at cycle t; T words give 64 T vectors and 64 (T - 1) transitions per net.
+#include "kern_common.cuh"
+
+namespace dp {
+namespace {
+
+__host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// floor(p * 2^32) clamped to [0, 2^32]: a draw u (32 bits) is 1 iff u < thr
+__device__ __forceinline__ uint64_t threshold(double p) {
+    if (!(p > 0.0)) return 0ull;
+    if (p >= 1.0) return 4294967296ull;
+    return (uint64_t)floor(p * 4294967296.0);
+}
+
+// One half-warp per startpoint k; thread q runs lanes q, q+16, q+32, q+48.
+// Philox4x32-10 counter (k, t, q, 0) under key (seed lo, seed hi); output
+// component r drives lane 16 r + q.  t = 0 draws the initial state with
+// P(1) = SP; t >= 1 flips a 1 with p10 = TR / 2SP and a 0 with
+// p01 = TR / 2(1 - SP), which keeps SP stationary and makes TR the expected
+// toggle rate.
+__global__ void __launch_bounds__(256) k_sim_start(const float *__restrict__ sp_in, const float *__restrict__ tr_in,
+                                                   uint64_t *words, uint32_t *toggles, uint32_t *ones, int64_t ns,
+                                                   int T, uint32_t key0, uint32_t key1) {
+    const int q = threadIdx.x & 15;
+    const int half = (threadIdx.x >> 4) & 1;
+    const int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 4) + (threadIdx.x >> 4);
+    const bool valid = k < ns;
+    uint64_t t_init = 0, t10 = 0, t01 = 0;
+    if (valid) {
+        const double sp = (double)sp_in[k], tr = (double)tr_in[k];
+        const double p10 = sp > 0.0 ? tr / (2.0 * sp) : 0.0;
+        const double p01 = sp < 1.0 ? tr / (2.0 * (1.0 - sp)) : 0.0;
+        t_init = threshold(sp);
+        t10 = threshold(p10);
+        t01 = threshold(p01);
+    }
+    uint32_t state = 0;        // bit r = current value of lane 16 r + q
+    uint32_t n_flip = 0, n_one = 0;
+    uint64_t mine = 0;         // word t with t % 16 == q of the current group of 16 cycles
+    for (int t = 0; t < T; t++) {
+        const uint4 u = philox4x32_10(make_uint4((uint32_t)k, (uint32_t)t, (uint32_t)q, 0u), key0, key1);
+        const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            uint32_t b = (state >> r) & 1u;
+            if (t == 0) {
+                b = (uint64_t)uu[r] < t_init;
+            } else {
+                const uint32_t f = (uint64_t)uu[r] < (b ? t10 : t01);
+                b ^= f;
+                n_flip += f;
+            }
+            n_one += b;
+            state = (state & ~(1u << r)) | (b << r);
+        }
+        uint64_t w = 0;
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, (state >> r) & 1u);
+            w |= (uint64_t)((bal >> (16 * half)) & 0xFFFFu) << (16 * r);
+        }
+        if ((t & 15) == q) mine = w;
+        if ((t & 15) == 15 || t == T - 1) {
+            const int t_q = (t & ~15) + q;
+            if (valid && t_q < T) words[k * T + t_q] = mine;
+        }
+    }
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {
+        n_flip += __shfl_xor_sync(0xFFFFFFFFu, n_flip, o);
+        n_one += __shfl_xor_sync(0xFFFFFFFFu, n_one, o);
+    }
+    if (valid && q == 0) {
+        toggles[k] = n_flip;
+        ones[k] = n_one;
+    }
+}
+
+// One warp per cell of a level: lane l evaluates word t = 32 i + l of the
+// cell on its fanin words (bitwise), writes it, and counts ones and toggles;
+// the previous word comes from the neighbour lane (or the last lane of the
+// previous chunk).
+__global__ void __launch_bounds__(256) k_sim_level(const uint4 *__restrict__ fanin, uint64_t *words,
+                                                   uint32_t *toggles, uint32_t *ones, int32_t c0, int32_t c1,
+                                                   int64_t ns, int T, OpTable ops) {
+    const int lane = threadIdx.x & 31;
+    const int32_t c = c0 + (int32_t)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (c >= c1) return;  // whole warp
+    const uint4 r = fanin[c];
+    const uint32_t op = r.x >> 24;
+    const int k = op_arity(ops, op);
+    const uint32_t tt = op_tt(ops, op);
+    // fanin rows (slots beyond the arity are unused and never formed)
+    const uint64_t *in0 = k > 0 ? words + (size_t)(r.x & kMask24) * T : words;
+    const uint64_t *in1 = k > 1 ? words + (size_t)r.y * T : words;
+    const uint64_t *in2 = k > 2 ? words + (size_t)r.z * T : words;
+    const uint64_t *in3 = k > 3 ? words + (size_t)r.w * T : words;
+    uint64_t *out = words + (size_t)(ns + c) * T;
+    uint32_t tg = 0, on = 0;
+    uint64_t carry = 0;
+    for (int base = 0; base < T; base += 32) {
+        const int t = base + lane;
+        const bool act = t < T;
+        uint64_t x[4] = {0, 0, 0, 0};
+        if (act) {
+            if (k > 0) x[0] = in0[t];
+            if (k > 1) x[1] = in1[t];
+            if (k > 2) x[2] = in2[t];
+            if (k > 3) x[3] = in3[t];
+        }
+        const uint64_t w = cell_bits(k, tt, x);
+        uint64_t prev = __shfl_up_sync(0xFFFFFFFFu, w, 1);
+        if (lane == 0) prev = carry;
+        if (act) {
+            out[t] = w;
+            on += __popcll(w);
+            if (t > 0) tg += __popcll(w ^ prev);
+        }
+        carry = __shfl_sync(0xFFFFFFFFu, w, 31);
+    }
+    tg = __reduce_add_sync(0xFFFFFFFFu, tg);
+    on = __reduce_add_sync(0xFFFFFFFFu, on);
+    if (lane == 0) {
+        toggles[ns + c] = tg;
+        ones[ns + c] = on;
+    }
+}
+
+// Eq. 4 and Eq. 5: TR_acc = toggles / 64(T-1); beta = clip(TR_acc / TR_model);
+// TR_model = 0 gives beta = 1 without toggles, else beta_max.
+__global__ void k_hybrid(const uint32_t *__restrict__ toggles, const float *__restrict__ tr, float *beta, float *trh,
+                         int64_t nn, float nsim, float bmin, float bmax) {
+    int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= nn) return;
+    const uint32_t tg = toggles[n];
+    const float acc = (float)tg / nsim;
+    const float m = tr[n];
+    float b;
+    if (m > 0.f) b = fminf(fmaxf(acc / m, bmin), bmax);
+    else b = tg == 0 ? 1.f : bmax;
+    beta[n] = b;
+    trh[n] = b * m;
+}
+
+}  // namespace
+
+void launch_sim_start(const DevDesign &d, int T, uint64_t seed, cudaStream_t s) {
+    if (d.n_start == 0) return;
+    k_sim_start<<<(unsigned)cdiv(d.n_start, 16), 256, 0, s>>>(d.sp_in, d.tr_in, d.words, d.toggles, d.ones,
+                                                              d.n_start, T, (uint32_t)seed, (uint32_t)(seed >> 32));
+}
+
+void launch_sim_level(const DevDesign &d, const OpTable &ops, int32_t c0, int32_t c1, int T, cudaStream_t s) {
+    if (c1 <= c0) return;
+    k_sim_level<<<(unsigned)cdiv((int64_t)(c1 - c0) * 32, 256), 256, 0, s>>>(d.fanin, d.words, d.toggles, d.ones,
+                                                                              c0, c1, d.n_start, T, ops);
+}
+
+void launch_hybrid(const DevDesign &d, int T, float beta_min, float beta_max, cudaStream_t s) {
+    if (d.n_nets == 0) return;
+    const float nsim = 64.f * (float)(T - 1);
+    k_hybrid<<<(unsigned)cdiv(d.n_nets, 256), 256, 0, s>>>(d.toggles, d.tr, d.beta, d.trh, d.n_nets, nsim, beta_min,
+                                                           beta_max);
+}
+
+}  // namespace dp

@@ -1,0 +1,66 @@
+// Launch wrappers for the GPU kernels (implemented in kern_*.cu).
+#pragma once
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace dp {
+
+// Per-design function table passed by value to kernels (lives in the
+// constant bank): entry = truth table (bits 0..15) | arity << 16.
+struct OpTable {
+    uint32_t e[256];
+};
+
+// Device-resident design state; every pointer is device memory.
+struct DevDesign {
+    int64_t n_nets, n_start, n_cells;
+    int32_t n_levels;
+    const uint4 *fanin;        // [n_cells]: 4 internal net ids, logic id in bits 24..31 of .x
+    const int32_t *fout_ptr;   // [n_nets+1]
+    const int32_t *fout_edge;  // [n_edges]: 4*cell + slot
+    const int32_t *net_of_user;
+    const int32_t *cell_of_user;
+    const float *base_cap;     // wire + DFF D pin caps
+    float *pincap;             // [n_cells]
+    float *cload;              // [n_nets]
+    float *sp_in, *tr_in;      // [n_start] staged inputs
+    float *sp, *tr;            // [n_nets] SP and TR_model
+    float *beta, *trh;         // [n_nets] beta and hybrid TR
+    uint32_t *toggles, *ones;  // [n_nets]
+    float *gnet;               // [n_nets] SP adjoint per net
+    float4 *gedge;             // [n_cells]: adjoint contribution of each fanin edge
+    uint64_t *words;           // [n_nets * T]
+    double *partials;          // [2 * power_blocks]
+    double *power;             // [4]: model, hybrid
+    float *stage;              // output staging, n_nets floats
+};
+
+constexpr int kPowerBlocks = 304;   // fixed grid of the power reduction -> deterministic order
+constexpr int kPowerThreads = 256;
+
+// forward (kern_fwd.cu)
+void launch_init_start(const DevDesign &d, int tr_mode, cudaStream_t s);
+void launch_fwd_level(const DevDesign &d, const OpTable &ops, int32_t c0, int32_t c1, cudaStream_t s);
+void launch_cload(const DevDesign &d, cudaStream_t s);
+void launch_set_pincap(const DevDesign &d, const int32_t *cells, const float *caps, int32_t n, cudaStream_t s);
+// power: sum_n alpha_n C_n (alpha = tr, or beta*tr when hybrid), times K, into d.power[slot]
+void launch_power(const DevDesign &d, bool hybrid, double K, int slot, cudaStream_t s);
+// outputs in user order: grad_cload (K alpha), grad_pincap (K sum fanin alpha), grad_tr_in (K beta C or 0)
+void launch_cap_grads(const DevDesign &d, const OpTable &ops, bool hybrid, int tr_mode, double K, float *grad_cload,
+                      float *grad_pincap, float *grad_tr_in, cudaStream_t s);
+void launch_gather_f32(const float *src, const int32_t *idx, float *dst, int64_t n, cudaStream_t s);
+void launch_gather_u32(const uint32_t *src, const int32_t *idx, uint32_t *dst, int64_t n, cudaStream_t s);
+void launch_trh_user(const DevDesign &d, float *dst, cudaStream_t s);
+
+// backward (kern_bwd.cu)
+void launch_bwd_level(const DevDesign &d, const OpTable &ops, int32_t c0, int32_t c1, int grad_mode, float K,
+                      cudaStream_t s);
+void launch_bwd_start(const DevDesign &d, int grad_mode, int tr_mode, float K, float *grad_sp_in, cudaStream_t s);
+
+// simulation (kern_sim.cu)
+void launch_sim_start(const DevDesign &d, int T, uint64_t seed, cudaStream_t s);
+void launch_sim_level(const DevDesign &d, const OpTable &ops, int32_t c0, int32_t c1, int T, cudaStream_t s);
+void launch_hybrid(const DevDesign &d, int T, float beta_min, float beta_max, cudaStream_t s);
+
+}  // namespace dp

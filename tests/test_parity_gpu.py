@@ -1,0 +1,313 @@
+"""GPU path vs the FP64 oracle, element by element, through the C-ABI.
+
+Tolerances (spec bar):
+* SP and TR of every net: 1e-5 absolute;
+* toggle and ones counts: bit-exact;
+* gradients: |g - g*| <= 1e-4 max(|g*|, 1e-3 max|g*|) (relative, near-zero floor);
+* total power (FP64 reduction on the GPU of binary32 terms): 1e-6 relative;
+* beta: hybrid TR within 1e-5 absolute, and beta itself within 1e-4 relative where the
+  model TR is at least 1e-2 (below that the binary32 TR_model's relative error dominates).
+"""
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle
+from paper_2608_03778_gb300 import netgen
+from tests import _gates as G
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def dp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2608_03778_gb300 import dp as _dp
+    return _dp
+
+
+@pytest.fixture(scope="module")
+def ctx(dp):
+    c = dp.dp_create(0, torch.cuda.current_stream().cuda_stream)
+    yield c
+    dp.dp_destroy(c)
+
+
+def grad_close(g, g_star):
+    g, g_star = np.asarray(g, np.float64), np.asarray(g_star, np.float64)
+    if g_star.size == 0:
+        return True
+    floor = 1e-3 * np.abs(g_star).max()
+    bad = np.abs(g - g_star) > 1e-4 * np.maximum(np.abs(g_star), floor)
+    if bad.any():
+        i = np.argmax(np.abs(g - g_star) / np.maximum(np.abs(g_star), floor + 1e-300))
+        print(f"worst at {i}: {g[i]} vs {g_star[i]}")
+    return not bad.any()
+
+
+def gpu_run(dp, ctx, text, lib, sp_in, tr_in, cfg, use_step=False, on_device=False):
+    d = dp.dp_design_load(ctx, text, lib)
+    try:
+        info = dp.dp_design_info(d)
+        ns, nc, nn = info.n_start, info.n_cells, info.n_nets
+        out = {}
+        if on_device:
+            dev = torch.device("cuda")
+            sp_t = torch.from_numpy(np.ascontiguousarray(sp_in, np.float32)).to(dev)
+            tr_t = torch.from_numpy(np.ascontiguousarray(tr_in, np.float32)).to(dev)
+            dp.dp_set_inputs(ctx, d, sp_t, tr_t, 1, 1)
+            bufs = {k: torch.zeros(n, dtype=torch.float32, device=dev)
+                    for k, n in [("grad_sp_in", ns), ("grad_tr_in", ns), ("grad_pincap", nc), ("grad_cload", nn)]}
+        else:
+            dp.dp_set_inputs(ctx, d, np.ascontiguousarray(sp_in, np.float32), np.ascontiguousarray(tr_in, np.float32))
+            bufs = {k: np.zeros(n, np.float32)
+                    for k, n in [("grad_sp_in", ns), ("grad_tr_in", ns), ("grad_pincap", nc), ("grad_cload", nn)]}
+        od = 1 if on_device else 0
+        if use_step:
+            watts = np.zeros(2)
+            dp.dp_step(ctx, d, cfg, bufs["grad_sp_in"], bufs["grad_tr_in"], bufs["grad_pincap"],
+                       bufs["grad_cload"], watts, od)
+            out["power_model"], out["power_hybrid"] = watts
+        else:
+            dp.dp_propagate(ctx, d, cfg)
+            out["power_model"] = dp.dp_total_power(ctx, d, 0)
+            dp.dp_simulate(ctx, d, cfg)
+            out["power_hybrid"] = dp.dp_total_power(ctx, d, 1)
+            dp.dp_backward(ctx, d, cfg, bufs["grad_sp_in"], bufs["grad_tr_in"], bufs["grad_pincap"],
+                           bufs["grad_cload"], od)
+        if on_device:
+            torch.cuda.synchronize()
+            for k, v in bufs.items():
+                out[k] = v.cpu().numpy()
+        else:
+            out.update(bufs)
+        for k, dt in [("sp", np.float32), ("tr", np.float32), ("beta", np.float32), ("tr_hyb", np.float32),
+                      ("toggles", np.uint32), ("ones", np.uint32)]:
+            out[k] = np.zeros(nn, dt)
+        dp.dp_get_nets(ctx, d, out["sp"], out["tr"], out["beta"], out["tr_hyb"], out["toggles"], out["ones"])
+        out["info"] = info
+        return out
+    finally:
+        dp.dp_design_free(d)
+
+
+def check_against_oracle(o, g, sp_in, tr_in, cfg):
+    ref = o.step(sp_in, tr_in, seed=cfg.seed, T=cfg.sim_words, grad_mode=cfg.grad_mode, tr_mode=cfg.tr_mode,
+                 vdd=cfg.vdd, fclk=cfg.fclk, beta_min=cfg.beta_min, beta_max=cfg.beta_max)
+    assert np.abs(g["sp"] - ref["sp"]).max(initial=0) <= 1e-5
+    assert np.abs(g["tr"] - ref["tr"]).max(initial=0) <= 1e-5
+    np.testing.assert_array_equal(g["toggles"], ref["toggles"])
+    np.testing.assert_array_equal(g["ones"], ref["ones"])
+    assert np.abs(g["tr_hyb"] - ref["tr_hyb"]).max(initial=0) <= 1e-5
+    big = ref["tr"] >= 1e-2
+    assert np.all(np.abs(g["beta"][big] - ref["beta"][big]) <= 1e-4 * ref["beta"][big])
+    assert g["power_model"] == pytest.approx(ref["power_model"], rel=1e-6, abs=1e-30)
+    assert g["power_hybrid"] == pytest.approx(ref["power_hybrid"], rel=1e-6, abs=1e-30)
+    for k in ["grad_sp_in", "grad_tr_in", "grad_pincap", "grad_cload"]:
+        assert grad_close(g[k], ref[k]), k
+    return ref
+
+
+@pytest.mark.parametrize("grad_mode", [0, 1, 2])
+@pytest.mark.parametrize("tr_mode", [0, 1])
+def test_small_all_modes(dp, ctx, library_text, grad_mode, tr_mode):
+    text = netgen.netlist_text(netgen.WORKLOADS["small"])
+    o = Oracle(text, library_text)
+    sp, tr = netgen.scenario_inputs(o.n_start, 1000)
+    cfg = dp.config(grad_mode=grad_mode, tr_mode=tr_mode)
+    g = gpu_run(dp, ctx, text, library_text, sp[:, 0], tr[:, 0], cfg)
+    check_against_oracle(o, g, sp[:, 0], tr[:, 0], cfg)
+
+
+@pytest.mark.parametrize("use_step,on_device", [(False, True), (True, False), (True, True)])
+def test_mid_paths(dp, ctx, library_text, use_step, on_device):
+    text = netgen.netlist_text(netgen.WORKLOADS["mid"])
+    o = Oracle(text, library_text)
+    sp, tr = netgen.scenario_inputs(o.n_start, 1000)
+    cfg = dp.config()
+    g = gpu_run(dp, ctx, text, library_text, sp[:, 0], tr[:, 0], cfg, use_step, on_device)
+    check_against_oracle(o, g, sp[:, 0], tr[:, 0], cfg)
+
+
+def test_roofline_full_size(dp, ctx, library_text):
+    """The 2M-cell netlist in the configuration the benchmark times (dp_step, device buffers)."""
+    text = netgen.netlist_text(netgen.WORKLOADS["roofline"])
+    o = Oracle(text, library_text)
+    sp, tr = netgen.scenario_inputs(o.n_start, 1000)
+    cfg = dp.config()
+    g = gpu_run(dp, ctx, text, library_text, sp[:, 0], tr[:, 0], cfg, use_step=True, on_device=True)
+    check_against_oracle(o, g, sp[:, 0], tr[:, 0], cfg)
+
+
+def test_step_is_deterministic(dp, ctx, library_text):
+    text = netgen.netlist_text(netgen.WORKLOADS["mid"])
+    sp, tr = netgen.scenario_inputs(netgen.WORKLOADS["mid"].n_start, 1000)
+    cfg = dp.config()
+    a = gpu_run(dp, ctx, text, library_text, sp[:, 0], tr[:, 0], cfg, use_step=True)
+    b = gpu_run(dp, ctx, text, library_text, sp[:, 0], tr[:, 0], cfg, use_step=True)
+    for k in ["sp", "tr", "beta", "toggles", "grad_sp_in", "grad_pincap", "grad_cload", "grad_tr_in"]:
+        np.testing.assert_array_equal(a[k], b[k])
+    assert a["power_model"] == b["power_model"] and a["power_hybrid"] == b["power_hybrid"]
+
+
+# ---------------------------------------------------------------- edge cases
+
+
+def custom_case(rng, n_in=6, n_cells=40, lib_extra=""):
+    """Random reconvergent netlist over a library with 0..4-input cells (incl. constants,
+    repeated pins in one expression and duplicated fanin nets)."""
+    lib = ("cell AOI22 ZN 1.1 !((A1 & A2) | (B1 & B2))\n"
+           "cell OAI211 ZN 0.9 !((A1 | A2) & B & C)\n"
+           "cell MAJ Z 1.3 (A & B) | (A & C) | (B & C)\n"
+           "cell XOR4 Z 2.0 A ^ B ^ C ^ D\n"
+           "cell MUX2 Z 1.0 (A & !S) | (B & S)\n"
+           "cell TIEHI Y 0.5 1\ncell TIELO Y 0.5 0\ncell BUF Z 0.7 A\ncell INV ZN 0.6 !A\n"
+           "seq DFF D Q 0.8\n" + lib_extra)
+    cells = [("AOI22", ["A1", "A2", "B1", "B2"], "ZN"), ("OAI211", ["A1", "A2", "B", "C"], "ZN"),
+             ("MAJ", ["A", "B", "C"], "Z"), ("XOR4", ["A", "B", "C", "D"], "Z"), ("MUX2", ["A", "B", "S"], "Z"),
+             ("TIEHI", [], "Y"), ("TIELO", [], "Y"), ("BUF", ["A"], "Z"), ("INV", ["A"], "ZN")]
+    lines, avail = [], []
+    for i in range(n_in + n_cells):
+        lines.append(f"net n{i} {rng.uniform(0.5, 2.0):.5f}")
+    for i in range(n_in - 2):
+        lines.append(f"input n{i}")
+        avail.append(i)
+    lines.append(f"dff r0 DFF D=n{n_in + n_cells - 1} Q=n{n_in - 2}")
+    lines.append(f"dff r1 DFF D=n{n_in + 3} Q=n{n_in - 1}")
+    avail += [n_in - 2, n_in - 1]
+    for c in range(n_cells):
+        ref, pins, out = cells[rng.integers(len(cells))]
+        ins = [avail[rng.integers(len(avail))] for _ in pins]   # duplicates allowed
+        nid = n_in + c
+        lines.append(f"cell u{c} {ref} " + " ".join(f"{p}=n{x}" for p, x in zip(pins, ins)) + f" {out}=n{nid}")
+        avail.append(nid)
+    return "\n".join(lines) + "\n", lib
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+@pytest.mark.parametrize("T", [2, 33, 64, 97])
+def test_wide_and_constant_cells_ragged_words(dp, ctx, seed, T):
+    rng = np.random.default_rng(seed)
+    text, lib = custom_case(rng)
+    o = Oracle(text, lib)
+    sp = rng.uniform(0, 1, o.n_start).astype(np.float32)
+    sp[0], sp[1] = 0.0, 1.0                      # degenerate inputs
+    tr = (rng.uniform(0, 1, o.n_start) * 2 * np.minimum(sp, 1 - sp)).astype(np.float32)
+    tr[2] = 0.0
+    for grad_mode in [0, 1, 2]:
+        cfg = dp.config(sim_words=T, grad_mode=grad_mode, seed=seed * 7)
+        g = gpu_run(dp, ctx, text, lib, sp, tr, cfg)
+        check_against_oracle(o, g, sp, tr, cfg)
+
+
+def test_boolean_inputs_exact(dp, ctx, library_text):
+    text = netgen.netlist_text(netgen.WORKLOADS["small"])
+    o = Oracle(text, library_text)
+    rng = np.random.default_rng(5)
+    bits = rng.integers(0, 2, o.n_start)
+    g = gpu_run(dp, ctx, text, library_text, bits.astype(np.float32), np.zeros(o.n_start, np.float32),
+                dp.config(grad_mode=0))
+    want = G.boolean_eval(text, list(bits.astype(np.int64)))
+    np.testing.assert_array_equal(g["sp"], want.astype(np.float32))
+
+
+def test_only_startpoints_and_empty(dp, ctx, library_text):
+    text = "net a 1.5\nnet b 0.5\ninput a\ninput b\noutput a\n"
+    o = Oracle(text, library_text)
+    sp, tr = np.array([0.3, 0.6], np.float32), np.array([0.2, 0.1], np.float32)
+    cfg = dp.config()
+    g = gpu_run(dp, ctx, text, library_text, sp, tr, cfg)
+    check_against_oracle(o, g, sp, tr, cfg)
+    d = dp.dp_design_load(ctx, "", library_text)
+    dp.dp_set_inputs(ctx, d, np.zeros(0, np.float32), np.zeros(0, np.float32))
+    dp.dp_propagate(ctx, d, cfg)
+    assert dp.dp_total_power(ctx, d, 0) == 0.0
+    dp.dp_design_free(d)
+
+
+def test_sizing_delta(dp, ctx, library_text):
+    text = netgen.netlist_text(netgen.WORKLOADS["small"])
+    o = Oracle(text, library_text)
+    sp, tr = netgen.scenario_inputs(o.n_start, 1000)
+    cfg = dp.config(grad_mode=0)
+    rng = np.random.default_rng(8)
+    cells = rng.choice(o.n_cells, 20, replace=False).astype(np.int32)
+    caps = rng.choice([1.6, 3.2], 20).astype(np.float32)
+    d = dp.dp_design_load(ctx, text, library_text)
+    try:
+        dp.dp_set_inputs(ctx, d, sp[:, 0].copy(), tr[:, 0].copy())
+        dp.dp_set_pincap(ctx, d, cells, caps)
+        dp.dp_propagate(ctx, d, cfg)
+        p = dp.dp_total_power(ctx, d, 0)
+        gsp = np.zeros(o.n_start, np.float32)
+        gpin = np.zeros(o.n_cells, np.float32)
+        dp.dp_backward(ctx, d, cfg, gsp, None, gpin, None)
+    finally:
+        dp.dp_design_free(d)
+    for c, v in zip(cells, caps):
+        o.set_pincap(int(c), float(v))
+    rsp, rtr = o.forward(sp[:, 0], tr[:, 0])
+    assert p == pytest.approx(o.power(rtr), rel=1e-6)
+    ref = o.backward(rsp, rtr)
+    assert grad_close(gsp, ref["grad_sp_in"]) and grad_close(gpin, ref["grad_pincap"])
+
+
+def test_call_order_and_argument_errors(dp, ctx, library_text):
+    text = netgen.netlist_text(netgen.WORKLOADS["small"])
+    d = dp.dp_design_load(ctx, text, library_text)
+    try:
+        cfg = dp.config()
+        with pytest.raises(dp.DPError) as e:
+            dp.dp_propagate(ctx, d, cfg)
+        assert e.value.name == "DP_ESTATE"
+        ns = dp.dp_design_info(d).n_start
+        bad = np.full(ns, 0.5, np.float32)
+        bad[3] = 1.5
+        with pytest.raises(dp.DPError) as e:
+            dp.dp_set_inputs(ctx, d, bad, np.zeros(ns, np.float32))
+        assert e.value.name == "DP_EINVAL"
+        with pytest.raises(dp.DPError) as e:
+            dp.dp_set_inputs(ctx, d, np.zeros(2 * ns, np.float32), np.zeros(2 * ns, np.float32), 2)
+        assert e.value.name == "DP_EUNSUPPORTED"
+        dp.dp_set_inputs(ctx, d, np.full(ns, 0.5, np.float32), np.zeros(ns, np.float32))
+        with pytest.raises(dp.DPError) as e:
+            dp.dp_simulate(ctx, d, cfg)
+        assert e.value.name == "DP_ESTATE"
+        for bad_cfg in [dp.config(sim_words=1), dp.config(grad_mode=3), dp.config(beta_min=0.0),
+                        dp.config(vdd=-1.0), dp.config(reserved=1)]:
+            with pytest.raises(dp.DPError) as e:
+                dp.dp_propagate(ctx, d, bad_cfg)
+            assert e.value.name == "DP_EINVAL"
+        dp.dp_propagate(ctx, d, dp.config(grad_mode=0))
+        with pytest.raises(dp.DPError) as e:
+            dp.dp_backward(ctx, d, dp.config(grad_mode=1), np.zeros(ns, np.float32))
+        assert e.value.name == "DP_ESTATE"
+        with pytest.raises(dp.DPError) as e:
+            dp.dp_set_pincap(ctx, d, np.array([10 ** 7], np.int32), np.array([1.0], np.float32))
+        assert e.value.name == "DP_EINVAL"
+    finally:
+        dp.dp_design_free(d)
+
+
+def test_injected_allocation_failure(dp):
+    """DP_FAULT=alloc:N fails the N-th device allocation on the host side: the load reports
+    DP_ENOMEM and the process keeps working."""
+    import subprocess
+    import sys
+    code = (
+        "import numpy as np, torch\n"
+        "from paper_2608_03778_gb300 import dp, netgen\n"
+        "lib = netgen.library_text(); text = netgen.netlist_text(netgen.WORKLOADS['small'])\n"
+        "ctx = dp.dp_create(0, None)\n"
+        "try:\n    dp.dp_design_load(ctx, text, lib); print('NOFAIL')\n"
+        "except dp.DPError as e:\n    print(e.name)\n"
+        "d = dp.dp_design_load(ctx, text, lib); dp.dp_design_free(d); print('RECOVERED')\n"
+    )
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], env=dict(os.environ, DP_FAULT="alloc:5"), cwd=root,
+                       capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert "DP_ENOMEM" in r.stdout and "RECOVERED" in r.stdout
