@@ -17,6 +17,11 @@
  *     (sum over input minterms of f(m) * prod_i (m_i ? a_i : 1 - a_i)); this is
  *     the exact SP under input independence and equals the paper's stack
  *     interpreter (Algorithm 2) on every read-once expression.
+ *   - 1 - P of a net is evaluated as P(net = 0) under the same independence
+ *     model (sum over the minterms where f is 0), never as 1 minus a rounded
+ *     P: many nets of deep netlists sit within 1e-15 of 0 or 1, where the
+ *     subtraction would lose all relative accuracy of TR_model = 2P(1-P)
+ *     (Eq. 2) and could even make it negative.
  *   - Startpoint TR is the given input TR (tr_mode 0) or 2P(1-P) (tr_mode 1).
  *   - Local gradient term: d(K C (2P(1-P)))/dP = K C (2 - 4P) (Sec. III-E).
  *   - Hybrid gradient modes: 1 = paper (the accumulated gradient of each net is
@@ -517,50 +522,64 @@ void orc_cload(const void *h, double *cl) {
     }
 }
 
-/* SP of a cell: multilinear extension of its truth table at the fanin SPs. */
-static double cell_sp(const LibCell *L, const double *a) {
+/* Probability that a cell's output is v (v = 1: its SP) under input independence:
+ * sum over the input minterms m with f(m) = v of prod_i P(input i = m_i), where
+ * P(input i = 1) = a1[i] and P(input i = 0) = a0[i]. */
+static double cell_prob(const LibCell *L, const double *a1, const double *a0, int v) {
     int64_t M = (int64_t)1 << L->k;
     double s = 0.0;
     for (int64_t m = 0; m < M; m++) {
-        if (!L->tt[m]) continue;
+        if (L->tt[m] != v) continue;
         double p = 1.0;
-        for (int i = 0; i < L->k; i++) p *= ((m >> i) & 1) ? a[i] : 1.0 - a[i];
+        for (int i = 0; i < L->k; i++) p *= ((m >> i) & 1) ? a1[i] : a0[i];
         s += p;
     }
     return s;
 }
 
 /* d SP / d a_j of the same extension: sum_m f(m) (m_j ? 1 : -1) prod_{i != j}(...). */
-static double cell_dsp(const LibCell *L, const double *a, int j) {
+static double cell_dsp(const LibCell *L, const double *a1, const double *a0, int j) {
     int64_t M = (int64_t)1 << L->k;
     double s = 0.0;
     for (int64_t m = 0; m < M; m++) {
         if (!L->tt[m]) continue;
         double p = ((m >> j) & 1) ? 1.0 : -1.0;
-        for (int i = 0; i < L->k; i++) if (i != j) p *= ((m >> i) & 1) ? a[i] : 1.0 - a[i];
+        for (int i = 0; i < L->k; i++) if (i != j) p *= ((m >> i) & 1) ? a1[i] : a0[i];
         s += p;
     }
     return s;
 }
 
 /* Pass 1 (Sec. III-B, Algorithm 2) and Eq. 2.  Inputs per startpoint (binary64, so that
- * finite differences can perturb them); outputs per net, declaration order. */
-int orc_forward(const void *h, const double *sp_in, const double *tr_in, int tr_mode, double *sp, double *tr) {
+ * finite differences can perturb them); outputs per net, declaration order:
+ * sp = P(net = 1), sq = P(net = 0), tr = TR_model (startpoints: input TR when tr_mode 0). */
+int orc_forward(const void *h, const double *sp_in, const double *tr_in, int tr_mode, double *sp, double *tr,
+                double *sq) {
     const Orc *o = (const Orc *)h;
     for (int64_t k = 0; k < o->ns; k++) {
         int64_t n = o->start_net[k];
         sp[n] = sp_in[k];
-        tr[n] = tr_mode == 0 ? tr_in[k] : 2.0 * sp[n] * (1.0 - sp[n]);
+        sq[n] = 1.0 - sp_in[k];
+        tr[n] = tr_mode == 0 ? tr_in[k] : 2.0 * sp[n] * sq[n];
     }
-    double a[ORC_MAX_IN];
+    double a1[ORC_MAX_IN], a0[ORC_MAX_IN];
     for (int64_t t = 0; t < o->nc; t++) {
         int64_t c = o->topo[t];
         const LibCell *L = &o->lib[o->cell_lib[c]];
-        for (int i = 0; i < L->k; i++) a[i] = sp[o->fin_net[o->fin_ptr[c] + i]];
-        double p = cell_sp(L, a);
+        for (int i = 0; i < L->k; i++) {
+            int64_t f = o->fin_net[o->fin_ptr[c] + i];
+            a1[i] = sp[f];
+            a0[i] = sq[f];
+        }
         int64_t n = o->cell_out[c];
-        sp[n] = p;
-        tr[n] = 2.0 * p * (1.0 - p);
+        /* P(out=1) and P(out=0) sum to 1 in exact arithmetic; dividing by their computed
+         * sum keeps rounding from accumulating along the exponentially many paths of a
+         * reconvergent netlist (the sum of a cell's minterm weights is the product of its
+         * fanins' sums, so any drift from 1 would otherwise add up undamped) */
+        double p1 = cell_prob(L, a1, a0, 1), p0 = cell_prob(L, a1, a0, 0), s = p1 + p0;
+        sp[n] = p1 / s;
+        sq[n] = p0 / s;
+        tr[n] = 2.0 * sp[n] * sq[n];
     }
     return 0;
 }
@@ -582,26 +601,32 @@ double orc_power(const void *h, const double *alpha, double vdd, double fclk) {
     return 0.5 * vdd * vdd * fclk * 1e-15 * (s + comp);
 }
 
-/* Sec. III-E, Eq. 7 (and Eq. 6 for the hybrid modes).
- *   sp, alpha : forward SP and the activity used in the power (model or hybrid TR)
- *   beta      : per-net beta (NULL for grad_mode 0)
+/* Sec. III-E, Eq. 7 (and Eq. 6 for the hybrid modes), at the startpoint inputs sp_in/tr_in.
+ *   beta      : per-net beta (NULL for grad_mode 0); the power's activity is beta * TR_model
+ *               for the hybrid modes and TR_model for the model
  *   grad_mode : 0 model, 1 paper hybrid (scale accumulated gradient by beta),
  *               2 exact hybrid with beta held fixed
  * Outputs (any may be NULL): dP/d sp_in[ns], dP/d tr_in[ns], dP/d pincap[nc],
  * dP/d C_load[nn], and the full per-net SP adjoint[nn]. */
-int orc_backward(const void *h, const double *sp, const double *alpha, const double *beta, int grad_mode,
+int orc_backward(const void *h, const double *sp_in, const double *tr_in, const double *beta, int grad_mode,
                  int tr_mode, double vdd, double fclk, double *g_sp_in, double *g_tr_in, double *g_pincap,
                  double *g_cload, double *g_net) {
     const Orc *o = (const Orc *)h;
     const double K = 0.5 * vdd * vdd * fclk * 1e-15;
-    double *cl = (double *)malloc(sizeof(double) * (size_t)(o->nn + 1));
-    double *adj = (double *)calloc((size_t)o->nn + 1, sizeof(double));
+    size_t nb = sizeof(double) * (size_t)(o->nn + 1);
+    double *cl = (double *)malloc(nb), *adj = (double *)calloc((size_t)o->nn + 1, sizeof(double));
     double *tot = (double *)calloc((size_t)o->nn + 1, sizeof(double));
-    if (!cl || !adj || !tot) { free(cl); free(adj); free(tot); return -1; }
+    double *sp = (double *)malloc(nb), *sq = (double *)malloc(nb), *tr = (double *)malloc(nb);
+    if (!cl || !adj || !tot || !sp || !sq || !tr) {
+        free(cl); free(adj); free(tot); free(sp); free(sq); free(tr);
+        return -1;
+    }
     orc_cload(o, cl);
-    double a[ORC_MAX_IN];
-    /* local term d(K C 2P(1-P))/dP = K C (2 - 4P) on every net whose TR comes from its SP */
-    #define LOCAL(n) ((o->drv[n] >= 0 || (o->drv[n] == -1 && tr_mode == 1)) ? K * cl[n] * (2.0 - 4.0 * sp[n]) : 0.0)
+    orc_forward(o, sp_in, tr_in, tr_mode, sp, tr, sq);
+    double a1[ORC_MAX_IN], a0[ORC_MAX_IN];
+    /* local term d(K C 2P(1-P))/dP = K C (2 - 4P) = 2 K C ((1-P) - P), on every net whose TR
+     * comes from its SP */
+    #define LOCAL(n) ((o->drv[n] >= 0 || (o->drv[n] == -1 && tr_mode == 1)) ? 2.0 * K * cl[n] * (sq[n] - sp[n]) : 0.0)
     for (int64_t t = o->nc - 1; t >= 0; t--) {
         int64_t c = o->topo[t];
         int64_t n = o->cell_out[c];
@@ -609,8 +634,12 @@ int orc_backward(const void *h, const double *sp, const double *alpha, const dou
         double g = grad_mode == 1 ? b * (adj[n] + LOCAL(n)) : (grad_mode == 2 ? adj[n] + b * LOCAL(n) : adj[n] + LOCAL(n));
         tot[n] = g;
         const LibCell *L = &o->lib[o->cell_lib[c]];
-        for (int i = 0; i < L->k; i++) a[i] = sp[o->fin_net[o->fin_ptr[c] + i]];
-        for (int j = 0; j < L->k; j++) adj[o->fin_net[o->fin_ptr[c] + j]] += g * cell_dsp(L, a, j);
+        for (int i = 0; i < L->k; i++) {
+            int64_t f = o->fin_net[o->fin_ptr[c] + i];
+            a1[i] = sp[f];
+            a0[i] = sq[f];
+        }
+        for (int j = 0; j < L->k; j++) adj[o->fin_net[o->fin_ptr[c] + j]] += g * cell_dsp(L, a1, a0, j);
     }
     for (int64_t n = 0; n < o->nn; n++) {
         if (o->drv[n] >= 0) continue;
@@ -625,15 +654,17 @@ int orc_backward(const void *h, const double *sp, const double *alpha, const dou
         if (g_sp_in) g_sp_in[k] = tot[n];
         if (g_tr_in) g_tr_in[k] = tr_mode == 0 ? K * b * cl[n] : 0.0;
     }
-    if (g_cload) for (int64_t n = 0; n < o->nn; n++) g_cload[n] = K * alpha[n];
+    #define ALPHA(n) (grad_mode ? beta[n] * tr[n] : tr[n])
+    if (g_cload) for (int64_t n = 0; n < o->nn; n++) g_cload[n] = K * ALPHA(n);
     if (g_pincap)
         for (int64_t c = 0; c < o->nc; c++) {
             double s = 0.0;
-            for (int64_t e = o->fin_ptr[c]; e < o->fin_ptr[c + 1]; e++) s += alpha[o->fin_net[e]];
+            for (int64_t e = o->fin_ptr[c]; e < o->fin_ptr[c + 1]; e++) s += ALPHA(o->fin_net[e]);
             g_pincap[c] = K * s;
         }
+    #undef ALPHA
     if (g_net) memcpy(g_net, tot, sizeof(double) * (size_t)o->nn);
-    free(cl); free(adj); free(tot);
+    free(cl); free(adj); free(tot); free(sp); free(sq); free(tr);
     return 0;
 }
 

@@ -63,7 +63,7 @@ def _load():
             L.orc_cell_outs.argtypes = [_P, _I64]
             L.orc_set_pincap.argtypes = [_P, ctypes.c_int64, ctypes.c_double]
             L.orc_cload.argtypes = [_P, _D]
-            L.orc_forward.argtypes = [_P, _D, _D, ctypes.c_int, _D, _D]
+            L.orc_forward.argtypes = [_P, _D, _D, ctypes.c_int, _D, _D, _D]
             L.orc_forward.restype = ctypes.c_int
             L.orc_power.argtypes = [_P, _D, ctypes.c_double, ctypes.c_double]
             L.orc_power.restype = ctypes.c_double
@@ -123,22 +123,25 @@ class Oracle:
         _load().orc_cload(self._h, out)
         return out
 
-    def forward(self, sp_in, tr_in, tr_mode: int = 0):
+    def forward(self, sp_in, tr_in, tr_mode: int = 0, want_sq: bool = False):
         """Per-net SP and TR (Algorithm 2, Eq. 2) from startpoint inputs (binary32 inputs
-        convert exactly; binary64 inputs allow finite differences)."""
+        convert exactly; binary64 inputs allow finite differences).  With ``want_sq`` also
+        P(net = 0), evaluated as its own probability sum rather than as 1 - SP."""
         sp = np.zeros(self.n_nets, np.float64)
         tr = np.zeros(self.n_nets, np.float64)
+        sq = np.zeros(self.n_nets, np.float64)
         _load().orc_forward(self._h, np.ascontiguousarray(sp_in, np.float64),
-                            np.ascontiguousarray(tr_in, np.float64), int(tr_mode), sp, tr)
-        return sp, tr
+                            np.ascontiguousarray(tr_in, np.float64), int(tr_mode), sp, tr, sq)
+        return (sp, tr, sq) if want_sq else (sp, tr)
 
     def power(self, alpha, vdd: float = 0.8, fclk: float = 1e9) -> float:
         """Eq. 1 in watts, caps in fF."""
         return float(_load().orc_power(self._h, np.ascontiguousarray(alpha, np.float64), vdd, fclk))
 
-    def backward(self, sp, alpha, beta=None, grad_mode: int = 0, tr_mode: int = 0,
+    def backward(self, sp_in, tr_in, beta=None, grad_mode: int = 0, tr_mode: int = 0,
                  vdd: float = 0.8, fclk: float = 1e9) -> dict:
-        """Gradients of Eq. 1 (Eq. 7; Eq. 6 for grad_mode 1)."""
+        """Gradients of Eq. 1 at the startpoint inputs (Eq. 7; Eq. 6 for grad_mode 1).  The
+        hybrid modes (grad_mode 1, 2) differentiate sum K beta TR C with the given beta."""
         out = {
             "grad_sp_in": np.zeros(self.n_start), "grad_tr_in": np.zeros(self.n_start),
             "grad_pincap": np.zeros(self.n_cells), "grad_cload": np.zeros(self.n_nets),
@@ -146,8 +149,8 @@ class Oracle:
         }
         if grad_mode and beta is None:
             raise ValueError("beta required for hybrid gradient modes")
-        rc = _load().orc_backward(self._h, np.ascontiguousarray(sp, np.float64),
-                                  np.ascontiguousarray(alpha, np.float64),
+        rc = _load().orc_backward(self._h, np.ascontiguousarray(sp_in, np.float64),
+                                  np.ascontiguousarray(tr_in, np.float64),
                                   None if beta is None else np.ascontiguousarray(beta, np.float64),
                                   int(grad_mode), int(tr_mode), vdd, fclk, out["grad_sp_in"],
                                   out["grad_tr_in"], out["grad_pincap"], out["grad_cload"], out["grad_net"])
@@ -182,8 +185,7 @@ class Oracle:
         tg, on = self.simulate(sp_in, tr_in, seed, T)
         beta, trh = self.hybrid(tr, tg, T, beta_min, beta_max)
         p_hyb = self.power(trh, vdd, fclk)
-        alpha = trh if grad_mode else tr
-        g = self.backward(sp, alpha, beta if grad_mode else None, grad_mode, tr_mode, vdd, fclk)
+        g = self.backward(sp_in, tr_in, beta if grad_mode else None, grad_mode, tr_mode, vdd, fclk)
         g.update(sp=sp, tr=tr, toggles=tg, ones=on, beta=beta, tr_hyb=trh, power_model=p_model,
                  power_hybrid=p_hyb)
         return g

@@ -26,7 +26,7 @@ def test_model_gradients(case):
     o, v = case
     K = v["K"][0]
     sp, tr = o.forward(np.array(v["sp_in"]), np.array(v["tr_in"]))
-    g = o.backward(sp, tr, None, 0, 0, v["vdd"][0], v["fclk"][0])
+    g = o.backward(np.array(v["sp_in"]), np.array(v["tr_in"]), None, 0, 0, v["vdd"][0], v["fclk"][0])
     np.testing.assert_allclose(g["grad_sp_in"], np.array(v["grad_sp_in_K"]) * K, rtol=1e-13)
     np.testing.assert_allclose(g["grad_tr_in"], np.array(v["grad_tr_in_K"]) * K, rtol=1e-13)
     np.testing.assert_allclose(g["grad_pincap"], np.array(v["grad_pincap_K"]) * K, rtol=1e-13)
@@ -41,7 +41,7 @@ def test_hybrid_gradients(case, mode, key):
     beta = np.array(v["beta"])
     alpha = beta * tr
     assert o.power(alpha, v["vdd"][0], v["fclk"][0]) == pytest.approx(v["power_hybrid_K"][0] * K, rel=1e-14)
-    g = o.backward(sp, alpha, beta, mode, 0, v["vdd"][0], v["fclk"][0])
+    g = o.backward(np.array(v["sp_in"]), np.array(v["tr_in"]), beta, mode, 0, v["vdd"][0], v["fclk"][0])
     np.testing.assert_allclose(g["grad_sp_in"], np.array(v[key]) * K, rtol=1e-13)
     np.testing.assert_allclose(g["grad_tr_in"], np.array(v["grad_tr_in_hybrid_K"]) * K, rtol=1e-13)
     np.testing.assert_allclose(g["grad_pincap"], np.array(v["grad_pincap_hybrid_K"]) * K, rtol=1e-13)

@@ -43,7 +43,7 @@ def fd_ok(g, fd):
 def test_grad_sp_central_fd(small, tr_mode):
     o, sp_in, tr_in = small
     sp, tr = o.forward(sp_in, tr_in, tr_mode)
-    g = o.backward(sp, tr, None, 0, tr_mode, VDD, F)["grad_sp_in"]
+    g = o.backward(sp_in, tr_in, None, 0, tr_mode, VDD, F)["grad_sp_in"]
     h = 1e-5
     fd = np.empty(o.n_start)
     for k in range(o.n_start):
@@ -57,7 +57,7 @@ def test_grad_sp_central_fd(small, tr_mode):
 def test_paper_protocol_thresholds(small):
     o, sp_in, tr_in = small
     sp, tr = o.forward(sp_in, tr_in)
-    g = o.backward(sp, tr, None, 0, 0, VDD, F)["grad_sp_in"]
+    g = o.backward(sp_in, tr_in, None, 0, 0, VDD, F)["grad_sp_in"]
     rng = np.random.default_rng(32)
     roots = rng.choice(o.n_start, 32, replace=False)
     eps = 1e-4
@@ -75,7 +75,7 @@ def test_paper_protocol_thresholds(small):
 def test_one_sided_difference_converges_first_order(small):
     o, sp_in, tr_in = small
     sp, tr = o.forward(sp_in, tr_in)
-    g = o.backward(sp, tr, None, 0, 0, VDD, F)["grad_sp_in"]
+    g = o.backward(sp_in, tr_in, None, 0, 0, VDD, F)["grad_sp_in"]
     p0 = P_of(o, sp_in, tr_in)
     k = int(np.argmax(np.abs(g)))
     errs = []
@@ -90,7 +90,7 @@ def test_one_sided_difference_converges_first_order(small):
 def test_grad_tr_in_exact_linearity(small):
     o, sp_in, tr_in = small
     sp, tr = o.forward(sp_in, tr_in)
-    g = o.backward(sp, tr)["grad_tr_in"]
+    g = o.backward(sp_in, tr_in)["grad_tr_in"]
     cl = o.cload()
     np.testing.assert_allclose(g, K * cl[o.start_nets()], rtol=1e-14)
     d = 1e-3
@@ -106,7 +106,7 @@ def test_grad_pincap_exact_linearity(library_text):
     o = Oracle(netgen.netlist_text(spec), library_text)
     sp_in, tr_in = netgen.scenario_inputs(o.n_start, 1000)
     sp, tr = o.forward(sp_in[:, 0], tr_in[:, 0])
-    g = o.backward(sp, tr)["grad_pincap"]
+    g = o.backward(sp_in[:, 0], tr_in[:, 0])["grad_pincap"]
     p0 = o.power(tr, VDD, F)
     for c in [0, 7, 123, o.n_cells - 1]:
         o2 = Oracle(netgen.netlist_text(spec), library_text)
@@ -124,7 +124,7 @@ def test_grad_pincap_exact_linearity(library_text):
 def test_grad_cload_is_K_tr(small):
     o, sp_in, tr_in = small
     sp, tr = o.forward(sp_in, tr_in)
-    g = o.backward(sp, tr)["grad_cload"]
+    g = o.backward(sp_in, tr_in)["grad_cload"]
     # P = K sum tr C exactly: rebuild P from the gradient and the loads
     assert (g * o.cload()).sum() == pytest.approx(o.power(tr, VDD, F), rel=1e-12)
     np.testing.assert_allclose(g, K * tr, rtol=1e-15)
@@ -135,7 +135,7 @@ def test_hybrid_exact_mode_central_fd(small):
     rng = np.random.default_rng(4)
     beta = rng.uniform(0.1, 3.0, o.n_nets)
     sp, tr = o.forward(sp_in, tr_in)
-    g = o.backward(sp, beta * tr, beta, 2, 0, VDD, F)["grad_sp_in"]
+    g = o.backward(sp_in, tr_in, beta, 2, 0, VDD, F)["grad_sp_in"]
     h = 1e-5
     fd = np.empty(o.n_start)
     for k in range(o.n_start):
@@ -159,12 +159,12 @@ def test_hybrid_paper_mode_chain_closed_form(x, library_text):
     rng = np.random.default_rng(9)
     beta = rng.uniform(0.2, 4.0, n + 1)
     sp, tr = o.forward(np.array([x]), np.array([0.1]))
-    g = o.backward(sp, beta * tr, beta, 1, 0, VDD, F)["grad_sp_in"][0]
+    g = o.backward(np.array([x]), np.array([0.1]), beta, 1, 0, VDD, F)["grad_sp_in"][0]
     cl = o.cload()
     # net i (i >= 1) has SP x or 1-x; d sp_i / d x = (-1)^i; local_i = K C_i (2 - 4 sp_i)
     want = sum(np.prod(beta[: i + 1]) * K * cl[i] * (2 - 4 * sp[i]) * (-1) ** i for i in range(1, n + 1))
     assert g == pytest.approx(want, rel=1e-13)
     # all beta = 1 reduces to the model gradient
-    g1 = o.backward(sp, tr, np.ones(n + 1), 1, 0, VDD, F)["grad_sp_in"][0]
-    g0 = o.backward(sp, tr, None, 0, 0, VDD, F)["grad_sp_in"][0]
+    g1 = o.backward(np.array([x]), np.array([0.1]), np.ones(n + 1), 1, 0, VDD, F)["grad_sp_in"][0]
+    g0 = o.backward(np.array([x]), np.array([0.1]), None, 0, 0, VDD, F)["grad_sp_in"][0]
     assert g1 == pytest.approx(g0, rel=1e-15)

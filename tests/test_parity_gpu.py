@@ -250,7 +250,7 @@ def test_sizing_delta(dp, ctx, library_text):
         o.set_pincap(int(c), float(v))
     rsp, rtr = o.forward(sp[:, 0], tr[:, 0])
     assert p == pytest.approx(o.power(rtr), rel=1e-6)
-    ref = o.backward(rsp, rtr)
+    ref = o.backward(sp[:, 0], tr[:, 0])
     assert grad_close(gsp, ref["grad_sp_in"]) and grad_close(gpin, ref["grad_pincap"])
 
 
