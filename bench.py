@@ -287,7 +287,7 @@ def main() -> None:
         per_phase[n] = {"ms": float(ph[i]), "algorithmic_bytes": ab[n], "achieved_gbs": ach,
                         "frac": ach / pk["hbm_gbs"]}
     dom = max(names[:3], key=lambda n: per_phase[n]["ms"])
-    fb_ms = per_phase["forward"]["ms"] + per_phase["backward"]["ms"]
+    fb_ms = max(per_phase["forward"]["ms"] + per_phase["backward"]["ms"], 1e-9)
     line = {
         "metric": METRIC,
         "value": nc * world / (ms / 1e3),

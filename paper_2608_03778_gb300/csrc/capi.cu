@@ -310,7 +310,7 @@ dp_status dp_design_upload(dp_ctx *ctx, const dp_compiled *cp, dp_design **out) 
     TRY(dalloc(D, &d.cload, nn));
     TRY(dalloc(D, &d.sp_in, ns));
     TRY(dalloc(D, &d.tr_in, ns));
-    TRY(dalloc(D, &d.sp, nn));
+    TRY(dalloc(D, &d.pq, nn));
     TRY(dalloc(D, &d.tr, nn));
     TRY(dalloc(D, &d.beta, nn));
     TRY(dalloc(D, &d.trh, nn));
@@ -525,7 +525,7 @@ dp_status dp_get_nets(dp_design *D, float *sp, float *tr, float *beta, float *tr
         if (!o.dst) continue;
         void *dst = on_device ? o.dst : (void *)stage;
         switch (o.kind) {
-            case 0: dp::launch_gather_f32(D->d.sp, D->d.net_of_user, (float *)dst, nn, st); break;
+            case 0: dp::launch_sp_user(D->d, (float *)dst, st); break;
             case 1: dp::launch_gather_f32(D->d.tr, D->d.net_of_user, (float *)dst, nn, st); break;
             case 2: dp::launch_gather_f32(D->d.beta, D->d.net_of_user, (float *)dst, nn, st); break;
             case 3: dp::launch_trh_user(D->d, (float *)dst, st); break;
@@ -557,13 +557,15 @@ dp_status dp_step(dp_design *D, const dp_config *cfg, float *gsp, float *gtr, fl
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_err(D->ctx, e, "graph capture");
-        cudaEventRecord(D->ev[0], cs);
+        // external event records become timing nodes of the graph (a plain record
+        // inside a capture would only express a dependency)
+        cudaEventRecordWithFlags(D->ev[0], cs, cudaEventRecordExternal);
         q_forward(D, *cfg, cs);
-        cudaEventRecord(D->ev[1], cs);
+        cudaEventRecordWithFlags(D->ev[1], cs, cudaEventRecordExternal);
         q_simulate(D, *cfg, cs);
-        cudaEventRecord(D->ev[2], cs);
+        cudaEventRecordWithFlags(D->ev[2], cs, cudaEventRecordExternal);
         q_backward(D, *cfg, nullptr, cs);
-        cudaEventRecord(D->ev[3], cs);
+        cudaEventRecordWithFlags(D->ev[3], cs, cudaEventRecordExternal);
         e = cudaStreamEndCapture(cs, &graph);
         D->graph_kernels = 0;
         if (e == cudaSuccess) {

@@ -29,39 +29,36 @@ __device__ __forceinline__ float combine(int grad_mode, float acc, float local, 
 }
 
 __global__ void k_bwd_level(const uint4 *__restrict__ fanin, const int32_t *__restrict__ fptr,
-                            const int32_t *__restrict__ fedge, const float *__restrict__ sp,
+                            const int32_t *__restrict__ fedge, const float2 *__restrict__ pq,
                             const float *__restrict__ cload, const float *__restrict__ beta, float *gnet,
                             float4 *gedge, int32_t c0, int32_t c1, int64_t ns, int grad_mode, float K, OpTable ops) {
     int32_t c = c0 + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
     if (c >= c1) return;
     const int64_t n = ns + c;
     const float acc = fanout_sum(fptr, fedge, reinterpret_cast<const float *>(gedge), n);
-    const float p = sp[n];
-    // local term: d(K C 2P(1-P))/dP = K C (2 - 4P)
-    const float g = combine(grad_mode, acc, K * cload[n] * (2.f - 4.f * p), beta, n);
+    const float2 o = pq[n];
+    // local term: d(K C 2P(1-P))/dP = K C (2 - 4P) = 2 K C (Q - P)
+    const float g = combine(grad_mode, acc, 2.f * K * cload[n] * (o.y - o.x), beta, n);
     gnet[n] = g;
     const uint4 r = fanin[c];
     const uint32_t op = r.x >> 24;
     const int k = op_arity(ops, op);
-    float a[4] = {0.f, 0.f, 0.f, 0.f};
-    if (k > 0) a[0] = sp[r.x & kMask24];
-    if (k > 1) a[1] = sp[r.y];
-    if (k > 2) a[2] = sp[r.z];
-    if (k > 3) a[3] = sp[r.w];
-    float d[4];
-    cell_partials(k, op_tt(ops, op), a, d);
+    float p[4], q[4], d[4];
+    gather_pairs(pq, r, k, p, q);
+    cell_partials(k, op_tt(ops, op), p, q, d);
     gedge[c] = make_float4(g * d[0], g * d[1], g * d[2], g * d[3]);
 }
 
 __global__ void k_bwd_start(const int32_t *__restrict__ fptr, const int32_t *__restrict__ fedge,
-                            const float *__restrict__ sp, const float *__restrict__ cload,
+                            const float2 *__restrict__ pq, const float *__restrict__ cload,
                             const float *__restrict__ beta, float *gnet, const float4 *gedge, int64_t ns,
                             int grad_mode, int tr_mode, float K, float *out) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= ns) return;
     const float acc = fanout_sum(fptr, fedge, reinterpret_cast<const float *>(gedge), k);
     // a startpoint has a local SP term only when its TR is derived from its SP (tr_mode 1)
-    const float local = tr_mode ? K * cload[k] * (2.f - 4.f * sp[k]) : 0.f;
+    const float2 o = pq[k];
+    const float local = tr_mode ? 2.f * K * cload[k] * (o.y - o.x) : 0.f;
     const float g = combine(grad_mode, acc, local, beta, k);
     gnet[k] = g;
     if (out) out[k] = g;
@@ -79,14 +76,14 @@ void launch_bwd_level(const DevDesign &d, const OpTable &ops, int32_t c0, int32_
                       cudaStream_t s) {
     if (c1 <= c0) return;
     int b = level_block(c1 - c0);
-    k_bwd_level<<<(unsigned)cdiv(c1 - c0, b), b, 0, s>>>(d.fanin, d.fout_ptr, d.fout_edge, d.sp, d.cload, d.beta,
+    k_bwd_level<<<(unsigned)cdiv(c1 - c0, b), b, 0, s>>>(d.fanin, d.fout_ptr, d.fout_edge, d.pq, d.cload, d.beta,
                                                          d.gnet, d.gedge, c0, c1, d.n_start, grad_mode, K, ops);
 }
 
 void launch_bwd_start(const DevDesign &d, int grad_mode, int tr_mode, float K, float *grad_sp_in, cudaStream_t s) {
     if (d.n_start == 0) return;
     int b = level_block(d.n_start);
-    k_bwd_start<<<(unsigned)cdiv(d.n_start, b), b, 0, s>>>(d.fout_ptr, d.fout_edge, d.sp, d.cload, d.beta, d.gnet,
+    k_bwd_start<<<(unsigned)cdiv(d.n_start, b), b, 0, s>>>(d.fout_ptr, d.fout_edge, d.pq, d.cload, d.beta, d.gnet,
                                                            d.gedge, d.n_start, grad_mode, tr_mode, K, grad_sp_in);
 }
 

@@ -12,28 +12,42 @@ constexpr uint32_t kMask24 = 0xFFFFFFu;
 __device__ __forceinline__ int op_arity(const OpTable &t, uint32_t op) { return (int)(t.e[op] >> 16); }
 __device__ __forceinline__ uint32_t op_tt(const OpTable &t, uint32_t op) { return t.e[op] & 0xFFFFu; }
 
-// SP of a cell with K inputs: the multilinear extension of its truth table,
-// sum_m f(m) prod_i (m_i ? a_i : 1 - a_i), evaluated as nested linear
-// interpolations along inputs 0, 1, ... (exact under input independence,
-// Sec. III-B; equals the stack interpreter of Algorithm 2 on read-once cells).
+// Probabilities of a net are carried as the pair (P, Q) = (P(net=1), P(net=0)).
+// Q is never formed as 1 - P: deep reconvergent netlists have many nets within
+// 1e-15 of 0 or 1, where that subtraction would destroy the relative accuracy
+// of TR_model = 2PQ (Eq. 2).
+//
+// The output pair of a cell with K inputs is the multilinear extension of its
+// truth table and of the complemented table (Sec. III-B; exact under input
+// independence, equal to the stack interpreter of Algorithm 2 on read-once
+// cells), folded input by input as v = Q_i v[.., 0] + P_i v[.., 1]: every
+// term is non-negative, so both P and Q keep full relative accuracy.  The pair
+// is then divided by its sum (1 in exact arithmetic) so that rounding cannot
+// accumulate along the exponentially many paths of a reconvergent netlist.
 template <int K>
-__device__ __forceinline__ float ml_eval(uint32_t tt, const float (&a)[4]) {
-    float v[1 << K];
+__device__ __forceinline__ float2 ml_pair(uint32_t tt, const float (&p)[4], const float (&q)[4]) {
+    float v1[1 << K], v0[1 << K];
 #pragma unroll
-    for (int m = 0; m < (1 << K); m++) v[m] = (float)((tt >> m) & 1u);
+    for (int m = 0; m < (1 << K); m++) {
+        v1[m] = (float)((tt >> m) & 1u);
+        v0[m] = 1.f - v1[m];
+    }
 #pragma unroll
     for (int i = 0; i < K; i++) {
 #pragma unroll
-        for (int m = 0; m < (1 << (K - 1 - i)); m++) v[m] = fmaf(a[i], v[2 * m + 1] - v[2 * m], v[2 * m]);
+        for (int m = 0; m < (1 << (K - 1 - i)); m++) {
+            v1[m] = fmaf(p[i], v1[2 * m + 1], q[i] * v1[2 * m]);
+            v0[m] = fmaf(p[i], v0[2 * m + 1], q[i] * v0[2 * m]);
+        }
     }
-    return v[0];
+    const float r = 1.f / (v1[0] + v0[0]);
+    return make_float2(v1[0] * r, v0[0] * r);
 }
 
-// d SP / d a_J: the multilinear extension, over the other inputs, of the
-// difference table f(.., a_J = 1, ..) - f(.., a_J = 0, ..) (entries in {-1,0,1},
-// so no cancellation between two large values).
+// d P / d a_J: the multilinear extension, over the other inputs, of the
+// difference table f(.., a_J = 1, ..) - f(.., a_J = 0, ..) (entries in {-1,0,1}).
 template <int K, int J>
-__device__ __forceinline__ float ml_partial(uint32_t tt, const float (&a)[4]) {
+__device__ __forceinline__ float ml_partial(uint32_t tt, const float (&p)[4], const float (&q)[4]) {
     constexpr int M = 1 << (K - 1);
     float v[M];
 #pragma unroll
@@ -48,35 +62,51 @@ __device__ __forceinline__ float ml_partial(uint32_t tt, const float (&a)[4]) {
         if (i == J) continue;
         const int f = i < J ? i : i - 1;  // folds already done
 #pragma unroll
-        for (int m = 0; m < (M >> (f + 1)); m++) v[m] = fmaf(a[i], v[2 * m + 1] - v[2 * m], v[2 * m]);
+        for (int m = 0; m < (M >> (f + 1)); m++) v[m] = fmaf(p[i], v[2 * m + 1], q[i] * v[2 * m]);
     }
     return v[0];
 }
 
-__device__ __forceinline__ float cell_sp(int k, uint32_t tt, const float (&a)[4]) {
+__device__ __forceinline__ float2 cell_pair(int k, uint32_t tt, const float (&p)[4], const float (&q)[4]) {
     switch (k) {
-        case 0: return (float)(tt & 1u);
-        case 1: return ml_eval<1>(tt, a);
-        case 2: return ml_eval<2>(tt, a);
-        case 3: return ml_eval<3>(tt, a);
-        default: return ml_eval<4>(tt, a);
+        case 0: return (tt & 1u) ? make_float2(1.f, 0.f) : make_float2(0.f, 1.f);
+        case 1: return ml_pair<1>(tt, p, q);
+        case 2: return ml_pair<2>(tt, p, q);
+        case 3: return ml_pair<3>(tt, p, q);
+        default: return ml_pair<4>(tt, p, q);
     }
 }
 
 // all partials of a cell into d[0..3] (unused slots 0)
-__device__ __forceinline__ void cell_partials(int k, uint32_t tt, const float (&a)[4], float (&d)[4]) {
+__device__ __forceinline__ void cell_partials(int k, uint32_t tt, const float (&p)[4], const float (&q)[4],
+                                              float (&d)[4]) {
     d[0] = d[1] = d[2] = d[3] = 0.f;
     switch (k) {
         case 0: break;
-        case 1: d[0] = ml_partial<1, 0>(tt, a); break;
-        case 2: d[0] = ml_partial<2, 0>(tt, a); d[1] = ml_partial<2, 1>(tt, a); break;
+        case 1: d[0] = ml_partial<1, 0>(tt, p, q); break;
+        case 2: d[0] = ml_partial<2, 0>(tt, p, q); d[1] = ml_partial<2, 1>(tt, p, q); break;
         case 3:
-            d[0] = ml_partial<3, 0>(tt, a); d[1] = ml_partial<3, 1>(tt, a); d[2] = ml_partial<3, 2>(tt, a);
+            d[0] = ml_partial<3, 0>(tt, p, q); d[1] = ml_partial<3, 1>(tt, p, q); d[2] = ml_partial<3, 2>(tt, p, q);
             break;
         default:
-            d[0] = ml_partial<4, 0>(tt, a); d[1] = ml_partial<4, 1>(tt, a);
-            d[2] = ml_partial<4, 2>(tt, a); d[3] = ml_partial<4, 3>(tt, a);
+            d[0] = ml_partial<4, 0>(tt, p, q); d[1] = ml_partial<4, 1>(tt, p, q);
+            d[2] = ml_partial<4, 2>(tt, p, q); d[3] = ml_partial<4, 3>(tt, p, q);
             break;
+    }
+}
+
+// gathers the (P, Q) pairs of a cell's inputs
+__device__ __forceinline__ void gather_pairs(const float2 *pq, const uint4 &r, int k, float (&p)[4], float (&q)[4]) {
+    const uint32_t n[4] = {r.x & kMask24, r.y, r.z, r.w};
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        p[j] = 0.f;
+        q[j] = 1.f;
+        if (j < k) {
+            const float2 v = pq[n[j]];
+            p[j] = v.x;
+            q[j] = v.y;
+        }
     }
 }
 

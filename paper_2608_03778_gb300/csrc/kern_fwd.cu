@@ -7,34 +7,30 @@ namespace {
 
 __host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-// startpoints: SP = input SP; TR = input TR (tr_mode 0) or 2P(1-P) (tr_mode 1)
-__global__ void k_init_start(const float *__restrict__ sp_in, const float *__restrict__ tr_in, float *sp, float *tr,
+// startpoints: (P, Q) = (SP, 1 - SP); TR = input TR (tr_mode 0) or 2PQ (tr_mode 1)
+__global__ void k_init_start(const float *__restrict__ sp_in, const float *__restrict__ tr_in, float2 *pq, float *tr,
                              int64_t ns, int tr_mode) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= ns) return;
-    float p = sp_in[k];
-    sp[k] = p;
-    tr[k] = tr_mode ? 2.f * p * (1.f - p) : tr_in[k];
+    const float p = sp_in[k], q = 1.f - p;
+    pq[k] = make_float2(p, q);
+    tr[k] = tr_mode ? 2.f * p * q : tr_in[k];
 }
 
-// one thread per cell of one level: gather fanin SPs, evaluate the cell's
-// multilinear extension, write SP and TR_model = 2P(1-P) of its output net
-__global__ void k_fwd_level(const uint4 *__restrict__ fanin, float *sp, float *tr, int32_t c0, int32_t c1,
+// one thread per cell of one level: gather the fanin (P, Q) pairs, evaluate
+// the cell's pair, write it and TR_model = 2PQ (Eq. 2) for its output net
+__global__ void k_fwd_level(const uint4 *__restrict__ fanin, float2 *pq, float *tr, int32_t c0, int32_t c1,
                             int64_t ns, OpTable ops) {
     int32_t c = c0 + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
     if (c >= c1) return;
     const uint4 r = fanin[c];
     const uint32_t op = r.x >> 24;
     const int k = op_arity(ops, op);
-    float a[4] = {0.f, 0.f, 0.f, 0.f};
-    if (k > 0) a[0] = sp[r.x & kMask24];
-    if (k > 1) a[1] = sp[r.y];
-    if (k > 2) a[2] = sp[r.z];
-    if (k > 3) a[3] = sp[r.w];
-    float p = cell_sp(k, op_tt(ops, op), a);
-    p = fminf(fmaxf(p, 0.f), 1.f);  // safety clamp only (values are in [0,1] mathematically)
-    sp[ns + c] = p;
-    tr[ns + c] = 2.f * p * (1.f - p);
+    float p[4], q[4];
+    gather_pairs(pq, r, k, p, q);
+    const float2 o = cell_pair(k, op_tt(ops, op), p, q);
+    pq[ns + c] = o;
+    tr[ns + c] = 2.f * o.x * o.y;
 }
 
 // Eq. 1 loads: C_load = wire + DFF D caps + sum of the input pin caps of the driven cells
@@ -143,6 +139,10 @@ __global__ void k_gather_u32(const uint32_t *__restrict__ src, const int32_t *__
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) dst[i] = src[idx[i]];
 }
+__global__ void k_sp_user(const float2 *__restrict__ pq, const int32_t *__restrict__ idx, float *dst, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = pq[idx[i]].x;
+}
 __global__ void k_trh_user(const float *__restrict__ tr, const float *__restrict__ beta,
                            const int32_t *__restrict__ idx, float *dst, int64_t n) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -161,13 +161,13 @@ static inline int level_block(int64_t n) {
 
 void launch_init_start(const DevDesign &d, int tr_mode, cudaStream_t s) {
     if (d.n_start == 0) return;
-    k_init_start<<<(unsigned)cdiv(d.n_start, 256), 256, 0, s>>>(d.sp_in, d.tr_in, d.sp, d.tr, d.n_start, tr_mode);
+    k_init_start<<<(unsigned)cdiv(d.n_start, 256), 256, 0, s>>>(d.sp_in, d.tr_in, d.pq, d.tr, d.n_start, tr_mode);
 }
 
 void launch_fwd_level(const DevDesign &d, const OpTable &ops, int32_t c0, int32_t c1, cudaStream_t s) {
     if (c1 <= c0) return;
     int b = level_block(c1 - c0);
-    k_fwd_level<<<(unsigned)cdiv(c1 - c0, b), b, 0, s>>>(d.fanin, d.sp, d.tr, c0, c1, d.n_start, ops);
+    k_fwd_level<<<(unsigned)cdiv(c1 - c0, b), b, 0, s>>>(d.fanin, d.pq, d.tr, c0, c1, d.n_start, ops);
 }
 
 void launch_cload(const DevDesign &d, cudaStream_t s) {
@@ -206,6 +206,9 @@ void launch_gather_f32(const float *src, const int32_t *idx, float *dst, int64_t
 }
 void launch_gather_u32(const uint32_t *src, const int32_t *idx, uint32_t *dst, int64_t n, cudaStream_t s) {
     if (n) k_gather_u32<<<(unsigned)cdiv(n, 256), 256, 0, s>>>(src, idx, dst, n);
+}
+void launch_sp_user(const DevDesign &d, float *dst, cudaStream_t s) {
+    if (d.n_nets) k_sp_user<<<(unsigned)cdiv(d.n_nets, 256), 256, 0, s>>>(d.pq, d.net_of_user, dst, d.n_nets);
 }
 void launch_trh_user(const DevDesign &d, float *dst, cudaStream_t s) {
     if (d.n_nets) k_trh_user<<<(unsigned)cdiv(d.n_nets, 256), 256, 0, s>>>(d.tr, d.beta, d.net_of_user, dst, d.n_nets);

@@ -25,7 +25,8 @@ struct DevDesign {
     float *pincap;             // [n_cells]
     float *cload;              // [n_nets]
     float *sp_in, *tr_in;      // [n_start] staged inputs
-    float *sp, *tr;            // [n_nets] SP and TR_model
+    float2 *pq;                // [n_nets] (P(net=1), P(net=0)); P is the SP
+    float *tr;                 // [n_nets] TR_model (startpoints: input TR in tr_mode 0)
     float *beta, *trh;         // [n_nets] beta and hybrid TR
     uint32_t *toggles, *ones;  // [n_nets]
     float *gnet;               // [n_nets] SP adjoint per net
@@ -52,6 +53,7 @@ void launch_cap_grads(const DevDesign &d, const OpTable &ops, bool hybrid, int t
 void launch_gather_f32(const float *src, const int32_t *idx, float *dst, int64_t n, cudaStream_t s);
 void launch_gather_u32(const uint32_t *src, const int32_t *idx, uint32_t *dst, int64_t n, cudaStream_t s);
 void launch_trh_user(const DevDesign &d, float *dst, cudaStream_t s);
+void launch_sp_user(const DevDesign &d, float *dst, cudaStream_t s);
 
 // backward (kern_bwd.cu)
 void launch_bwd_level(const DevDesign &d, const OpTable &ops, int32_t c0, int32_t c1, int grad_mode, float K,
