@@ -169,7 +169,7 @@ def run_reference(args, rank: int, world: int) -> None:
         beta, trh = o.hybrid(t, tg, T_sample)
         o.power(trh)
         t2 = time.perf_counter()
-        o.backward(s, trh, beta, 1, 0)
+        o.backward(sp, tr, beta, 1, 0)
         t3 = time.perf_counter()
         return (t1 - t0) + (t3 - t2) + (t2 - t1) * (T / T_sample)
 
