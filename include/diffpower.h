@@ -159,8 +159,9 @@ dp_status dp_compile_function(const char *func, uint8_t *ops, int8_t *args, int3
 
 /* ------------------------------ GPU side ------------------------------- */
 
-/* Creates a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
- * to queue work on (NULL: the library creates a private non-blocking stream). */
+/* Creates a context on CUDA device `device`.  `cuda_stream` is the
+ * cudaStream_t to queue work on, used as given: NULL is the device's default
+ * (legacy) stream, which is also PyTorch's default current stream. */
 dp_status dp_create(int device, void *cuda_stream, dp_ctx **out);
 void dp_destroy(dp_ctx *ctx);
 

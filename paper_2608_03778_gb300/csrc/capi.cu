@@ -249,15 +249,8 @@ dp_status dp_create(int device, void *cuda_stream, dp_ctx **out) {
     if (!c) return DP_ENOMEM;
     c->device = device;
     DeviceGuard g(device);
-    if (cuda_stream) {
-        c->stream = static_cast<cudaStream_t>(cuda_stream);
-    } else {
-        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
-            delete c;
-            return DP_ECUDA;
-        }
-        c->own_stream = true;
-    }
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    c->own_stream = false;
     *out = c;
     return DP_OK;
 }
