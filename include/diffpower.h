@@ -231,6 +231,33 @@ dp_status dp_phase_times(dp_design *d, float *ms4);
  * graph plus the output kernels queued after it (0 before the first dp_step). */
 dp_status dp_step_kernels(const dp_design *d, int64_t *kernels);
 
+/* Total switching power K * sum_n alpha_n * C_n with K = 1/2 Vdd^2 f 1e-15 and
+ * alpha_n = tr[n] * (beta ? beta[n] : 1), from caller-owned device arrays
+ * (tr, beta, cload: n binary32 values each; C in fF), written as one double
+ * into the device pointer `watts`, asynchronously on `cuda_stream` (NULL:
+ * the device's default stream).  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory - code running
+ * inside a host framework that owns every device byte through its own pool,
+ * or a service that plans its memory ahead and must not let a cudaMalloc
+ * implicitly synchronise the device and stall the other streams.  It calls no
+ * cudaMalloc, cudaFree or allocating routine: its scratch (one FP64 partial
+ * per 8,192 nets) is a fixed 32 KB array in the library's device memory,
+ * held by every GPU that loads the library until the process exits.
+ * Limits and behaviour:
+ *  - n <= 33,554,432 (4,096 partials); larger n returns DP_EUNSUPPORTED
+ *    before any GPU work.  NULL tr/cload with n > 0, NULL watts, n < 0, a
+ *    bad device or non-positive vdd/fclk return DP_EINVAL.
+ *  - The first call on a device looks up the scratch array's device address
+ *    (with that device made current) and caches it; make that first call
+ *    before any stream capture.
+ *  - Every call shares the scratch and overwrites the partials it reads
+ *    (nothing needs clearing); calls that overlap on the GPU (other streams,
+ *    other threads) race on it and must be serialised by the caller.
+ *  - The summation order is fixed, so results are reproducible.
+ *  - There is no context, so dp_last_error() has no message for this call. */
+dp_status dp_power_noalloc(int device, const float *tr, const float *beta, const float *cload, int64_t n,
+                           double vdd, double fclk, double *watts, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

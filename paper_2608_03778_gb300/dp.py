@@ -93,12 +93,13 @@ _sig("dp_get_nets", [_P, _P, _P, _P, _P, _P, _P, _S])
 _sig("dp_step", [_P, ctypes.POINTER(dp_config), _P, _P, _P, _P, _P, _S])
 _sig("dp_phase_times", [_P, _P])
 _sig("dp_step_kernels", [_P, ctypes.POINTER(ctypes.c_int64)])
+_sig("dp_power_noalloc", [ctypes.c_int, _P, _P, _P, ctypes.c_int64, ctypes.c_double, ctypes.c_double, _P, _P])
 
 EXPORTED = ["dp_config_default", "dp_last_error", "dp_compile", "dp_compiled_free", "dp_compiled_info",
             "dp_compiled_view_get", "dp_compile_function", "dp_create", "dp_destroy", "dp_sync", "dp_design_load",
             "dp_design_upload", "dp_design_free", "dp_design_info", "dp_set_inputs", "dp_set_pincap",
             "dp_propagate", "dp_simulate", "dp_total_power", "dp_backward", "dp_get_nets", "dp_step",
-            "dp_phase_times", "dp_step_kernels"]
+            "dp_phase_times", "dp_step_kernels", "dp_power_noalloc"]
 
 
 def _ptr(x):
@@ -283,3 +284,8 @@ def dp_step_kernels(d) -> int:
     k = ctypes.c_int64()
     _check(_lib.dp_step_kernels(d, ctypes.byref(k)))
     return k.value
+
+
+def dp_power_noalloc(device: int, tr, beta, cload, n: int, vdd: float, fclk: float, watts, stream=None) -> None:
+    """Power reduction that allocates no device memory (all arrays are caller-owned device memory)."""
+    _check(_lib.dp_power_noalloc(device, _ptr(tr), _ptr(beta), _ptr(cload), n, vdd, fclk, _ptr(watts), stream))
