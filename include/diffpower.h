@@ -87,7 +87,9 @@ typedef struct {
                                is multiplied by its beta (Eq. 6);
                             2: hybrid, exact gradient of sum K beta TR C with beta fixed */
     int32_t sim_words;   /* T, 64-bit words per net: 64*T vectors, 64*(T-1) transitions (Eq. 4); 2..4096 */
-    int32_t reserved;    /* must be 0 */
+    int32_t schedule;    /* 0: one persistent cooperative launch per pass with grid-wide level
+                               barriers (falls back to 1 where the grid cannot be co-resident);
+                            1: one launch per level.  Both give bitwise identical results. */
     uint64_t seed;       /* Philox4x32-10 key for the startpoint Markov chains (Sec. III-C) */
 } dp_config;
 
@@ -166,8 +168,15 @@ dp_status dp_create(int device, void *cuda_stream, dp_ctx **out);
 void dp_destroy(dp_ctx *ctx);
 
 /* Waits for all work queued by this context; returns DP_ETIMEOUT if a bounded
- * device wait gave up since the last synchronisation. */
+ * device wait gave up since the last synchronisation (the error word is then
+ * cleared and the context stays usable). */
 dp_status dp_sync(dp_ctx *ctx);
+
+/* Self-test of the bounded device wait: runs a two-block grid barrier that
+ * waits for an arrival that never comes, with a limit of `seconds`; the wait
+ * gives up, and the call returns DP_ETIMEOUT with the context still usable.
+ * No GPU fault is involved. */
+dp_status dp_selftest_wait(dp_ctx *ctx, double seconds);
 
 /* Compiles (as dp_compile) and uploads a netlist; the design keeps its whole
  * graph and per-net state resident in device memory (Sec. III). */

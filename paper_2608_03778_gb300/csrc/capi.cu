@@ -16,6 +16,9 @@ struct dp_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    int sm_count = 0;
+    int clock_khz = 0;
+    int *d_err = nullptr;   // device error word: a bounded wait gave up
     std::string err;
 };
 
@@ -40,6 +43,7 @@ struct dp_design {
     cudaGraphExec_t graph = nullptr;
     dp_config graph_cfg{};
     cudaStream_t cap_stream = nullptr;
+    int grid[3] = {0, 0, 0};   // persistent grids: forward, simulation, backward (0 = per-level launches)
     int64_t graph_kernels = 0;
     int64_t step_kernels = 0;
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -86,6 +90,20 @@ dp_status cuda_err(dp_ctx *c, cudaError_t e, const char *where) {
 
 dp_status launch_check(dp_ctx *c, const char *where) { return cuda_err(c, cudaGetLastError(), where); }
 
+// Reads and clears the device error word (synchronises the stream).
+dp_status check_device_error(dp_ctx *c) {
+    int v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_err(c, e, "device error word");
+    if (v != 0) {
+        cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+        cudaStreamSynchronize(c->stream);
+        return set_err(c, DP_ETIMEOUT, "a bounded device wait gave up (grid barrier timeout)");
+    }
+    return DP_OK;
+}
+
 template <class T>
 dp_status dalloc(dp_design *D, T **p, size_t count) {
     *p = nullptr;
@@ -115,7 +133,7 @@ dp_status check_cfg(dp_ctx *ctx, const dp_config *c) {
     if (c->tr_mode < 0 || c->tr_mode > 1) return set_err(ctx, DP_EINVAL, "tr_mode must be 0 or 1");
     if (c->grad_mode < 0 || c->grad_mode > 2) return set_err(ctx, DP_EINVAL, "grad_mode must be 0, 1 or 2");
     if (c->sim_words < 2 || c->sim_words > 4096) return set_err(ctx, DP_EINVAL, "sim_words must be in [2, 4096]");
-    if (c->reserved != 0) return set_err(ctx, DP_EINVAL, "reserved must be 0");
+    if (c->schedule < 0 || c->schedule > 1) return set_err(ctx, DP_EINVAL, "schedule must be 0 or 1");
     return DP_OK;
 }
 
@@ -166,25 +184,45 @@ void rec(dp_design *D, int i, cudaStream_t s) {
 }
 
 // ---- the phases, queued on stream s (also used under graph capture) ----
-void q_forward(dp_design *D, const dp_config &c, cudaStream_t s) {
-    dp::launch_init_start(D->d, c.tr_mode, s);
-    for (int l = 1; l <= D->d.n_levels; l++) dp::launch_fwd_level(D->d, D->ops, D->lvl_ptr[l - 1], D->lvl_ptr[l], s);
-    dp::launch_power(D->d, false, power_K(c), 0, s);
+bool persistent(const dp_design *D, const dp_config &c, int which) {
+    return c.schedule == 0 && D->grid[which] > 0 && D->d.n_levels > 0;
 }
 
-void q_simulate(dp_design *D, const dp_config &c, cudaStream_t s) {
+// each q_* returns the first launch error (a cooperative launch reports it directly)
+cudaError_t q_forward(dp_design *D, const dp_config &c, cudaStream_t s) {
+    if (persistent(D, c, 0)) {
+        cudaError_t e = dp::launch_fwd_persist(D->d, D->ops, c.tr_mode, D->grid[0], s);
+        if (e != cudaSuccess) return e;
+    } else {
+        dp::launch_init_start(D->d, c.tr_mode, s);
+        for (int l = 1; l <= D->d.n_levels; l++)
+            dp::launch_fwd_level(D->d, D->ops, D->lvl_ptr[l - 1], D->lvl_ptr[l], s);
+    }
+    dp::launch_power(D->d, false, power_K(c), 0, s);
+    return cudaGetLastError();
+}
+
+cudaError_t q_simulate(dp_design *D, const dp_config &c, cudaStream_t s) {
     dp::launch_sim_start(D->d, c.sim_words, c.seed, s);
-    for (int l = 1; l <= D->d.n_levels; l++)
-        dp::launch_sim_level(D->d, D->ops, D->lvl_ptr[l - 1], D->lvl_ptr[l], c.sim_words, s);
+    if (persistent(D, c, 1)) {
+        cudaError_t e = dp::launch_sim_persist(D->d, D->ops, c.sim_words, D->grid[1], s);
+        if (e != cudaSuccess) return e;
+    } else {
+        for (int l = 1; l <= D->d.n_levels; l++)
+            dp::launch_sim_level(D->d, D->ops, D->lvl_ptr[l - 1], D->lvl_ptr[l], c.sim_words, s);
+    }
     dp::launch_hybrid(D->d, c.sim_words, c.beta_min, c.beta_max, s);
     dp::launch_power(D->d, true, power_K(c), 1, s);
+    return cudaGetLastError();
 }
 
-void q_backward(dp_design *D, const dp_config &c, float *gsp, cudaStream_t s) {
+cudaError_t q_backward(dp_design *D, const dp_config &c, float *gsp, cudaStream_t s) {
     const float K = (float)power_K(c);
+    if (persistent(D, c, 2)) return dp::launch_bwd_persist(D->d, D->ops, c.grad_mode, c.tr_mode, K, gsp, D->grid[2], s);
     for (int l = D->d.n_levels; l >= 1; l--)
         dp::launch_bwd_level(D->d, D->ops, D->lvl_ptr[l - 1], D->lvl_ptr[l], c.grad_mode, K, s);
     dp::launch_bwd_start(D->d, c.grad_mode, c.tr_mode, K, gsp, s);
+    return cudaGetLastError();
 }
 
 // gradient outputs (user order) into device pointers, staged when the caller's buffers are host memory
@@ -213,7 +251,8 @@ dp_status q_outputs(dp_design *D, const dp_config &c, float *gsp, float *gtr, fl
     if (e == cudaSuccess && gcl && D->d.n_nets)
         e = cudaMemcpyAsync(gcl, D->st_gcl, sizeof(float) * (size_t)D->d.n_nets, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    return cuda_err(D->ctx, e, "gradient copy");
+    if (e != cudaSuccess) return cuda_err(D->ctx, e, "gradient copy");
+    return check_device_error(D->ctx);
 }
 
 }  // namespace
@@ -230,7 +269,7 @@ void dp_config_default(dp_config *c) {
     c->tr_mode = 0;
     c->grad_mode = 1;
     c->sim_words = 64;
-    c->reserved = 0;
+    c->schedule = 0;
     c->seed = 42;
 }
 
@@ -251,6 +290,15 @@ dp_status dp_create(int device, void *cuda_stream, dp_ctx **out) {
     DeviceGuard g(device);
     c->stream = static_cast<cudaStream_t>(cuda_stream);
     c->own_stream = false;
+    if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->clock_khz, cudaDevAttrClockRate, device) != cudaSuccess ||
+        cudaMalloc((void **)&c->d_err, 4 * sizeof(int)) != cudaSuccess ||
+        cudaMemset(c->d_err, 0, 4 * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        if (c->d_err) cudaFree(c->d_err);
+        delete c;
+        return DP_ECUDA;
+    }
     *out = c;
     return DP_OK;
 }
@@ -258,17 +306,31 @@ dp_status dp_create(int device, void *cuda_stream, dp_ctx **out) {
 void dp_destroy(dp_ctx *c) {
     if (!c) return;
     DeviceGuard g(c->device);
-    if (c->own_stream) {
-        cudaStreamSynchronize(c->stream);
-        cudaStreamDestroy(c->stream);
-    }
+    cudaStreamSynchronize(c->stream);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    if (c->d_err) cudaFree(c->d_err);
     delete c;
 }
 
 dp_status dp_sync(dp_ctx *c) {
     if (!c) return DP_EINVAL;
     DeviceGuard g(c->device);
-    return cuda_err(c, cudaStreamSynchronize(c->stream), "dp_sync");
+    dp_status s = cuda_err(c, cudaStreamSynchronize(c->stream), "dp_sync");
+    return s == DP_OK ? check_device_error(c) : s;
+}
+
+dp_status dp_selftest_wait(dp_ctx *c, double seconds) {
+    if (!c || !(seconds > 0) || seconds > 60) return set_err(c, DP_EINVAL, "seconds must be in (0, 60]");
+    DeviceGuard g(c->device);
+    unsigned *gs = nullptr;
+    cudaError_t e = cudaMalloc((void **)&gs, 128);
+    if (e != cudaSuccess) return cuda_err(c, e, "dp_selftest_wait");
+    const long long limit = (long long)(seconds * (double)c->clock_khz * 1e3);
+    e = dp::launch_wait_selftest(gs, c->d_err, limit, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(gs);
+    if (e != cudaSuccess) return cuda_err(c, e, "dp_selftest_wait");
+    return check_device_error(c);
 }
 
 dp_status dp_design_upload(dp_ctx *ctx, const dp_compiled *cp, dp_design **out) {
@@ -290,7 +352,7 @@ dp_status dp_design_upload(dp_ctx *ctx, const dp_compiled *cp, dp_design **out) 
     const size_t nn = (size_t)d.n_nets, nc = (size_t)d.n_cells, ns = (size_t)d.n_start;
     dp_status s = DP_OK;
     uint4 *fanin = nullptr;
-    int32_t *fptr = nullptr, *fedge = nullptr, *nou = nullptr, *cou = nullptr;
+    int32_t *fptr = nullptr, *fedge = nullptr, *nou = nullptr, *cou = nullptr, *efpos = nullptr, *lvl = nullptr;
     float *base = nullptr;
 #define TRY(x) do { if ((s = (x)) != DP_OK) { free_design(D); return s; } } while (0)
     TRY(dalloc(D, &fanin, nc));
@@ -310,12 +372,18 @@ dp_status dp_design_upload(dp_ctx *ctx, const dp_compiled *cp, dp_design **out) 
     TRY(dalloc(D, &d.toggles, nn));
     TRY(dalloc(D, &d.ones, nn));
     TRY(dalloc(D, &d.gnet, nn));
-    TRY(dalloc(D, &d.gedge, nc));
+    TRY(dalloc(D, &d.gfo, (size_t)cp->n_edges));
+    TRY(dalloc(D, &efpos, 4 * nc));
+    TRY(dalloc(D, &lvl, (size_t)cp->n_levels + 1));
+    TRY(dalloc(D, &d.bar, dp::persist_bar_words(cp->n_levels)));
     TRY(dalloc(D, &d.partials, (size_t)dp::kPowerBlocks));
     TRY(dalloc(D, &d.power, 4));
     d.fanin = fanin;
     d.fout_ptr = fptr;
     d.fout_edge = fedge;
+    d.edge_fpos = efpos;
+    d.lvl = lvl;
+    d.err = ctx->d_err;
     d.net_of_user = nou;
     d.cell_of_user = cou;
     d.base_cap = base;
@@ -327,11 +395,15 @@ dp_status dp_design_upload(dp_ctx *ctx, const dp_compiled *cp, dp_design **out) 
     up(fanin, cp->fanin.data(), sizeof(uint32_t) * cp->fanin.size());
     up(fptr, cp->fout_ptr.data(), sizeof(int32_t) * cp->fout_ptr.size());
     up(fedge, cp->fout_edge.data(), sizeof(int32_t) * cp->fout_edge.size());
+    up(efpos, cp->edge_fpos.data(), sizeof(int32_t) * cp->edge_fpos.size());
+    up(lvl, cp->lvl_ptr.data(), sizeof(int32_t) * cp->lvl_ptr.size());
     up(nou, cp->net_of_user.data(), sizeof(int32_t) * nn);
     up(cou, cp->cell_of_user.data(), sizeof(int32_t) * nc);
     up(base, cp->base_cap.data(), sizeof(float) * nn);
     up(d.pincap, cp->pincap.data(), sizeof(float) * nc);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.power, 0, 4 * sizeof(double), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.bar, 0, sizeof(unsigned) * dp::persist_bar_words(cp->n_levels), st);
+    for (int w = 0; w < 3; w++) D->grid[w] = dp::persist_grid(w, ctx->sm_count);
     if (e != cudaSuccess) { s = cuda_err(ctx, e, "upload"); free_design(D); return s; }
     dp::launch_cload(d, st);
     for (auto &ev : D->ev)
@@ -439,9 +511,9 @@ dp_status dp_propagate(dp_design *D, const dp_config *cfg) {
     DeviceGuard g(D->ctx->device);
     cudaStream_t st = D->ctx->stream;
     rec(D, 0, st);
-    q_forward(D, *cfg, st);
+    cudaError_t le = q_forward(D, *cfg, st);
     rec(D, 1, st);
-    if ((s = launch_check(D->ctx, "dp_propagate")) != DP_OK) return s;
+    if ((s = cuda_err(D->ctx, le, "dp_propagate")) != DP_OK) return s;
     D->fwd_valid = true;
     D->fwd_tr_mode = cfg->tr_mode;
     D->sim_valid = false;
@@ -458,9 +530,9 @@ dp_status dp_simulate(dp_design *D, const dp_config *cfg) {
     if ((s = ensure_words(D, cfg->sim_words)) != DP_OK) return s;
     cudaStream_t st = D->ctx->stream;
     rec(D, 1, st);
-    q_simulate(D, *cfg, st);
+    cudaError_t le = q_simulate(D, *cfg, st);
     rec(D, 2, st);
-    if ((s = launch_check(D->ctx, "dp_simulate")) != DP_OK) return s;
+    if ((s = cuda_err(D->ctx, le, "dp_simulate")) != DP_OK) return s;
     D->sim_valid = true;
     return DP_OK;
 }
@@ -473,7 +545,8 @@ dp_status dp_total_power(dp_design *D, int hybrid, double *watts) {
     cudaError_t e = cudaMemcpyAsync(watts, D->d.power + (hybrid ? 1 : 0), sizeof(double), cudaMemcpyDeviceToHost,
                                     D->ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(D->ctx->stream);
-    return cuda_err(D->ctx, e, "dp_total_power");
+    if (e != cudaSuccess) return cuda_err(D->ctx, e, "dp_total_power");
+    return check_device_error(D->ctx);
 }
 
 dp_status dp_backward(dp_design *D, const dp_config *cfg, float *gsp, float *gtr, float *gpin, float *gcl,
@@ -488,9 +561,9 @@ dp_status dp_backward(dp_design *D, const dp_config *cfg, float *gsp, float *gtr
     DeviceGuard g(D->ctx->device);
     cudaStream_t st = D->ctx->stream;
     rec(D, 2, st);
-    q_backward(D, *cfg, on_device ? gsp : nullptr, st);
+    cudaError_t le = q_backward(D, *cfg, on_device ? gsp : nullptr, st);
     rec(D, 3, st);
-    if ((s = launch_check(D->ctx, "dp_backward")) != DP_OK) return s;
+    if ((s = cuda_err(D->ctx, le, "dp_backward")) != DP_OK) return s;
     s = q_outputs(D, *cfg, gsp, gtr, gpin, gcl, on_device, on_device != 0);
     rec(D, 4, st);
     return s;
@@ -532,7 +605,7 @@ dp_status dp_get_nets(dp_design *D, float *sp, float *tr, float *beta, float *tr
             if (e != cudaSuccess) return cuda_err(c, e, "dp_get_nets");
         }
     }
-    return DP_OK;
+    return on_device ? DP_OK : check_device_error(c);
 }
 
 dp_status dp_step(dp_design *D, const dp_config *cfg, float *gsp, float *gtr, float *gpin, float *gcl, double *watts,
@@ -553,13 +626,14 @@ dp_status dp_step(dp_design *D, const dp_config *cfg, float *gsp, float *gtr, fl
         // external event records become timing nodes of the graph (a plain record
         // inside a capture would only express a dependency)
         cudaEventRecordWithFlags(D->ev[0], cs, cudaEventRecordExternal);
-        q_forward(D, *cfg, cs);
+        cudaError_t le = q_forward(D, *cfg, cs);
         cudaEventRecordWithFlags(D->ev[1], cs, cudaEventRecordExternal);
-        q_simulate(D, *cfg, cs);
+        if (le == cudaSuccess) le = q_simulate(D, *cfg, cs);
         cudaEventRecordWithFlags(D->ev[2], cs, cudaEventRecordExternal);
-        q_backward(D, *cfg, nullptr, cs);
+        if (le == cudaSuccess) le = q_backward(D, *cfg, nullptr, cs);
         cudaEventRecordWithFlags(D->ev[3], cs, cudaEventRecordExternal);
         e = cudaStreamEndCapture(cs, &graph);
+        if (e == cudaSuccess && le != cudaSuccess) e = le;
         D->graph_kernels = 0;
         if (e == cudaSuccess) {
             size_t nn = 0;
@@ -592,6 +666,7 @@ dp_status dp_step(dp_design *D, const dp_config *cfg, float *gsp, float *gtr, fl
         e = cudaMemcpyAsync(watts, D->d.power, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cuda_err(D->ctx, e, "dp_step power");
+        return check_device_error(D->ctx);
     }
     return DP_OK;
 }

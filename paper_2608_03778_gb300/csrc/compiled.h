@@ -35,6 +35,7 @@ struct dp_compiled {
     std::vector<int32_t> lvl_ptr;
     std::vector<uint32_t> fanin;       // 4 per cell
     std::vector<int32_t> fout_ptr, fout_edge;
+    std::vector<int32_t> edge_fpos;    // 4 per cell: position of edge (cell, slot) in fout_edge, -1 unused
     std::vector<int32_t> net_of_user, user_of_net, cell_of_user, user_of_cell;
     std::vector<float> base_cap, pincap;
     uint8_t op_arity[256] = {0};

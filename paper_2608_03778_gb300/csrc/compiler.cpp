@@ -564,12 +564,16 @@ extern "C" dp_status dp_compile(const char *netlist, size_t netlist_len, const c
             }
         for (int64_t n = 0; n < nn; n++) c->fout_ptr[n + 1] += c->fout_ptr[n];
         c->fout_edge.assign((size_t)nedge, 0);
+        c->edge_fpos.assign((size_t)nc * 4, -1);
         {
             std::vector<int32_t> fill(c->fout_ptr.begin(), c->fout_ptr.end() - 1);
             for (int64_t ic = 0; ic < nc; ic++)
                 for (int j = 0; j < dp::kMaxArity; j++) {
                     uint32_t n = c->fanin[ic * 4 + j] & dp::kNetMask;
-                    if (j < c->op_arity[c->fanin[ic * 4] >> 24]) c->fout_edge[fill[n]++] = (int32_t)(ic * 4 + j);
+                    if (j < c->op_arity[c->fanin[ic * 4] >> 24]) {
+                        c->edge_fpos[ic * 4 + j] = fill[n];
+                        c->fout_edge[fill[n]++] = (int32_t)(ic * 4 + j);
+                    }
                 }
         }
     } catch (const std::bad_alloc &) {

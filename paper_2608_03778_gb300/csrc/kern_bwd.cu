@@ -1,11 +1,12 @@
 // Reverse pass (Sec. III-E, Eq. 7; Eq. 6 for the paper's hybrid rule).
 // Nets are visited in reverse level order.  A net's adjoint is the sum of the
 // contributions its fanout cells left on their input edges plus its local
-// term; a cell then writes one contribution per input edge into its own
-// slots.  Every fanout cell of a level-l net sits on a level above l, so the
-// edge contributions are complete when the net is visited: a gather over the
-// transposed fanout CSR replaces atomic scatters, and the result is
-// reproducible bit for bit.
+// term; a cell then writes one contribution per input edge.  Edge
+// contributions are stored in fanout-CSR order (each cell knows the fanout
+// position of its input edges), so a net sums one contiguous range.  Every
+// fanout cell of a level-l net sits on a level above l, so the range is
+// complete when the net is visited: a gather replaces atomic scatters, and
+// the result is reproducible bit for bit.
 #include "kern_common.cuh"
 
 namespace dp {
@@ -13,11 +14,11 @@ namespace {
 
 __host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-__device__ __forceinline__ float fanout_sum(const int32_t *__restrict__ fptr, const int32_t *__restrict__ fedge,
-                                            const float *__restrict__ ge, int64_t n) {
+__device__ __forceinline__ float fanout_sum(const int32_t *__restrict__ fptr, const float *__restrict__ gfo,
+                                            int64_t n) {
     float acc = 0.f;
     const int32_t e1 = fptr[n + 1];
-    for (int32_t e = fptr[n]; e < e1; e++) acc += ge[fedge[e]];
+    for (int32_t e = fptr[n]; e < e1; e++) acc += gfo[e];
     return acc;
 }
 
@@ -29,13 +30,13 @@ __device__ __forceinline__ float combine(int grad_mode, float acc, float local, 
 }
 
 __global__ void k_bwd_level(const uint4 *__restrict__ fanin, const int32_t *__restrict__ fptr,
-                            const int32_t *__restrict__ fedge, const float2 *__restrict__ pq,
+                            const int4 *__restrict__ efpos, const float2 *__restrict__ pq,
                             const float *__restrict__ cload, const float *__restrict__ beta, float *gnet,
-                            float4 *gedge, int32_t c0, int32_t c1, int64_t ns, int grad_mode, float K, OpTable ops) {
+                            float *gfo, int32_t c0, int32_t c1, int64_t ns, int grad_mode, float K, OpTable ops) {
     int32_t c = c0 + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
     if (c >= c1) return;
     const int64_t n = ns + c;
-    const float acc = fanout_sum(fptr, fedge, reinterpret_cast<const float *>(gedge), n);
+    const float acc = fanout_sum(fptr, gfo, n);
     const float2 o = pq[n];
     // local term: d(K C 2P(1-P))/dP = K C (2 - 4P) = 2 K C (Q - P)
     const float g = combine(grad_mode, acc, 2.f * K * cload[n] * (o.y - o.x), beta, n);
@@ -46,16 +47,19 @@ __global__ void k_bwd_level(const uint4 *__restrict__ fanin, const int32_t *__re
     float p[4], q[4], d[4];
     gather_pairs(pq, r, k, p, q);
     cell_partials(k, op_tt(ops, op), p, q, d);
-    gedge[c] = make_float4(g * d[0], g * d[1], g * d[2], g * d[3]);
+    const int4 ep = efpos[c];
+    if (k > 0) gfo[ep.x] = g * d[0];
+    if (k > 1) gfo[ep.y] = g * d[1];
+    if (k > 2) gfo[ep.z] = g * d[2];
+    if (k > 3) gfo[ep.w] = g * d[3];
 }
 
-__global__ void k_bwd_start(const int32_t *__restrict__ fptr, const int32_t *__restrict__ fedge,
-                            const float2 *__restrict__ pq, const float *__restrict__ cload,
-                            const float *__restrict__ beta, float *gnet, const float4 *gedge, int64_t ns,
-                            int grad_mode, int tr_mode, float K, float *out) {
+__global__ void k_bwd_start(const int32_t *__restrict__ fptr, const float2 *__restrict__ pq,
+                            const float *__restrict__ cload, const float *__restrict__ beta, float *gnet,
+                            const float *gfo, int64_t ns, int grad_mode, int tr_mode, float K, float *out) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= ns) return;
-    const float acc = fanout_sum(fptr, fedge, reinterpret_cast<const float *>(gedge), k);
+    const float acc = fanout_sum(fptr, gfo, k);
     // a startpoint has a local SP term only when its TR is derived from its SP (tr_mode 1)
     const float2 o = pq[k];
     const float local = tr_mode ? 2.f * K * cload[k] * (o.y - o.x) : 0.f;
@@ -76,15 +80,16 @@ void launch_bwd_level(const DevDesign &d, const OpTable &ops, int32_t c0, int32_
                       cudaStream_t s) {
     if (c1 <= c0) return;
     int b = level_block(c1 - c0);
-    k_bwd_level<<<(unsigned)cdiv(c1 - c0, b), b, 0, s>>>(d.fanin, d.fout_ptr, d.fout_edge, d.pq, d.cload, d.beta,
-                                                         d.gnet, d.gedge, c0, c1, d.n_start, grad_mode, K, ops);
+    k_bwd_level<<<(unsigned)cdiv(c1 - c0, b), b, 0, s>>>(d.fanin, d.fout_ptr, (const int4 *)d.edge_fpos, d.pq,
+                                                         d.cload, d.beta, d.gnet, d.gfo, c0, c1, d.n_start,
+                                                         grad_mode, K, ops);
 }
 
 void launch_bwd_start(const DevDesign &d, int grad_mode, int tr_mode, float K, float *grad_sp_in, cudaStream_t s) {
     if (d.n_start == 0) return;
     int b = level_block(d.n_start);
-    k_bwd_start<<<(unsigned)cdiv(d.n_start, b), b, 0, s>>>(d.fout_ptr, d.fout_edge, d.pq, d.cload, d.beta, d.gnet,
-                                                           d.gedge, d.n_start, grad_mode, tr_mode, K, grad_sp_in);
+    k_bwd_start<<<(unsigned)cdiv(d.n_start, b), b, 0, s>>>(d.fout_ptr, d.pq, d.cload, d.beta, d.gnet, d.gfo,
+                                                           d.n_start, grad_mode, tr_mode, K, grad_sp_in);
 }
 
 }  // namespace dp

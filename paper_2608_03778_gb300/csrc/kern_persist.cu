@@ -1,0 +1,349 @@
+// Persistent schedule: one cooperative launch per pass (forward, simulation,
+// backward) that walks all levels, with a grid-wide barrier between levels
+// instead of one kernel launch per level.  Every wait is bounded: a block
+// that waits longer than the limit records an error word and returns, the
+// others see the word and return too, and the host reports DP_ETIMEOUT.
+//
+// Data written by other blocks during the launch is read through L2
+// (ld.global.cg); the barrier's release/acquire pair orders it.  Static data
+// of the next level (fanin records, fanout ranges, forward results) is loaded
+// before a block waits at the barrier, so the wait hides its latency.
+#include "kern_common.cuh"
+
+namespace dp {
+namespace {
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Level barrier over all blocks of the grid.  Each barrier of a launch has
+// its own arrival counter (own 128-byte line, zeroed before the launch):
+// thread 0 of every block arrives with a release reduction (no round trip)
+// and polls the counter with acquire loads until every block has arrived.
+// Returns false, identically in every thread of the block, when the wait
+// gave up (limit reached, or another block reported an error).
+__device__ bool level_barrier(unsigned *ctr, int *err, unsigned nblocks, long long limit) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(ctr) : "memory");
+        const long long t0 = clock64();
+        unsigned spins = 0;
+        while (ld_acquire_u32(ctr) < nblocks) {
+            if ((++spins & 255u) == 0) {
+                if (ld_relaxed_u32(reinterpret_cast<unsigned *>(err)) != 0) { ok = 0; break; }
+                if (clock64() - t0 > limit) {
+                    atomicExch(err, 1);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// thread index that spreads consecutive 32-element groups over all blocks
+// (and so over all SMs) before giving any block a second warp of work
+__device__ __forceinline__ int64_t spread_tid() {
+    return ((int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x) * 32 + (threadIdx.x & 31);
+}
+__device__ __forceinline__ int64_t spread_warp() { return (int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x; }
+
+__device__ __forceinline__ void gather_pairs_l2(const float2 *pq, const uint4 &r, int k, float (&p)[4],
+                                                float (&q)[4]) {
+    const uint32_t n[4] = {r.x & kMask24, r.y, r.z, r.w};
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        p[j] = 0.f;
+        q[j] = 1.f;
+        if (j < k) {
+            const float2 v = __ldcg(pq + n[j]);
+            p[j] = v.x;
+            q[j] = v.y;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- forward
+__device__ __forceinline__ void fwd_cell(const uint4 &r, int64_t c, float2 *pq, float *tr, int64_t ns,
+                                         const OpTable &ops) {
+    const uint32_t op = r.x >> 24;
+    const int k = op_arity(ops, op);
+    float p[4], q[4];
+    gather_pairs_l2(pq, r, k, p, q);
+    const float2 o = cell_pair(k, op_tt(ops, op), p, q);
+    pq[ns + c] = o;
+    tr[ns + c] = 2.f * o.x * o.y;
+}
+
+__global__ void __launch_bounds__(kPersistThreads) k_fwd_persist(
+    const uint4 *__restrict__ fanin, float2 *pq, float *tr, const float *__restrict__ sp_in,
+    const float *__restrict__ tr_in, const int32_t *__restrict__ lvl, int L, int64_t ns, int tr_mode, OpTable ops,
+    unsigned *bar, int *err, long long limit) {
+    const int64_t tid = spread_tid();
+    const int64_t T = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = tid; k < ns; k += T) {
+        const float p = sp_in[k], q = 1.f - p;
+        pq[k] = make_float2(p, q);
+        tr[k] = tr_mode ? 2.f * p * q : tr_in[k];
+    }
+    for (int l = 1; l <= L; l++) {
+        const int32_t c0 = lvl[l - 1], c1 = lvl[l];
+        const int64_t c = c0 + tid;
+        uint4 r = make_uint4(0, 0, 0, 0);
+        if (c < c1) r = fanin[c];   // static: loaded before the wait
+        if (!level_barrier(bar + 32 * (l - 1), err, gridDim.x, limit)) return;
+        if (c < c1) fwd_cell(r, c, pq, tr, ns, ops);
+        for (int64_t cc = c + T; cc < c1; cc += T) fwd_cell(fanin[cc], cc, pq, tr, ns, ops);
+    }
+}
+
+// --------------------------------------------------------------- backward
+__device__ __forceinline__ float combine(int grad_mode, float acc, float local, float b) {
+    if (grad_mode == 1) return b * (acc + local);
+    if (grad_mode == 2) return acc + b * local;
+    return acc + local;
+}
+
+// everything the adjoint of one cell needs except its fanout contributions
+struct BwdStatic {
+    int32_t e0, e1;
+    int4 ep;
+    float local, b;
+    float d[4];
+    int k;
+};
+
+__device__ __forceinline__ BwdStatic bwd_static(const uint4 *fanin, const int32_t *fptr, const int4 *efpos,
+                                                const float2 *pq, const float *cload, const float *beta, int64_t c,
+                                                int64_t ns, int grad_mode, float K, const OpTable &ops) {
+    BwdStatic s;
+    const int64_t n = ns + c;
+    const uint4 r = fanin[c];
+    s.ep = efpos[c];
+    s.e0 = fptr[n];
+    s.e1 = fptr[n + 1];
+    const float2 o = pq[n];
+    // local term: d(K C 2P(1-P))/dP = 2 K C (Q - P)
+    s.local = 2.f * K * cload[n] * (o.y - o.x);
+    s.b = grad_mode ? beta[n] : 1.f;
+    const uint32_t op = r.x >> 24;
+    s.k = op_arity(ops, op);
+    float p[4], q[4];
+    gather_pairs(pq, r, s.k, p, q);
+    cell_partials(s.k, op_tt(ops, op), p, q, s.d);
+    return s;
+}
+
+__device__ __forceinline__ void bwd_finish(const BwdStatic &s, int64_t n, float *gnet, float *gfo, int grad_mode) {
+    float acc = 0.f;
+    for (int32_t e = s.e0; e < s.e1; e++) acc += __ldcg(gfo + e);
+    const float g = combine(grad_mode, acc, s.local, s.b);
+    gnet[n] = g;
+    if (s.k > 0) gfo[s.ep.x] = g * s.d[0];
+    if (s.k > 1) gfo[s.ep.y] = g * s.d[1];
+    if (s.k > 2) gfo[s.ep.z] = g * s.d[2];
+    if (s.k > 3) gfo[s.ep.w] = g * s.d[3];
+}
+
+__global__ void __launch_bounds__(kPersistThreads) k_bwd_persist(
+    const uint4 *__restrict__ fanin, const int32_t *__restrict__ fptr, const int4 *__restrict__ efpos,
+    const float2 *__restrict__ pq, const float *__restrict__ cload, const float *__restrict__ beta, float *gnet,
+    float *gfo, const int32_t *__restrict__ lvl, int L, int64_t ns, int grad_mode, int tr_mode, float K,
+    float *out_gsp, OpTable ops, unsigned *bar, int *err, long long limit) {
+    const int64_t tid = spread_tid();
+    const int64_t T = (int64_t)gridDim.x * blockDim.x;
+    for (int l = L; l >= 1; l--) {
+        const int32_t c0 = lvl[l - 1], c1 = lvl[l];
+        const int64_t c = c0 + tid;
+        BwdStatic s;
+        if (c < c1) s = bwd_static(fanin, fptr, efpos, pq, cload, beta, c, ns, grad_mode, K, ops);
+        // the top level has no fanout inside the pass: no wait before it
+        if (l < L && !level_barrier(bar + 32 * (L - 1 - l), err, gridDim.x, limit)) return;
+        if (c < c1) bwd_finish(s, ns + c, gnet, gfo, grad_mode);
+        for (int64_t cc = c + T; cc < c1; cc += T)
+            bwd_finish(bwd_static(fanin, fptr, efpos, pq, cload, beta, cc, ns, grad_mode, K, ops), ns + cc, gnet,
+                       gfo, grad_mode);
+    }
+    if (!level_barrier(bar + 32 * (L - 1), err, gridDim.x, limit)) return;
+    for (int64_t k = tid; k < ns; k += T) {
+        float acc = 0.f;
+        const int32_t e1 = fptr[k + 1];
+        for (int32_t e = fptr[k]; e < e1; e++) acc += __ldcg(gfo + e);
+        const float2 o = pq[k];
+        const float local = tr_mode ? 2.f * K * cload[k] * (o.y - o.x) : 0.f;
+        const float g = combine(grad_mode, acc, local, grad_mode ? beta[k] : 1.f);
+        gnet[k] = g;
+        if (out_gsp) out_gsp[k] = g;
+    }
+}
+
+// ------------------------------------------------------------- simulation
+// One warp per cell.  Chunks of 64 words: lane l evaluates words 2l and
+// 2l + 1 (one 16-byte load per fanin when T is even, two 8-byte loads
+// otherwise), counts ones, and counts toggles against the previous word
+// (its own first word, or the last word of the neighbour lane / chunk).
+__device__ __forceinline__ void sim_cell(const uint4 &r, int64_t c, uint64_t *words, uint32_t *toggles,
+                                         uint32_t *ones, int64_t ns, int T, const OpTable &ops, int lane) {
+    const uint32_t op = r.x >> 24;
+    const int k = op_arity(ops, op);
+    const uint32_t tt = op_tt(ops, op);
+    const uint64_t *in[4] = {words, words, words, words};
+    if (k > 0) in[0] = words + (size_t)(r.x & kMask24) * T;
+    if (k > 1) in[1] = words + (size_t)r.y * T;
+    if (k > 2) in[2] = words + (size_t)r.z * T;
+    if (k > 3) in[3] = words + (size_t)r.w * T;
+    uint64_t *out = words + (size_t)(ns + c) * T;
+    const bool even = (T & 1) == 0;
+    uint32_t tg = 0, on = 0;
+    uint64_t carry = 0;
+    for (int base = 0; base < T; base += 64) {
+        const int t0 = base + 2 * lane, t1 = t0 + 1;
+        uint64_t x0[4] = {0, 0, 0, 0}, x1[4] = {0, 0, 0, 0};
+        if (even && t1 < T) {
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+                if (j < k) {
+                    const ulonglong2 v = __ldcg(reinterpret_cast<const ulonglong2 *>(in[j] + t0));
+                    x0[j] = v.x;
+                    x1[j] = v.y;
+                }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+                if (j < k) {
+                    if (t0 < T) x0[j] = __ldcg(in[j] + t0);
+                    if (t1 < T) x1[j] = __ldcg(in[j] + t1);
+                }
+        }
+        const uint64_t w0 = cell_bits(k, tt, x0);
+        const uint64_t w1 = cell_bits(k, tt, x1);
+        uint64_t prev = __shfl_up_sync(0xFFFFFFFFu, w1, 1);
+        if (lane == 0) prev = carry;
+        if (even && t1 < T) {
+            *reinterpret_cast<ulonglong2 *>(out + t0) = make_ulonglong2(w0, w1);
+        } else {
+            if (t0 < T) out[t0] = w0;
+            if (t1 < T) out[t1] = w1;
+        }
+        if (t0 < T) {
+            on += __popcll(w0);
+            if (t0 > 0) tg += __popcll(w0 ^ prev);
+        }
+        if (t1 < T) {
+            on += __popcll(w1);
+            tg += __popcll(w1 ^ w0);
+        }
+        carry = __shfl_sync(0xFFFFFFFFu, w1, 31);
+    }
+    tg = __reduce_add_sync(0xFFFFFFFFu, tg);
+    on = __reduce_add_sync(0xFFFFFFFFu, on);
+    if (lane == 0) {
+        toggles[ns + c] = tg;
+        ones[ns + c] = on;
+    }
+}
+
+__global__ void __launch_bounds__(kSimThreads) k_sim_persist(const uint4 *__restrict__ fanin, uint64_t *words,
+                                                             uint32_t *toggles, uint32_t *ones,
+                                                             const int32_t *__restrict__ lvl, int L, int64_t ns,
+                                                             int T, OpTable ops, unsigned *bar, int *err,
+                                                             long long limit) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = spread_warp();
+    const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int l = 1; l <= L; l++) {
+        const int32_t c0 = lvl[l - 1], c1 = lvl[l];
+        const int64_t c = c0 + gw;
+        uint4 r = make_uint4(0, 0, 0, 0);
+        if (c < c1) r = fanin[c];
+        // level 1 reads only startpoint words, written by the previous launch
+        if (l > 1 && !level_barrier(bar + 32 * (l - 2), err, gridDim.x, limit)) return;
+        if (c < c1) sim_cell(r, c, words, toggles, ones, ns, T, ops, lane);
+        for (int64_t cc = c + W; cc < c1; cc += W) sim_cell(fanin[cc], cc, words, toggles, ones, ns, T, ops, lane);
+    }
+}
+
+// self-test of the bounded wait: the barrier expects one arrival more than
+// the grid has blocks, so it can only end by giving up
+__global__ void k_wait_selftest(unsigned *bar, int *err, long long limit) {
+    level_barrier(bar, err, gridDim.x + 1, limit);
+}
+
+template <class... Args>
+cudaError_t launch_coop(void (*kern)(Args...), int grid, int block, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+size_t bar_bytes(const DevDesign &d) { return sizeof(unsigned) * 32 * ((size_t)d.n_levels + 2); }
+
+}  // namespace
+
+int persist_grid(int which, int sm_count) {
+    int per = 0;
+    cudaError_t e;
+    if (which == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fwd_persist, kPersistThreads, 0);
+    else if (which == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sim_persist, kSimThreads, 0);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bwd_persist, kPersistThreads, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    const int cap = which == 1 ? 2 : 1;   // blocks per SM used: enough warps, few barrier arrivals
+    return sm_count * (per < cap ? per : cap);
+}
+
+size_t persist_bar_words(int n_levels) { return 3 * 32 * ((size_t)n_levels + 2); }
+
+cudaError_t launch_fwd_persist(const DevDesign &d, const OpTable &ops, int tr_mode, int grid, cudaStream_t s) {
+    unsigned *bar = d.bar;
+    cudaMemsetAsync(bar, 0, bar_bytes(d), s);
+    return launch_coop(k_fwd_persist, grid, kPersistThreads, s, d.fanin, d.pq, d.tr, (const float *)d.sp_in,
+                       (const float *)d.tr_in, d.lvl, d.n_levels, d.n_start, tr_mode, ops, bar, d.err,
+                       kWaitLimitCycles);
+}
+
+cudaError_t launch_sim_persist(const DevDesign &d, const OpTable &ops, int T, int grid, cudaStream_t s) {
+    unsigned *bar = d.bar + 32 * ((size_t)d.n_levels + 2);
+    cudaMemsetAsync(bar, 0, bar_bytes(d), s);
+    return launch_coop(k_sim_persist, grid, kSimThreads, s, d.fanin, d.words, d.toggles, d.ones, d.lvl, d.n_levels,
+                       d.n_start, T, ops, bar, d.err, kWaitLimitCycles);
+}
+
+cudaError_t launch_bwd_persist(const DevDesign &d, const OpTable &ops, int grad_mode, int tr_mode, float K,
+                               float *out_gsp, int grid, cudaStream_t s) {
+    unsigned *bar = d.bar + 2 * 32 * ((size_t)d.n_levels + 2);
+    cudaMemsetAsync(bar, 0, bar_bytes(d), s);
+    return launch_coop(k_bwd_persist, grid, kPersistThreads, s, d.fanin, d.fout_ptr, (const int4 *)d.edge_fpos,
+                       (const float2 *)d.pq, (const float *)d.cload, (const float *)d.beta, d.gnet, d.gfo, d.lvl,
+                       d.n_levels, d.n_start, grad_mode, tr_mode, K, out_gsp, ops, bar, d.err, kWaitLimitCycles);
+}
+
+cudaError_t launch_wait_selftest(unsigned *bar, int *err, long long limit, cudaStream_t s) {
+    cudaMemsetAsync(bar, 0, 128, s);
+    return launch_coop(k_wait_selftest, 2, 32, s, bar, err, limit);
+}
+
+}  // namespace dp

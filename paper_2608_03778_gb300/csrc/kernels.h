@@ -12,6 +12,11 @@ struct OpTable {
     uint32_t e[256];
 };
 
+constexpr int kPersistThreads = 512;
+constexpr int kSimThreads = 512;
+// bounded waits give up after this many SM cycles (about 2 s at 2 GHz)
+constexpr long long kWaitLimitCycles = 4000000000LL;
+
 // Device-resident design state; every pointer is device memory.
 struct DevDesign {
     int64_t n_nets, n_start, n_cells;
@@ -19,6 +24,8 @@ struct DevDesign {
     const uint4 *fanin;        // [n_cells]: 4 internal net ids, logic id in bits 24..31 of .x
     const int32_t *fout_ptr;   // [n_nets+1]
     const int32_t *fout_edge;  // [n_edges]: 4*cell + slot
+    const int32_t *edge_fpos;  // [4*n_cells]: position of edge (cell, slot) in the fanout CSR, -1 unused
+    const int32_t *lvl;        // [n_levels+1] level boundaries over internal cells
     const int32_t *net_of_user;
     const int32_t *cell_of_user;
     const float *base_cap;     // wire + DFF D pin caps
@@ -30,11 +37,12 @@ struct DevDesign {
     float *beta, *trh;         // [n_nets] beta and hybrid TR
     uint32_t *toggles, *ones;  // [n_nets]
     float *gnet;               // [n_nets] SP adjoint per net
-    float4 *gedge;             // [n_cells]: adjoint contribution of each fanin edge
+    float *gfo;                // [n_edges] adjoint contribution of each edge, in fanout-CSR order
     uint64_t *words;           // [n_nets * T]
     double *partials;          // [2 * power_blocks]
     double *power;             // [4]: model, hybrid
-    float *stage;              // output staging, n_nets floats
+    unsigned *bar;             // level-barrier arrival counters of the persistent passes (128-byte lines)
+    int *err;                  // device error word of the context (bounded wait gave up)
 };
 
 constexpr int kPowerBlocks = 304;   // fixed grid of the power reduction -> deterministic order
@@ -59,6 +67,15 @@ void launch_sp_user(const DevDesign &d, float *dst, cudaStream_t s);
 void launch_bwd_level(const DevDesign &d, const OpTable &ops, int32_t c0, int32_t c1, int grad_mode, float K,
                       cudaStream_t s);
 void launch_bwd_start(const DevDesign &d, int grad_mode, int tr_mode, float K, float *grad_sp_in, cudaStream_t s);
+
+// persistent schedule (kern_persist.cu): one cooperative launch per pass
+int persist_grid(int which, int sm_count);   // which: 0 forward, 1 simulation, 2 backward; 0 = unavailable
+size_t persist_bar_words(int n_levels);      // counters needed by the three passes
+cudaError_t launch_fwd_persist(const DevDesign &d, const OpTable &ops, int tr_mode, int grid, cudaStream_t s);
+cudaError_t launch_sim_persist(const DevDesign &d, const OpTable &ops, int T, int grid, cudaStream_t s);
+cudaError_t launch_bwd_persist(const DevDesign &d, const OpTable &ops, int grad_mode, int tr_mode, float K,
+                               float *out_gsp, int grid, cudaStream_t s);
+cudaError_t launch_wait_selftest(unsigned *bar, int *err, long long limit, cudaStream_t s);
 
 // simulation (kern_sim.cu)
 void launch_sim_start(const DevDesign &d, int T, uint64_t seed, cudaStream_t s);

@@ -35,7 +35,7 @@ class DPError(RuntimeError):
 class dp_config(ctypes.Structure):
     _fields_ = [("vdd", ctypes.c_double), ("fclk", ctypes.c_double), ("beta_min", ctypes.c_float),
                 ("beta_max", ctypes.c_float), ("tr_mode", ctypes.c_int32), ("grad_mode", ctypes.c_int32),
-                ("sim_words", ctypes.c_int32), ("reserved", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+                ("sim_words", ctypes.c_int32), ("schedule", ctypes.c_int32), ("seed", ctypes.c_uint64)]
 
 
 class dp_info(ctypes.Structure):
@@ -79,6 +79,7 @@ _sig("dp_compile_function", [ctypes.c_char_p, _P, _P, ctypes.c_int32, ctypes.POI
 _sig("dp_create", [ctypes.c_int, _P, ctypes.POINTER(_P)])
 _sig("dp_destroy", [_P], None)
 _sig("dp_sync", [_P])
+_sig("dp_selftest_wait", [_P, ctypes.c_double])
 _sig("dp_design_load", [_P, ctypes.c_char_p, ctypes.c_size_t, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(_P)])
 _sig("dp_design_upload", [_P, _P, ctypes.POINTER(_P)])
 _sig("dp_design_free", [_P], None)
@@ -99,7 +100,7 @@ EXPORTED = ["dp_config_default", "dp_last_error", "dp_compile", "dp_compiled_fre
             "dp_compiled_view_get", "dp_compile_function", "dp_create", "dp_destroy", "dp_sync", "dp_design_load",
             "dp_design_upload", "dp_design_free", "dp_design_info", "dp_set_inputs", "dp_set_pincap",
             "dp_propagate", "dp_simulate", "dp_total_power", "dp_backward", "dp_get_nets", "dp_step",
-            "dp_phase_times", "dp_step_kernels", "dp_power_noalloc"]
+            "dp_phase_times", "dp_step_kernels", "dp_power_noalloc", "dp_selftest_wait"]
 
 
 def _ptr(x):
@@ -209,6 +210,10 @@ def dp_destroy(ctx) -> None:
 
 def dp_sync(ctx) -> None:
     _check(_lib.dp_sync(ctx), ctx)
+
+
+def dp_selftest_wait(ctx, seconds: float) -> None:
+    _check(_lib.dp_selftest_wait(ctx, seconds), ctx)
 
 
 def dp_design_load(ctx, netlist: str, library: str):

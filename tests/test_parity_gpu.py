@@ -110,13 +110,14 @@ def check_against_oracle(o, g, sp_in, tr_in, cfg):
     return ref
 
 
+@pytest.mark.parametrize("schedule", [0, 1])
 @pytest.mark.parametrize("grad_mode", [0, 1, 2])
 @pytest.mark.parametrize("tr_mode", [0, 1])
-def test_small_all_modes(dp, ctx, library_text, grad_mode, tr_mode):
+def test_small_all_modes(dp, ctx, library_text, grad_mode, tr_mode, schedule):
     text = netgen.netlist_text(netgen.WORKLOADS["small"])
     o = Oracle(text, library_text)
     sp, tr = netgen.scenario_inputs(o.n_start, 1000)
-    cfg = dp.config(grad_mode=grad_mode, tr_mode=tr_mode)
+    cfg = dp.config(grad_mode=grad_mode, tr_mode=tr_mode, schedule=schedule)
     g = gpu_run(dp, ctx, text, library_text, sp[:, 0], tr[:, 0], cfg)
     check_against_oracle(o, g, sp[:, 0], tr[:, 0], cfg)
 
@@ -141,12 +142,13 @@ def test_roofline_full_size(dp, ctx, library_text):
     check_against_oracle(o, g, sp[:, 0], tr[:, 0], cfg)
 
 
-def test_step_is_deterministic(dp, ctx, library_text):
+@pytest.mark.parametrize("other_schedule", [0, 1])
+def test_step_is_deterministic(dp, ctx, library_text, other_schedule):
+    """Two runs, and the persistent and per-level schedules, agree bit for bit."""
     text = netgen.netlist_text(netgen.WORKLOADS["mid"])
     sp, tr = netgen.scenario_inputs(netgen.WORKLOADS["mid"].n_start, 1000)
-    cfg = dp.config()
-    a = gpu_run(dp, ctx, text, library_text, sp[:, 0], tr[:, 0], cfg, use_step=True)
-    b = gpu_run(dp, ctx, text, library_text, sp[:, 0], tr[:, 0], cfg, use_step=True)
+    a = gpu_run(dp, ctx, text, library_text, sp[:, 0], tr[:, 0], dp.config(), use_step=True)
+    b = gpu_run(dp, ctx, text, library_text, sp[:, 0], tr[:, 0], dp.config(schedule=other_schedule), use_step=True)
     for k in ["sp", "tr", "beta", "toggles", "grad_sp_in", "grad_pincap", "grad_cload", "grad_tr_in"]:
         np.testing.assert_array_equal(a[k], b[k])
     assert a["power_model"] == b["power_model"] and a["power_hybrid"] == b["power_hybrid"]
@@ -276,7 +278,7 @@ def test_call_order_and_argument_errors(dp, ctx, library_text):
             dp.dp_simulate(ctx, d, cfg)
         assert e.value.name == "DP_ESTATE"
         for bad_cfg in [dp.config(sim_words=1), dp.config(grad_mode=3), dp.config(beta_min=0.0),
-                        dp.config(vdd=-1.0), dp.config(reserved=1)]:
+                        dp.config(vdd=-1.0), dp.config(schedule=2)]:
             with pytest.raises(dp.DPError) as e:
                 dp.dp_propagate(ctx, d, bad_cfg)
             assert e.value.name == "DP_EINVAL"
@@ -289,6 +291,21 @@ def test_call_order_and_argument_errors(dp, ctx, library_text):
         assert e.value.name == "DP_EINVAL"
     finally:
         dp.dp_design_free(d)
+
+
+def test_bounded_wait_gives_up(dp, ctx, library_text):
+    """A grid barrier whose last arrival never comes gives up after its limit: DP_ETIMEOUT,
+    and the context keeps working (no GPU fault is involved)."""
+    with pytest.raises(dp.DPError) as e:
+        dp.dp_selftest_wait(ctx, 0.05)
+    assert e.value.name == "DP_ETIMEOUT"
+    dp.dp_sync(ctx)   # the error word was cleared
+    text = netgen.netlist_text(netgen.WORKLOADS["small"])
+    o = Oracle(text, library_text)
+    sp, tr = netgen.scenario_inputs(o.n_start, 1000)
+    cfg = dp.config()
+    g = gpu_run(dp, ctx, text, library_text, sp[:, 0], tr[:, 0], cfg, use_step=True)
+    check_against_oracle(o, g, sp[:, 0], tr[:, 0], cfg)
 
 
 def test_injected_allocation_failure(dp):
