@@ -28,8 +28,9 @@
  *     multiplied by its beta, Eq. 6); 2 = exact gradient of the hybrid power
  *     with beta held fixed.
  *   - Simulation: bit b of word t is lane b at cycle t; 64 independent Markov
- *     chains per startpoint; Philox4x32-10 counter (stream, t, b mod 16, 0),
- *     output component b / 16; thresholds floor(p * 2^32) in binary64.
+ *     chains per startpoint; Philox4x32-10 counter (stream, t / 2, b mod 16, 0),
+ *     output component b / 16, whose low 16 bits drive even cycles and high
+ *     16 bits odd cycles; thresholds floor(p * 2^16) in binary64.
  *   - beta when TR_model = 0: 1 if TR_acc = 0, else beta_max.
  *
  * Pins (what fixes each function independently of itself) are in the tests:
@@ -691,10 +692,11 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
     out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
 }
 
-static uint64_t thr(double p) {
+/* a 16-bit draw u is below the threshold with probability thr(p) / 2^16 */
+static uint32_t thr(double p) {
     if (!(p > 0.0)) return 0;
-    if (p >= 1.0) return 4294967296ull;
-    return (uint64_t)floor(p * 4294967296.0);
+    if (p >= 1.0) return 65536u;
+    return (uint32_t)floor(p * 65536.0);
 }
 
 static int popc64(uint64_t x) { int c = 0; while (x) { x &= x - 1; c++; } return c; }
@@ -715,15 +717,19 @@ int orc_simulate(const void *h, const float *sp_in, const float *tr_in, uint64_t
         double sp = (double)sp_in[k], tr = (double)tr_in[k];
         double p10 = sp > 0.0 ? tr / (2.0 * sp) : 0.0;
         double p01 = sp < 1.0 ? tr / (2.0 * (1.0 - sp)) : 0.0;
-        uint64_t t_init = thr(sp), t10 = thr(p10), t01 = thr(p01);
+        uint32_t t_init = thr(sp), t10 = thr(p10), t01 = thr(p01);
         for (int q = 0; q < 16; q++) {
             int bit[4] = {0, 0, 0, 0};
+            uint32_t u[4] = {0, 0, 0, 0};
             for (int t = 0; t < T; t++) {
-                uint32_t ctr[4] = {(uint32_t)k, (uint32_t)t, (uint32_t)q, 0u}, u[4];
-                orc_philox4x32_10(ctr, key, u);
+                if ((t & 1) == 0) {
+                    uint32_t ctr[4] = {(uint32_t)k, (uint32_t)(t / 2), (uint32_t)q, 0u};
+                    orc_philox4x32_10(ctr, key, u);
+                }
                 for (int r = 0; r < 4; r++) {
-                    if (t == 0) bit[r] = (uint64_t)u[r] < t_init;
-                    else if ((uint64_t)u[r] < (bit[r] ? t10 : t01)) bit[r] ^= 1;
+                    uint32_t d = (t & 1) ? (u[r] >> 16) : (u[r] & 0xFFFFu);
+                    if (t == 0) bit[r] = d < t_init;
+                    else if (d < (bit[r] ? t10 : t01)) bit[r] ^= 1;
                     if (bit[r]) wk[t] |= 1ull << (16 * r + q);
                 }
             }
