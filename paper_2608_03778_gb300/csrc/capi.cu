@@ -42,7 +42,8 @@ struct dp_design {
     // graph of the whole step for one config
     cudaGraphExec_t graph = nullptr;
     dp_config graph_cfg{};
-    cudaStream_t cap_stream = nullptr;
+    cudaStream_t cap_stream = nullptr, cap_stream2 = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
     int grid[3] = {0, 0, 0};   // persistent grids: forward, simulation, backward (0 = per-level launches)
     int64_t graph_kernels = 0;
     int64_t step_kernels = 0;
@@ -143,6 +144,9 @@ void free_design(dp_design *D) {
     if (D->ctx) cudaStreamSynchronize(D->ctx->stream);
     if (D->graph) cudaGraphExecDestroy(D->graph);
     if (D->cap_stream) cudaStreamDestroy(D->cap_stream);
+    if (D->cap_stream2) cudaStreamDestroy(D->cap_stream2);
+    if (D->fork) cudaEventDestroy(D->fork);
+    if (D->join) cudaEventDestroy(D->join);
     for (auto &e : D->ev)
         if (e) cudaEventDestroy(e);
     for (void *p : D->allocs) cudaFree(p);
@@ -202,8 +206,13 @@ cudaError_t q_forward(dp_design *D, const dp_config &c, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t q_simulate(dp_design *D, const dp_config &c, cudaStream_t s) {
+// the startpoint generator alone (needs only the inputs, not the forward pass)
+void q_sim_start(dp_design *D, const dp_config &c, cudaStream_t s) {
     dp::launch_sim_start(D->d, c.sim_words, c.seed, s);
+}
+
+// the simulation levels, beta and the hybrid power (after the generator and the forward pass)
+cudaError_t q_sim_levels(dp_design *D, const dp_config &c, cudaStream_t s) {
     if (persistent(D, c, 1)) {
         cudaError_t e = dp::launch_sim_persist(D->d, D->ops, c.sim_words, D->grid[1], s);
         if (e != cudaSuccess) return e;
@@ -211,9 +220,14 @@ cudaError_t q_simulate(dp_design *D, const dp_config &c, cudaStream_t s) {
         for (int l = 1; l <= D->d.n_levels; l++)
             dp::launch_sim_level(D->d, D->ops, D->lvl_ptr[l - 1], D->lvl_ptr[l], c.sim_words, s);
     }
-    dp::launch_hybrid(D->d, c.sim_words, c.beta_min, c.beta_max, s);
+    dp::launch_hybrid(D->d, c.sim_words, c.tr_mode, c.beta_min, c.beta_max, s);
     dp::launch_power(D->d, true, power_K(c), 1, s);
     return cudaGetLastError();
+}
+
+cudaError_t q_simulate(dp_design *D, const dp_config &c, cudaStream_t s) {
+    q_sim_start(D, c, s);
+    return q_sim_levels(D, c, s);
 }
 
 cudaError_t q_backward(dp_design *D, const dp_config &c, float *gsp, cudaStream_t s) {
@@ -409,6 +423,9 @@ dp_status dp_design_upload(dp_ctx *ctx, const dp_compiled *cp, dp_design **out) 
     for (auto &ev : D->ev)
         if (e == cudaSuccess) e = cudaEventCreate(&ev);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&D->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&D->cap_stream2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&D->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&D->join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) { s = cuda_err(ctx, e, "upload"); free_design(D); return s; }
@@ -624,11 +641,18 @@ dp_status dp_step(dp_design *D, const dp_config *cfg, float *gsp, float *gtr, fl
         cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_err(D->ctx, e, "graph capture");
         // external event records become timing nodes of the graph (a plain record
-        // inside a capture would only express a dependency)
+        // inside a capture only expresses a dependency).  The startpoint generator
+        // (ALU-bound) runs on a second branch, concurrently with the forward pass
+        // (latency-bound); the simulation levels wait for both.
         cudaEventRecordWithFlags(D->ev[0], cs, cudaEventRecordExternal);
+        cudaEventRecord(D->fork, cs);
+        cudaStreamWaitEvent(D->cap_stream2, D->fork, 0);
         cudaError_t le = q_forward(D, *cfg, cs);
         cudaEventRecordWithFlags(D->ev[1], cs, cudaEventRecordExternal);
-        if (le == cudaSuccess) le = q_simulate(D, *cfg, cs);
+        q_sim_start(D, *cfg, D->cap_stream2);
+        cudaEventRecord(D->join, D->cap_stream2);
+        cudaStreamWaitEvent(cs, D->join, 0);
+        if (le == cudaSuccess) le = q_sim_levels(D, *cfg, cs);
         cudaEventRecordWithFlags(D->ev[2], cs, cudaEventRecordExternal);
         if (le == cudaSuccess) le = q_backward(D, *cfg, nullptr, cs);
         cudaEventRecordWithFlags(D->ev[3], cs, cudaEventRecordExternal);

@@ -30,16 +30,15 @@ __device__ __forceinline__ float combine(int grad_mode, float acc, float local, 
 }
 
 __global__ void k_bwd_level(const uint4 *__restrict__ fanin, const int32_t *__restrict__ fptr,
-                            const int4 *__restrict__ efpos, const float2 *__restrict__ pq,
+                            const int4 *__restrict__ efpos, const float4 *__restrict__ pq,
                             const float *__restrict__ cload, const float *__restrict__ beta, float *gnet,
                             float *gfo, int32_t c0, int32_t c1, int64_t ns, int grad_mode, float K, OpTable ops) {
     int32_t c = c0 + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
     if (c >= c1) return;
     const int64_t n = ns + c;
     const float acc = fanout_sum(fptr, gfo, n);
-    const float2 o = pq[n];
     // local term: d(K C 2P(1-P))/dP = K C (2 - 4P) = 2 K C (Q - P)
-    const float g = combine(grad_mode, acc, 2.f * K * cload[n] * (o.y - o.x), beta, n);
+    const float g = combine(grad_mode, acc, 2.f * K * cload[n] * pair_qmp(pq[n]), beta, n);
     gnet[n] = g;
     const uint4 r = fanin[c];
     const uint32_t op = r.x >> 24;
@@ -54,15 +53,14 @@ __global__ void k_bwd_level(const uint4 *__restrict__ fanin, const int32_t *__re
     if (k > 3) gfo[ep.w] = g * d[3];
 }
 
-__global__ void k_bwd_start(const int32_t *__restrict__ fptr, const float2 *__restrict__ pq,
+__global__ void k_bwd_start(const int32_t *__restrict__ fptr, const float4 *__restrict__ pq,
                             const float *__restrict__ cload, const float *__restrict__ beta, float *gnet,
                             const float *gfo, int64_t ns, int grad_mode, int tr_mode, float K, float *out) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= ns) return;
     const float acc = fanout_sum(fptr, gfo, k);
     // a startpoint has a local SP term only when its TR is derived from its SP (tr_mode 1)
-    const float2 o = pq[k];
-    const float local = tr_mode ? 2.f * K * cload[k] * (o.y - o.x) : 0.f;
+    const float local = tr_mode ? 2.f * K * cload[k] * pair_qmp(pq[k]) : 0.f;
     const float g = combine(grad_mode, acc, local, beta, k);
     gnet[k] = g;
     if (out) out[k] = g;

@@ -12,10 +12,49 @@ constexpr uint32_t kMask24 = 0xFFFFFFu;
 __device__ __forceinline__ int op_arity(const OpTable &t, uint32_t op) { return (int)(t.e[op] >> 16); }
 __device__ __forceinline__ uint32_t op_tt(const OpTable &t, uint32_t op) { return t.e[op] & 0xFFFFu; }
 
-// Probabilities of a net are carried as the pair (P, Q) = (P(net=1), P(net=0)).
-// Q is never formed as 1 - P: deep reconvergent netlists have many nets within
+// ---- float-float arithmetic (an unevaluated sum hi + lo of two binary32
+// values, about 44 significant bits), built from error-free transforms on the
+// FP32 pipes.  The _rn intrinsics are never contracted into FMAs, which the
+// transforms rely on.
+struct ff {
+    float hi, lo;
+};
+__device__ __forceinline__ ff ff_make(float a) { return ff{a, 0.f}; }
+// Knuth's TwoSum: s + e == a + b exactly
+__device__ __forceinline__ ff two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return ff{s, e};
+}
+// Dekker's FastTwoSum, valid when |a| >= |b| (or a == 0)
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return ff{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+    const ff s = two_sum(a.hi, b.hi);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = fmaf(a.hi, b.hi, -p);   // exact product error
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ ff ff_div(ff a, ff b) {
+    const float q1 = __fdiv_rn(a.hi, b.hi);
+    const ff r = ff_add(a, ff_mul(ff_make(-q1), b));
+    return fast_two_sum(q1, __fdiv_rn(r.hi, b.hi));
+}
+
+// Probabilities of a net are carried as the pair (P, Q) = (P(net=1), P(net=0)),
+// each a float-float value, stored as float4 (P.hi, P.lo, Q.hi, Q.lo).  Q is
+// never formed as 1 - P: deep reconvergent netlists have many nets within
 // 1e-15 of 0 or 1, where that subtraction would destroy the relative accuracy
-// of TR_model = 2PQ (Eq. 2).
+// of TR_model = 2PQ (Eq. 2), and the hybrid beta (Eq. 5) multiplies the
+// paper's gradient at every net (Eq. 6), so its error compounds along paths.
 //
 // The output pair of a cell with K inputs is the multilinear extension of its
 // truth table and of the complemented table (Sec. III-B; exact under input
@@ -24,24 +63,84 @@ __device__ __forceinline__ uint32_t op_tt(const OpTable &t, uint32_t op) { retur
 // term is non-negative, so both P and Q keep full relative accuracy.  The pair
 // is then divided by its sum (1 in exact arithmetic) so that rounding cannot
 // accumulate along the exponentially many paths of a reconvergent netlist.
+struct pair_ff {
+    ff p, q;
+};
+__device__ __forceinline__ pair_ff pair_load(const float4 &v) { return pair_ff{ff{v.x, v.y}, ff{v.z, v.w}}; }
+__device__ __forceinline__ float4 pair_store(const pair_ff &a) { return make_float4(a.p.hi, a.p.lo, a.q.hi, a.q.lo); }
+
+// (P, 1 - P) of a binary32 probability, exactly
+__device__ __forceinline__ pair_ff pair_of(float p) { return pair_ff{ff_make(p), two_sum(1.f, -p)}; }
+
+// TR_model = 2PQ rounded once to binary32
+__device__ __forceinline__ float pair_tr(const pair_ff &a) {
+    const ff t = ff_mul(a.p, a.q);
+    return 2.f * (t.hi + t.lo);
+}
+
 template <int K>
-__device__ __forceinline__ float2 ml_pair(uint32_t tt, const float (&p)[4], const float (&q)[4]) {
-    float v1[1 << K], v0[1 << K];
+__device__ __forceinline__ pair_ff ml_pair(uint32_t tt, const pair_ff (&x)[4]) {
+    ff v1[1 << K], v0[1 << K];
+    // first fold: leaves are 0/1, so each term is Q_0, P_0, both or neither
 #pragma unroll
-    for (int m = 0; m < (1 << K); m++) {
-        v1[m] = (float)((tt >> m) & 1u);
-        v0[m] = 1.f - v1[m];
+    for (int m = 0; m < (1 << (K - 1)); m++) {
+        const bool a1 = (tt >> (2 * m)) & 1u, b1 = (tt >> (2 * m + 1)) & 1u;
+        const ff z = ff_make(0.f);
+        v1[m] = ff_add(a1 ? x[0].q : z, b1 ? x[0].p : z);
+        v0[m] = ff_add(a1 ? z : x[0].q, b1 ? z : x[0].p);
     }
 #pragma unroll
-    for (int i = 0; i < K; i++) {
+    for (int i = 1; i < K; i++) {
 #pragma unroll
         for (int m = 0; m < (1 << (K - 1 - i)); m++) {
-            v1[m] = fmaf(p[i], v1[2 * m + 1], q[i] * v1[2 * m]);
-            v0[m] = fmaf(p[i], v0[2 * m + 1], q[i] * v0[2 * m]);
+            v1[m] = ff_add(ff_mul(x[i].q, v1[2 * m]), ff_mul(x[i].p, v1[2 * m + 1]));
+            v0[m] = ff_add(ff_mul(x[i].q, v0[2 * m]), ff_mul(x[i].p, v0[2 * m + 1]));
         }
     }
-    const float r = 1.f / (v1[0] + v0[0]);
-    return make_float2(v1[0] * r, v0[0] * r);
+    const ff s = ff_add(v1[0], v0[0]);
+    return pair_ff{ff_div(v1[0], s), ff_div(v0[0], s)};
+}
+
+__device__ __forceinline__ pair_ff cell_pair(int k, uint32_t tt, const pair_ff (&x)[4]) {
+    switch (k) {
+        case 0: return (tt & 1u) ? pair_ff{ff_make(1.f), ff_make(0.f)} : pair_ff{ff_make(0.f), ff_make(1.f)};
+        case 1: return ml_pair<1>(tt, x);
+        case 2: return ml_pair<2>(tt, x);
+        case 3: return ml_pair<3>(tt, x);
+        default: return ml_pair<4>(tt, x);
+    }
+}
+
+// gathers the (P, Q) pairs of a cell's inputs (unused slots: P = 0, Q = 1)
+template <bool L2>
+__device__ __forceinline__ void gather_ff(const float4 *pq, const uint4 &r, int k, pair_ff (&x)[4]) {
+    const uint32_t n[4] = {r.x & kMask24, r.y, r.z, r.w};
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        x[j] = pair_ff{ff_make(0.f), ff_make(1.f)};
+        if (j < k) x[j] = pair_load(L2 ? __ldcg(pq + n[j]) : pq[n[j]]);
+    }
+}
+
+// (Q - P) of a pair, rounded once to binary32
+__device__ __forceinline__ float pair_qmp(const float4 &v) {
+    const ff d = ff_add(ff{v.z, v.w}, ff{-v.x, -v.y});
+    return d.hi + d.lo;
+}
+
+// binary32 (P, Q) of a cell's inputs, for the partial derivatives
+__device__ __forceinline__ void gather_pairs(const float4 *pq, const uint4 &r, int k, float (&p)[4], float (&q)[4]) {
+    const uint32_t n[4] = {r.x & kMask24, r.y, r.z, r.w};
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        p[j] = 0.f;
+        q[j] = 1.f;
+        if (j < k) {
+            const float4 v = pq[n[j]];
+            p[j] = v.x + v.y;
+            q[j] = v.z + v.w;
+        }
+    }
 }
 
 // d P / d a_J: the multilinear extension, over the other inputs, of the
@@ -67,16 +166,6 @@ __device__ __forceinline__ float ml_partial(uint32_t tt, const float (&p)[4], co
     return v[0];
 }
 
-__device__ __forceinline__ float2 cell_pair(int k, uint32_t tt, const float (&p)[4], const float (&q)[4]) {
-    switch (k) {
-        case 0: return (tt & 1u) ? make_float2(1.f, 0.f) : make_float2(0.f, 1.f);
-        case 1: return ml_pair<1>(tt, p, q);
-        case 2: return ml_pair<2>(tt, p, q);
-        case 3: return ml_pair<3>(tt, p, q);
-        default: return ml_pair<4>(tt, p, q);
-    }
-}
-
 // all partials of a cell into d[0..3] (unused slots 0)
 __device__ __forceinline__ void cell_partials(int k, uint32_t tt, const float (&p)[4], const float (&q)[4],
                                               float (&d)[4]) {
@@ -92,21 +181,6 @@ __device__ __forceinline__ void cell_partials(int k, uint32_t tt, const float (&
             d[0] = ml_partial<4, 0>(tt, p, q); d[1] = ml_partial<4, 1>(tt, p, q);
             d[2] = ml_partial<4, 2>(tt, p, q); d[3] = ml_partial<4, 3>(tt, p, q);
             break;
-    }
-}
-
-// gathers the (P, Q) pairs of a cell's inputs
-__device__ __forceinline__ void gather_pairs(const float2 *pq, const uint4 &r, int k, float (&p)[4], float (&q)[4]) {
-    const uint32_t n[4] = {r.x & kMask24, r.y, r.z, r.w};
-#pragma unroll
-    for (int j = 0; j < 4; j++) {
-        p[j] = 0.f;
-        q[j] = 1.f;
-        if (j < k) {
-            const float2 v = pq[n[j]];
-            p[j] = v.x;
-            q[j] = v.y;
-        }
     }
 }
 

@@ -8,29 +8,29 @@ namespace {
 __host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 // startpoints: (P, Q) = (SP, 1 - SP); TR = input TR (tr_mode 0) or 2PQ (tr_mode 1)
-__global__ void k_init_start(const float *__restrict__ sp_in, const float *__restrict__ tr_in, float2 *pq, float *tr,
+__global__ void k_init_start(const float *__restrict__ sp_in, const float *__restrict__ tr_in, float4 *pq, float *tr,
                              int64_t ns, int tr_mode) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= ns) return;
-    const float p = sp_in[k], q = 1.f - p;
-    pq[k] = make_float2(p, q);
-    tr[k] = tr_mode ? 2.f * p * q : tr_in[k];
+    const pair_ff a = pair_of(sp_in[k]);
+    pq[k] = pair_store(a);
+    tr[k] = tr_mode ? pair_tr(a) : tr_in[k];
 }
 
 // one thread per cell of one level: gather the fanin (P, Q) pairs, evaluate
 // the cell's pair, write it and TR_model = 2PQ (Eq. 2) for its output net
-__global__ void k_fwd_level(const uint4 *__restrict__ fanin, float2 *pq, float *tr, int32_t c0, int32_t c1,
+__global__ void k_fwd_level(const uint4 *__restrict__ fanin, float4 *pq, float *tr, int32_t c0, int32_t c1,
                             int64_t ns, OpTable ops) {
     int32_t c = c0 + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
     if (c >= c1) return;
     const uint4 r = fanin[c];
     const uint32_t op = r.x >> 24;
     const int k = op_arity(ops, op);
-    float p[4], q[4];
-    gather_pairs(pq, r, k, p, q);
-    const float2 o = cell_pair(k, op_tt(ops, op), p, q);
-    pq[ns + c] = o;
-    tr[ns + c] = 2.f * o.x * o.y;
+    pair_ff x[4];
+    gather_ff<false>(pq, r, k, x);
+    const pair_ff o = cell_pair(k, op_tt(ops, op), x);
+    pq[ns + c] = pair_store(o);
+    tr[ns + c] = pair_tr(o);
 }
 
 // Eq. 1 loads: C_load = wire + DFF D caps + sum of the input pin caps of the driven cells
@@ -139,7 +139,7 @@ __global__ void k_gather_u32(const uint32_t *__restrict__ src, const int32_t *__
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) dst[i] = src[idx[i]];
 }
-__global__ void k_sp_user(const float2 *__restrict__ pq, const int32_t *__restrict__ idx, float *dst, int64_t n) {
+__global__ void k_sp_user(const float4 *__restrict__ pq, const int32_t *__restrict__ idx, float *dst, int64_t n) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) dst[i] = pq[idx[i]].x;
 }

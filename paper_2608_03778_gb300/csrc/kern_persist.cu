@@ -61,43 +61,28 @@ __device__ __forceinline__ int64_t spread_tid() {
 }
 __device__ __forceinline__ int64_t spread_warp() { return (int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x; }
 
-__device__ __forceinline__ void gather_pairs_l2(const float2 *pq, const uint4 &r, int k, float (&p)[4],
-                                                float (&q)[4]) {
-    const uint32_t n[4] = {r.x & kMask24, r.y, r.z, r.w};
-#pragma unroll
-    for (int j = 0; j < 4; j++) {
-        p[j] = 0.f;
-        q[j] = 1.f;
-        if (j < k) {
-            const float2 v = __ldcg(pq + n[j]);
-            p[j] = v.x;
-            q[j] = v.y;
-        }
-    }
-}
-
 // ---------------------------------------------------------------- forward
-__device__ __forceinline__ void fwd_cell(const uint4 &r, int64_t c, float2 *pq, float *tr, int64_t ns,
+__device__ __forceinline__ void fwd_cell(const uint4 &r, int64_t c, float4 *pq, float *tr, int64_t ns,
                                          const OpTable &ops) {
     const uint32_t op = r.x >> 24;
     const int k = op_arity(ops, op);
-    float p[4], q[4];
-    gather_pairs_l2(pq, r, k, p, q);
-    const float2 o = cell_pair(k, op_tt(ops, op), p, q);
-    pq[ns + c] = o;
-    tr[ns + c] = 2.f * o.x * o.y;
+    pair_ff x[4];
+    gather_ff<true>(pq, r, k, x);
+    const pair_ff o = cell_pair(k, op_tt(ops, op), x);
+    pq[ns + c] = pair_store(o);
+    tr[ns + c] = pair_tr(o);
 }
 
 __global__ void __launch_bounds__(kPersistThreads) k_fwd_persist(
-    const uint4 *__restrict__ fanin, float2 *pq, float *tr, const float *__restrict__ sp_in,
+    const uint4 *__restrict__ fanin, float4 *pq, float *tr, const float *__restrict__ sp_in,
     const float *__restrict__ tr_in, const int32_t *__restrict__ lvl, int L, int64_t ns, int tr_mode, OpTable ops,
     unsigned *bar, int *err, long long limit) {
     const int64_t tid = spread_tid();
     const int64_t T = (int64_t)gridDim.x * blockDim.x;
     for (int64_t k = tid; k < ns; k += T) {
-        const float p = sp_in[k], q = 1.f - p;
-        pq[k] = make_float2(p, q);
-        tr[k] = tr_mode ? 2.f * p * q : tr_in[k];
+        const pair_ff a = pair_of(sp_in[k]);
+        pq[k] = pair_store(a);
+        tr[k] = tr_mode ? pair_tr(a) : tr_in[k];
     }
     for (int l = 1; l <= L; l++) {
         const int32_t c0 = lvl[l - 1], c1 = lvl[l];
@@ -127,7 +112,7 @@ struct BwdStatic {
 };
 
 __device__ __forceinline__ BwdStatic bwd_static(const uint4 *fanin, const int32_t *fptr, const int4 *efpos,
-                                                const float2 *pq, const float *cload, const float *beta, int64_t c,
+                                                const float4 *pq, const float *cload, const float *beta, int64_t c,
                                                 int64_t ns, int grad_mode, float K, const OpTable &ops) {
     BwdStatic s;
     const int64_t n = ns + c;
@@ -135,9 +120,8 @@ __device__ __forceinline__ BwdStatic bwd_static(const uint4 *fanin, const int32_
     s.ep = efpos[c];
     s.e0 = fptr[n];
     s.e1 = fptr[n + 1];
-    const float2 o = pq[n];
     // local term: d(K C 2P(1-P))/dP = 2 K C (Q - P)
-    s.local = 2.f * K * cload[n] * (o.y - o.x);
+    s.local = 2.f * K * cload[n] * pair_qmp(pq[n]);
     s.b = grad_mode ? beta[n] : 1.f;
     const uint32_t op = r.x >> 24;
     s.k = op_arity(ops, op);
@@ -160,7 +144,7 @@ __device__ __forceinline__ void bwd_finish(const BwdStatic &s, int64_t n, float 
 
 __global__ void __launch_bounds__(kPersistThreads) k_bwd_persist(
     const uint4 *__restrict__ fanin, const int32_t *__restrict__ fptr, const int4 *__restrict__ efpos,
-    const float2 *__restrict__ pq, const float *__restrict__ cload, const float *__restrict__ beta, float *gnet,
+    const float4 *__restrict__ pq, const float *__restrict__ cload, const float *__restrict__ beta, float *gnet,
     float *gfo, const int32_t *__restrict__ lvl, int L, int64_t ns, int grad_mode, int tr_mode, float K,
     float *out_gsp, OpTable ops, unsigned *bar, int *err, long long limit) {
     const int64_t tid = spread_tid();
@@ -182,8 +166,7 @@ __global__ void __launch_bounds__(kPersistThreads) k_bwd_persist(
         float acc = 0.f;
         const int32_t e1 = fptr[k + 1];
         for (int32_t e = fptr[k]; e < e1; e++) acc += __ldcg(gfo + e);
-        const float2 o = pq[k];
-        const float local = tr_mode ? 2.f * K * cload[k] * (o.y - o.x) : 0.f;
+        const float local = tr_mode ? 2.f * K * cload[k] * pair_qmp(pq[k]) : 0.f;
         const float g = combine(grad_mode, acc, local, grad_mode ? beta[k] : 1.f);
         gnet[k] = g;
         if (out_gsp) out_gsp[k] = g;
@@ -337,7 +320,7 @@ cudaError_t launch_bwd_persist(const DevDesign &d, const OpTable &ops, int grad_
     unsigned *bar = d.bar + 2 * 32 * ((size_t)d.n_levels + 2);
     cudaMemsetAsync(bar, 0, bar_bytes(d), s);
     return launch_coop(k_bwd_persist, grid, kPersistThreads, s, d.fanin, d.fout_ptr, (const int4 *)d.edge_fpos,
-                       (const float2 *)d.pq, (const float *)d.cload, (const float *)d.beta, d.gnet, d.gfo, d.lvl,
+                       (const float4 *)d.pq, (const float *)d.cload, (const float *)d.beta, d.gnet, d.gfo, d.lvl,
                        d.n_levels, d.n_start, grad_mode, tr_mode, K, out_gsp, ops, bar, d.err, kWaitLimitCycles);
 }
 

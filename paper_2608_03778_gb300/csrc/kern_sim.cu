@@ -11,19 +11,21 @@ namespace {
 
 __host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-// floor(p * 2^32) clamped to [0, 2^32]: a draw u (32 bits) is 1 iff u < thr
-__device__ __forceinline__ uint64_t threshold(double p) {
-    if (!(p > 0.0)) return 0ull;
-    if (p >= 1.0) return 4294967296ull;
-    return (uint64_t)floor(p * 4294967296.0);
+// floor(p * 2^16) clamped to [0, 2^16]: a 16-bit draw u is 1 iff u < thr
+__device__ __forceinline__ uint32_t threshold16(double p) {
+    if (!(p > 0.0)) return 0u;
+    if (p >= 1.0) return 65536u;
+    return (uint32_t)floor(p * 65536.0);
 }
 
 // One half-warp per startpoint k; thread q runs lanes q, q+16, q+32, q+48.
-// Philox4x32-10 counter (k, t, q, 0) under key (seed lo, seed hi); output
-// component r drives lane 16 r + q.  t = 0 draws the initial state with
+// Philox4x32-10 counter (k, t / 2, q, 0) under key (seed lo, seed hi);
+// output component r drives lane 16 r + q, its low 16 bits at even cycles
+// and its high 16 bits at odd cycles.  t = 0 draws the initial state with
 // P(1) = SP; t >= 1 flips a 1 with p10 = TR / 2SP and a 0 with
 // p01 = TR / 2(1 - SP), which keeps SP stationary and makes TR the expected
-// toggle rate.
+// toggle rate.  The four lanes' states live in a 4-bit mask; the 64-bit word
+// of each cycle is assembled from four warp ballots.
 __global__ void __launch_bounds__(256) k_sim_start(const float *__restrict__ sp_in, const float *__restrict__ tr_in,
                                                    uint64_t *words, uint32_t *toggles, uint32_t *ones, int64_t ns,
                                                    int T, uint32_t key0, uint32_t key1) {
@@ -31,40 +33,40 @@ __global__ void __launch_bounds__(256) k_sim_start(const float *__restrict__ sp_
     const int half = (threadIdx.x >> 4) & 1;
     const int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 4) + (threadIdx.x >> 4);
     const bool valid = k < ns;
-    uint64_t t_init = 0, t10 = 0, t01 = 0;
+    uint32_t t_init = 0, t10 = 0, t01 = 0;
     if (valid) {
         const double sp = (double)sp_in[k], tr = (double)tr_in[k];
         const double p10 = sp > 0.0 ? tr / (2.0 * sp) : 0.0;
         const double p01 = sp < 1.0 ? tr / (2.0 * (1.0 - sp)) : 0.0;
-        t_init = threshold(sp);
-        t10 = threshold(p10);
-        t01 = threshold(p01);
+        t_init = threshold16(sp);
+        t10 = threshold16(p10);
+        t01 = threshold16(p01);
     }
-    uint32_t state = 0;        // bit r = current value of lane 16 r + q
+    const uint32_t sel = half ? 0x7632u : 0x5410u;  // this half-warp's 16 ballot bits of two ballots
+    uint32_t st = 0;                                // bit r = current value of lane 16 r + q
     uint32_t n_flip = 0, n_one = 0;
-    uint64_t mine = 0;         // word t with t % 16 == q of the current group of 16 cycles
+    uint64_t mine = 0;                              // word t with t % 16 == q of the current 16 cycles
+    uint4 u = make_uint4(0, 0, 0, 0);
     for (int t = 0; t < T; t++) {
-        const uint4 u = philox4x32_10(make_uint4((uint32_t)k, (uint32_t)t, (uint32_t)q, 0u), key0, key1);
-        const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-        for (int r = 0; r < 4; r++) {
-            uint32_t b = (state >> r) & 1u;
-            if (t == 0) {
-                b = (uint64_t)uu[r] < t_init;
-            } else {
-                const uint32_t f = (uint64_t)uu[r] < (b ? t10 : t01);
-                b ^= f;
-                n_flip += f;
-            }
-            n_one += b;
-            state = (state & ~(1u << r)) | (b << r);
+        if ((t & 1) == 0) u = philox4x32_10(make_uint4((uint32_t)k, (uint32_t)(t >> 1), (uint32_t)q, 0u), key0, key1);
+        const int sh = (t & 1) << 4;
+        const uint32_t d0 = (u.x >> sh) & 0xFFFFu, d1 = (u.y >> sh) & 0xFFFFu;
+        const uint32_t d2 = (u.z >> sh) & 0xFFFFu, d3 = (u.w >> sh) & 0xFFFFu;
+        if (t == 0) {
+            st = (uint32_t)(d0 < t_init) | ((uint32_t)(d1 < t_init) << 1) | ((uint32_t)(d2 < t_init) << 2) |
+                 ((uint32_t)(d3 < t_init) << 3);
+        } else {
+            const uint32_t f = (uint32_t)(d0 < ((st & 1u) ? t10 : t01)) |
+                               ((uint32_t)(d1 < ((st & 2u) ? t10 : t01)) << 1) |
+                               ((uint32_t)(d2 < ((st & 4u) ? t10 : t01)) << 2) |
+                               ((uint32_t)(d3 < ((st & 8u) ? t10 : t01)) << 3);
+            n_flip += __popc(f);
+            st ^= f;
         }
-        uint64_t w = 0;
-#pragma unroll
-        for (int r = 0; r < 4; r++) {
-            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, (state >> r) & 1u);
-            w |= (uint64_t)((bal >> (16 * half)) & 0xFFFFu) << (16 * r);
-        }
+        n_one += __popc(st);
+        const uint32_t b0 = __ballot_sync(0xFFFFFFFFu, st & 1u), b1 = __ballot_sync(0xFFFFFFFFu, st & 2u);
+        const uint32_t b2 = __ballot_sync(0xFFFFFFFFu, st & 4u), b3 = __ballot_sync(0xFFFFFFFFu, st & 8u);
+        const uint64_t w = (uint64_t)__byte_perm(b0, b1, sel) | ((uint64_t)__byte_perm(b2, b3, sel) << 32);
         if ((t & 15) == q) mine = w;
         if ((t & 15) == 15 || t == T - 1) {
             const int t_q = (t & ~15) + q;
@@ -133,17 +135,32 @@ __global__ void __launch_bounds__(256) k_sim_level(const uint4 *__restrict__ fan
 }
 
 // Eq. 4 and Eq. 5: TR_acc = toggles / 64(T-1); beta = clip(TR_acc / TR_model);
-// TR_model = 0 gives beta = 1 without toggles, else beta_max.
-__global__ void k_hybrid(const uint32_t *__restrict__ toggles, const float *__restrict__ tr, float *beta, float *trh,
-                         int64_t nn, float nsim, float bmin, float bmax) {
+// TR_model = 0 gives beta = 1 without toggles, else beta_max.  The ratio is
+// formed in float-float from the float-float (P, Q) pair and rounded once:
+// the paper's gradient rule multiplies by beta at every net (Eq. 6), so
+// beta's rounding error compounds along paths.
+__global__ void k_hybrid(const uint32_t *__restrict__ toggles, const float *__restrict__ tr,
+                         const float4 *__restrict__ pq, float *beta, float *trh, int64_t nn, int64_t ns, int tr_mode,
+                         float nsim, float bmin, float bmax) {
     int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= nn) return;
     const uint32_t tg = toggles[n];
-    const float acc = (float)tg / nsim;
     const float m = tr[n];
+    ff model;
+    if (n < ns && tr_mode == 0) {
+        model = ff_make(m);
+    } else {
+        const float4 v = pq[n];
+        const ff t = ff_mul(ff{v.x, v.y}, ff{v.z, v.w});
+        model = ff{2.f * t.hi, 2.f * t.lo};
+    }
     float b;
-    if (m > 0.f) b = fminf(fmaxf(acc / m, bmin), bmax);
-    else b = tg == 0 ? 1.f : bmax;
+    if (model.hi > 0.f) {
+        const ff r = ff_div(ff_div(ff_make((float)tg), ff_make(nsim)), model);
+        b = fminf(fmaxf(r.hi + r.lo, bmin), bmax);
+    } else {
+        b = tg == 0 ? 1.f : bmax;
+    }
     beta[n] = b;
     trh[n] = b * m;
 }
@@ -162,11 +179,11 @@ void launch_sim_level(const DevDesign &d, const OpTable &ops, int32_t c0, int32_
                                                                               c0, c1, d.n_start, T, ops);
 }
 
-void launch_hybrid(const DevDesign &d, int T, float beta_min, float beta_max, cudaStream_t s) {
+void launch_hybrid(const DevDesign &d, int T, int tr_mode, float beta_min, float beta_max, cudaStream_t s) {
     if (d.n_nets == 0) return;
     const float nsim = 64.f * (float)(T - 1);
-    k_hybrid<<<(unsigned)cdiv(d.n_nets, 256), 256, 0, s>>>(d.toggles, d.tr, d.beta, d.trh, d.n_nets, nsim, beta_min,
-                                                           beta_max);
+    k_hybrid<<<(unsigned)cdiv(d.n_nets, 256), 256, 0, s>>>(d.toggles, d.tr, d.pq, d.beta, d.trh, d.n_nets,
+                                                           d.n_start, tr_mode, nsim, beta_min, beta_max);
 }
 
 }  // namespace dp

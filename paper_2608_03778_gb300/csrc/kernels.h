@@ -32,7 +32,7 @@ struct DevDesign {
     float *pincap;             // [n_cells]
     float *cload;              // [n_nets]
     float *sp_in, *tr_in;      // [n_start] staged inputs
-    float2 *pq;                // [n_nets] (P(net=1), P(net=0)); P is the SP
+    float4 *pq;                // [n_nets] (P(net=1), P(net=0)) as float-float pairs (P.hi, P.lo, Q.hi, Q.lo)
     float *tr;                 // [n_nets] TR_model (startpoints: input TR in tr_mode 0)
     float *beta, *trh;         // [n_nets] beta and hybrid TR
     uint32_t *toggles, *ones;  // [n_nets]
@@ -80,6 +80,6 @@ cudaError_t launch_wait_selftest(unsigned *bar, int *err, long long limit, cudaS
 // simulation (kern_sim.cu)
 void launch_sim_start(const DevDesign &d, int T, uint64_t seed, cudaStream_t s);
 void launch_sim_level(const DevDesign &d, const OpTable &ops, int32_t c0, int32_t c1, int T, cudaStream_t s);
-void launch_hybrid(const DevDesign &d, int T, float beta_min, float beta_max, cudaStream_t s);
+void launch_hybrid(const DevDesign &d, int T, int tr_mode, float beta_min, float beta_max, cudaStream_t s);
 
 }  // namespace dp
