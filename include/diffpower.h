@@ -87,9 +87,13 @@ typedef struct {
                                is multiplied by its beta (Eq. 6);
                             2: hybrid, exact gradient of sum K beta TR C with beta fixed */
     int32_t sim_words;   /* T, 64-bit words per net: 64*T vectors, 64*(T-1) transitions (Eq. 4); 2..4096 */
-    int32_t schedule;    /* 0: one persistent cooperative launch per pass with grid-wide level
-                               barriers (falls back to 1 where the grid cannot be co-resident);
-                            1: one launch per level.  Both give bitwise identical results. */
+    int32_t schedule;    /* 0 (default) and 2: one cooperative launch per pass with grid-wide
+                               level barriers;
+                            1: one launch per level;
+                            3: dataflow forward pass - warps take cells in topological order and
+                               wait only for their own fanins (other passes as 2).
+                            Where a cooperative grid cannot be co-resident the library uses 1.
+                            All give bitwise identical results. */
     uint64_t seed;       /* Philox4x32-10 key for the startpoint Markov chains (Sec. III-C) */
 } dp_config;
 

@@ -44,7 +44,11 @@ struct dp_design {
     dp_config graph_cfg{};
     cudaStream_t cap_stream = nullptr, cap_stream2 = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
-    int grid[3] = {0, 0, 0};   // persistent grids: forward, simulation, backward (0 = per-level launches)
+    int grid[4] = {0, 0, 0, 0};   // persistent grids: forward, simulation, backward, staged simulation
+    int flow_grid[1] = {0};        // dataflow grids: forward
+    // launch-shape tuning (defaults, overridable by DP_FLOW_BLOCKS / DP_FLOW_SLEEP for sweeps)
+    int flow_blocks_per_sm = 2;
+    unsigned flow_sleep = 0;
     int64_t graph_kernels = 0;
     int64_t step_kernels = 0;
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -134,7 +138,7 @@ dp_status check_cfg(dp_ctx *ctx, const dp_config *c) {
     if (c->tr_mode < 0 || c->tr_mode > 1) return set_err(ctx, DP_EINVAL, "tr_mode must be 0 or 1");
     if (c->grad_mode < 0 || c->grad_mode > 2) return set_err(ctx, DP_EINVAL, "grad_mode must be 0, 1 or 2");
     if (c->sim_words < 2 || c->sim_words > 4096) return set_err(ctx, DP_EINVAL, "sim_words must be in [2, 4096]");
-    if (c->schedule < 0 || c->schedule > 1) return set_err(ctx, DP_EINVAL, "schedule must be 0 or 1");
+    if (c->schedule < 0 || c->schedule > 3) return set_err(ctx, DP_EINVAL, "schedule must be 0, 1, 2 or 3");
     return DP_OK;
 }
 
@@ -189,12 +193,19 @@ void rec(dp_design *D, int i, cudaStream_t s) {
 
 // ---- the phases, queued on stream s (also used under graph capture) ----
 bool persistent(const dp_design *D, const dp_config &c, int which) {
-    return c.schedule == 0 && D->grid[which] > 0 && D->d.n_levels > 0;
+    return c.schedule != 1 && D->grid[which] > 0 && D->d.n_levels > 0;
+}
+bool dataflow(const dp_design *D, const dp_config &c, int which) {
+    return c.schedule == 3 && D->flow_grid[which] > 0 && D->d.n_levels > 0;
 }
 
 // each q_* returns the first launch error (a cooperative launch reports it directly)
 cudaError_t q_forward(dp_design *D, const dp_config &c, cudaStream_t s) {
-    if (persistent(D, c, 0)) {
+    dp::launch_bump(D->d.epoch, s);   // new parity for the stored (P, Q) pairs
+    if (dataflow(D, c, 0)) {
+        cudaError_t e = dp::launch_fwd_flow(D->d, D->ops, c.tr_mode, D->flow_grid[0], D->flow_sleep, s);
+        if (e != cudaSuccess) return e;
+    } else if (persistent(D, c, 0)) {
         cudaError_t e = dp::launch_fwd_persist(D->d, D->ops, c.tr_mode, D->grid[0], s);
         if (e != cudaSuccess) return e;
     } else {
@@ -213,7 +224,10 @@ void q_sim_start(dp_design *D, const dp_config &c, cudaStream_t s) {
 
 // the simulation levels, beta and the hybrid power (after the generator and the forward pass)
 cudaError_t q_sim_levels(dp_design *D, const dp_config &c, cudaStream_t s) {
-    if (persistent(D, c, 1)) {
+    if (persistent(D, c, 3) && dp::staged_ok(c.sim_words)) {
+        cudaError_t e = dp::launch_sim_staged(D->d, D->ops, c.sim_words, D->grid[3], s);
+        if (e != cudaSuccess) return e;
+    } else if (persistent(D, c, 1)) {
         cudaError_t e = dp::launch_sim_persist(D->d, D->ops, c.sim_words, D->grid[1], s);
         if (e != cudaSuccess) return e;
     } else {
@@ -362,11 +376,23 @@ dp_status dp_design_upload(dp_ctx *ctx, const dp_compiled *cp, dp_design **out) 
     D->n_edges = cp->n_edges;
     D->n_ops = cp->n_ops;
     D->lvl_ptr = cp->lvl_ptr;
-    for (int i = 0; i < 256; i++) D->ops.e[i] = (uint32_t)cp->op_tt[i] | ((uint32_t)cp->op_arity[i] << 16);
+    for (int i = 0; i < 256; i++) {
+        const uint32_t k = cp->op_arity[i], tt = cp->op_tt[i];
+        uint32_t lut = 0;
+        if (k <= 3)
+            for (uint32_t m = 0; m < 8; m++) lut |= ((tt >> (m & ((1u << k) - 1u))) & 1u) << m;
+        D->ops.e[i] = tt | (k << 16) | (lut << 24);
+    }
     const size_t nn = (size_t)d.n_nets, nc = (size_t)d.n_cells, ns = (size_t)d.n_start;
     dp_status s = DP_OK;
     uint4 *fanin = nullptr;
     int32_t *fptr = nullptr, *fedge = nullptr, *nou = nullptr, *cou = nullptr, *efpos = nullptr, *lvl = nullptr;
+    int32_t *chunks = nullptr;
+    // level-aligned chunks of 32: level 0 = startpoints, then each level of cells
+    std::vector<int32_t> chunk_ptr((size_t)cp->n_levels + 2, 0);
+    chunk_ptr[1] = (int32_t)((cp->n_start + 31) / 32);
+    for (int l = 1; l <= cp->n_levels; l++)
+        chunk_ptr[l + 1] = chunk_ptr[l] + (cp->lvl_ptr[l] - cp->lvl_ptr[l - 1] + 31) / 32;
     float *base = nullptr;
 #define TRY(x) do { if ((s = (x)) != DP_OK) { free_design(D); return s; } } while (0)
     TRY(dalloc(D, &fanin, nc));
@@ -390,6 +416,8 @@ dp_status dp_design_upload(dp_ctx *ctx, const dp_compiled *cp, dp_design **out) 
     TRY(dalloc(D, &efpos, 4 * nc));
     TRY(dalloc(D, &lvl, (size_t)cp->n_levels + 1));
     TRY(dalloc(D, &d.bar, dp::persist_bar_words(cp->n_levels)));
+    TRY(dalloc(D, &d.epoch, 4));
+    TRY(dalloc(D, &chunks, chunk_ptr.size()));
     TRY(dalloc(D, &d.partials, (size_t)dp::kPowerBlocks));
     TRY(dalloc(D, &d.power, 4));
     d.fanin = fanin;
@@ -397,6 +425,7 @@ dp_status dp_design_upload(dp_ctx *ctx, const dp_compiled *cp, dp_design **out) 
     d.fout_edge = fedge;
     d.edge_fpos = efpos;
     d.lvl = lvl;
+    d.chunk_ptr = chunks;
     d.err = ctx->d_err;
     d.net_of_user = nou;
     d.cell_of_user = cou;
@@ -411,13 +440,20 @@ dp_status dp_design_upload(dp_ctx *ctx, const dp_compiled *cp, dp_design **out) 
     up(fedge, cp->fout_edge.data(), sizeof(int32_t) * cp->fout_edge.size());
     up(efpos, cp->edge_fpos.data(), sizeof(int32_t) * cp->edge_fpos.size());
     up(lvl, cp->lvl_ptr.data(), sizeof(int32_t) * cp->lvl_ptr.size());
+    up(chunks, chunk_ptr.data(), sizeof(int32_t) * chunk_ptr.size());
     up(nou, cp->net_of_user.data(), sizeof(int32_t) * nn);
     up(cou, cp->cell_of_user.data(), sizeof(int32_t) * nc);
     up(base, cp->base_cap.data(), sizeof(float) * nn);
     up(d.pincap, cp->pincap.data(), sizeof(float) * nc);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.power, 0, 4 * sizeof(double), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.epoch, 0, 4 * sizeof(uint32_t), st);
+    // tag 0 everywhere: the first forward pass writes tag 1
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.pq, 0, sizeof(float4) * nn, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.bar, 0, sizeof(unsigned) * dp::persist_bar_words(cp->n_levels), st);
-    for (int w = 0; w < 3; w++) D->grid[w] = dp::persist_grid(w, ctx->sm_count);
+    for (int w = 0; w < 4; w++) D->grid[w] = dp::persist_grid(w, ctx->sm_count);
+    if (const char *v = std::getenv("DP_FLOW_BLOCKS")) D->flow_blocks_per_sm = std::atoi(v);
+    if (const char *v = std::getenv("DP_FLOW_SLEEP")) D->flow_sleep = (unsigned)std::atoi(v);
+    D->flow_grid[0] = dp::flow_grid(0, ctx->sm_count, D->flow_blocks_per_sm);
     if (e != cudaSuccess) { s = cuda_err(ctx, e, "upload"); free_design(D); return s; }
     dp::launch_cload(d, st);
     for (auto &ev : D->ev)

@@ -9,7 +9,8 @@ namespace dp {
 
 constexpr uint32_t kMask24 = 0xFFFFFFu;
 
-__device__ __forceinline__ int op_arity(const OpTable &t, uint32_t op) { return (int)(t.e[op] >> 16); }
+__device__ __forceinline__ int op_arity(const OpTable &t, uint32_t op) { return (int)((t.e[op] >> 16) & 0xFFu); }
+__device__ __forceinline__ uint32_t op_lut(const OpTable &t, uint32_t op) { return t.e[op] >> 24; }
 __device__ __forceinline__ uint32_t op_tt(const OpTable &t, uint32_t op) { return t.e[op] & 0xFFFFu; }
 
 // ---- float-float arithmetic (an unevaluated sum hi + lo of two binary32
@@ -66,8 +67,28 @@ __device__ __forceinline__ ff ff_div(ff a, ff b) {
 struct pair_ff {
     ff p, q;
 };
-__device__ __forceinline__ pair_ff pair_load(const float4 &v) { return pair_ff{ff{v.x, v.y}, ff{v.z, v.w}}; }
-__device__ __forceinline__ float4 pair_store(const pair_ff &a) { return make_float4(a.p.hi, a.p.lo, a.q.hi, a.q.lo); }
+// Storage tag: P.hi and Q.hi are never negative, so their sign bits carry the
+// parity of the forward pass that wrote them (a counter in device memory,
+// advanced once per pass).  A reader of the dataflow schedule knows a pair is
+// from the current pass when both tags match; every reader masks the tags.
+__device__ __forceinline__ float untag(float v) { return __int_as_float(__float_as_int(v) & 0x7FFFFFFF); }
+__device__ __forceinline__ float4 pq_decode(float4 v) { return make_float4(untag(v.x), v.y, untag(v.z), v.w); }
+__device__ __forceinline__ pair_ff pair_load(const float4 &v) {
+    return pair_ff{ff{untag(v.x), v.y}, ff{untag(v.z), v.w}};
+}
+__device__ __forceinline__ float4 pair_store(const pair_ff &a, uint32_t parity) {
+    const int t = (int)(parity << 31);
+    return make_float4(__int_as_float(__float_as_int(a.p.hi) | t), a.p.lo, __int_as_float(__float_as_int(a.q.hi) | t),
+                       a.q.lo);
+}
+// writes a tagged pair as two 8-byte halves (P.hi, P.lo) and (Q.hi, Q.lo), each
+// single-copy atomic, so a concurrent reader never sees a half torn
+__device__ __forceinline__ void pair_put(float4 *dst, const pair_ff &a, uint32_t parity) {
+    const float4 v = pair_store(a, parity);
+    const unsigned long long h0 = (unsigned long long)__float_as_uint(v.x) | ((unsigned long long)__float_as_uint(v.y) << 32);
+    const unsigned long long h1 = (unsigned long long)__float_as_uint(v.z) | ((unsigned long long)__float_as_uint(v.w) << 32);
+    asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(dst), "l"(h0), "l"(h1) : "memory");
+}
 
 // (P, 1 - P) of a binary32 probability, exactly
 __device__ __forceinline__ pair_ff pair_of(float p) { return pair_ff{ff_make(p), two_sum(1.f, -p)}; }
@@ -122,8 +143,9 @@ __device__ __forceinline__ void gather_ff(const float4 *pq, const uint4 &r, int 
     }
 }
 
-// (Q - P) of a pair, rounded once to binary32
-__device__ __forceinline__ float pair_qmp(const float4 &v) {
+// (Q - P) of a stored pair, rounded once to binary32
+__device__ __forceinline__ float pair_qmp(const float4 &t) {
+    const float4 v = pq_decode(t);
     const ff d = ff_add(ff{v.z, v.w}, ff{-v.x, -v.y});
     return d.hi + d.lo;
 }
@@ -136,7 +158,7 @@ __device__ __forceinline__ void gather_pairs(const float4 *pq, const uint4 &r, i
         p[j] = 0.f;
         q[j] = 1.f;
         if (j < k) {
-            const float4 v = pq[n[j]];
+            const float4 v = pq_decode(pq[n[j]]);
             p[j] = v.x + v.y;
             q[j] = v.z + v.w;
         }
@@ -206,6 +228,57 @@ __device__ __forceinline__ uint64_t cell_bits(int k, uint32_t tt, const uint64_t
         case 2: return bits_eval<2>(tt, x);
         case 3: return bits_eval<3>(tt, x);
         default: return bits_eval<4>(tt, x);
+    }
+}
+
+// One LOP3 (any 3-input Boolean function, table as an immediate) per 32 bits.
+template <int LUT>
+__device__ __forceinline__ uint32_t lop3(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t d;
+    asm("lop3.b32 %0, %1, %2, %3, %4;" : "=r"(d) : "r"(a), "r"(b), "r"(c), "n"(LUT));
+    return d;
+}
+
+// Two 64-bit words of a cell with at most 3 inputs: the cell's 8-bit LOP3
+// table selects, through one warp-uniform indirect branch, the LOP3
+// instruction carrying that table, applied to (x2, x1, x0).
+__device__ __forceinline__ void cell_bits_lop3(uint32_t lut, const uint64_t (&x0)[4], const uint64_t (&x1)[4],
+                                               uint64_t &w0, uint64_t &w1) {
+    const uint32_t a0 = (uint32_t)x0[2], b0 = (uint32_t)x0[1], c0 = (uint32_t)x0[0];
+    const uint32_t a1 = (uint32_t)(x0[2] >> 32), b1 = (uint32_t)(x0[1] >> 32), c1 = (uint32_t)(x0[0] >> 32);
+    const uint32_t a2 = (uint32_t)x1[2], b2 = (uint32_t)x1[1], c2 = (uint32_t)x1[0];
+    const uint32_t a3 = (uint32_t)(x1[2] >> 32), b3 = (uint32_t)(x1[1] >> 32), c3 = (uint32_t)(x1[0] >> 32);
+    uint32_t r0 = 0, r1 = 0, r2 = 0, r3 = 0;
+    switch (lut) {
+#define DP_LOP3_CASE(N)                  \
+    case N:                              \
+        r0 = lop3<N>(a0, b0, c0);        \
+        r1 = lop3<N>(a1, b1, c1);        \
+        r2 = lop3<N>(a2, b2, c2);        \
+        r3 = lop3<N>(a3, b3, c3);        \
+        break;
+#define DP_LOP3_4(N) DP_LOP3_CASE(N) DP_LOP3_CASE(N + 1) DP_LOP3_CASE(N + 2) DP_LOP3_CASE(N + 3)
+#define DP_LOP3_16(N) DP_LOP3_4(N) DP_LOP3_4(N + 4) DP_LOP3_4(N + 8) DP_LOP3_4(N + 12)
+#define DP_LOP3_64(N) DP_LOP3_16(N) DP_LOP3_16(N + 16) DP_LOP3_16(N + 32) DP_LOP3_16(N + 48)
+        DP_LOP3_64(0) DP_LOP3_64(64) DP_LOP3_64(128) DP_LOP3_64(192)
+#undef DP_LOP3_64
+#undef DP_LOP3_16
+#undef DP_LOP3_4
+#undef DP_LOP3_CASE
+        default: break;
+    }
+    w0 = (uint64_t)r0 | ((uint64_t)r1 << 32);
+    w1 = (uint64_t)r2 | ((uint64_t)r3 << 32);
+}
+
+// both words of a cell, LOP3 for up to 3 inputs, multiplexer tree for 4
+__device__ __forceinline__ void cell_bits2(int k, uint32_t tt, uint32_t lut, const uint64_t (&x0)[4],
+                                           const uint64_t (&x1)[4], uint64_t &w0, uint64_t &w1) {
+    if (k <= 3) {
+        cell_bits_lop3(lut, x0, x1, w0, w1);
+    } else {
+        w0 = bits_eval<4>(tt, x0);
+        w1 = bits_eval<4>(tt, x1);
     }
 }
 

@@ -9,18 +9,18 @@ __host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 
 
 // startpoints: (P, Q) = (SP, 1 - SP); TR = input TR (tr_mode 0) or 2PQ (tr_mode 1)
 __global__ void k_init_start(const float *__restrict__ sp_in, const float *__restrict__ tr_in, float4 *pq, float *tr,
-                             int64_t ns, int tr_mode) {
+                             int64_t ns, int tr_mode, const uint32_t *epoch) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= ns) return;
     const pair_ff a = pair_of(sp_in[k]);
-    pq[k] = pair_store(a);
+    pq[k] = pair_store(a, epoch[0] & 1u);
     tr[k] = tr_mode ? pair_tr(a) : tr_in[k];
 }
 
 // one thread per cell of one level: gather the fanin (P, Q) pairs, evaluate
 // the cell's pair, write it and TR_model = 2PQ (Eq. 2) for its output net
 __global__ void k_fwd_level(const uint4 *__restrict__ fanin, float4 *pq, float *tr, int32_t c0, int32_t c1,
-                            int64_t ns, OpTable ops) {
+                            int64_t ns, OpTable ops, const uint32_t *epoch) {
     int32_t c = c0 + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
     if (c >= c1) return;
     const uint4 r = fanin[c];
@@ -29,7 +29,7 @@ __global__ void k_fwd_level(const uint4 *__restrict__ fanin, float4 *pq, float *
     pair_ff x[4];
     gather_ff<false>(pq, r, k, x);
     const pair_ff o = cell_pair(k, op_tt(ops, op), x);
-    pq[ns + c] = pair_store(o);
+    pq[ns + c] = pair_store(o, epoch[0] & 1u);
     tr[ns + c] = pair_tr(o);
 }
 
@@ -141,7 +141,7 @@ __global__ void k_gather_u32(const uint32_t *__restrict__ src, const int32_t *__
 }
 __global__ void k_sp_user(const float4 *__restrict__ pq, const int32_t *__restrict__ idx, float *dst, int64_t n) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) dst[i] = pq[idx[i]].x;
+    if (i < n) dst[i] = untag(pq[idx[i]].x);
 }
 __global__ void k_trh_user(const float *__restrict__ tr, const float *__restrict__ beta,
                            const int32_t *__restrict__ idx, float *dst, int64_t n) {
@@ -161,13 +161,14 @@ static inline int level_block(int64_t n) {
 
 void launch_init_start(const DevDesign &d, int tr_mode, cudaStream_t s) {
     if (d.n_start == 0) return;
-    k_init_start<<<(unsigned)cdiv(d.n_start, 256), 256, 0, s>>>(d.sp_in, d.tr_in, d.pq, d.tr, d.n_start, tr_mode);
+    k_init_start<<<(unsigned)cdiv(d.n_start, 256), 256, 0, s>>>(d.sp_in, d.tr_in, d.pq, d.tr, d.n_start, tr_mode,
+                                                                 d.epoch);
 }
 
 void launch_fwd_level(const DevDesign &d, const OpTable &ops, int32_t c0, int32_t c1, cudaStream_t s) {
     if (c1 <= c0) return;
     int b = level_block(c1 - c0);
-    k_fwd_level<<<(unsigned)cdiv(c1 - c0, b), b, 0, s>>>(d.fanin, d.pq, d.tr, c0, c1, d.n_start, ops);
+    k_fwd_level<<<(unsigned)cdiv(c1 - c0, b), b, 0, s>>>(d.fanin, d.pq, d.tr, c0, c1, d.n_start, ops, d.epoch);
 }
 
 void launch_cload(const DevDesign &d, cudaStream_t s) {

@@ -150,7 +150,7 @@ __global__ void k_hybrid(const uint32_t *__restrict__ toggles, const float *__re
     if (n < ns && tr_mode == 0) {
         model = ff_make(m);
     } else {
-        const float4 v = pq[n];
+        const float4 v = pq_decode(pq[n]);
         const ff t = ff_mul(ff{v.x, v.y}, ff{v.z, v.w});
         model = ff{2.f * t.hi, 2.f * t.lo};
     }

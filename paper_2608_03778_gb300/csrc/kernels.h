@@ -7,7 +7,9 @@
 namespace dp {
 
 // Per-design function table passed by value to kernels (lives in the
-// constant bank): entry = truth table (bits 0..15) | arity << 16.
+// constant bank): entry = truth table (bits 0..15) | arity << 16 |
+// (for arity <= 3) the 8-bit LOP3 table of the function << 24, whose entry
+// 4 x2 + 2 x1 + x0 is f(x0, x1, x2) (inputs beyond the arity ignored).
 struct OpTable {
     uint32_t e[256];
 };
@@ -42,6 +44,8 @@ struct DevDesign {
     double *partials;          // [2 * power_blocks]
     double *power;             // [4]: model, hybrid
     unsigned *bar;             // level-barrier arrival counters of the persistent passes (128-byte lines)
+    uint32_t *epoch;           // [4] pass counters: [0] forward (its parity tags the stored pairs)
+    const int32_t *chunk_ptr;  // [n_levels+2] level-aligned chunks of 32 (level 0 = startpoints)
     int *err;                  // device error word of the context (bounded wait gave up)
 };
 
@@ -68,8 +72,16 @@ void launch_bwd_level(const DevDesign &d, const OpTable &ops, int32_t c0, int32_
                       cudaStream_t s);
 void launch_bwd_start(const DevDesign &d, int grad_mode, int tr_mode, float K, float *grad_sp_in, cudaStream_t s);
 
+// pass counters and the dataflow schedule (kern_flow.cu)
+void launch_bump(uint32_t *counter, cudaStream_t s);
+int flow_grid(int which, int sm_count, int blocks_per_sm);   // which: 0 forward; 0 = unavailable
+cudaError_t launch_fwd_flow(const DevDesign &d, const OpTable &ops, int tr_mode, int grid, unsigned sleep_max,
+                            cudaStream_t s);
+
 // persistent schedule (kern_persist.cu): one cooperative launch per pass
-int persist_grid(int which, int sm_count);   // which: 0 forward, 1 simulation, 2 backward; 0 = unavailable
+int persist_grid(int which, int sm_count);   // which: 0 forward, 1 simulation, 2 backward, 3 staged simulation
+bool staged_ok(int T);                       // the staged simulation handles this word count
+cudaError_t launch_sim_staged(const DevDesign &d, const OpTable &ops, int T, int grid, cudaStream_t s);
 size_t persist_bar_words(int n_levels);      // counters needed by the three passes
 cudaError_t launch_fwd_persist(const DevDesign &d, const OpTable &ops, int tr_mode, int grid, cudaStream_t s);
 cudaError_t launch_sim_persist(const DevDesign &d, const OpTable &ops, int T, int grid, cudaStream_t s);

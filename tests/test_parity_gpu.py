@@ -110,7 +110,7 @@ def check_against_oracle(o, g, sp_in, tr_in, cfg):
     return ref
 
 
-@pytest.mark.parametrize("schedule", [0, 1])
+@pytest.mark.parametrize("schedule", [0, 1, 3])
 @pytest.mark.parametrize("grad_mode", [0, 1, 2])
 @pytest.mark.parametrize("tr_mode", [0, 1])
 def test_small_all_modes(dp, ctx, library_text, grad_mode, tr_mode, schedule):
@@ -142,7 +142,7 @@ def test_roofline_full_size(dp, ctx, library_text):
     check_against_oracle(o, g, sp[:, 0], tr[:, 0], cfg)
 
 
-@pytest.mark.parametrize("other_schedule", [0, 1])
+@pytest.mark.parametrize("other_schedule", [0, 1, 3])
 def test_step_is_deterministic(dp, ctx, library_text, other_schedule):
     """Two runs, and the persistent and per-level schedules, agree bit for bit."""
     text = netgen.netlist_text(netgen.WORKLOADS["mid"])
@@ -278,7 +278,7 @@ def test_call_order_and_argument_errors(dp, ctx, library_text):
             dp.dp_simulate(ctx, d, cfg)
         assert e.value.name == "DP_ESTATE"
         for bad_cfg in [dp.config(sim_words=1), dp.config(grad_mode=3), dp.config(beta_min=0.0),
-                        dp.config(vdd=-1.0), dp.config(schedule=2)]:
+                        dp.config(vdd=-1.0), dp.config(schedule=4)]:
             with pytest.raises(dp.DPError) as e:
                 dp.dp_propagate(ctx, d, bad_cfg)
             assert e.value.name == "DP_EINVAL"
