@@ -44,7 +44,7 @@ struct dp_design {
     dp_config graph_cfg{};
     cudaStream_t cap_stream = nullptr, cap_stream2 = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
-    int grid[4] = {0, 0, 0, 0};   // persistent grids: forward, simulation, backward, staged simulation
+    int grid[4] = {0, 0, 0, 0};   // persistent grids: forward, simulation, backward, wide simulation
     int flow_grid[1] = {0};        // dataflow grids: forward
     // launch-shape tuning (defaults, overridable by DP_FLOW_BLOCKS / DP_FLOW_SLEEP for sweeps)
     int flow_blocks_per_sm = 2;
@@ -224,8 +224,8 @@ void q_sim_start(dp_design *D, const dp_config &c, cudaStream_t s) {
 
 // the simulation levels, beta and the hybrid power (after the generator and the forward pass)
 cudaError_t q_sim_levels(dp_design *D, const dp_config &c, cudaStream_t s) {
-    if (persistent(D, c, 3) && dp::staged_ok(c.sim_words)) {
-        cudaError_t e = dp::launch_sim_staged(D->d, D->ops, c.sim_words, D->grid[3], s);
+    if (persistent(D, c, 3) && dp::wide_ok(c.sim_words)) {
+        cudaError_t e = dp::launch_sim_wide(D->d, D->ops, c.sim_words, D->grid[3], s);
         if (e != cudaSuccess) return e;
     } else if (persistent(D, c, 1)) {
         cudaError_t e = dp::launch_sim_persist(D->d, D->ops, c.sim_words, D->grid[1], s);

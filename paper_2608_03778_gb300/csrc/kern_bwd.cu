@@ -16,10 +16,7 @@ __host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 
 
 __device__ __forceinline__ float fanout_sum(const int32_t *__restrict__ fptr, const float *__restrict__ gfo,
                                             int64_t n) {
-    float acc = 0.f;
-    const int32_t e1 = fptr[n + 1];
-    for (int32_t e = fptr[n]; e < e1; e++) acc += gfo[e];
-    return acc;
+    return fanout_sum_l2(gfo, fptr[n], fptr[n + 1]);
 }
 
 // grad_mode 0: g = acc + local; 1: g = beta (acc + local) (Eq. 6); 2: g = acc + beta local

@@ -206,6 +206,23 @@ __device__ __forceinline__ void cell_partials(int k, uint32_t tt, const float (&
     }
 }
 
+// Sum of a net's edge adjoints gfo[e0..e1) in index order (the order every
+// schedule uses, so results match bit for bit).  Loads go out in batches of
+// 8 before the additions, so a high-fanout net costs one L2 round trip per
+// batch instead of one per edge.
+__device__ __forceinline__ float fanout_sum_l2(const float *gfo, int32_t e0, int32_t e1) {
+    float acc = 0.f;
+    for (int32_t e = e0; e < e1; e += 8) {
+        float v[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) v[i] = e + i < e1 ? __ldcg(gfo + e + i) : 0.f;
+#pragma unroll
+        for (int i = 0; i < 8; i++)
+            if (e + i < e1) acc += v[i];
+    }
+    return acc;
+}
+
 // The cell's Boolean function on 64 lanes at once: a multiplexer tree over
 // the truth table, selecting on input 0 first (one LOP3 per mux and half word).
 template <int K>
@@ -269,6 +286,24 @@ __device__ __forceinline__ void cell_bits_lop3(uint32_t lut, const uint64_t (&x0
     }
     w0 = (uint64_t)r0 | ((uint64_t)r1 << 32);
     w1 = (uint64_t)r2 | ((uint64_t)r3 << 32);
+}
+
+// Four 64-bit words of a cell (x[j][i] = word i of input j): two LOP3 pairs
+// for up to 3 inputs, the multiplexer tree for 4.
+__device__ __forceinline__ void cell_words4(int k, uint32_t tt, uint32_t lut, const uint64_t (&x)[4][4],
+                                            uint64_t (&w)[4]) {
+    if (k <= 3) {
+        const uint64_t a0[4] = {x[0][0], x[1][0], x[2][0], 0}, a1[4] = {x[0][1], x[1][1], x[2][1], 0};
+        const uint64_t b0[4] = {x[0][2], x[1][2], x[2][2], 0}, b1[4] = {x[0][3], x[1][3], x[2][3], 0};
+        cell_bits_lop3(lut, a0, a1, w[0], w[1]);
+        cell_bits_lop3(lut, b0, b1, w[2], w[3]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const uint64_t xi[4] = {x[0][i], x[1][i], x[2][i], x[3][i]};
+            w[i] = bits_eval<4>(tt, xi);
+        }
+    }
 }
 
 // both words of a cell, LOP3 for up to 3 inputs, multiplexer tree for 4

@@ -133,8 +133,7 @@ __device__ __forceinline__ BwdStatic bwd_static(const uint4 *fanin, const int32_
 }
 
 __device__ __forceinline__ void bwd_finish(const BwdStatic &s, int64_t n, float *gnet, float *gfo, int grad_mode) {
-    float acc = 0.f;
-    for (int32_t e = s.e0; e < s.e1; e++) acc += __ldcg(gfo + e);
+    const float acc = fanout_sum_l2(gfo, s.e0, s.e1);
     const float g = combine(grad_mode, acc, s.local, s.b);
     gnet[n] = g;
     if (s.k > 0) gfo[s.ep.x] = g * s.d[0];
@@ -164,9 +163,7 @@ __global__ void __launch_bounds__(kPersistThreads) k_bwd_persist(
     }
     if (!level_barrier(bar + 32 * (L - 1), err, gridDim.x, limit)) return;
     for (int64_t k = tid; k < ns; k += T) {
-        float acc = 0.f;
-        const int32_t e1 = fptr[k + 1];
-        for (int32_t e = fptr[k]; e < e1; e++) acc += __ldcg(gfo + e);
+        const float acc = fanout_sum_l2(gfo, fptr[k], fptr[k + 1]);
         const float local = tr_mode ? 2.f * K * cload[k] * pair_qmp(pq[k]) : 0.f;
         const float g = combine(grad_mode, acc, local, grad_mode ? beta[k] : 1.f);
         gnet[k] = g;
@@ -260,160 +257,97 @@ __global__ void __launch_bounds__(kSimThreads) k_sim_persist(const uint4 *__rest
     }
 }
 
-// ---------------------------------------------- simulation, staged rows
-// Same computation as k_sim_persist for even T <= 64, with the fanin rows of
-// each cell brought into shared memory by bulk asynchronous copies
-// (cp.async.bulk, completion counted in bytes on an mbarrier).  Each warp
-// runs its own ring of kSimStages slots, so up to kSimStages cells per warp
-// have their rows in flight while it evaluates the oldest one; no register
-// holds in-flight data.  Every mbarrier wait is bounded; a warp that gives up
-// records the error, waits (bounded) for the copies it issued and returns.
-constexpr int kSimStages = 3;
-constexpr int kStagedMaxT = 64;
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// waits for phase `parity` of the barrier; false when the wait gave up
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, long long limit) {
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > limit) return false;
-    return true;
-}
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_addr(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
-}
-
-__global__ void __launch_bounds__(kSimThreads, 2) k_sim_staged(const uint4 *__restrict__ fanin, uint64_t *words,
+// ------------------------------------------------ simulation, wide lanes
+// Same computation as k_sim_persist for T divisible by 4: 16 lanes per cell,
+// lane h of a half-warp owns words 4h .. 4h+3 of each 64-word chunk, so a
+// warp evaluates two consecutive cells (usually the same logic id, since
+// cells are sorted by it inside a level).  Every lane issues its two 16-byte
+// loads per fanin before using any of them, which keeps several kilobytes in
+// flight per warp; toggle and ones counts are reduced over the half-warp.
+__global__ void __launch_bounds__(kSimThreads, 2) k_sim_wide(const uint4 *__restrict__ fanin, uint64_t *words,
                                                             uint32_t *toggles, uint32_t *ones,
                                                             const int32_t *__restrict__ lvl, int L, int64_t ns,
                                                             int T, OpTable ops, unsigned *bar, int *err,
                                                             long long limit) {
-    extern __shared__ __align__(128) uint64_t rows[];   // [warps][stages][4][T]
-    __shared__ uint64_t mb[kSimThreads / 32][kSimStages];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
     const int64_t gw = spread_warp();
-    const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const uint32_t row_bytes = (uint32_t)T * 8u;
-    uint64_t *my_rows = rows + (size_t)wib * kSimStages * 4 * T;
-    if (lane == 0)
-        for (int s = 0; s < kSimStages; s++) mbar_init(&mb[wib][s], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    uint32_t phase = 0;      // bit s: parity of the next completion of stage s
-    uint32_t pending = 0;    // bit s: stage s has copies in flight
-    bool failed = false;
-
-    // The warp's cells of a level are c = first + i W, i = 0, 1, ...; lane i holds
-    // the fanin record of cell i of the current round of 32 and issues its copies.
-    auto issue = [&](int i, const uint4 &r) {
-        const int s = i % kSimStages;
-        if (lane == i) {
-            const int k = op_arity(ops, r.x >> 24);
-            // the slot was last read through the generic proxy; order that before the async writes
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_arrive_tx(&mb[wib][s], (uint32_t)k * row_bytes);
-            const uint32_t n[4] = {r.x & kMask24, r.y, r.z, r.w};
-#pragma unroll
-            for (int j = 0; j < 4; j++)
-                if (j < k)
-                    bulk_g2s(my_rows + ((size_t)s * 4 + j) * T, words + (size_t)n[j] * T, row_bytes, &mb[wib][s]);
-        }
-        pending |= 1u << s;
-    };
-
+    const int64_t step = 2 * (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int l = 1; l <= L; l++) {
         const int32_t c0 = lvl[l - 1], c1 = lvl[l];
-        const int64_t first = c0 + gw;
-        const int64_t ncells = first < c1 ? (c1 - first + W - 1) / W : 0;
-        // static records of the first round, loaded before the wait
-        uint4 myrec = make_uint4(0, 0, 0, 0);
-        if (lane < ncells) myrec = fanin[first + (int64_t)lane * W];
-        // a warp whose wait gave up still reaches every block barrier; the error word it set
-        // makes the next barrier return false in every block
+        const int64_t cfirst = c0 + 2 * gw + half;
+        uint4 r = make_uint4(0, 0, 0, 0);
+        if (cfirst < c1) r = fanin[cfirst];   // static: loaded before the wait
         if (l > 1 && !level_barrier(bar + 32 * (l - 2), err, gridDim.x, limit)) return;
-        if (failed) continue;
-        // rows written by generic stores of other blocks are read by the async proxy next
-        asm volatile("fence.proxy.async.global;" ::: "memory");
-        for (int64_t base = 0; base < ncells && !failed; base += 32) {
-            const int nr = (int)((ncells - base) < 32 ? (ncells - base) : 32);
-            if (base > 0) {
-                myrec = make_uint4(0, 0, 0, 0);
-                if (lane < nr) myrec = fanin[first + (base + lane) * W];
-            }
-            for (int i = 0; i < kSimStages && i < nr; i++) issue(i, myrec);
-            for (int i = 0; i < nr; i++) {
-                const int64_t c = first + (base + i) * W;
-                const int s = i % kSimStages;
-                if (!mbar_wait_bounded(&mb[wib][s], (phase >> s) & 1u, limit)) {
-                    failed = true;
-                    if (lane == 0) atomicExch(err, 1);
-                    // wait, bounded, for the copies this warp still has in flight
-                    for (int q = 0; q < kSimStages; q++)
-                        if ((pending >> q) & 1u) mbar_wait_bounded(&mb[wib][q], (phase >> q) & 1u, limit);
-                    pending = 0;
-                    break;
-                }
-                phase ^= 1u << s;
-                pending &= ~(1u << s);
-                uint4 r;
-                r.x = __shfl_sync(0xFFFFFFFFu, myrec.x, i);
-                r.y = __shfl_sync(0xFFFFFFFFu, myrec.y, i);
-                r.z = __shfl_sync(0xFFFFFFFFu, myrec.z, i);
-                r.w = __shfl_sync(0xFFFFFFFFu, myrec.w, i);
-                const uint32_t op = r.x >> 24;
-                const int k = op_arity(ops, op);
-                const uint32_t tt = op_tt(ops, op);
-                const int t0 = 2 * lane, t1 = t0 + 1;
-                uint64_t x0[4] = {0, 0, 0, 0}, x1[4] = {0, 0, 0, 0};
-                if (t1 < T) {
+        for (int64_t c = cfirst;; c += step) {
+            const bool valid = c < c1;
+            if (!__any_sync(0xFFFFFFFFu, valid)) break;
+            if (c != cfirst) r = valid ? fanin[c] : make_uint4(0, 0, 0, 0);
+            const uint32_t op = r.x >> 24;
+            const int k = valid ? op_arity(ops, op) : 0;
+            const uint32_t tt = op_tt(ops, op), lut = op_lut(ops, op);
+            const uint32_t nid[4] = {r.x & kMask24, r.y, r.z, r.w};
+            uint64_t *out = words + (size_t)(ns + (valid ? c : 0)) * T;
+            uint32_t tg = 0, on = 0;
+            uint64_t carry = 0;
+            for (int base = 0; base < T; base += 64) {
+                const int t = base + 4 * hl;
+                const bool act = valid && t < T;
+                uint64_t w[4];
+                if (k <= 3) {
+                    uint64_t x[3][4];
 #pragma unroll
-                    for (int q = 0; q < 4; q++)
-                        if (q < k) {
-                            const ulonglong2 v =
-                                *reinterpret_cast<const ulonglong2 *>(my_rows + ((size_t)s * 4 + q) * T + t0);
-                            x0[q] = v.x;
-                            x1[q] = v.y;
+                    for (int j = 0; j < 3; j++) {
+                        x[j][0] = x[j][1] = x[j][2] = x[j][3] = 0;
+                        if (act && j < k) {
+                            const uint64_t *src = words + (size_t)nid[j] * T + t;
+                            const ulonglong2 a = __ldcg(reinterpret_cast<const ulonglong2 *>(src));
+                            const ulonglong2 b = __ldcg(reinterpret_cast<const ulonglong2 *>(src + 2));
+                            x[j][0] = a.x;
+                            x[j][1] = a.y;
+                            x[j][2] = b.x;
+                            x[j][3] = b.y;
                         }
+                    }
+                    const uint64_t a0[4] = {x[0][0], x[1][0], x[2][0], 0}, a1[4] = {x[0][1], x[1][1], x[2][1], 0};
+                    const uint64_t b0[4] = {x[0][2], x[1][2], x[2][2], 0}, b1[4] = {x[0][3], x[1][3], x[2][3], 0};
+                    cell_bits_lop3(lut, a0, a1, w[0], w[1]);
+                    cell_bits_lop3(lut, b0, b1, w[2], w[3]);
+                } else {
+                    // 4-input cells: two words at a time through the multiplexer tree
+#pragma unroll
+                    for (int h2 = 0; h2 < 2; h2++) {
+                        uint64_t x0[4] = {0, 0, 0, 0}, x1[4] = {0, 0, 0, 0};
+                        if (act)
+#pragma unroll
+                            for (int j = 0; j < 4; j++) {
+                                const ulonglong2 a = __ldcg(
+                                    reinterpret_cast<const ulonglong2 *>(words + (size_t)nid[j] * T + t + 2 * h2));
+                                x0[j] = a.x;
+                                x1[j] = a.y;
+                            }
+                        w[2 * h2] = bits_eval<4>(tt, x0);
+                        w[2 * h2 + 1] = bits_eval<4>(tt, x1);
+                    }
                 }
-                uint64_t w0, w1;
-                cell_bits2(k, tt, op_lut(ops, op), x0, x1, w0, w1);
-                const uint64_t prev = __shfl_up_sync(0xFFFFFFFFu, w1, 1);
-                uint32_t tg = 0, on = 0;
-                if (t1 < T) {
-                    *reinterpret_cast<ulonglong2 *>(words + (size_t)(ns + c) * T + t0) = make_ulonglong2(w0, w1);
-                    on = __popcll(w0) + __popcll(w1);
-                    tg = __popcll(w1 ^ w0) + (lane > 0 ? __popcll(w0 ^ prev) : 0);
+                const uint64_t prev = __shfl_up_sync(0xFFFFFFFFu, w[3], 1, 16);
+                const uint64_t last = __shfl_sync(0xFFFFFFFFu, w[3], 15, 16);
+                if (act) {
+                    *reinterpret_cast<ulonglong2 *>(out + t) = make_ulonglong2(w[0], w[1]);
+                    *reinterpret_cast<ulonglong2 *>(out + t + 2) = make_ulonglong2(w[2], w[3]);
+                    on += __popcll(w[0]) + __popcll(w[1]) + __popcll(w[2]) + __popcll(w[3]);
+                    tg += __popcll(w[1] ^ w[0]) + __popcll(w[2] ^ w[1]) + __popcll(w[3] ^ w[2]);
+                    if (t > 0) tg += __popcll(w[0] ^ (hl > 0 ? prev : carry));
                 }
-                tg = __reduce_add_sync(0xFFFFFFFFu, tg);
-                on = __reduce_add_sync(0xFFFFFFFFu, on);
-                if (lane == 0) {
-                    toggles[ns + c] = tg;
-                    ones[ns + c] = on;
-                }
-                __syncwarp();   // every lane has read stage s before it is refilled
-                if (i + kSimStages < nr) issue(i + kSimStages, myrec);
+                carry = last;
+            }
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) {
+                tg += __shfl_xor_sync(0xFFFFFFFFu, tg, o);
+                on += __shfl_xor_sync(0xFFFFFFFFu, on, o);
+            }
+            if (valid && hl == 0) {
+                toggles[ns + c] = tg;
+                ones[ns + c] = on;
             }
         }
     }
@@ -444,16 +378,9 @@ size_t bar_bytes(const DevDesign &d) { return sizeof(unsigned) * 32 * ((size_t)d
 
 }  // namespace
 
-static size_t staged_smem(int T) { return sizeof(uint64_t) * (size_t)(kSimThreads / 32) * kSimStages * 4 * T; }
-
-int staged_grid(int sm_count) {
-    const size_t smem = staged_smem(kStagedMaxT);
-    if (cudaFuncSetAttribute(k_sim_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
-    }
+int wide_grid(int sm_count) {
     int per = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sim_staged, kSimThreads, smem) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sim_wide, kSimThreads, 0) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -463,7 +390,7 @@ int staged_grid(int sm_count) {
 int persist_grid(int which, int sm_count) {
     int per = 0;
     cudaError_t e;
-    if (which == 3) return staged_grid(sm_count);
+    if (which == 3) return wide_grid(sm_count);
     if (which == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fwd_persist, kPersistThreads, 0);
     else if (which == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sim_persist, kSimThreads, 0);
     else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bwd_persist, kPersistThreads, 0);
@@ -492,23 +419,13 @@ cudaError_t launch_sim_persist(const DevDesign &d, const OpTable &ops, int T, in
                        d.n_start, T, ops, bar, d.err, kWaitLimitCycles);
 }
 
-bool staged_ok(int T) { return T >= 2 && T <= kStagedMaxT && (T & 1) == 0; }
+bool wide_ok(int T) { return T >= 4 && (T & 3) == 0; }
 
-cudaError_t launch_sim_staged(const DevDesign &d, const OpTable &ops, int T, int grid, cudaStream_t s) {
+cudaError_t launch_sim_wide(const DevDesign &d, const OpTable &ops, int T, int grid, cudaStream_t s) {
     unsigned *bar = d.bar + 32 * ((size_t)d.n_levels + 2);
     cudaMemsetAsync(bar, 0, bar_bytes(d), s);
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3((unsigned)kSimThreads);
-    cfg.dynamicSmemBytes = staged_smem(T);
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeCooperative;
-    at[0].val.cooperative = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_sim_staged, d.fanin, d.words, d.toggles, d.ones, d.lvl, d.n_levels, d.n_start,
-                              T, ops, bar, d.err, kWaitLimitCycles);
+    return launch_coop(k_sim_wide, grid, kSimThreads, s, d.fanin, d.words, d.toggles, d.ones, d.lvl, d.n_levels,
+                       d.n_start, T, ops, bar, d.err, kWaitLimitCycles);
 }
 
 cudaError_t launch_bwd_persist(const DevDesign &d, const OpTable &ops, int grad_mode, int tr_mode, float K,

@@ -79,9 +79,9 @@ cudaError_t launch_fwd_flow(const DevDesign &d, const OpTable &ops, int tr_mode,
                             cudaStream_t s);
 
 // persistent schedule (kern_persist.cu): one cooperative launch per pass
-int persist_grid(int which, int sm_count);   // which: 0 forward, 1 simulation, 2 backward, 3 staged simulation
-bool staged_ok(int T);                       // the staged simulation handles this word count
-cudaError_t launch_sim_staged(const DevDesign &d, const OpTable &ops, int T, int grid, cudaStream_t s);
+int persist_grid(int which, int sm_count);   // which: 0 forward, 1 simulation, 2 backward, 3 wide simulation
+bool wide_ok(int T);                         // the wide simulation handles this word count
+cudaError_t launch_sim_wide(const DevDesign &d, const OpTable &ops, int T, int grid, cudaStream_t s);
 size_t persist_bar_words(int n_levels);      // counters needed by the three passes
 cudaError_t launch_fwd_persist(const DevDesign &d, const OpTable &ops, int tr_mode, int grid, cudaStream_t s);
 cudaError_t launch_sim_persist(const DevDesign &d, const OpTable &ops, int T, int grid, cudaStream_t s);
