@@ -769,6 +769,32 @@ int orc_simulate(const void *h, const float *sp_in, const float *tr_in, uint64_t
     return 0;
 }
 
+/* Logic values of every net for 64 input vectors at once (Eq. 3 needs val_i(v)):
+ * bit b of start_words[k] is the value of startpoint k in vector b; each cell, in
+ * topological order, ORs the AND-terms of its true minterms over its input words.
+ * net_words[nn] in declaration order. */
+void orc_logic_words(const void *h, const uint64_t *start_words, uint64_t *net_words) {
+    const Orc *o = (const Orc *)h;
+    for (int64_t n = 0; n < o->nn; n++) net_words[n] = 0;
+    for (int64_t k = 0; k < o->ns; k++) net_words[o->start_net[k]] = start_words[k];
+    for (int64_t t0 = 0; t0 < o->nc; t0++) {
+        int64_t c = o->topo[t0];
+        const LibCell *L = &o->lib[o->cell_lib[c]];
+        int64_t M = (int64_t)1 << L->k;
+        uint64_t acc = 0;
+        for (int64_t m = 0; m < M; m++) {
+            if (!L->tt[m]) continue;
+            uint64_t term = ~0ull;
+            for (int i = 0; i < L->k; i++) {
+                uint64_t x = net_words[o->fin_net[o->fin_ptr[c] + i]];
+                term &= ((m >> i) & 1) ? x : ~x;
+            }
+            acc |= term;
+        }
+        net_words[o->cell_out[c]] = acc;
+    }
+}
+
 /* Sec. III-D, Eq. 4 and Eq. 5: TR_acc = toggles / (64 (T-1)), beta = clip(TR_acc / TR_model),
  * hybrid activity = beta * TR_model. */
 void orc_hybrid(const void *h, const double *tr_model, const uint32_t *toggles, int T, double beta_min,

@@ -10,6 +10,7 @@ appearance).
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -74,6 +75,7 @@ def _load():
             L.orc_simulate.argtypes = [_P, _F, _F, ctypes.c_uint64, ctypes.c_int, _opt(_U64), _U32, _U32]
             L.orc_simulate.restype = ctypes.c_int
             L.orc_hybrid.argtypes = [_P, _D, _U32, ctypes.c_int, ctypes.c_double, ctypes.c_double, _D, _D]
+            L.orc_logic_words.argtypes = [_P, _U64, _U64]
             _lib = L
     return _lib
 
@@ -189,3 +191,81 @@ class Oracle:
         g.update(sp=sp, tr=tr, toggles=tg, ones=on, beta=beta, tr_hyb=trh, power_model=p_model,
                  power_hybrid=p_hyb)
         return g
+
+    # ---- batched scenarios, Algorithm 4 and Eq. 3 ----
+    # A batch is S independent scenarios; arrays are [rows, S] (scenario innermost).
+
+    def forward_batch(self, sp_in, tr_in, tr_mode: int = 0):
+        """Per-net SP and TR [n_nets, S] of every scenario (each an independent forward pass)."""
+        sp_in = np.asarray(sp_in)
+        S = sp_in.shape[1]
+        sp = np.zeros((self.n_nets, S))
+        tr = np.zeros((self.n_nets, S))
+        for s in range(S):
+            sp[:, s], tr[:, s] = self.forward(sp_in[:, s], np.asarray(tr_in)[:, s], tr_mode)
+        return sp, tr
+
+    def backward_batch(self, sp_in, tr_in, weights=None, tr_mode: int = 0, vdd: float = 0.8,
+                       fclk: float = 1e9) -> dict:
+        """Model gradients (Eq. 7) of sum_s w_s P_s, per scenario ([rows, S]); the cap
+        gradients also summed over the scenarios ("grad_pincap_sum", "grad_cload_sum")."""
+        sp_in = np.asarray(sp_in)
+        tr_in = np.asarray(tr_in)
+        S = sp_in.shape[1]
+        w = np.ones(S) if weights is None else np.asarray(weights, np.float64)
+        out = {k: np.zeros((n, S)) for k, n in [("grad_sp_in", self.n_start), ("grad_tr_in", self.n_start),
+                                                ("grad_pincap", self.n_cells), ("grad_cload", self.n_nets)]}
+        for s in range(S):
+            g = self.backward(sp_in[:, s], tr_in[:, s], None, 0, tr_mode, vdd, fclk)
+            for k in out:
+                out[k][:, s] = w[s] * g[k]
+        out["grad_pincap_sum"] = out["grad_pincap"].sum(axis=1)
+        out["grad_cload_sum"] = out["grad_cload"].sum(axis=1)
+        return out
+
+    def logic(self, start_words) -> np.ndarray:
+        """Logic value words of every net (bit b = vector b) from startpoint words."""
+        out = np.zeros(self.n_nets, np.uint64)
+        _load().orc_logic_words(self._h, np.ascontiguousarray(start_words, np.uint64), out)
+        return out
+
+    def p_virus(self, sp_in):
+        """Eq. 3 for candidate inputs sp_in [n_start, S] (Algorithm 4, last steps): v0 =
+        [sp >= 0.5] decided in binary32, v1 = not v0, logic values of both vectors, and
+        per scenario the exactly rounded sum of C_load (fF) over the nets that differ.
+        Returns (p_virus[S], v0[n_start, S] as uint8)."""
+        sp32 = np.asarray(sp_in, np.float32)
+        S = sp32.shape[1]
+        v0 = (sp32 >= np.float32(0.5)).astype(np.uint8)
+        cl = self.cload()
+        out = np.zeros(S)
+        for s in range(S):
+            # bit 0 carries v0, bit 1 carries v1 = not v0
+            w = v0[:, s].astype(np.uint64) | ((1 - v0[:, s]).astype(np.uint64) << np.uint64(1))
+            vals = self.logic(w)
+            diff = ((vals ^ (vals >> np.uint64(1))) & np.uint64(1)).astype(bool)
+            out[s] = math.fsum(cl[diff].tolist())
+        return out, v0
+
+    def ascent(self, sp_in, tr_in, steps: int, eta_sp: float, eta_tr: float = 0.0, tr_mode: int = 1,
+               vdd: float = 0.8, fclk: float = 1e9):
+        """Algorithm 4 on every scenario ([n_start, S]) in binary64: each step takes the gradient of
+        the proxy sum_n C_n TR_n (the power divided by K = 1/2 Vdd^2 f; Eq. 9 when tr_mode is 1)
+        at the current inputs, then SP <- clip(SP + eta_sp dSP, 0, 1) and, in tr_mode 0,
+        TR <- clip(TR + eta_tr dTR, 0, 1).  Returns the final (sp, tr)."""
+        K = 0.5 * vdd * vdd * fclk * 1e-15
+        sp = np.array(sp_in, np.float64)
+        tr = np.array(tr_in, np.float64)
+        for _ in range(steps):
+            for s in range(sp.shape[1]):
+                g = self.backward(sp[:, s], tr[:, s], None, 0, tr_mode, vdd, fclk)
+                sp[:, s] = np.clip(sp[:, s] + eta_sp * (g["grad_sp_in"] / K), 0.0, 1.0)
+                if tr_mode == 0:
+                    tr[:, s] = np.clip(tr[:, s] + eta_tr * (g["grad_tr_in"] / K), 0.0, 1.0)
+        return sp, tr
+
+    def proxy(self, sp_in, tr_in, tr_mode: int = 1) -> float:
+        """sum_n C_n TR_n in fF (the power without K; Eq. 9 when tr_mode is 1)."""
+        _, tr = self.forward(sp_in, tr_in, tr_mode)
+        cl = self.cload()
+        return math.fsum((tr * cl).tolist())
