@@ -191,14 +191,20 @@ dp_status dp_design_upload(dp_ctx *ctx, const dp_compiled *c, dp_design **out);
 void dp_design_free(dp_design *d);
 dp_status dp_design_info(const dp_design *d, dp_info *info);
 
-/* Startpoint SP and TR (Sec. III-A), n_start values each, binary32.  Only
- * n_scen = 1 is supported (DP_EUNSUPPORTED otherwise).  SP must lie in [0,1]
- * and TR in [0,1]; values are not checked on the device path. */
+/* Startpoint SP and TR (Sec. III-A), binary32.  n_scen = 1: n_start values
+ * each, analysed by the single-scenario path (float-float pairs, simulation,
+ * hybrid).  n_scen > 1: the same as dp_set_inputs_batch.  SP must lie in
+ * [0,1] and TR in [0,1]; values are not checked on the device path. */
 dp_status dp_set_inputs(dp_design *d, const float *sp, const float *tr, int32_t n_scen, int on_device);
+
+/* Switches the stream that later calls on this context queue their work on
+ * (e.g. PyTorch's current stream, or a stream being captured into a graph). */
+dp_status dp_set_stream(dp_ctx *ctx, void *cuda_stream);
 
 /* Sizing delta: sets the input pin cap (fF) of n cells given by cell-line index
  * and updates the loads C_load of the nets they read (Eq. 1). Indices must be
- * in range (checked for host input only). */
+ * in range (checked for host input only).  cells = NULL with n = n_cells sets
+ * every cell's cap, in cell-line order. */
 dp_status dp_set_pincap(dp_design *d, const int32_t *cells, const float *pincap, int32_t n, int on_device);
 
 /* Pass 1 (Sec. III-B, Algorithm 2): SP and TR_model (Eq. 2) of every net, and the
@@ -212,8 +218,13 @@ dp_status dp_propagate(dp_design *d, const dp_config *cfg);
 dp_status dp_simulate(dp_design *d, const dp_config *cfg);
 
 /* Total switching power (Eq. 1) in watts into watts[0] (host):
- * hybrid = 0 model TR, 1 hybrid TR.  Synchronises. */
+ * hybrid = 0 model TR, 1 hybrid TR.  Synchronises.  Batched inputs: one
+ * value per scenario, watts[n_scen], model TR only. */
 dp_status dp_total_power(dp_design *d, int hybrid, double *watts);
+
+/* dp_total_power into host or device memory; with on_device = 1 the copy is
+ * queued on the context stream without synchronising. */
+dp_status dp_get_power(dp_design *d, int hybrid, double *watts, int on_device);
 
 /* Sec. III-E: gradient of the power with respect to the startpoint SP
  * (grad_sp_in[n_start]), startpoint TR (grad_tr_in[n_start]), the input pin
@@ -225,7 +236,9 @@ dp_status dp_backward(dp_design *d, const dp_config *cfg, float *grad_sp_in, flo
                       float *grad_pincap, float *grad_cload, int on_device);
 
 /* Per-net results: SP, TR_model, beta, hybrid TR, toggle and ones counts.
- * Any output may be NULL; beta/tr_hyb/toggles/ones need dp_simulate. */
+ * Any output may be NULL; beta/tr_hyb/toggles/ones need dp_simulate.
+ * Batched inputs: sp and tr as [n_nets][n_scen] (scenario innermost); the
+ * simulation outputs must be NULL (DP_EUNSUPPORTED). */
 dp_status dp_get_nets(dp_design *d, float *sp, float *tr, float *beta, float *tr_hyb, uint32_t *toggles,
                       uint32_t *ones, int on_device);
 
@@ -237,8 +250,66 @@ dp_status dp_step(dp_design *d, const dp_config *cfg, float *grad_sp_in, float *
 
 /* Device time in milliseconds of the last dp_step / dp_propagate / dp_simulate /
  * dp_backward per phase (CUDA events on the context stream; synchronises):
- * ms[0] forward, ms[1] simulation + hybrid, ms[2] backward, ms[3] power + cap gradients. */
-dp_status dp_phase_times(dp_design *d, float *ms4);
+ * ms5[0] forward + model power, ms5[1] simulation levels (the bitwise cells;
+ * in dp_step the startpoint generator runs beside the forward pass),
+ * ms5[2] beta + hybrid power, ms5[3] backward, ms5[4] gradient outputs. */
+dp_status dp_phase_times(dp_design *d, float *ms5);
+
+/* ------------------ batched scenarios (S scenarios per launch) ------------------
+ * Every per-scenario array is [rows][n_scen]: row-major with the scenario
+ * innermost, rows in the orders above.  After dp_set_inputs_batch, the calls
+ * dp_propagate, dp_total_power / dp_get_power, dp_backward and dp_get_nets
+ * work on the batch; dp_simulate and dp_step return DP_EUNSUPPORTED (the
+ * simulation and the hybrid objective run on single-scenario inputs).
+ * Probabilities are float-float (P, P(net=0)) pairs renormalised at every cell,
+ * as for one scenario; the adjoint is binary32;
+ * powers and scenario sums are FP64 in a fixed order (reproducible).  Calls
+ * with device outputs neither allocate nor synchronise once a call with the
+ * largest n_scen has been made, so they may be captured into a CUDA graph. */
+
+/* Stages n_scen scenarios of startpoint SP and TR, sp[n_start][n_scen] and
+ * tr[n_start][n_scen].  The first call with a larger n_scen allocates the
+ * batch buffers (about (16 n_nets + 4 n_edges + 12 n_start) bytes per
+ * scenario) and must not be made under stream capture (DP_ESTATE); a call
+ * with a new n_scen outside capture also runs the launch-shape autotuner
+ * (times every candidate shape of the forward and reverse kernels on the
+ * staged inputs and keeps the fastest; synchronises).  The environment
+ * variable DP_BATCH_SHAPE="bx,by[,bx2,by2]" fixes the shapes instead.
+ * Every shape gives bitwise identical results. */
+dp_status dp_set_inputs_batch(dp_design *d, const float *sp, const float *tr, int32_t n_scen, int on_device);
+
+/* Shapes in use (bx threads over scenarios x by cells per block) for the
+ * forward (shape4[0..1]) and the reverse pass (shape4[2..3]), and the tuner's
+ * best times in ms (ms2, may be NULL; 0 when fixed by the environment). */
+dp_status dp_batch_tuning(const dp_design *d, int32_t *shape4, float *ms2);
+
+/* Reverse pass of the model power (Sec. III-E, Eq. 7) for every scenario,
+ * scaled by weights[n_scen] (NULL: all 1): the gradient of
+ * sum_s weights[s] * P_s, i.e. the vector-Jacobian product an autograd
+ * engine asks for.  weights live where the outputs live (on_device).
+ * Outputs (any may be NULL): grad_sp_in and grad_tr_in [n_start][n_scen];
+ * grad_pincap [n_cells][n_scen] and grad_cload [n_nets][n_scen], or, with
+ * cap_reduce = 1, summed over the scenarios in FP64 into [n_cells] and
+ * [n_nets] (the gradient with respect to caps shared by all scenarios).
+ * Needs dp_propagate with the same tr_mode and cfg->grad_mode = 0
+ * (DP_EUNSUPPORTED otherwise).  Single-scenario inputs: weights must be NULL
+ * and the call is dp_backward. */
+dp_status dp_backward_weighted(dp_design *d, const dp_config *cfg, const double *weights, int32_t cap_reduce,
+                               float *grad_sp_in, float *grad_tr_in, float *grad_pincap, float *grad_cload,
+                               int on_device);
+
+/* One projected gradient-ascent step of Algorithm 4 on device arrays:
+ * x[i] <- clip(x[i] + eta * g[i], 0, 1), in binary32 with the product and the
+ * sum each rounded once.  Queued on the context stream; no synchronisation. */
+dp_status dp_ascent_step(dp_ctx *ctx, float *x, const float *g, int64_t n, float eta);
+
+/* P_virus of Eq. 3 for n_scen candidate inputs sp[n_start][n_scen]
+ * (Algorithm 4, last steps): v0 = [sp >= 0.5] (compared in binary32),
+ * v1 = not v0, two bitwise forward passes, and per scenario the sum of
+ * C_load (fF, FP64, fixed order) over the nets whose values differ between
+ * v0 and v1.  p_virus[n_scen]; v0[n_start][n_scen] as 0/1 bytes (may be NULL).
+ * Works on any design state.  The first call with a larger n_scen allocates. */
+dp_status dp_virus_eval(dp_design *d, const float *sp, int32_t n_scen, uint8_t *v0, double *p_virus, int on_device);
 
 /* Number of kernels the last dp_step launched: the kernel nodes of its CUDA
  * graph plus the output kernels queued after it (0 before the first dp_step). */

@@ -8,59 +8,15 @@
 #include <string>
 #include <vector>
 
+#include "capi_internal.h"
 #include "compiled.h"
-#include "diffpower.h"
-#include "kernels.h"
 
-struct dp_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    int sm_count = 0;
-    int clock_khz = 0;
-    int *d_err = nullptr;   // device error word: a bounded wait gave up
-    std::string err;
-};
-
-struct dp_design {
-    dp_ctx *ctx = nullptr;
-    dp::DevDesign d{};
-    dp::OpTable ops{};
-    std::vector<int32_t> lvl_ptr;
-    int64_t n_edges = 0;
-    int32_t n_ops = 0;
-    std::vector<void *> allocs;
-    size_t bytes = 0;
-    int words_T = 0;
-    // output staging for host outputs
-    float *st_gsp = nullptr, *st_gtr = nullptr, *st_gpin = nullptr, *st_gcl = nullptr;
-    // state
-    bool inputs_set = false;
-    bool fwd_valid = false;
-    int fwd_tr_mode = -1;
-    bool sim_valid = false;
-    // graph of the whole step for one config
-    cudaGraphExec_t graph = nullptr;
-    dp_config graph_cfg{};
-    cudaStream_t cap_stream = nullptr, cap_stream2 = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
-    int grid[4] = {0, 0, 0, 0};   // persistent grids: forward, simulation, backward, wide simulation
-    int flow_grid[1] = {0};        // dataflow grids: forward
-    // launch-shape tuning (defaults, overridable by DP_FLOW_BLOCKS / DP_FLOW_SLEEP for sweeps)
-    int flow_blocks_per_sm = 2;
-    unsigned flow_sleep = 0;
-    int64_t graph_kernels = 0;
-    int64_t step_kernels = 0;
-    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-    bool ev_valid[5] = {false, false, false, false, false};
-};
-
-namespace {
+namespace dpi {
 
 // Host-side fault injection for tests: DP_FAULT=alloc:N fails the N-th
 // device allocation of the process with DP_ENOMEM (no GPU fault involved).
-long g_alloc_count = 0;
-long fault_alloc_at() {
+static long g_alloc_count = 0;
+static long fault_alloc_at() {
     static long at = -2;
     if (at == -2) {
         at = -1;
@@ -69,18 +25,6 @@ long fault_alloc_at() {
     }
     return at;
 }
-
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
 
 dp_status set_err(dp_ctx *c, dp_status s, const std::string &m) {
     if (c) c->err = m;
@@ -95,7 +39,6 @@ dp_status cuda_err(dp_ctx *c, cudaError_t e, const char *where) {
 
 dp_status launch_check(dp_ctx *c, const char *where) { return cuda_err(c, cudaGetLastError(), where); }
 
-// Reads and clears the device error word (synchronises the stream).
 dp_status check_device_error(dp_ctx *c) {
     int v = 0;
     cudaError_t e = cudaMemcpyAsync(&v, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
@@ -109,22 +52,29 @@ dp_status check_device_error(dp_ctx *c) {
     return DP_OK;
 }
 
-template <class T>
-dp_status dalloc(dp_design *D, T **p, size_t count) {
+dp_status alloc_into(dp_ctx *c, void **p, size_t bytes, std::vector<void *> *list, size_t *total) {
     *p = nullptr;
-    size_t bytes = sizeof(T) * (count ? count : 1);
     long n = ++g_alloc_count;
-    if (fault_alloc_at() == n) return set_err(D->ctx, DP_ENOMEM, "injected allocation failure (DP_FAULT)");
+    if (fault_alloc_at() == n) return set_err(c, DP_ENOMEM, "injected allocation failure (DP_FAULT)");
     void *v = nullptr;
-    cudaError_t e = cudaMalloc(&v, bytes);
+    cudaError_t e = cudaMalloc(&v, bytes ? bytes : 1);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        return cuda_err(D->ctx, e, "cudaMalloc");
+        return cuda_err(c, e, "cudaMalloc");
     }
-    D->allocs.push_back(v);
-    D->bytes += bytes;
-    *p = static_cast<T *>(v);
+    list->push_back(v);
+    *total += bytes;
+    *p = v;
     return DP_OK;
+}
+
+bool capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &st) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return st != cudaStreamCaptureStatusNone;
 }
 
 double power_K(const dp_config &c) { return 0.5 * c.vdd * c.vdd * c.fclk * 1e-15; }
@@ -142,6 +92,12 @@ dp_status check_cfg(dp_ctx *ctx, const dp_config *c) {
     return DP_OK;
 }
 
+}  // namespace dpi
+
+using namespace dpi;
+
+namespace {
+
 void free_design(dp_design *D) {
     if (!D) return;
     DeviceGuard g(D->ctx ? D->ctx->device : 0);
@@ -153,6 +109,7 @@ void free_design(dp_design *D) {
     if (D->join) cudaEventDestroy(D->join);
     for (auto &e : D->ev)
         if (e) cudaEventDestroy(e);
+    free_batch(D);
     for (void *p : D->allocs) cudaFree(p);
     delete D;
 }
@@ -234,14 +191,14 @@ cudaError_t q_sim_levels(dp_design *D, const dp_config &c, cudaStream_t s) {
         for (int l = 1; l <= D->d.n_levels; l++)
             dp::launch_sim_level(D->d, D->ops, D->lvl_ptr[l - 1], D->lvl_ptr[l], c.sim_words, s);
     }
-    dp::launch_hybrid(D->d, c.sim_words, c.tr_mode, c.beta_min, c.beta_max, s);
-    dp::launch_power(D->d, true, power_K(c), 1, s);
     return cudaGetLastError();
 }
 
-cudaError_t q_simulate(dp_design *D, const dp_config &c, cudaStream_t s) {
-    q_sim_start(D, c, s);
-    return q_sim_levels(D, c, s);
+// beta, hybrid TR and the hybrid power (after the simulation levels)
+cudaError_t q_hybrid(dp_design *D, const dp_config &c, cudaStream_t s) {
+    dp::launch_hybrid(D->d, c.sim_words, c.tr_mode, c.beta_min, c.beta_max, s);
+    dp::launch_power(D->d, true, power_K(c), 1, s);
+    return cudaGetLastError();
 }
 
 cudaError_t q_backward(dp_design *D, const dp_config &c, float *gsp, cudaStream_t s) {
@@ -345,6 +302,12 @@ dp_status dp_sync(dp_ctx *c) {
     DeviceGuard g(c->device);
     dp_status s = cuda_err(c, cudaStreamSynchronize(c->stream), "dp_sync");
     return s == DP_OK ? check_device_error(c) : s;
+}
+
+dp_status dp_set_stream(dp_ctx *c, void *cuda_stream) {
+    if (!c) return DP_EINVAL;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    return DP_OK;
 }
 
 dp_status dp_selftest_wait(dp_ctx *c, double seconds) {
@@ -492,14 +455,15 @@ dp_status dp_design_info(const dp_design *D, dp_info *info) {
     info->n_edges = D->n_edges;
     info->n_levels = D->d.n_levels;
     info->n_ops = D->n_ops;
-    info->device_bytes = D->bytes;
+    info->device_bytes = D->bytes + D->batch.bytes + D->batch.vbytes;
     return DP_OK;
 }
 
 dp_status dp_set_inputs(dp_design *D, const float *sp, const float *tr, int32_t n_scen, int on_device) {
     if (!D) return DP_EINVAL;
     dp_ctx *c = D->ctx;
-    if (n_scen != 1) return set_err(c, DP_EUNSUPPORTED, "only one scenario per design is supported");
+    if (n_scen < 1) return set_err(c, DP_EINVAL, "n_scen must be at least 1");
+    if (n_scen > 1) return dp_set_inputs_batch(D, sp, tr, n_scen, on_device);
     const int64_t ns = D->d.n_start;
     if (ns && (!sp || !tr)) return set_err(c, DP_EINVAL, "NULL input");
     if (!on_device)
@@ -513,15 +477,18 @@ dp_status dp_set_inputs(dp_design *D, const float *sp, const float *tr, int32_t 
     if (ns && e == cudaSuccess) e = cudaMemcpyAsync(D->d.tr_in, tr, sizeof(float) * (size_t)ns, kind, c->stream);
     if (e != cudaSuccess) return cuda_err(c, e, "dp_set_inputs");
     D->inputs_set = true;
+    D->batched = false;
     D->fwd_valid = false;
     D->sim_valid = false;
+    D->batch.fwd_valid = false;
     return DP_OK;
 }
 
 dp_status dp_set_pincap(dp_design *D, const int32_t *cells, const float *caps, int32_t n, int on_device) {
     if (!D) return DP_EINVAL;
     dp_ctx *c = D->ctx;
-    if (n < 0 || (n > 0 && (!cells || !caps))) return set_err(c, DP_EINVAL, "bad sizing delta");
+    if (n < 0 || (n > 0 && !caps)) return set_err(c, DP_EINVAL, "bad sizing delta");
+    if (!cells && n != D->d.n_cells) return set_err(c, DP_EINVAL, "a NULL cell list needs one cap per cell");
     if (n == 0) return DP_OK;
     DeviceGuard g(c->device);
     int32_t *dc = nullptr;
@@ -530,11 +497,12 @@ dp_status dp_set_pincap(dp_design *D, const int32_t *cells, const float *caps, i
     cudaError_t e = cudaSuccess;
     if (!on_device) {
         for (int32_t i = 0; i < n; i++)
-            if (cells[i] < 0 || cells[i] >= D->d.n_cells || !(caps[i] >= 0.f) || !std::isfinite(caps[i]))
+            if ((cells && (cells[i] < 0 || cells[i] >= D->d.n_cells)) || !(caps[i] >= 0.f) || !std::isfinite(caps[i]))
                 return set_err(c, DP_EINVAL, "cell index or pin cap out of range");
-        e = cudaMallocAsync((void **)&dc, sizeof(int32_t) * (size_t)n, c->stream);
+        if (cells) e = cudaMallocAsync((void **)&dc, sizeof(int32_t) * (size_t)n, c->stream);
         if (e == cudaSuccess) e = cudaMallocAsync((void **)&dv, sizeof(float) * (size_t)n, c->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(dc, cells, sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess && cells)
+            e = cudaMemcpyAsync(dc, cells, sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(dv, caps, sizeof(float) * (size_t)n, cudaMemcpyHostToDevice, c->stream);
         if (e != cudaSuccess) {
             if (dc) cudaFreeAsync(dc, c->stream);
@@ -549,7 +517,7 @@ dp_status dp_set_pincap(dp_design *D, const int32_t *cells, const float *caps, i
     dp::launch_cload(D->d, c->stream);
     dp_status s = launch_check(c, "dp_set_pincap");
     if (!on_device) {
-        cudaFreeAsync(dc, c->stream);
+        if (dc) cudaFreeAsync(dc, c->stream);
         cudaFreeAsync(dv, c->stream);
     }
     // loads changed: the powers and gradients must be recomputed (SP and TR stay valid)
@@ -561,6 +529,7 @@ dp_status dp_propagate(dp_design *D, const dp_config *cfg) {
     dp_status s = check_cfg(D->ctx, cfg);
     if (s != DP_OK) return s;
     if (!D->inputs_set) return set_err(D->ctx, DP_ESTATE, "dp_propagate before dp_set_inputs");
+    if (D->batched) return batch_propagate(D, *cfg);
     DeviceGuard g(D->ctx->device);
     cudaStream_t st = D->ctx->stream;
     rec(D, 0, st);
@@ -577,34 +546,44 @@ dp_status dp_simulate(dp_design *D, const dp_config *cfg) {
     if (!D) return DP_EINVAL;
     dp_status s = check_cfg(D->ctx, cfg);
     if (s != DP_OK) return s;
+    if (D->batched) return set_err(D->ctx, DP_EUNSUPPORTED, "the simulation runs on single-scenario inputs");
     if (!D->fwd_valid || D->fwd_tr_mode != cfg->tr_mode)
         return set_err(D->ctx, DP_ESTATE, "dp_simulate needs dp_propagate with the same tr_mode");
     DeviceGuard g(D->ctx->device);
     if ((s = ensure_words(D, cfg->sim_words)) != DP_OK) return s;
     cudaStream_t st = D->ctx->stream;
     rec(D, 1, st);
-    cudaError_t le = q_simulate(D, *cfg, st);
+    q_sim_start(D, *cfg, st);
+    cudaError_t le = q_sim_levels(D, *cfg, st);
     rec(D, 2, st);
+    if (le == cudaSuccess) le = q_hybrid(D, *cfg, st);
+    rec(D, 3, st);
     if ((s = cuda_err(D->ctx, le, "dp_simulate")) != DP_OK) return s;
     D->sim_valid = true;
     return DP_OK;
 }
 
-dp_status dp_total_power(dp_design *D, int hybrid, double *watts) {
+dp_status dp_total_power(dp_design *D, int hybrid, double *watts) { return dp_get_power(D, hybrid, watts, 0); }
+
+dp_status dp_get_power(dp_design *D, int hybrid, double *watts, int on_device) {
     if (!D || !watts) return DP_EINVAL;
+    if (D->batched) return batch_get_power(D, hybrid, watts, on_device);
     if (!D->fwd_valid || (hybrid && !D->sim_valid))
         return set_err(D->ctx, DP_ESTATE, hybrid ? "hybrid power needs dp_simulate" : "power needs dp_propagate");
     DeviceGuard g(D->ctx->device);
-    cudaError_t e = cudaMemcpyAsync(watts, D->d.power + (hybrid ? 1 : 0), sizeof(double), cudaMemcpyDeviceToHost,
-                                    D->ctx->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(D->ctx->stream);
-    if (e != cudaSuccess) return cuda_err(D->ctx, e, "dp_total_power");
+    cudaError_t e = cudaMemcpyAsync(watts, D->d.power + (hybrid ? 1 : 0), sizeof(double),
+                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, D->ctx->stream);
+    if (e != cudaSuccess) return cuda_err(D->ctx, e, "dp_get_power");
+    if (on_device) return DP_OK;
+    e = cudaStreamSynchronize(D->ctx->stream);
+    if (e != cudaSuccess) return cuda_err(D->ctx, e, "dp_get_power");
     return check_device_error(D->ctx);
 }
 
 dp_status dp_backward(dp_design *D, const dp_config *cfg, float *gsp, float *gtr, float *gpin, float *gcl,
                       int on_device) {
     if (!D) return DP_EINVAL;
+    if (D->batched) return dp_backward_weighted(D, cfg, nullptr, 0, gsp, gtr, gpin, gcl, on_device);
     dp_status s = check_cfg(D->ctx, cfg);
     if (s != DP_OK) return s;
     if (!D->fwd_valid || D->fwd_tr_mode != cfg->tr_mode)
@@ -613,12 +592,12 @@ dp_status dp_backward(dp_design *D, const dp_config *cfg, float *gsp, float *gtr
         return set_err(D->ctx, DP_ESTATE, "hybrid gradients need dp_simulate");
     DeviceGuard g(D->ctx->device);
     cudaStream_t st = D->ctx->stream;
-    rec(D, 2, st);
-    cudaError_t le = q_backward(D, *cfg, on_device ? gsp : nullptr, st);
     rec(D, 3, st);
+    cudaError_t le = q_backward(D, *cfg, on_device ? gsp : nullptr, st);
+    rec(D, 4, st);
     if ((s = cuda_err(D->ctx, le, "dp_backward")) != DP_OK) return s;
     s = q_outputs(D, *cfg, gsp, gtr, gpin, gcl, on_device, on_device != 0);
-    rec(D, 4, st);
+    rec(D, 5, st);
     return s;
 }
 
@@ -626,6 +605,11 @@ dp_status dp_get_nets(dp_design *D, float *sp, float *tr, float *beta, float *tr
                       int on_device) {
     if (!D) return DP_EINVAL;
     dp_ctx *c = D->ctx;
+    if (D->batched) {
+        if (beta || trh || tg || on)
+            return set_err(c, DP_EUNSUPPORTED, "simulation outputs exist for single-scenario inputs only");
+        return batch_get_nets(D, sp, tr, on_device);
+    }
     if ((sp || tr) && !D->fwd_valid) return set_err(c, DP_ESTATE, "SP/TR need dp_propagate");
     if ((beta || trh || tg || on) && !D->sim_valid) return set_err(c, DP_ESTATE, "simulation outputs need dp_simulate");
     DeviceGuard g(c->device);
@@ -667,6 +651,7 @@ dp_status dp_step(dp_design *D, const dp_config *cfg, float *gsp, float *gtr, fl
     dp_status s = check_cfg(D->ctx, cfg);
     if (s != DP_OK) return s;
     if (!D->inputs_set) return set_err(D->ctx, DP_ESTATE, "dp_step before dp_set_inputs");
+    if (D->batched) return set_err(D->ctx, DP_EUNSUPPORTED, "dp_step runs on single-scenario inputs");
     DeviceGuard g(D->ctx->device);
     if ((s = ensure_words(D, cfg->sim_words)) != DP_OK) return s;
     cudaStream_t st = D->ctx->stream;
@@ -690,8 +675,10 @@ dp_status dp_step(dp_design *D, const dp_config *cfg, float *gsp, float *gtr, fl
         cudaStreamWaitEvent(cs, D->join, 0);
         if (le == cudaSuccess) le = q_sim_levels(D, *cfg, cs);
         cudaEventRecordWithFlags(D->ev[2], cs, cudaEventRecordExternal);
-        if (le == cudaSuccess) le = q_backward(D, *cfg, nullptr, cs);
+        if (le == cudaSuccess) le = q_hybrid(D, *cfg, cs);
         cudaEventRecordWithFlags(D->ev[3], cs, cudaEventRecordExternal);
+        if (le == cudaSuccess) le = q_backward(D, *cfg, nullptr, cs);
+        cudaEventRecordWithFlags(D->ev[4], cs, cudaEventRecordExternal);
         e = cudaStreamEndCapture(cs, &graph);
         if (e == cudaSuccess && le != cudaSuccess) e = le;
         D->graph_kernels = 0;
@@ -713,12 +700,12 @@ dp_status dp_step(dp_design *D, const dp_config *cfg, float *gsp, float *gtr, fl
     }
     cudaError_t e = cudaGraphLaunch(D->graph, st);
     if (e != cudaSuccess) return cuda_err(D->ctx, e, "graph launch");
-    for (int i = 0; i < 4; i++) D->ev_valid[i] = true;
+    for (int i = 0; i < 5; i++) D->ev_valid[i] = true;
     D->fwd_valid = true;
     D->fwd_tr_mode = cfg->tr_mode;
     D->sim_valid = true;
     s = q_outputs(D, *cfg, gsp, gtr, gpin, gcl, on_device, false);
-    rec(D, 4, st);
+    rec(D, 5, st);
     D->step_kernels = D->graph_kernels + (gcl && D->d.n_nets ? 1 : 0) + (gpin && D->d.n_cells ? 1 : 0) +
                       (gtr && D->d.n_start ? 1 : 0);
     if (s != DP_OK) return s;
@@ -742,7 +729,7 @@ dp_status dp_phase_times(dp_design *D, float *ms) {
     DeviceGuard g(D->ctx->device);
     cudaError_t e = cudaStreamSynchronize(D->ctx->stream);
     if (e != cudaSuccess) return cuda_err(D->ctx, e, "dp_phase_times");
-    for (int i = 0; i < 4; i++) {
+    for (int i = 0; i < 5; i++) {
         ms[i] = 0.f;
         if (D->ev_valid[i] && D->ev_valid[i + 1]) {
             float t = 0.f;

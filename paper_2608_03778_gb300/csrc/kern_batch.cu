@@ -1,0 +1,423 @@
+// Batched scenarios: S input-activity scenarios of one design per launch.
+// Every per-net value is stored scenario-innermost (value[n * S + s]), so the
+// S values of one fanin are contiguous: a warp covering 32 scenarios of one
+// cell reads each fanin as 256 consecutive bytes.  A block is bx scenarios x
+// by cells; blockIdx.y walks the cells of a level.  Each thread computes one
+// (cell, scenario) independently of the block shape, so every shape gives
+// bitwise identical results and the shape is free for the autotuner.
+//
+// Probabilities are the single-scenario path's float-float (P, Q) pairs, P(net=0)
+// evaluated as its own minterm sum and the pair renormalised by P + Q at every
+// cell (the same reading of Eq. 2), stored untagged as float4 per (net,
+// scenario).  The gradient is the model gradient (Sec. III-E, Eq. 7) in
+// binary32 from the rounded pairs, scaled per scenario by a seed K * w_s so
+// that a caller can back-propagate any weighted sum of the scenario powers.
+#include "kern_common.cuh"
+
+namespace dp {
+namespace {
+
+__host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// a stored (untagged) pair and its binary32 roundings
+__device__ __forceinline__ pair_ff pair_get(const float4 &v) { return pair_ff{ff{v.x, v.y}, ff{v.z, v.w}}; }
+__device__ __forceinline__ float4 pair_set(const pair_ff &a) { return make_float4(a.p.hi, a.p.lo, a.q.hi, a.q.lo); }
+
+__device__ __forceinline__ void gather_ffb(const float4 *pq, const uint4 &r, int k, int64_t S, int64_t s,
+                                           pair_ff (&x)[4]) {
+    const uint32_t n[4] = {r.x & kMask24, r.y, r.z, r.w};
+    float4 v[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) v[j] = j < k ? pq[(int64_t)n[j] * S + s] : make_float4(0.f, 0.f, 1.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < 4; j++) x[j] = pair_get(v[j]);
+}
+
+// binary32 (P, Q) of a cell's inputs for the partial derivatives
+__device__ __forceinline__ void gather32(const float4 *pq, const uint4 &r, int k, int64_t S, int64_t s,
+                                         float (&p)[4], float (&q)[4]) {
+    const uint32_t n[4] = {r.x & kMask24, r.y, r.z, r.w};
+    float4 v[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) v[j] = j < k ? pq[(int64_t)n[j] * S + s] : make_float4(0.f, 0.f, 1.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        p[j] = v[j].x + v[j].y;
+        q[j] = v[j].z + v[j].w;
+    }
+}
+
+// switching activity of net n in scenario s: the input TR at a startpoint in
+// tr_mode 0, else TR_model = 2 P Q (Eq. 2) rounded once to binary32
+__device__ __forceinline__ float alpha32(const float4 *pq, const float *tr_in, int64_t n, int64_t ns, int64_t S,
+                                         int64_t s, int tr_mode) {
+    if (n < ns && tr_mode == 0) return tr_in[n * S + s];
+    return pair_tr(pair_get(pq[n * S + s]));
+}
+
+__global__ void k_fwdb_start(const float *__restrict__ sp_in, float4 *pq, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    pq[i] = pair_set(pair_of(sp_in[i]));
+}
+
+__global__ void k_fwdb_level(const uint4 *__restrict__ fanin, float4 *pq, int32_t c0, int32_t c1, int64_t ns,
+                             int64_t S, OpTable ops) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    const int64_t step = (int64_t)gridDim.y * blockDim.y;
+    for (int64_t c = c0 + (int64_t)blockIdx.y * blockDim.y + threadIdx.y; c < c1; c += step) {
+        const uint4 r = fanin[c];
+        const uint32_t op = r.x >> 24;
+        const int k = op_arity(ops, op);
+        pair_ff x[4];
+        gather_ffb(pq, r, k, S, s, x);
+        pq[(ns + c) * S + s] = pair_set(cell_pair(k, op_tt(ops, op), x));
+    }
+}
+
+// Eq. 1 per scenario in FP64: chunk b of the nets -> partials[b * S + s], then
+// the chunks summed in index order (a fixed order: reproducible)
+__global__ void k_powerb_partials(const float4 *__restrict__ pq, const float *__restrict__ tr_in,
+                                  const float *__restrict__ cload, double *partials, int64_t nn, int64_t ns,
+                                  int64_t S, int64_t chunk, int tr_mode) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    const int64_t n0 = (int64_t)blockIdx.y * chunk, n1 = n0 + chunk < nn ? n0 + chunk : nn;
+    double acc = 0.0;
+    for (int64_t n = n0; n < n1; n++) {
+        double a;
+        if (n < ns && tr_mode == 0) {
+            a = (double)tr_in[n * S + s];
+        } else {
+            const float4 o = pq[n * S + s];
+            a = 2.0 * ((double)o.x + (double)o.y) * ((double)o.z + (double)o.w);
+        }
+        acc += a * (double)cload[n];
+    }
+    partials[(int64_t)blockIdx.y * S + s] = acc;
+}
+
+__global__ void k_sumb_final(const double *__restrict__ partials, int nchunks, int64_t S, double K, double *out) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    double acc = 0.0;
+    for (int b = 0; b < nchunks; b++) acc += partials[(int64_t)b * S + s];
+    out[s] = K * acc;
+}
+
+__global__ void k_seedb(float *ks, const double *__restrict__ w, double K, int64_t S) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < S) ks[s] = (float)(w ? K * w[s] : K);
+}
+
+// reverse level: each net's adjoint is its fanout range summed in index order
+// plus its local term d(K_s C 2PQ)/dP = 2 K_s C (Q - P); the cell then writes
+// one contribution per input edge (no atomics)
+__global__ void k_bwdb_level(const uint4 *__restrict__ fanin, const int32_t *__restrict__ fptr,
+                             const int4 *__restrict__ efpos, const float4 *__restrict__ pq,
+                             const float *__restrict__ cload, const float *__restrict__ ks, float *gfo, int32_t c0,
+                             int32_t c1, int64_t ns, int64_t S, OpTable ops) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    const float Ks = ks[s];
+    const int64_t step = (int64_t)gridDim.y * blockDim.y;
+    for (int64_t c = c0 + (int64_t)blockIdx.y * blockDim.y + threadIdx.y; c < c1; c += step) {
+        const int64_t n = ns + c;
+        const int32_t e0 = fptr[n], e1 = fptr[n + 1];
+        float acc = 0.f;
+        for (int32_t e = e0; e < e1; e++) acc += gfo[(int64_t)e * S + s];
+        const float g = acc + 2.f * Ks * cload[n] * pair_qmp(pq[n * S + s]);
+        const uint4 r = fanin[c];
+        const uint32_t op = r.x >> 24;
+        const int k = op_arity(ops, op);
+        float p[4], q[4], d[4];
+        gather32(pq, r, k, S, s, p, q);
+        cell_partials(k, op_tt(ops, op), p, q, d);
+        const int4 ep = efpos[c];
+        if (k > 0) gfo[(int64_t)ep.x * S + s] = g * d[0];
+        if (k > 1) gfo[(int64_t)ep.y * S + s] = g * d[1];
+        if (k > 2) gfo[(int64_t)ep.z * S + s] = g * d[2];
+        if (k > 3) gfo[(int64_t)ep.w * S + s] = g * d[3];
+    }
+}
+
+// startpoints: fanout sum, plus the local term when their TR derives from their SP (tr_mode 1)
+__global__ void k_bwdb_start(const int32_t *__restrict__ fptr, const float4 *__restrict__ pq,
+                             const float *__restrict__ cload, const float *__restrict__ ks,
+                             const float *__restrict__ gfo, float *gsp, int64_t ns, int64_t S, int tr_mode) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    const float Ks = ks[s];
+    const int64_t step = (int64_t)gridDim.y * blockDim.y;
+    for (int64_t k = (int64_t)blockIdx.y * blockDim.y + threadIdx.y; k < ns; k += step) {
+        const int32_t e0 = fptr[k], e1 = fptr[k + 1];
+        float acc = 0.f;
+        for (int32_t e = e0; e < e1; e++) acc += gfo[(int64_t)e * S + s];
+        float g = acc;
+        if (tr_mode) g += 2.f * Ks * cload[k] * pair_qmp(pq[k * S + s]);
+        gsp[k * S + s] = g;
+    }
+}
+
+// dP_s/dC_n = K_s alpha_n(s); dP_s/dpincap_c = K_s sum_j alpha_{fanin j}(s)
+// (one pin cap per cell, loading each of its fanin nets); dP_s/dTR_k = K_s C_k
+// at a startpoint in tr_mode 0, else 0
+__global__ void k_gradb_rows(const uint4 *__restrict__ fanin, const float4 *__restrict__ pq,
+                             const float *__restrict__ tr_in, const float *__restrict__ cload,
+                             const int32_t *__restrict__ net_of_user, const int32_t *__restrict__ cell_of_user,
+                             const float *__restrict__ ks, float *gcl, float *gpin, float *gtr, int64_t nn,
+                             int64_t nc, int64_t ns, int64_t S, int tr_mode, OpTable ops) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    const float Ks = ks[s];
+    const int64_t rows = (gcl ? nn : 0) + (gpin ? nc : 0) + (gtr ? ns : 0);
+    const int64_t step = (int64_t)gridDim.y * blockDim.y;
+    for (int64_t r = (int64_t)blockIdx.y * blockDim.y + threadIdx.y; r < rows; r += step) {
+        int64_t u = r;
+        if (gcl) {
+            if (u < nn) {
+                gcl[u * S + s] = Ks * alpha32(pq, tr_in, net_of_user[u], ns, S, s, tr_mode);
+                continue;
+            }
+            u -= nn;
+        }
+        if (gpin) {
+            if (u < nc) {
+                const uint4 f = fanin[cell_of_user[u]];
+                const int k = op_arity(ops, f.x >> 24);
+                const uint32_t n[4] = {f.x & kMask24, f.y, f.z, f.w};
+                float a = 0.f;
+#pragma unroll
+                for (int j = 0; j < 4; j++)
+                    if (j < k) a += alpha32(pq, tr_in, n[j], ns, S, s, tr_mode);
+                gpin[u * S + s] = Ks * a;
+                continue;
+            }
+            u -= nc;
+        }
+        gtr[u * S + s] = tr_mode ? 0.f : Ks * cload[u];
+    }
+}
+
+// Cap gradients summed over the scenarios in FP64: one warp per row, lane l
+// takes scenarios l, l + 32, ... in order, then a fixed shuffle tree.
+__global__ void k_gradb_reduce(const uint4 *__restrict__ fanin, const float4 *__restrict__ pq,
+                               const float *__restrict__ tr_in, const int32_t *__restrict__ net_of_user,
+                               const int32_t *__restrict__ cell_of_user, const float *__restrict__ ks, float *gcl,
+                               float *gpin, int64_t nn, int64_t nc, int64_t ns, int64_t S, int tr_mode, OpTable ops) {
+    const int lane = threadIdx.x & 31;
+    const int64_t rows = (gcl ? nn : 0) + (gpin ? nc : 0);
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t W = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = w0; r < rows; r += W) {
+        int64_t u = r;
+        const bool is_cl = gcl && u < nn;
+        if (gcl && !is_cl) u -= nn;
+        uint32_t n[4] = {0, 0, 0, 0};
+        int k = 1;
+        if (is_cl) {
+            n[0] = (uint32_t)net_of_user[u];
+        } else {
+            const uint4 f = fanin[cell_of_user[u]];
+            k = op_arity(ops, f.x >> 24);
+            n[0] = f.x & kMask24;
+            n[1] = f.y;
+            n[2] = f.z;
+            n[3] = f.w;
+        }
+        double acc = 0.0;
+        for (int64_t s = lane; s < S; s += 32) {
+            float a = 0.f;
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+                if (j < k) a += alpha32(pq, tr_in, n[j], ns, S, s, tr_mode);
+            acc += (double)(ks[s] * a);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) {
+            if (is_cl) gcl[u] = (float)acc;
+            else gpin[u] = (float)acc;
+        }
+    }
+}
+
+__global__ void k_netb_user(const float4 *__restrict__ pq, const float *__restrict__ tr_in,
+                            const int32_t *__restrict__ net_of_user, float *sp_out, float *tr_out, int64_t nn,
+                            int64_t ns, int64_t S, int tr_mode) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    const int64_t step = (int64_t)gridDim.y * blockDim.y;
+    for (int64_t u = (int64_t)blockIdx.y * blockDim.y + threadIdx.y; u < nn; u += step) {
+        const int64_t n = net_of_user[u];
+        if (sp_out) {
+            const float4 v = pq[n * S + s];
+            sp_out[u * S + s] = v.x + v.y;
+        }
+        if (tr_out) tr_out[u * S + s] = alpha32(pq, tr_in, n, ns, S, s, tr_mode);
+    }
+}
+
+__global__ void k_ascent(float *x, const float *__restrict__ g, int64_t n, float eta) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float v = __fadd_rn(x[i], __fmul_rn(eta, g[i]));
+    x[i] = fminf(fmaxf(v, 0.f), 1.f);
+}
+
+// ---- Eq. 3: P_virus of the thresholded vectors ----
+// words of net n: [2W] with W = ceil(S / 64); word w < W holds v0 of scenarios
+// 64 w .. 64 w + 63, word W + w holds v1 = not v0 of the same scenarios
+__global__ void k_virus_start(const float *__restrict__ sp, uint64_t *words, uint8_t *v0, int64_t ns, int64_t S,
+                              int64_t W) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ns * W) return;
+    const int64_t k = i / W, w = i - k * W;
+    uint64_t b0 = 0, valid = 0;
+    for (int b = 0; b < 64; b++) {
+        const int64_t s = w * 64 + b;
+        if (s >= S) break;
+        const bool one = sp[k * S + s] >= 0.5f;
+        if (v0) v0[k * S + s] = one ? 1 : 0;
+        b0 |= (uint64_t)one << b;
+        valid |= 1ull << b;
+    }
+    words[k * 2 * W + w] = b0;
+    words[k * 2 * W + W + w] = ~b0 & valid;
+}
+
+__global__ void k_virus_level(const uint4 *__restrict__ fanin, uint64_t *words, int32_t c0, int32_t c1, int64_t ns,
+                              int64_t W2, OpTable ops) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)(c1 - c0) * W2) return;
+    const int64_t c = c0 + i / W2, w = i % W2;
+    const uint4 r = fanin[c];
+    const uint32_t op = r.x >> 24;
+    const int k = op_arity(ops, op);
+    const uint32_t n[4] = {r.x & kMask24, r.y, r.z, r.w};
+    uint64_t x[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) x[j] = j < k ? words[(int64_t)n[j] * W2 + w] : 0ull;
+    words[(ns + c) * W2 + w] = cell_bits(k, op_tt(ops, op), x);
+}
+
+__global__ void k_virus_partials(const uint64_t *__restrict__ words, const float *__restrict__ cload,
+                                 double *partials, int64_t nn, int64_t S, int64_t W, int64_t chunk) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    const int64_t w = s >> 6;
+    const int b = (int)(s & 63);
+    const int64_t n0 = (int64_t)blockIdx.y * chunk, n1 = n0 + chunk < nn ? n0 + chunk : nn;
+    double acc = 0.0;
+    for (int64_t n = n0; n < n1; n++) {
+        const uint64_t d = words[n * 2 * W + w] ^ words[n * 2 * W + W + w];
+        if ((d >> b) & 1ull) acc += (double)cload[n];
+    }
+    partials[(int64_t)blockIdx.y * S + s] = acc;
+}
+
+dim3 bgrid(int64_t S, BatchShape sh, int64_t rows) {
+    const int64_t gy = cdiv(rows > 0 ? rows : 1, sh.by);
+    return dim3((unsigned)cdiv(S, sh.bx), (unsigned)(gy < 65535 ? gy : 65535));
+}
+
+int nchunks_of(int64_t nn, int64_t *chunk) {
+    const int64_t m = nn > 0 ? nn : 1;
+    *chunk = cdiv(m, kBatchPowerChunks);
+    return (int)cdiv(m, *chunk);
+}
+
+}  // namespace
+
+void launch_fwdb(const DevDesign &d, const BatchBufs &b, const OpTable &ops, const int32_t *lvl, int tr_mode,
+                 BatchShape sh, cudaStream_t s) {
+    (void)tr_mode;   // startpoint TR is read from the inputs where it is needed
+    const int64_t S = b.S;
+    if (d.n_start) k_fwdb_start<<<(unsigned)cdiv(d.n_start * S, 256), 256, 0, s>>>(b.sp_in, b.pq, d.n_start * S);
+    const dim3 blk((unsigned)sh.bx, (unsigned)sh.by);
+    for (int l = 1; l <= d.n_levels; l++) {
+        const int32_t c0 = lvl[l - 1], c1 = lvl[l];
+        if (c1 > c0) k_fwdb_level<<<bgrid(S, sh, c1 - c0), blk, 0, s>>>(d.fanin, b.pq, c0, c1, d.n_start, S, ops);
+    }
+}
+
+void launch_powerb(const DevDesign &d, const BatchBufs &b, int tr_mode, double K, cudaStream_t s) {
+    const int64_t S = b.S;
+    int64_t chunk = 0;
+    const int nch = nchunks_of(d.n_nets, &chunk);
+    k_powerb_partials<<<dim3((unsigned)cdiv(S, 128), (unsigned)nch), 128, 0, s>>>(
+        b.pq, b.tr_in, d.cload, b.partials, d.n_nets, d.n_start, S, chunk, tr_mode);
+    k_sumb_final<<<(unsigned)cdiv(S, 128), 128, 0, s>>>(b.partials, nch, S, K, b.power);
+}
+
+void launch_seedb(const BatchBufs &b, double K, const double *weights, cudaStream_t s) {
+    k_seedb<<<(unsigned)cdiv(b.S, 128), 128, 0, s>>>(b.ks, weights, K, b.S);
+}
+
+void launch_bwdb(const DevDesign &d, const BatchBufs &b, const OpTable &ops, const int32_t *lvl, int tr_mode,
+                 BatchShape sh, cudaStream_t s) {
+    const int64_t S = b.S;
+    const dim3 blk((unsigned)sh.bx, (unsigned)sh.by);
+    for (int l = d.n_levels; l >= 1; l--) {
+        const int32_t c0 = lvl[l - 1], c1 = lvl[l];
+        if (c1 > c0)
+            k_bwdb_level<<<bgrid(S, sh, c1 - c0), blk, 0, s>>>(d.fanin, d.fout_ptr, (const int4 *)d.edge_fpos, b.pq,
+                                                               d.cload, b.ks, b.gfo, c0, c1, d.n_start, S, ops);
+    }
+    if (d.n_start)
+        k_bwdb_start<<<bgrid(S, sh, d.n_start), blk, 0, s>>>(d.fout_ptr, b.pq, d.cload, b.ks, b.gfo, b.gsp,
+                                                             d.n_start, S, tr_mode);
+}
+
+void launch_gradb(const DevDesign &d, const BatchBufs &b, const OpTable &ops, int tr_mode, bool reduce, float *gtr,
+                  float *gpin, float *gcl, cudaStream_t s) {
+    const int64_t S = b.S;
+    if (reduce) {
+        const int64_t rows = (gcl ? d.n_nets : 0) + (gpin ? d.n_cells : 0);
+        if (rows) {
+            const int64_t blocks = cdiv(rows, 8);
+            k_gradb_reduce<<<(unsigned)(blocks < 152 * 16 ? blocks : 152 * 16), 256, 0, s>>>(
+                d.fanin, b.pq, b.tr_in, d.net_of_user, d.cell_of_user, b.ks, gcl, gpin, d.n_nets, d.n_cells,
+                d.n_start, S, tr_mode, ops);
+        }
+        gcl = gpin = nullptr;
+    }
+    const int64_t rows = (gcl ? d.n_nets : 0) + (gpin ? d.n_cells : 0) + (gtr ? d.n_start : 0);
+    if (rows == 0) return;
+    const BatchShape sh{S >= 128 ? 128 : 32, S >= 128 ? 1 : 4};
+    k_gradb_rows<<<bgrid(S, sh, rows), dim3((unsigned)sh.bx, (unsigned)sh.by), 0, s>>>(
+        d.fanin, b.pq, b.tr_in, d.cload, d.net_of_user, d.cell_of_user, b.ks, gcl, gpin, gtr, d.n_nets, d.n_cells,
+        d.n_start, S, tr_mode, ops);
+}
+
+void launch_netb_user(const DevDesign &d, const BatchBufs &b, int tr_mode, float *sp, float *tr, cudaStream_t s) {
+    if (!d.n_nets || (!sp && !tr)) return;
+    const BatchShape sh{b.S >= 128 ? 128 : 32, b.S >= 128 ? 1 : 4};
+    k_netb_user<<<bgrid(b.S, sh, d.n_nets), dim3((unsigned)sh.bx, (unsigned)sh.by), 0, s>>>(
+        b.pq, b.tr_in, d.net_of_user, sp, tr, d.n_nets, d.n_start, b.S, tr_mode);
+}
+
+void launch_ascent(float *x, const float *g, int64_t n, float eta, cudaStream_t s) {
+    if (n) k_ascent<<<(unsigned)cdiv(n, 256), 256, 0, s>>>(x, g, n, eta);
+}
+
+void launch_virus(const DevDesign &d, const OpTable &ops, const int32_t *lvl, const float *sp, int64_t S,
+                  uint64_t *words, uint8_t *v0, double *partials, double *out, cudaStream_t s) {
+    const int64_t W = cdiv(S, 64), W2 = 2 * W;
+    if (d.n_start)
+        k_virus_start<<<(unsigned)cdiv(d.n_start * W, 128), 128, 0, s>>>(sp, words, v0, d.n_start, S, W);
+    for (int l = 1; l <= d.n_levels; l++) {
+        const int64_t m = (int64_t)(lvl[l] - lvl[l - 1]) * W2;
+        if (m)
+            k_virus_level<<<(unsigned)cdiv(m, 256), 256, 0, s>>>(d.fanin, words, lvl[l - 1], lvl[l], d.n_start, W2,
+                                                                 ops);
+    }
+    int64_t chunk = 0;
+    const int nch = nchunks_of(d.n_nets, &chunk);
+    k_virus_partials<<<dim3((unsigned)cdiv(S, 128), (unsigned)nch), 128, 0, s>>>(words, d.cload, partials, d.n_nets,
+                                                                                S, W, chunk);
+    k_sumb_final<<<(unsigned)cdiv(S, 128), 128, 0, s>>>(partials, nch, S, 1.0, out);
+}
+
+}  // namespace dp

@@ -47,7 +47,7 @@ __global__ void k_set_pincap(const int32_t *__restrict__ cells, const float *__r
                              const int32_t *__restrict__ cell_of_user, float *pincap, int32_t n, int64_t nc) {
     int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    int32_t u = cells[i];
+    int32_t u = cells ? cells[i] : i;   // no index list: cells in cell-line order
     if (u >= 0 && u < nc) pincap[cell_of_user[u]] = caps[i];
 }
 

@@ -89,6 +89,41 @@ cudaError_t launch_bwd_persist(const DevDesign &d, const OpTable &ops, int grad_
                                float *out_gsp, int grid, cudaStream_t s);
 cudaError_t launch_wait_selftest(unsigned *bar, int *err, long long limit, cudaStream_t s);
 
+// Batched scenarios (kern_batch.cu): S scenarios of one design, every per-net
+// value stored scenario-innermost (value[n * S + s]).
+struct BatchBufs {
+    int64_t S;
+    float *sp_in, *tr_in;   // [n_start * S] staged inputs
+    float4 *pq;             // [n_nets * S] float-float (P.hi, P.lo, Q.hi, Q.lo), untagged
+    float *gfo;             // [n_edges * S] edge adjoints in fanout-CSR order
+    float *gsp;             // [n_start * S] SP adjoint of the startpoints
+    double *partials;       // [kBatchPowerChunks * S]
+    double *power;          // [S] model power per scenario
+    float *ks;              // [S] per-scenario seed of the backward (K * weight), binary32
+};
+constexpr int kBatchPowerChunks = 256;   // fixed split of the nets -> deterministic FP64 sums
+
+struct BatchShape {
+    int bx, by;   // threads over scenarios x cells per block
+};
+
+void launch_fwdb(const DevDesign &d, const BatchBufs &b, const OpTable &ops, const int32_t *lvl_host, int tr_mode,
+                 BatchShape sh, cudaStream_t s);
+void launch_powerb(const DevDesign &d, const BatchBufs &b, int tr_mode, double K, cudaStream_t s);
+// ks[s] = K * weights[s] (weights NULL: K)
+void launch_seedb(const BatchBufs &b, double K, const double *weights, cudaStream_t s);
+void launch_bwdb(const DevDesign &d, const BatchBufs &b, const OpTable &ops, const int32_t *lvl_host, int tr_mode,
+                 BatchShape sh, cudaStream_t s);
+// per-scenario gradient outputs ([x][S], user order), or summed over scenarios in FP64 ([x]) when reduce
+void launch_gradb(const DevDesign &d, const BatchBufs &b, const OpTable &ops, int tr_mode, bool reduce, float *gtr,
+                  float *gpin, float *gcl, cudaStream_t s);
+void launch_netb_user(const DevDesign &d, const BatchBufs &b, int tr_mode, float *sp, float *tr, cudaStream_t s);
+// x <- clip(x + eta g, 0, 1) (Algorithm 4 ascent step with projection)
+void launch_ascent(float *x, const float *g, int64_t n, float eta, cudaStream_t s);
+// Eq. 3: threshold SP at 0.5 into v0 (v1 = not v0), two bitwise forwards, sum of C over nets whose values differ
+void launch_virus(const DevDesign &d, const OpTable &ops, const int32_t *lvl_host, const float *sp, int64_t S,
+                  uint64_t *words, uint8_t *v0, double *partials, double *out, cudaStream_t s);
+
 // simulation (kern_sim.cu)
 void launch_sim_start(const DevDesign &d, int T, uint64_t seed, cudaStream_t s);
 void launch_sim_level(const DevDesign &d, const OpTable &ops, int32_t c0, int32_t c1, int T, cudaStream_t s);

@@ -88,19 +88,28 @@ _sig("dp_set_inputs", [_P, _P, _P, ctypes.c_int32, _S])
 _sig("dp_set_pincap", [_P, _P, _P, ctypes.c_int32, _S])
 _sig("dp_propagate", [_P, ctypes.POINTER(dp_config)])
 _sig("dp_simulate", [_P, ctypes.POINTER(dp_config)])
-_sig("dp_total_power", [_P, _S, ctypes.POINTER(ctypes.c_double)])
+_sig("dp_total_power", [_P, _S, _P])
 _sig("dp_backward", [_P, ctypes.POINTER(dp_config), _P, _P, _P, _P, _S])
 _sig("dp_get_nets", [_P, _P, _P, _P, _P, _P, _P, _S])
 _sig("dp_step", [_P, ctypes.POINTER(dp_config), _P, _P, _P, _P, _P, _S])
 _sig("dp_phase_times", [_P, _P])
 _sig("dp_step_kernels", [_P, ctypes.POINTER(ctypes.c_int64)])
 _sig("dp_power_noalloc", [ctypes.c_int, _P, _P, _P, ctypes.c_int64, ctypes.c_double, ctypes.c_double, _P, _P])
+_sig("dp_set_stream", [_P, _P])
+_sig("dp_get_power", [_P, _S, _P, _S])
+_sig("dp_set_inputs_batch", [_P, _P, _P, ctypes.c_int32, _S])
+_sig("dp_batch_tuning", [_P, _P, _P])
+_sig("dp_backward_weighted", [_P, ctypes.POINTER(dp_config), _P, ctypes.c_int32, _P, _P, _P, _P, _S])
+_sig("dp_ascent_step", [_P, _P, _P, ctypes.c_int64, ctypes.c_float])
+_sig("dp_virus_eval", [_P, _P, ctypes.c_int32, _P, _P, _S])
 
 EXPORTED = ["dp_config_default", "dp_last_error", "dp_compile", "dp_compiled_free", "dp_compiled_info",
             "dp_compiled_view_get", "dp_compile_function", "dp_create", "dp_destroy", "dp_sync", "dp_design_load",
             "dp_design_upload", "dp_design_free", "dp_design_info", "dp_set_inputs", "dp_set_pincap",
             "dp_propagate", "dp_simulate", "dp_total_power", "dp_backward", "dp_get_nets", "dp_step",
-            "dp_phase_times", "dp_step_kernels", "dp_power_noalloc", "dp_selftest_wait"]
+            "dp_phase_times", "dp_step_kernels", "dp_power_noalloc", "dp_selftest_wait", "dp_set_stream",
+            "dp_get_power", "dp_set_inputs_batch", "dp_batch_tuning", "dp_backward_weighted", "dp_ascent_step",
+            "dp_virus_eval"]
 
 
 def _ptr(x):
@@ -247,6 +256,11 @@ def dp_set_pincap(ctx, d, cells, pincap, on_device: int = 0) -> None:
     _check(_lib.dp_set_pincap(d, _ptr(cells), _ptr(pincap), len(cells), on_device), ctx)
 
 
+def dp_set_pincap_all(ctx, d, pincap, n_cells: int, on_device: int = 0) -> None:
+    """Every cell's input pin cap, in cell-line order (dp_set_pincap with a NULL cell list)."""
+    _check(_lib.dp_set_pincap(d, None, _ptr(pincap), n_cells, on_device), ctx)
+
+
 def dp_propagate(ctx, d, cfg: dp_config) -> None:
     _check(_lib.dp_propagate(d, ctypes.byref(cfg)), ctx)
 
@@ -255,10 +269,12 @@ def dp_simulate(ctx, d, cfg: dp_config) -> None:
     _check(_lib.dp_simulate(d, ctypes.byref(cfg)), ctx)
 
 
-def dp_total_power(ctx, d, hybrid: int = 0) -> float:
-    w = ctypes.c_double()
-    _check(_lib.dp_total_power(d, hybrid, ctypes.byref(w)), ctx)
-    return w.value
+def dp_total_power(ctx, d, hybrid: int = 0, n_scen: int = 1):
+    """Power in watts: a float for one scenario, an array of n_scen values for a batch
+    (n_scen must be the batch's size: the library writes that many values)."""
+    w = np.zeros(max(int(n_scen), 1), np.float64)
+    _check(_lib.dp_total_power(d, hybrid, w.ctypes.data), ctx)
+    return float(w[0]) if n_scen == 1 else w
 
 
 def dp_backward(ctx, d, cfg: dp_config, grad_sp_in=None, grad_tr_in=None, grad_pincap=None, grad_cload=None,
@@ -280,7 +296,7 @@ def dp_step(ctx, d, cfg: dp_config, grad_sp_in=None, grad_tr_in=None, grad_pinca
 
 
 def dp_phase_times(ctx, d) -> np.ndarray:
-    ms = np.zeros(4, np.float32)
+    ms = np.zeros(5, np.float32)
     _check(_lib.dp_phase_times(d, ms.ctypes.data), ctx)
     return ms
 
@@ -294,3 +310,39 @@ def dp_step_kernels(d) -> int:
 def dp_power_noalloc(device: int, tr, beta, cload, n: int, vdd: float, fclk: float, watts, stream=None) -> None:
     """Power reduction that allocates no device memory (all arrays are caller-owned device memory)."""
     _check(_lib.dp_power_noalloc(device, _ptr(tr), _ptr(beta), _ptr(cload), n, vdd, fclk, _ptr(watts), stream))
+
+
+def dp_set_stream(ctx, stream) -> None:
+    _check(_lib.dp_set_stream(ctx, stream), ctx)
+
+
+def dp_get_power(ctx, d, watts, hybrid: int = 0, on_device: int = 0) -> None:
+    """Powers into a caller buffer (float64: one value, or n_scen for batched inputs)."""
+    _check(_lib.dp_get_power(d, hybrid, _ptr(watts), on_device), ctx)
+
+
+def dp_set_inputs_batch(ctx, d, sp, tr, n_scen: int, on_device: int = 0) -> None:
+    _check(_lib.dp_set_inputs_batch(d, _ptr(sp), _ptr(tr), n_scen, on_device), ctx)
+
+
+def dp_batch_tuning(d):
+    """((fwd_bx, fwd_by), (bwd_bx, bwd_by), (fwd_ms, bwd_ms)) chosen by the autotuner."""
+    sh = np.zeros(4, np.int32)
+    ms = np.zeros(2, np.float32)
+    _check(_lib.dp_batch_tuning(d, sh.ctypes.data, ms.ctypes.data))
+    return (int(sh[0]), int(sh[1])), (int(sh[2]), int(sh[3])), (float(ms[0]), float(ms[1]))
+
+
+def dp_backward_weighted(ctx, d, cfg: dp_config, weights=None, cap_reduce: int = 0, grad_sp_in=None,
+                         grad_tr_in=None, grad_pincap=None, grad_cload=None, on_device: int = 0) -> None:
+    _check(_lib.dp_backward_weighted(d, ctypes.byref(cfg), _ptr(weights), cap_reduce, _ptr(grad_sp_in),
+                                     _ptr(grad_tr_in), _ptr(grad_pincap), _ptr(grad_cload), on_device), ctx)
+
+
+def dp_ascent_step(ctx, x, g, n: int, eta: float) -> None:
+    """x <- clip(x + eta g, 0, 1) on device arrays."""
+    _check(_lib.dp_ascent_step(ctx, _ptr(x), _ptr(g), n, eta), ctx)
+
+
+def dp_virus_eval(ctx, d, sp, n_scen: int, p_virus, v0=None, on_device: int = 0) -> None:
+    _check(_lib.dp_virus_eval(d, _ptr(sp), n_scen, _ptr(v0), _ptr(p_virus), on_device), ctx)

@@ -271,8 +271,10 @@ def test_call_order_and_argument_errors(dp, ctx, library_text):
             dp.dp_set_inputs(ctx, d, bad, np.zeros(ns, np.float32))
         assert e.value.name == "DP_EINVAL"
         with pytest.raises(dp.DPError) as e:
-            dp.dp_set_inputs(ctx, d, np.zeros(2 * ns, np.float32), np.zeros(2 * ns, np.float32), 2)
-        assert e.value.name == "DP_EUNSUPPORTED"
+            dp.dp_set_inputs(ctx, d, np.zeros(ns, np.float32), np.zeros(ns, np.float32), 0)
+        assert e.value.name == "DP_EINVAL"
+        # more than one scenario selects the batched path (tests/test_batch_gpu.py)
+        dp.dp_set_inputs(ctx, d, np.zeros(2 * ns, np.float32), np.zeros(2 * ns, np.float32), 2)
         dp.dp_set_inputs(ctx, d, np.full(ns, 0.5, np.float32), np.zeros(ns, np.float32))
         with pytest.raises(dp.DPError) as e:
             dp.dp_simulate(ctx, d, cfg)
