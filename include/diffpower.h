@@ -261,15 +261,16 @@ dp_status dp_phase_times(dp_design *d, float *ms5);
  * dp_propagate, dp_total_power / dp_get_power, dp_backward and dp_get_nets
  * work on the batch; dp_simulate and dp_step return DP_EUNSUPPORTED (the
  * simulation and the hybrid objective run on single-scenario inputs).
- * Probabilities are float-float (P, P(net=0)) pairs renormalised at every cell,
- * as for one scenario; the adjoint is binary32;
+ * Each cell's (P, P(net=0)) pair is evaluated in float-float and renormalised
+ * as for one scenario; P is kept in float-float (P(net=0) re-derived as 1 - P);
+ * the adjoint is binary32;
  * powers and scenario sums are FP64 in a fixed order (reproducible).  Calls
  * with device outputs neither allocate nor synchronise once a call with the
  * largest n_scen has been made, so they may be captured into a CUDA graph. */
 
 /* Stages n_scen scenarios of startpoint SP and TR, sp[n_start][n_scen] and
  * tr[n_start][n_scen].  The first call with a larger n_scen allocates the
- * batch buffers (about (16 n_nets + 4 n_edges + 12 n_start) bytes per
+ * batch buffers (about (8 n_nets + 4 n_edges + 12 n_start) bytes per
  * scenario) and must not be made under stream capture (DP_ESTATE); a call
  * with a new n_scen outside capture also runs the launch-shape autotuner
  * (times every candidate shape of the forward and reverse kernels on the

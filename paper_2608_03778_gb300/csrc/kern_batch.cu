@@ -6,12 +6,16 @@
 // (cell, scenario) independently of the block shape, so every shape gives
 // bitwise identical results and the shape is free for the autotuner.
 //
-// Probabilities are the single-scenario path's float-float (P, Q) pairs, P(net=0)
-// evaluated as its own minterm sum and the pair renormalised by P + Q at every
-// cell (the same reading of Eq. 2), stored untagged as float4 per (net,
-// scenario).  The gradient is the model gradient (Sec. III-E, Eq. 7) in
-// binary32 from the rounded pairs, scaled per scenario by a seed K * w_s so
-// that a caller can back-propagate any weighted sum of the scenario powers.
+// Each cell evaluates the single-scenario path's float-float (P, Q) pair, P(net=0)
+// its own minterm sum and the pair renormalised by P + Q (the same reading of
+// Eq. 2), but only P is stored, as a float-float value (8 bytes per net and
+// scenario): Q is re-derived as 1 - P in float-float, exact to about 1e-14
+// absolute.  That loses Q's relative accuracy only for nets within about 1e-9
+// of 1, which matters for the hybrid beta (Eq. 5, single-scenario only) and
+// not for the model power, SP, TR or gradients at their tolerances; it halves
+// the bytes every gather moves.  The gradient is the model gradient (Sec. III-E,
+// Eq. 7) in binary32, scaled per scenario by a seed K * w_s so that a caller
+// can back-propagate any weighted sum of the scenario powers.
 #include "kern_common.cuh"
 
 namespace dp {
@@ -19,49 +23,61 @@ namespace {
 
 __host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-// a stored (untagged) pair and its binary32 roundings
-__device__ __forceinline__ pair_ff pair_get(const float4 &v) { return pair_ff{ff{v.x, v.y}, ff{v.z, v.w}}; }
-__device__ __forceinline__ float4 pair_set(const pair_ff &a) { return make_float4(a.p.hi, a.p.lo, a.q.hi, a.q.lo); }
+// the stored float-float P of a net and its pair (P, 1 - P)
+__device__ __forceinline__ pair_ff pair_get(const float2 &v) {
+    const ff p{v.x, v.y};
+    const ff t = two_sum(1.f, -v.x);
+    return pair_ff{p, fast_two_sum(t.hi, __fsub_rn(t.lo, v.y))};
+}
+__device__ __forceinline__ float2 p_set(const pair_ff &a) { return make_float2(a.p.hi, a.p.lo); }
 
-__device__ __forceinline__ void gather_ffb(const float4 *pq, const uint4 &r, int k, int64_t S, int64_t s,
+__device__ __forceinline__ void gather_ffb(const float2 *pq, const uint4 &r, int k, int64_t S, int64_t s,
                                            pair_ff (&x)[4]) {
     const uint32_t n[4] = {r.x & kMask24, r.y, r.z, r.w};
-    float4 v[4];
+    float2 v[4];
 #pragma unroll
-    for (int j = 0; j < 4; j++) v[j] = j < k ? pq[(int64_t)n[j] * S + s] : make_float4(0.f, 0.f, 1.f, 0.f);
+    for (int j = 0; j < 4; j++) v[j] = j < k ? pq[(int64_t)n[j] * S + s] : make_float2(0.f, 0.f);
 #pragma unroll
     for (int j = 0; j < 4; j++) x[j] = pair_get(v[j]);
 }
 
 // binary32 (P, Q) of a cell's inputs for the partial derivatives
-__device__ __forceinline__ void gather32(const float4 *pq, const uint4 &r, int k, int64_t S, int64_t s,
+__device__ __forceinline__ void gather32(const float2 *pq, const uint4 &r, int k, int64_t S, int64_t s,
                                          float (&p)[4], float (&q)[4]) {
     const uint32_t n[4] = {r.x & kMask24, r.y, r.z, r.w};
-    float4 v[4];
+    float2 v[4];
 #pragma unroll
-    for (int j = 0; j < 4; j++) v[j] = j < k ? pq[(int64_t)n[j] * S + s] : make_float4(0.f, 0.f, 1.f, 0.f);
+    for (int j = 0; j < 4; j++) v[j] = j < k ? pq[(int64_t)n[j] * S + s] : make_float2(0.f, 0.f);
 #pragma unroll
     for (int j = 0; j < 4; j++) {
-        p[j] = v[j].x + v[j].y;
-        q[j] = v[j].z + v[j].w;
+        const pair_ff a = pair_get(v[j]);
+        p[j] = a.p.hi + a.p.lo;
+        q[j] = a.q.hi + a.q.lo;
     }
+}
+
+// Q - P of a stored net, rounded once to binary32
+__device__ __forceinline__ float qmp32(const float2 &v) {
+    const pair_ff a = pair_get(v);
+    const ff d = ff_add(a.q, ff{-a.p.hi, -a.p.lo});
+    return d.hi + d.lo;
 }
 
 // switching activity of net n in scenario s: the input TR at a startpoint in
 // tr_mode 0, else TR_model = 2 P Q (Eq. 2) rounded once to binary32
-__device__ __forceinline__ float alpha32(const float4 *pq, const float *tr_in, int64_t n, int64_t ns, int64_t S,
+__device__ __forceinline__ float alpha32(const float2 *pq, const float *tr_in, int64_t n, int64_t ns, int64_t S,
                                          int64_t s, int tr_mode) {
     if (n < ns && tr_mode == 0) return tr_in[n * S + s];
     return pair_tr(pair_get(pq[n * S + s]));
 }
 
-__global__ void k_fwdb_start(const float *__restrict__ sp_in, float4 *pq, int64_t n) {
+__global__ void k_fwdb_start(const float *__restrict__ sp_in, float2 *pq, int64_t n) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    pq[i] = pair_set(pair_of(sp_in[i]));
+    pq[i] = make_float2(sp_in[i], 0.f);
 }
 
-__global__ void k_fwdb_level(const uint4 *__restrict__ fanin, float4 *pq, int32_t c0, int32_t c1, int64_t ns,
+__global__ void k_fwdb_level(const uint4 *__restrict__ fanin, float2 *pq, int32_t c0, int32_t c1, int64_t ns,
                              int64_t S, OpTable ops) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S) return;
@@ -72,38 +88,51 @@ __global__ void k_fwdb_level(const uint4 *__restrict__ fanin, float4 *pq, int32_
         const int k = op_arity(ops, op);
         pair_ff x[4];
         gather_ffb(pq, r, k, S, s, x);
-        pq[(ns + c) * S + s] = pair_set(cell_pair(k, op_tt(ops, op), x));
+        pq[(ns + c) * S + s] = p_set(cell_pair(k, op_tt(ops, op), x));
     }
 }
 
-// Eq. 1 per scenario in FP64: chunk b of the nets -> partials[b * S + s], then
-// the chunks summed in index order (a fixed order: reproducible)
-__global__ void k_powerb_partials(const float4 *__restrict__ pq, const float *__restrict__ tr_in,
+// Eq. 1 per scenario: chunk b of the nets -> partials[s * nchunks + b], then
+// the chunks of each scenario summed in FP64 in a fixed order (reproducible).
+// Within a chunk a thread forms each term alpha * C as an exact float-float
+// product and adds it with TwoSum (about 48 significant bits), so the FP64
+// pipe, slow on this part, sees one conversion per chunk instead of several
+// operations per term.
+__global__ void k_powerb_partials(const float2 *__restrict__ pq, const float *__restrict__ tr_in,
                                   const float *__restrict__ cload, double *partials, int64_t nn, int64_t ns,
-                                  int64_t S, int64_t chunk, int tr_mode) {
+                                  int64_t S, int64_t chunk, int nchunks, int tr_mode) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S) return;
     const int64_t n0 = (int64_t)blockIdx.y * chunk, n1 = n0 + chunk < nn ? n0 + chunk : nn;
-    double acc = 0.0;
-    for (int64_t n = n0; n < n1; n++) {
-        double a;
-        if (n < ns && tr_mode == 0) {
-            a = (double)tr_in[n * S + s];
-        } else {
-            const float4 o = pq[n * S + s];
-            a = 2.0 * ((double)o.x + (double)o.y) * ((double)o.z + (double)o.w);
+    ff acc = ff_make(0.f);
+    for (int64_t n = n0; n < n1; n += 4) {
+        float a[4], c[4];
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const int64_t m = n + i;
+            a[i] = 0.f;
+            c[i] = 0.f;
+            if (m < n1) {
+                a[i] = alpha32(pq, tr_in, m, ns, S, s, tr_mode);
+                c[i] = cload[m];
+            }
         }
-        acc += a * (double)cload[n];
+#pragma unroll
+        for (int i = 0; i < 4; i++) acc = ff_add(acc, ff_mul(ff_make(a[i]), ff_make(c[i])));
     }
-    partials[(int64_t)blockIdx.y * S + s] = acc;
+    partials[s * nchunks + blockIdx.y] = (double)acc.hi + (double)acc.lo;
 }
 
+// one warp per scenario: lane l sums chunks l, l + 32, ... in order, then a fixed shuffle tree
 __global__ void k_sumb_final(const double *__restrict__ partials, int nchunks, int64_t S, double K, double *out) {
-    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (s >= S) return;
     double acc = 0.0;
-    for (int b = 0; b < nchunks; b++) acc += partials[(int64_t)b * S + s];
-    out[s] = K * acc;
+    for (int b = lane; b < nchunks; b += 32) acc += partials[s * nchunks + b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) out[s] = K * acc;
 }
 
 __global__ void k_seedb(float *ks, const double *__restrict__ w, double K, int64_t S) {
@@ -115,7 +144,7 @@ __global__ void k_seedb(float *ks, const double *__restrict__ w, double K, int64
 // plus its local term d(K_s C 2PQ)/dP = 2 K_s C (Q - P); the cell then writes
 // one contribution per input edge (no atomics)
 __global__ void k_bwdb_level(const uint4 *__restrict__ fanin, const int32_t *__restrict__ fptr,
-                             const int4 *__restrict__ efpos, const float4 *__restrict__ pq,
+                             const int4 *__restrict__ efpos, const float2 *__restrict__ pq,
                              const float *__restrict__ cload, const float *__restrict__ ks, float *gfo, int32_t c0,
                              int32_t c1, int64_t ns, int64_t S, OpTable ops) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -127,7 +156,7 @@ __global__ void k_bwdb_level(const uint4 *__restrict__ fanin, const int32_t *__r
         const int32_t e0 = fptr[n], e1 = fptr[n + 1];
         float acc = 0.f;
         for (int32_t e = e0; e < e1; e++) acc += gfo[(int64_t)e * S + s];
-        const float g = acc + 2.f * Ks * cload[n] * pair_qmp(pq[n * S + s]);
+        const float g = acc + 2.f * Ks * cload[n] * qmp32(pq[n * S + s]);
         const uint4 r = fanin[c];
         const uint32_t op = r.x >> 24;
         const int k = op_arity(ops, op);
@@ -143,7 +172,7 @@ __global__ void k_bwdb_level(const uint4 *__restrict__ fanin, const int32_t *__r
 }
 
 // startpoints: fanout sum, plus the local term when their TR derives from their SP (tr_mode 1)
-__global__ void k_bwdb_start(const int32_t *__restrict__ fptr, const float4 *__restrict__ pq,
+__global__ void k_bwdb_start(const int32_t *__restrict__ fptr, const float2 *__restrict__ pq,
                              const float *__restrict__ cload, const float *__restrict__ ks,
                              const float *__restrict__ gfo, float *gsp, int64_t ns, int64_t S, int tr_mode) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -155,7 +184,7 @@ __global__ void k_bwdb_start(const int32_t *__restrict__ fptr, const float4 *__r
         float acc = 0.f;
         for (int32_t e = e0; e < e1; e++) acc += gfo[(int64_t)e * S + s];
         float g = acc;
-        if (tr_mode) g += 2.f * Ks * cload[k] * pair_qmp(pq[k * S + s]);
+        if (tr_mode) g += 2.f * Ks * cload[k] * qmp32(pq[k * S + s]);
         gsp[k * S + s] = g;
     }
 }
@@ -163,7 +192,7 @@ __global__ void k_bwdb_start(const int32_t *__restrict__ fptr, const float4 *__r
 // dP_s/dC_n = K_s alpha_n(s); dP_s/dpincap_c = K_s sum_j alpha_{fanin j}(s)
 // (one pin cap per cell, loading each of its fanin nets); dP_s/dTR_k = K_s C_k
 // at a startpoint in tr_mode 0, else 0
-__global__ void k_gradb_rows(const uint4 *__restrict__ fanin, const float4 *__restrict__ pq,
+__global__ void k_gradb_rows(const uint4 *__restrict__ fanin, const float2 *__restrict__ pq,
                              const float *__restrict__ tr_in, const float *__restrict__ cload,
                              const int32_t *__restrict__ net_of_user, const int32_t *__restrict__ cell_of_user,
                              const float *__restrict__ ks, float *gcl, float *gpin, float *gtr, int64_t nn,
@@ -202,7 +231,7 @@ __global__ void k_gradb_rows(const uint4 *__restrict__ fanin, const float4 *__re
 
 // Cap gradients summed over the scenarios in FP64: one warp per row, lane l
 // takes scenarios l, l + 32, ... in order, then a fixed shuffle tree.
-__global__ void k_gradb_reduce(const uint4 *__restrict__ fanin, const float4 *__restrict__ pq,
+__global__ void k_gradb_reduce(const uint4 *__restrict__ fanin, const float2 *__restrict__ pq,
                                const float *__restrict__ tr_in, const int32_t *__restrict__ net_of_user,
                                const int32_t *__restrict__ cell_of_user, const float *__restrict__ ks, float *gcl,
                                float *gpin, int64_t nn, int64_t nc, int64_t ns, int64_t S, int tr_mode, OpTable ops) {
@@ -243,7 +272,7 @@ __global__ void k_gradb_reduce(const uint4 *__restrict__ fanin, const float4 *__
     }
 }
 
-__global__ void k_netb_user(const float4 *__restrict__ pq, const float *__restrict__ tr_in,
+__global__ void k_netb_user(const float2 *__restrict__ pq, const float *__restrict__ tr_in,
                             const int32_t *__restrict__ net_of_user, float *sp_out, float *tr_out, int64_t nn,
                             int64_t ns, int64_t S, int tr_mode) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -252,7 +281,7 @@ __global__ void k_netb_user(const float4 *__restrict__ pq, const float *__restri
     for (int64_t u = (int64_t)blockIdx.y * blockDim.y + threadIdx.y; u < nn; u += step) {
         const int64_t n = net_of_user[u];
         if (sp_out) {
-            const float4 v = pq[n * S + s];
+            const float2 v = pq[n * S + s];
             sp_out[u * S + s] = v.x + v.y;
         }
         if (tr_out) tr_out[u * S + s] = alpha32(pq, tr_in, n, ns, S, s, tr_mode);
@@ -303,7 +332,7 @@ __global__ void k_virus_level(const uint4 *__restrict__ fanin, uint64_t *words, 
 }
 
 __global__ void k_virus_partials(const uint64_t *__restrict__ words, const float *__restrict__ cload,
-                                 double *partials, int64_t nn, int64_t S, int64_t W, int64_t chunk) {
+                                 double *partials, int64_t nn, int64_t S, int64_t W, int64_t chunk, int nchunks) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S) return;
     const int64_t w = s >> 6;
@@ -314,7 +343,7 @@ __global__ void k_virus_partials(const uint64_t *__restrict__ words, const float
         const uint64_t d = words[n * 2 * W + w] ^ words[n * 2 * W + W + w];
         if ((d >> b) & 1ull) acc += (double)cload[n];
     }
-    partials[(int64_t)blockIdx.y * S + s] = acc;
+    partials[s * nchunks + blockIdx.y] = acc;
 }
 
 dim3 bgrid(int64_t S, BatchShape sh, int64_t rows) {
@@ -347,8 +376,8 @@ void launch_powerb(const DevDesign &d, const BatchBufs &b, int tr_mode, double K
     int64_t chunk = 0;
     const int nch = nchunks_of(d.n_nets, &chunk);
     k_powerb_partials<<<dim3((unsigned)cdiv(S, 128), (unsigned)nch), 128, 0, s>>>(
-        b.pq, b.tr_in, d.cload, b.partials, d.n_nets, d.n_start, S, chunk, tr_mode);
-    k_sumb_final<<<(unsigned)cdiv(S, 128), 128, 0, s>>>(b.partials, nch, S, K, b.power);
+        b.pq, b.tr_in, d.cload, b.partials, d.n_nets, d.n_start, S, chunk, nch, tr_mode);
+    k_sumb_final<<<(unsigned)cdiv(S * 32, 256), 256, 0, s>>>(b.partials, nch, S, K, b.power);
 }
 
 void launch_seedb(const BatchBufs &b, double K, const double *weights, cudaStream_t s) {
@@ -416,8 +445,8 @@ void launch_virus(const DevDesign &d, const OpTable &ops, const int32_t *lvl, co
     int64_t chunk = 0;
     const int nch = nchunks_of(d.n_nets, &chunk);
     k_virus_partials<<<dim3((unsigned)cdiv(S, 128), (unsigned)nch), 128, 0, s>>>(words, d.cload, partials, d.n_nets,
-                                                                                S, W, chunk);
-    k_sumb_final<<<(unsigned)cdiv(S, 128), 128, 0, s>>>(partials, nch, S, 1.0, out);
+                                                                                S, W, chunk, nch);
+    k_sumb_final<<<(unsigned)cdiv(S * 32, 256), 256, 0, s>>>(partials, nch, S, 1.0, out);
 }
 
 }  // namespace dp

@@ -99,6 +99,17 @@ __device__ __forceinline__ float pair_tr(const pair_ff &a) {
     return 2.f * (t.hi + t.lo);
 }
 
+// The pair divided by its sum s = P + Q.  In float-float s differs from 1 only
+// by accumulated rounding, d = s - 1 of order 1e-13, so x / s = x (1 - d) up
+// to d^2 (far below the format's 2^-44): one binary32 product and a
+// FastTwoSum per value instead of two float-float divisions.
+__device__ __forceinline__ pair_ff pair_renorm(const ff &p, const ff &q) {
+    const ff s = ff_add(p, q);
+    const float d = __fadd_rn(__fsub_rn(s.hi, 1.f), s.lo);   // s.hi - 1 is exact near 1
+    return pair_ff{fast_two_sum(p.hi, __fsub_rn(p.lo, __fmul_rn(p.hi, d))),
+                   fast_two_sum(q.hi, __fsub_rn(q.lo, __fmul_rn(q.hi, d)))};
+}
+
 template <int K>
 __device__ __forceinline__ pair_ff ml_pair(uint32_t tt, const pair_ff (&x)[4]) {
     ff v1[1 << K], v0[1 << K];
@@ -118,8 +129,7 @@ __device__ __forceinline__ pair_ff ml_pair(uint32_t tt, const pair_ff (&x)[4]) {
             v0[m] = ff_add(ff_mul(x[i].q, v0[2 * m]), ff_mul(x[i].p, v0[2 * m + 1]));
         }
     }
-    const ff s = ff_add(v1[0], v0[0]);
-    return pair_ff{ff_div(v1[0], s), ff_div(v0[0], s)};
+    return pair_renorm(v1[0], v0[0]);
 }
 
 __device__ __forceinline__ pair_ff cell_pair(int k, uint32_t tt, const pair_ff (&x)[4]) {

@@ -94,14 +94,14 @@ cudaError_t launch_wait_selftest(unsigned *bar, int *err, long long limit, cudaS
 struct BatchBufs {
     int64_t S;
     float *sp_in, *tr_in;   // [n_start * S] staged inputs
-    float4 *pq;             // [n_nets * S] float-float (P.hi, P.lo, Q.hi, Q.lo), untagged
+    float2 *pq;             // [n_nets * S] float-float P(net=1) (hi, lo); P(net=0) = 1 - P re-derived
     float *gfo;             // [n_edges * S] edge adjoints in fanout-CSR order
     float *gsp;             // [n_start * S] SP adjoint of the startpoints
     double *partials;       // [kBatchPowerChunks * S]
     double *power;          // [S] model power per scenario
     float *ks;              // [S] per-scenario seed of the backward (K * weight), binary32
 };
-constexpr int kBatchPowerChunks = 256;   // fixed split of the nets -> deterministic FP64 sums
+constexpr int kBatchPowerChunks = 1024;   // fixed split of the nets -> deterministic FP64 sums
 
 struct BatchShape {
     int bx, by;   // threads over scenarios x cells per block
