@@ -303,6 +303,125 @@ def bench_batched(args, dp, torch, dev, pk: dict) -> dict:
     return out
 
 
+def bench_serving(args, dp, torch, dev) -> dict:
+    """Served requests on 8 resident netlists (5K, 20K, 50K, 120K, 300K, 600K, 1M and 2M cells,
+    generator seeds 1-8): 2,000 requests, each naming a design uniformly and carrying either new
+    input SP/TR or a sizing delta (1 % of the design's X1 cells moved to X2 or X4), half of them
+    asking for gradients.  Three runs of the same requests: Poisson arrivals at 5,000 requests/s
+    through the continuous-batching server (latency from submission to completion, p50/p99); all
+    2,000 submitted at once (saturated throughput); and the plain loop - one request at a time,
+    synchronous, the same kernels with one scenario per launch.  The served results must equal the
+    plain loop's bit for bit."""
+    from paper_2608_03778_gb300 import netgen
+    names = [f"serve_{n}" for n in (5000, 20000, 50000, 120000, 300000, 600000, 1000000, 2000000)]
+    lib = netgen.library_text()
+    n_req, rate, max_batch = 2000, 5000.0, 64
+    rng = np.random.default_rng(2026)
+    texts = [netgen.netlist_text(netgen.WORKLOADS[n]) for n in names]
+    x1 = []
+    for t in texts:
+        c = dp.dp_compile(t, lib)
+        v = dp.dp_compiled_view_get(c)
+        dp.dp_compiled_free(c)
+        x1.append(np.flatnonzero(v["pincap"][v["cell_of_user"]] == np.float32(0.8)).astype(np.int32))
+    pin = lambda n, dt: torch.empty(n, dtype=dt, pin_memory=True).numpy()  # noqa: E731
+    srv = dp.dp_server_create(dp.server_config(device=dev.index or 0, max_batch=max_batch))
+    plain = dp.dp_server_create(dp.server_config(device=dev.index or 0, plain=1))
+    try:
+        infos = []
+        for i, t in enumerate(texts):
+            ns = netgen.WORKLOADS[names[i]].n_start
+            sp, tr = netgen.scenario_inputs(ns, 500 + i, 1)
+            ref = (np.ascontiguousarray(sp[:, 0]), np.ascontiguousarray(tr[:, 0]))
+            a = dp.dp_server_add_design(srv, t, lib, *ref)
+            b = dp.dp_server_add_design(plain, t, lib, *ref)
+            assert a == b == i
+            infos.append(dp.dp_server_design_info(srv, i))
+        jobs = []
+        for j in range(n_req):
+            k = int(rng.integers(len(names)))
+            ns, nc = infos[k].n_start, infos[k].n_cells
+            job = {"design": k, "grad": int(rng.integers(2)), "power": pin(1, torch.float64)}
+            if rng.integers(2):
+                sp, tr = netgen.scenario_inputs(ns, 10_000 + j, 1)
+                job["sp"], job["tr"] = pin(ns, torch.float32), pin(ns, torch.float32)
+                job["sp"][:], job["tr"][:] = sp[:, 0], tr[:, 0]
+                job["kind"] = "inputs"
+            else:
+                m = max(1, nc // 100)
+                cells = rng.choice(x1[k], min(m, len(x1[k])), replace=False).astype(np.int32)
+                job["cells"], job["caps"] = pin(len(cells), torch.int32), pin(len(cells), torch.float32)
+                job["cells"][:] = cells
+                job["caps"][:] = rng.choice(np.array([1.6, 3.2], np.float32), len(cells))
+                job["kind"] = "sizing"
+            if job["grad"]:
+                job["gsp"], job["gtr"], job["gpin"] = pin(ns, torch.float32), pin(ns, torch.float32), pin(
+                    nc, torch.float32)
+            job["req"] = dp.request(k, job["power"], job.get("sp"), job.get("tr"), job.get("cells"),
+                                    job.get("caps"), job["grad"], job.get("gsp"), job.get("gtr"), job.get("gpin"))
+            jobs.append(job)
+
+        def results():
+            return [[j["power"].copy()] + ([j["gsp"].copy(), j["gtr"].copy(), j["gpin"].copy()] if j["grad"] else [])
+                    for j in jobs]
+
+        # warm-up: every design once through each server
+        for k in range(len(names)):
+            w = [j for j in jobs if j["design"] == k][:2]
+            for j in w:
+                dp.dp_server_wait(srv, dp.dp_server_submit(srv, j["req"]), 120.0)
+                dp.dp_server_wait(plain, dp.dp_server_submit(plain, j["req"]), 120.0)
+
+        # Poisson arrivals
+        gaps = rng.exponential(1.0 / rate, n_req)
+        arrive = np.cumsum(gaps) - gaps[0]
+        st0 = dp.dp_server_get_stats(srv)
+        tickets = []
+        t0 = time.perf_counter()
+        for j, ta in zip(jobs, arrive):
+            while time.perf_counter() - t0 < ta:
+                pass
+            tickets.append(dp.dp_server_submit(srv, j["req"]))
+        lat = np.array([dp.dp_server_wait(srv, t, 600.0) for t in tickets])
+        t_poisson = time.perf_counter() - t0
+        st1 = dp.dp_server_get_stats(srv)
+        served = results()
+        # saturated
+        t0 = time.perf_counter()
+        tickets = [dp.dp_server_submit(srv, j["req"]) for j in jobs]
+        lat_sat = np.array([dp.dp_server_wait(srv, t, 600.0) for t in tickets])
+        t_sat = time.perf_counter() - t0
+        st2 = dp.dp_server_get_stats(srv)
+        saturated = results()
+        # plain loop
+        t0 = time.perf_counter()
+        lat_plain = np.array([dp.dp_server_wait(plain, dp.dp_server_submit(plain, j["req"]), 600.0) for j in jobs])
+        t_plain = time.perf_counter() - t0
+        base = results()
+        same = all(all(np.array_equal(x, y) for x, y in zip(a, b)) for a, b in zip(served, base)) and all(
+            all(np.array_equal(x, y) for x, y in zip(a, b)) for a, b in zip(saturated, base))
+        nb = st1.batches - st0.batches
+        return {
+            "workload": "8 resident netlists serve_5000 ... serve_2000000 (seeds 1-8); 2,000 requests, half new "
+                        "input SP/TR, half sizing deltas (1 % of X1 cells to X2/X4); gradients on half",
+            "max_batch": max_batch,
+            "poisson": {"rate_per_s": rate, "p50_ms": float(np.percentile(lat, 50)),
+                        "p99_ms": float(np.percentile(lat, 99)), "throughput_rps": n_req / t_poisson,
+                        "batches": int(nb), "mean_batch": (st1.requests - st0.requests) / max(nb, 1)},
+            "saturated": {"throughput_rps": n_req / t_sat, "p50_ms": float(np.percentile(lat_sat, 50)),
+                          "p99_ms": float(np.percentile(lat_sat, 99)),
+                          "mean_batch": (st2.requests - st1.requests) / max(st2.batches - st1.batches, 1)},
+            "plain_loop": {"throughput_rps": n_req / t_plain, "p50_ms": float(np.percentile(lat_plain, 50)),
+                           "p99_ms": float(np.percentile(lat_plain, 99))},
+            "speedup_saturated_vs_plain": t_plain / t_sat,
+            "identical_to_plain_loop": bool(same),
+            "device_bytes": int(dp.dp_server_get_stats(srv).device_bytes),
+        }
+    finally:
+        dp.dp_server_destroy(srv)
+        dp.dp_server_destroy(plain)
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -312,6 +431,7 @@ def main() -> None:
     ap.add_argument("--workload", default="roofline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-scenario measurement")
+    ap.add_argument("--no-serving", action="store_true", help="skip the request-server measurement")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -440,6 +560,8 @@ def main() -> None:
     dp.dp_destroy(ctx)
     if not args.no_batched:
         line["batched"] = bench_batched(args, dp, torch, dev, pk)
+    if not args.no_serving:
+        line["serving"] = bench_serving(args, dp, torch, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(text, lib, sp, tr, nc, cfg.sim_words)
     if rank == 0:

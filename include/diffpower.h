@@ -343,6 +343,77 @@ dp_status dp_step_kernels(const dp_design *d, int64_t *kernels);
 dp_status dp_power_noalloc(int device, const float *tr, const float *beta, const float *cload, int64_t n,
                            double vdd, double fclk, double *watts, void *cuda_stream);
 
+/* ------------------------------ request server ------------------------------
+ * Several designs resident on one GPU; power and gradient requests of any of
+ * them are served by continuous batching: a worker thread takes the requests
+ * waiting for a design whose batch slot is free (up to max_batch, in arrival
+ * order) and runs them as the scenarios of one batched pass on that design's
+ * own stream, so batches of different designs overlap on the device and
+ * requests that arrive meanwhile join the design's next batch.  A request's
+ * results do not depend on the requests it shares a batch with: they are
+ * bitwise the same alone and in any mix.  Model power and model gradient
+ * (Eq. 1, Eq. 2, Eq. 7); no simulation. */
+typedef struct dp_server dp_server;
+
+typedef struct {
+    int32_t device;       /* CUDA device */
+    int32_t max_batch;    /* requests per batch per design, 1..4096 (default 64) */
+    size_t hbm_budget;    /* device bytes the server may hold for designs and their batch buffers;
+                             0: 80 % of the free memory at creation */
+    int32_t plain;        /* 1: no worker and no batching - dp_server_submit runs the request on the
+                             calling thread and returns when it is done (the one-at-a-time loop) */
+    dp_config analysis;   /* vdd, fclk, tr_mode; grad_mode must be 0 */
+} dp_server_config;
+
+/* One request.  Every pointer is host memory borrowed until dp_server_wait
+ * returns for it; page-locked buffers make the copies asynchronous. */
+typedef struct {
+    int32_t design;        /* id from dp_server_add_design */
+    const float *sp;       /* n_start startpoint SP, or NULL for the design's reference inputs */
+    const float *tr;       /* n_start startpoint TR (NULL exactly when sp is) */
+    const int32_t *cells;  /* sizing delta: cell-line indices (may repeat: the last entry counts) */
+    const float *pincap;   /* their new input pin caps (absolute values, fF) */
+    int32_t n_delta;       /* entries in cells / pincap (0: the design's own caps) */
+    int32_t want_grad;     /* 1: also the gradients below */
+    double *power;         /* out: model power, W */
+    float *grad_sp;        /* out (want_grad, may be NULL): dP/dSP_in [n_start] */
+    float *grad_tr;        /* out (want_grad, may be NULL): dP/dTR_in [n_start] */
+    float *grad_pincap;    /* out (want_grad, may be NULL): dP/dpincap [n_cells], W/fF */
+} dp_request;
+
+typedef struct {
+    int64_t batches;          /* batches run */
+    int64_t requests;         /* requests finished */
+    int64_t max_batch_seen;   /* largest batch */
+    size_t device_bytes;      /* device bytes charged against the budget */
+    int32_t designs;          /* resident designs */
+} dp_server_stats;
+
+void dp_server_config_default(dp_server_config *cfg);
+/* Creates a server (and its worker thread unless cfg->plain).  DP_EINVAL for a
+ * bad max_batch or grad_mode != 0. */
+dp_status dp_server_create(const dp_server_config *cfg, dp_server **out);
+/* Stops the worker after the batches in flight, frees every design. */
+void dp_server_destroy(dp_server *srv);
+const char *dp_server_last_error(const dp_server *srv);
+/* Compiles and uploads a design, reserves its batch buffers for max_batch
+ * requests, tunes its launch shapes once (on max_batch copies of the reference
+ * inputs) and keeps them.  ref_sp / ref_tr (n_start each, may be NULL: 0.5 and
+ * 0.25) are the inputs of requests that give none.  Admission: DP_ENOMEM when
+ * the design would exceed the HBM budget. */
+dp_status dp_server_add_design(dp_server *srv, const char *netlist, size_t netlist_len, const char *library,
+                               size_t library_len, const float *ref_sp, const float *ref_tr, int32_t *id);
+/* Sizes of a resident design; device_bytes = what it is charged. */
+dp_status dp_server_design_info(dp_server *srv, int32_t id, dp_info *info);
+/* Queues a request (validated first: DP_EINVAL) and returns its ticket without
+ * waiting; thread-safe. */
+dp_status dp_server_submit(dp_server *srv, const dp_request *req, uint64_t *ticket);
+/* Waits until the request is done (timeout_s > 0: at most that long, then
+ * DP_ETIMEOUT and the ticket stays valid), reports its latency from submission
+ * to completion in ms and releases the ticket. */
+dp_status dp_server_wait(dp_server *srv, uint64_t ticket, double timeout_s, double *latency_ms);
+dp_status dp_server_get_stats(dp_server *srv, dp_server_stats *stats);
+
 #ifdef __cplusplus
 }
 #endif

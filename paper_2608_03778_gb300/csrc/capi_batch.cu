@@ -55,6 +55,7 @@ dp_status ensure_batch(dp_design *D, int64_t S) {
     B.stage = nullptr;
     B.cap = 0;
     B.tuned_S = 0;
+    B.shapes_locked = false;
     const size_t ns = (size_t)D->d.n_start, nn = (size_t)D->d.n_nets, ne = (size_t)D->n_edges, s = (size_t)S;
     dp_status st = DP_OK;
 #define TRYB(x) do { if ((st = (x)) != DP_OK) { free_list(B.allocs, B.bytes); B.b = dp::BatchBufs{}; return st; } } while (0)
@@ -160,6 +161,17 @@ void free_batch(dp_design *D) {
     D->batch = dp_batch{};
 }
 
+dp_status batch_reserve(dp_design *D, int64_t S) {
+    dp_status s = ensure_batch(D, S);
+    return s == DP_OK ? ensure_stage_batch(D) : s;
+}
+
+dp_status batch_tune_and_lock(dp_design *D) {
+    dp_status s = tune(D);
+    if (s == DP_OK) D->batch.shapes_locked = true;
+    return s;
+}
+
 dp_status batch_propagate(dp_design *D, const dp_config &c) {
     dp_batch &B = D->batch;
     DeviceGuard g(D->ctx->device);
@@ -243,7 +255,7 @@ dp_status dp_set_inputs_batch(dp_design *D, const float *sp, const float *tr, in
     D->batched = true;
     D->fwd_valid = false;
     D->sim_valid = false;
-    if (B.tuned_S != S && !capturing(c->stream)) return tune(D);
+    if (B.tuned_S != S && !B.shapes_locked && !capturing(c->stream)) return tune(D);
     return DP_OK;
 }
 

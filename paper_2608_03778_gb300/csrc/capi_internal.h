@@ -33,6 +33,7 @@ struct dp_batch {
     int fwd_tr_mode = -1;
     dp::BatchShape fwd_shape{128, 1}, bwd_shape{128, 1};
     int64_t tuned_S = 0;           // S the shapes were tuned for (0: not tuned)
+    bool shapes_locked = false;    // keep the shapes whatever S comes (a server fixes them once)
     float tune_ms[2] = {0.f, 0.f}; // best forward / backward time seen by the tuner
     // power-virus evaluation (Eq. 3): words [n_nets * 2 ceil(S/64)], partials, sums, staging
     int64_t vcap = 0;
@@ -112,6 +113,10 @@ void free_batch(dp_design *D);
 dp_status batch_propagate(dp_design *D, const dp_config &c);
 dp_status batch_get_power(dp_design *D, int hybrid, double *watts, int on_device);
 dp_status batch_get_nets(dp_design *D, float *sp, float *tr, int on_device);
+// batch buffers for S scenarios plus the host-output staging (synchronises; not under capture)
+dp_status batch_reserve(dp_design *D, int64_t S);
+// runs the launch-shape tuner on the staged batch of B.S scenarios, then locks the shapes
+dp_status batch_tune_and_lock(dp_design *D);
 
 template <class T>
 dp_status dalloc(dp_design *D, T **p, size_t count) {

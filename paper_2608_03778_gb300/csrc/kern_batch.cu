@@ -71,6 +71,11 @@ __device__ __forceinline__ float alpha32(const float2 *pq, const float *tr_in, i
     return pair_tr(pair_get(pq[n * S + s]));
 }
 
+// the load of net n in scenario s: C_load plus the scenario's sizing delta (if any)
+__device__ __forceinline__ float cl_of(const float *cload, const float *dcl, int64_t n, int64_t S, int64_t s) {
+    return dcl ? cload[n] + dcl[n * S + s] : cload[n];
+}
+
 __global__ void k_fwdb_start(const float *__restrict__ sp_in, float2 *pq, int64_t n) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -99,7 +104,8 @@ __global__ void k_fwdb_level(const uint4 *__restrict__ fanin, float2 *pq, int32_
 // pipe, slow on this part, sees one conversion per chunk instead of several
 // operations per term.
 __global__ void k_powerb_partials(const float2 *__restrict__ pq, const float *__restrict__ tr_in,
-                                  const float *__restrict__ cload, double *partials, int64_t nn, int64_t ns,
+                                  const float *__restrict__ cload, const float *__restrict__ dcl, double *partials,
+                                  int64_t nn, int64_t ns,
                                   int64_t S, int64_t chunk, int nchunks, int tr_mode) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S) return;
@@ -114,7 +120,7 @@ __global__ void k_powerb_partials(const float2 *__restrict__ pq, const float *__
             c[i] = 0.f;
             if (m < n1) {
                 a[i] = alpha32(pq, tr_in, m, ns, S, s, tr_mode);
-                c[i] = cload[m];
+                c[i] = cl_of(cload, dcl, m, S, s);
             }
         }
 #pragma unroll
@@ -145,8 +151,9 @@ __global__ void k_seedb(float *ks, const double *__restrict__ w, double K, int64
 // one contribution per input edge (no atomics)
 __global__ void k_bwdb_level(const uint4 *__restrict__ fanin, const int32_t *__restrict__ fptr,
                              const int4 *__restrict__ efpos, const float2 *__restrict__ pq,
-                             const float *__restrict__ cload, const float *__restrict__ ks, float *gfo, int32_t c0,
-                             int32_t c1, int64_t ns, int64_t S, OpTable ops) {
+                             const float *__restrict__ cload, const float *__restrict__ dcl,
+                             const float *__restrict__ ks, float *gfo, int32_t c0, int32_t c1, int64_t ns, int64_t S,
+                             OpTable ops) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S) return;
     const float Ks = ks[s];
@@ -156,7 +163,7 @@ __global__ void k_bwdb_level(const uint4 *__restrict__ fanin, const int32_t *__r
         const int32_t e0 = fptr[n], e1 = fptr[n + 1];
         float acc = 0.f;
         for (int32_t e = e0; e < e1; e++) acc += gfo[(int64_t)e * S + s];
-        const float g = acc + 2.f * Ks * cload[n] * qmp32(pq[n * S + s]);
+        const float g = acc + 2.f * Ks * cl_of(cload, dcl, n, S, s) * qmp32(pq[n * S + s]);
         const uint4 r = fanin[c];
         const uint32_t op = r.x >> 24;
         const int k = op_arity(ops, op);
@@ -173,7 +180,8 @@ __global__ void k_bwdb_level(const uint4 *__restrict__ fanin, const int32_t *__r
 
 // startpoints: fanout sum, plus the local term when their TR derives from their SP (tr_mode 1)
 __global__ void k_bwdb_start(const int32_t *__restrict__ fptr, const float2 *__restrict__ pq,
-                             const float *__restrict__ cload, const float *__restrict__ ks,
+                             const float *__restrict__ cload, const float *__restrict__ dcl,
+                             const float *__restrict__ ks,
                              const float *__restrict__ gfo, float *gsp, int64_t ns, int64_t S, int tr_mode) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S) return;
@@ -184,7 +192,7 @@ __global__ void k_bwdb_start(const int32_t *__restrict__ fptr, const float2 *__r
         float acc = 0.f;
         for (int32_t e = e0; e < e1; e++) acc += gfo[(int64_t)e * S + s];
         float g = acc;
-        if (tr_mode) g += 2.f * Ks * cload[k] * qmp32(pq[k * S + s]);
+        if (tr_mode) g += 2.f * Ks * cl_of(cload, dcl, k, S, s) * qmp32(pq[k * S + s]);
         gsp[k * S + s] = g;
     }
 }
@@ -194,6 +202,7 @@ __global__ void k_bwdb_start(const int32_t *__restrict__ fptr, const float2 *__r
 // at a startpoint in tr_mode 0, else 0
 __global__ void k_gradb_rows(const uint4 *__restrict__ fanin, const float2 *__restrict__ pq,
                              const float *__restrict__ tr_in, const float *__restrict__ cload,
+                             const float *__restrict__ dcl,
                              const int32_t *__restrict__ net_of_user, const int32_t *__restrict__ cell_of_user,
                              const float *__restrict__ ks, float *gcl, float *gpin, float *gtr, int64_t nn,
                              int64_t nc, int64_t ns, int64_t S, int tr_mode, OpTable ops) {
@@ -225,7 +234,7 @@ __global__ void k_gradb_rows(const uint4 *__restrict__ fanin, const float2 *__re
             }
             u -= nc;
         }
-        gtr[u * S + s] = tr_mode ? 0.f : Ks * cload[u];
+        gtr[u * S + s] = tr_mode ? 0.f : Ks * cl_of(cload, dcl, u, S, s);
     }
 }
 
@@ -346,6 +355,27 @@ __global__ void k_virus_partials(const uint64_t *__restrict__ words, const float
     partials[s * nchunks + blockIdx.y] = acc;
 }
 
+// dcl[at[i]] = v[i] (v NULL: 0), at[i] = net * S + scenario, one entry per (net, scenario)
+__global__ void k_scatter(float *dcl, const int64_t *__restrict__ at, const float *__restrict__ v, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dcl[at[i]] = v ? v[i] : 0.f;
+}
+
+// out[c * ldo + r] = in[r * C + c] for an R x C block, through 32 x 32 tiles in shared memory
+__global__ void k_transpose(const float *__restrict__ in, float *out, int64_t R, int64_t C, int64_t ldo) {
+    __shared__ float t[32][33];
+    const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int64_t r = r0 + i, c = c0 + threadIdx.x;
+        if (r < R && c < C) t[i][threadIdx.x] = in[r * C + c];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int64_t c = c0 + i, r = r0 + threadIdx.x;
+        if (r < R && c < C) out[c * ldo + r] = t[threadIdx.x][i];
+    }
+}
+
 dim3 bgrid(int64_t S, BatchShape sh, int64_t rows) {
     const int64_t gy = cdiv(rows > 0 ? rows : 1, sh.by);
     return dim3((unsigned)cdiv(S, sh.bx), (unsigned)(gy < 65535 ? gy : 65535));
@@ -376,7 +406,7 @@ void launch_powerb(const DevDesign &d, const BatchBufs &b, int tr_mode, double K
     int64_t chunk = 0;
     const int nch = nchunks_of(d.n_nets, &chunk);
     k_powerb_partials<<<dim3((unsigned)cdiv(S, 128), (unsigned)nch), 128, 0, s>>>(
-        b.pq, b.tr_in, d.cload, b.partials, d.n_nets, d.n_start, S, chunk, nch, tr_mode);
+        b.pq, b.tr_in, d.cload, b.dcl, b.partials, d.n_nets, d.n_start, S, chunk, nch, tr_mode);
     k_sumb_final<<<(unsigned)cdiv(S * 32, 256), 256, 0, s>>>(b.partials, nch, S, K, b.power);
 }
 
@@ -392,10 +422,11 @@ void launch_bwdb(const DevDesign &d, const BatchBufs &b, const OpTable &ops, con
         const int32_t c0 = lvl[l - 1], c1 = lvl[l];
         if (c1 > c0)
             k_bwdb_level<<<bgrid(S, sh, c1 - c0), blk, 0, s>>>(d.fanin, d.fout_ptr, (const int4 *)d.edge_fpos, b.pq,
-                                                               d.cload, b.ks, b.gfo, c0, c1, d.n_start, S, ops);
+                                                               d.cload, b.dcl, b.ks, b.gfo, c0, c1, d.n_start, S,
+                                                               ops);
     }
     if (d.n_start)
-        k_bwdb_start<<<bgrid(S, sh, d.n_start), blk, 0, s>>>(d.fout_ptr, b.pq, d.cload, b.ks, b.gfo, b.gsp,
+        k_bwdb_start<<<bgrid(S, sh, d.n_start), blk, 0, s>>>(d.fout_ptr, b.pq, d.cload, b.dcl, b.ks, b.gfo, b.gsp,
                                                              d.n_start, S, tr_mode);
 }
 
@@ -416,8 +447,8 @@ void launch_gradb(const DevDesign &d, const BatchBufs &b, const OpTable &ops, in
     if (rows == 0) return;
     const BatchShape sh{S >= 128 ? 128 : 32, S >= 128 ? 1 : 4};
     k_gradb_rows<<<bgrid(S, sh, rows), dim3((unsigned)sh.bx, (unsigned)sh.by), 0, s>>>(
-        d.fanin, b.pq, b.tr_in, d.cload, d.net_of_user, d.cell_of_user, b.ks, gcl, gpin, gtr, d.n_nets, d.n_cells,
-        d.n_start, S, tr_mode, ops);
+        d.fanin, b.pq, b.tr_in, d.cload, b.dcl, d.net_of_user, d.cell_of_user, b.ks, gcl, gpin, gtr, d.n_nets,
+        d.n_cells, d.n_start, S, tr_mode, ops);
 }
 
 void launch_netb_user(const DevDesign &d, const BatchBufs &b, int tr_mode, float *sp, float *tr, cudaStream_t s) {
@@ -425,6 +456,21 @@ void launch_netb_user(const DevDesign &d, const BatchBufs &b, int tr_mode, float
     const BatchShape sh{b.S >= 128 ? 128 : 32, b.S >= 128 ? 1 : 4};
     k_netb_user<<<bgrid(b.S, sh, d.n_nets), dim3((unsigned)sh.bx, (unsigned)sh.by), 0, s>>>(
         b.pq, b.tr_in, d.net_of_user, sp, tr, d.n_nets, d.n_start, b.S, tr_mode);
+}
+
+void launch_scatter(float *dcl, const int64_t *at, const float *v, int64_t n, cudaStream_t s) {
+    if (n > 0) k_scatter<<<(unsigned)cdiv(n, 256), 256, 0, s>>>(dcl, at, v, n);
+}
+
+void launch_transpose(const float *in, float *out, int64_t R, int64_t C, cudaStream_t s) {
+    if (R <= 0 || C <= 0) return;
+    const int64_t gy = cdiv(R, 32);
+    for (int64_t y0 = 0; y0 < gy; y0 += 65535) {   // grid.y limit: the rows go in slabs
+        const int64_t rows = (gy - y0 < 65535 ? gy - y0 : 65535) * 32;
+        const int64_t rr = R - y0 * 32 < rows ? R - y0 * 32 : rows;
+        k_transpose<<<dim3((unsigned)cdiv(C, 32), (unsigned)cdiv(rr, 32)), dim3(32, 8), 0, s>>>(
+            in + y0 * 32 * C, out + y0 * 32, rr, C, R);
+    }
 }
 
 void launch_ascent(float *x, const float *g, int64_t n, float eta, cudaStream_t s) {

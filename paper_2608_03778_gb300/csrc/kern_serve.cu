@@ -1,0 +1,108 @@
+// Sizing deltas of a served batch, turned into per-scenario C_load changes on
+// the device.  A delta entry (cell u, new pin cap, scenario s, position i in
+// its request) changes cell u's input pin cap in scenario s; the change loads
+// every input net of u (one pin cap per cell, R10).
+//
+//   1. win[c][s]  = the largest position i among the entries of cell c in s
+//                   (a cell listed more than once counts with its last entry);
+//   2. dpin[c][s] = new cap - base cap, written by that entry alone;
+//   3. every input net n of a changed cell is claimed once per scenario; the
+//      claimer sums dpin over n's sink cells in fanout-CSR order (so the value
+//      does not depend on which entry claimed it) into dcl[n][s] and records
+//      (n, s) for the clean-up;
+//   4. after the batch every touched entry of win, dpin, flag and dcl returns to
+//      its resting value.
+// All values written are independent of thread order: the batch's results are
+// reproducible bit for bit.
+#include "kern_common.cuh"
+
+namespace dp {
+namespace {
+
+__host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+__global__ void k_delta_win(const int32_t *__restrict__ cell, const int32_t *__restrict__ scen,
+                            const int32_t *__restrict__ pos, const int32_t *__restrict__ cell_of_user, int *win,
+                            int64_t ne, int64_t S) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ne) return;
+    const int64_t c = cell_of_user[cell[i]];
+    atomicMax(win + c * S + scen[i], pos[i]);
+}
+
+__global__ void k_delta_pin(const int32_t *__restrict__ cell, const float *__restrict__ cap,
+                            const int32_t *__restrict__ scen, const int32_t *__restrict__ pos,
+                            const int32_t *__restrict__ cell_of_user, const float *__restrict__ pincap,
+                            const int *__restrict__ win, float *dpin, int64_t ne, int64_t S) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ne) return;
+    const int64_t c = cell_of_user[cell[i]];
+    if (win[c * S + scen[i]] == pos[i]) dpin[c * S + scen[i]] = __fsub_rn(cap[i], pincap[c]);
+}
+
+__global__ void k_delta_claim(const int32_t *__restrict__ cell, const int32_t *__restrict__ scen,
+                              const int32_t *__restrict__ pos, const int32_t *__restrict__ cell_of_user,
+                              const int *__restrict__ win, const uint4 *__restrict__ fanin,
+                              const int32_t *__restrict__ fptr, const int32_t *__restrict__ fedge,
+                              const float *__restrict__ dpin, unsigned *flag, float *dcl, int64_t *list,
+                              unsigned long long *count, int64_t ne, int64_t S, int64_t ns, OpTable ops) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ne) return;
+    const int64_t c = cell_of_user[cell[i]], s = scen[i];
+    if (win[c * S + s] != pos[i]) return;
+    const uint4 r = fanin[c];
+    const int k = op_arity(ops, r.x >> 24);
+    const uint32_t n4[4] = {r.x & kMask24, r.y, r.z, r.w};
+    for (int j = 0; j < k; j++) {
+        const int64_t n = n4[j];
+        if (atomicCAS(flag + n * S + s, 0u, 1u) != 0u) continue;
+        float sum = 0.f;
+        for (int32_t e = fptr[n]; e < fptr[n + 1]; e++) sum += dpin[(int64_t)(fedge[e] >> 2) * S + s];
+        dcl[n * S + s] = sum;
+        list[atomicAdd(count, 1ull)] = n * S + s;
+    }
+    (void)ns;
+}
+
+__global__ void k_delta_clear_nets(const int64_t *__restrict__ list, const unsigned long long *__restrict__ count,
+                                   unsigned *flag, float *dcl, int64_t cap) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cap || (unsigned long long)i >= *count) return;
+    const int64_t at = list[i];
+    flag[at] = 0u;
+    dcl[at] = 0.f;
+}
+
+__global__ void k_delta_clear_cells(const int32_t *__restrict__ cell, const int32_t *__restrict__ scen,
+                                    const int32_t *__restrict__ cell_of_user, int *win, float *dpin, int64_t ne,
+                                    int64_t S) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ne) return;
+    const int64_t at = (int64_t)cell_of_user[cell[i]] * S + scen[i];
+    win[at] = -1;
+    dpin[at] = 0.f;
+}
+
+}  // namespace
+
+void launch_sizing_deltas(const DevDesign &d, const OpTable &ops, const SizingDeltas &z, int64_t ne, int64_t S,
+                          float *dcl, cudaStream_t s) {
+    if (ne <= 0) return;
+    const unsigned g = (unsigned)cdiv(ne, 256);
+    cudaMemsetAsync(z.count, 0, sizeof(unsigned long long), s);
+    k_delta_win<<<g, 256, 0, s>>>(z.cell, z.scen, z.pos, d.cell_of_user, z.win, ne, S);
+    k_delta_pin<<<g, 256, 0, s>>>(z.cell, z.cap, z.scen, z.pos, d.cell_of_user, d.pincap, z.win, z.dpin, ne, S);
+    k_delta_claim<<<g, 256, 0, s>>>(z.cell, z.scen, z.pos, d.cell_of_user, z.win, d.fanin, d.fout_ptr, d.fout_edge,
+                                    z.dpin, z.flag, dcl, z.list, z.count, ne, S, d.n_start, ops);
+}
+
+void launch_sizing_clear(const DevDesign &d, const SizingDeltas &z, int64_t ne, int64_t S, float *dcl,
+                         cudaStream_t s) {
+    if (ne <= 0) return;
+    const int64_t cap = ne * kMaxFanin;
+    k_delta_clear_nets<<<(unsigned)cdiv(cap, 256), 256, 0, s>>>(z.list, z.count, z.flag, dcl, cap);
+    k_delta_clear_cells<<<(unsigned)cdiv(ne, 256), 256, 0, s>>>(z.cell, z.scen, d.cell_of_user, z.win, z.dpin, ne,
+                                                                S);
+}
+
+}  // namespace dp

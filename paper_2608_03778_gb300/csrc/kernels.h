@@ -100,6 +100,7 @@ struct BatchBufs {
     double *partials;       // [kBatchPowerChunks * S]
     double *power;          // [S] model power per scenario
     float *ks;              // [S] per-scenario seed of the backward (K * weight), binary32
+    const float *dcl;       // [n_nets * S] per-scenario change of C_load (sizing deltas), or NULL
 };
 constexpr int kBatchPowerChunks = 1024;   // fixed split of the nets -> deterministic FP64 sums
 
@@ -118,6 +119,30 @@ void launch_bwdb(const DevDesign &d, const BatchBufs &b, const OpTable &ops, con
 void launch_gradb(const DevDesign &d, const BatchBufs &b, const OpTable &ops, int tr_mode, bool reduce, float *gtr,
                   float *gpin, float *gcl, cudaStream_t s);
 void launch_netb_user(const DevDesign &d, const BatchBufs &b, int tr_mode, float *sp, float *tr, cudaStream_t s);
+// Sizing deltas of a served batch (kern_serve.cu): per-scenario changes of cell
+// pin caps turned into per-scenario C_load changes, deterministically.
+constexpr int kMaxFanin = 4;
+struct SizingDeltas {
+    const int32_t *cell;        // [ne] cell-line index of each entry
+    const float *cap;           // [ne] its new input pin cap, fF
+    const int32_t *scen;        // [ne] scenario of the entry
+    const int32_t *pos;         // [ne] position of the entry within its request (the last one counts)
+    int *win;                   // [n_cells * S] -1 at rest
+    float *dpin;                // [n_cells * S] 0 at rest
+    unsigned *flag;             // [n_nets * S] 0 at rest
+    int64_t *list;              // [kMaxFanin * ne] claimed (net, scenario) slots
+    unsigned long long *count;  // entries of list
+};
+// fills dcl[n * S + s] for every net loaded by a changed cell
+void launch_sizing_deltas(const DevDesign &d, const OpTable &ops, const SizingDeltas &z, int64_t ne, int64_t S,
+                          float *dcl, cudaStream_t s);
+// returns win, dpin, flag and dcl to rest after the batch
+void launch_sizing_clear(const DevDesign &d, const SizingDeltas &z, int64_t ne, int64_t S, float *dcl,
+                         cudaStream_t s);
+// dcl[at[i]] = v[i] (v NULL: 0)
+void launch_scatter(float *dcl, const int64_t *at, const float *v, int64_t n, cudaStream_t s);
+// out[c][r] = in[r][c] (row-major R x C in, C x R out)
+void launch_transpose(const float *in, float *out, int64_t R, int64_t C, cudaStream_t s);
 // x <- clip(x + eta g, 0, 1) (Algorithm 4 ascent step with projection)
 void launch_ascent(float *x, const float *g, int64_t n, float eta, cudaStream_t s);
 // Eq. 3: threshold SP at 0.5 into v0 (v1 = not v0), two bitwise forwards, sum of C over nets whose values differ

@@ -1,0 +1,724 @@
+// Request server: several designs resident on one GPU, analysis and gradient
+// requests of any of them served by continuous batching.
+//
+// Each design owns a CUDA stream and one batch slot.  A worker thread takes
+// the requests waiting for a design whose slot is free - up to max_batch of
+// them, in arrival order - and runs them as the scenarios of one batched pass
+// (forward, power, and the reverse pass when any of them wants gradients);
+// batches of different designs overlap on the device.  Requests that arrive
+// while a design's batch runs wait for its slot and join the next batch.
+// Admission: a design is accepted only while the device bytes it needs (the
+// resident netlist plus its batch buffers for max_batch scenarios) fit in the
+// server's HBM budget.
+//
+// A request carries either new startpoint SP/TR or the design's reference
+// inputs, and optionally a sizing delta (new input pin caps of some cells,
+// relative to the design's own caps).  The delta enters the batch as a
+// per-scenario change of C_load on the nets those cells load, so requests with
+// different deltas share a batch.  Every (cell, scenario) is computed alone,
+// the power sums of a scenario run in a fixed order, and the launch shapes are
+// fixed per design, so a request's results do not depend on the requests it
+// is batched with.
+#include <algorithm>
+#include <array>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "capi_internal.h"
+#include "compiled.h"
+
+using namespace dpi;
+
+namespace {
+
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct Req {
+    dp_request r{};
+    uint64_t ticket = 0;
+    double t_submit = 0, t_done = 0;
+    int state = 0;                 // 0 queued, 1 in flight, 2 done
+    dp_status status = DP_OK;
+};
+
+struct Slot {
+    int id = 0;
+    dp_ctx *ctx = nullptr;                  // owns this design's stream
+    cudaStream_t stream = nullptr;
+    dp_design *D = nullptr;
+    int64_t ns = 0, nc = 0, nn = 0;
+    float *d_ref_sp = nullptr, *d_ref_tr = nullptr;   // [ns]
+    float *d_in_sp = nullptr, *d_in_tr = nullptr;     // [max_batch][ns] request-major inputs
+    float *d_dcl = nullptr;                            // [nn * max_batch], zero between batches
+    // sizing-delta entries of a batch (capacity delta_cap) and the device work arrays
+    int64_t delta_cap = 0;
+    int32_t *d_cell = nullptr, *d_scen = nullptr, *d_pos = nullptr;
+    float *d_cap = nullptr;
+    int32_t *h_scen = nullptr, *h_pos = nullptr;
+    int64_t *d_list = nullptr;
+    int *d_win = nullptr;                              // [nc * max_batch]
+    float *d_dpin = nullptr;                           // [nc * max_batch]
+    unsigned *d_flag = nullptr;                        // [nn * max_batch]
+    unsigned long long *d_count = nullptr;
+    double *h_power = nullptr;                         // [max_batch], pinned
+    float *d_out_sp = nullptr, *d_out_tr = nullptr, *d_out_pin = nullptr;   // [max_batch][rows]
+    cudaEvent_t done = nullptr;
+    std::vector<std::array<cudaGraphExec_t, 2>> graphs;   // [log2 batch size][with reverse pass]
+    std::vector<void *> dev, pinned;
+    size_t bytes = 0;
+    std::deque<Req *> queue;
+    std::vector<Req *> inflight;
+    int64_t inflight_deltas = 0;
+    bool busy = false;
+};
+
+}  // namespace
+
+struct dp_server {
+    dp_server_config cfg{};
+    dp_ctx *ctx = nullptr;                  // for allocation bookkeeping and messages
+    std::vector<Slot *> slots;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::unordered_map<uint64_t, Req *> reqs;
+    uint64_t next_ticket = 1;
+    std::thread worker;
+    std::atomic<int64_t> queued{0};   // requests in the design queues (read by the worker without the lock)
+    bool stop = false;
+    size_t bytes_used = 0;
+    dp_server_stats stats{};
+    std::mutex emu;               // guards err (written by any submitting thread)
+    std::string err;
+};
+
+namespace {
+
+dp_status srv_err(dp_server *s, dp_status st, const std::string &m) {
+    if (s) {
+        std::lock_guard<std::mutex> lk(s->emu);
+        s->err = m;
+    }
+    return st;
+}
+
+template <class T>
+cudaError_t dmalloc(Slot *sl, T **p, size_t n) {
+    void *v = nullptr;
+    cudaError_t e = cudaMalloc(&v, sizeof(T) * (n ? n : 1));
+    if (e == cudaSuccess) {
+        sl->dev.push_back(v);
+        sl->bytes += sizeof(T) * (n ? n : 1);
+    }
+    *p = static_cast<T *>(v);
+    return e;
+}
+
+template <class T>
+cudaError_t hmalloc(Slot *sl, T **p, size_t n) {
+    void *v = nullptr;
+    cudaError_t e = cudaMallocHost(&v, sizeof(T) * (n ? n : 1));
+    if (e == cudaSuccess) sl->pinned.push_back(v);
+    *p = static_cast<T *>(v);
+    return e;
+}
+
+void free_slot(Slot *sl) {
+    if (!sl) return;
+    if (sl->stream) cudaStreamSynchronize(sl->stream);
+    for (void *p : sl->dev) cudaFree(p);
+    for (void *p : sl->pinned) cudaFreeHost(p);
+    if (sl->done) cudaEventDestroy(sl->done);
+    for (auto &g : sl->graphs)
+        for (cudaGraphExec_t x : g)
+            if (x) cudaGraphExecDestroy(x);
+    if (sl->D) dp_design_free(sl->D);
+    if (sl->ctx) dp_destroy(sl->ctx);
+    if (sl->stream) cudaStreamDestroy(sl->stream);
+    delete sl;
+}
+
+// (growing) room for the sizing-delta entries of one batch
+cudaError_t ensure_delta_cap(Slot *sl, int64_t n) {
+    if (n <= sl->delta_cap) return cudaSuccess;
+    int64_t cap = sl->delta_cap ? sl->delta_cap : 4096;
+    while (cap < n) cap *= 2;
+    cudaStreamSynchronize(sl->stream);
+    auto drop = [](std::vector<void *> &l, void *p, bool host) {
+        auto it = std::find(l.begin(), l.end(), p);
+        if (it != l.end()) {
+            if (host) cudaFreeHost(p);
+            else cudaFree(p);
+            l.erase(it);
+        }
+    };
+    for (void *p : {(void *)sl->d_cell, (void *)sl->d_scen, (void *)sl->d_pos, (void *)sl->d_cap, (void *)sl->d_list})
+        if (p) drop(sl->dev, p, false);
+    for (void *p : {(void *)sl->h_scen, (void *)sl->h_pos})
+        if (p) drop(sl->pinned, p, true);
+    sl->d_cell = sl->d_scen = sl->d_pos = nullptr;
+    sl->d_cap = nullptr;
+    sl->d_list = nullptr;
+    sl->h_scen = sl->h_pos = nullptr;
+    sl->delta_cap = 0;
+    cudaError_t e = dmalloc(sl, &sl->d_cell, (size_t)cap);
+    if (e == cudaSuccess) e = dmalloc(sl, &sl->d_scen, (size_t)cap);
+    if (e == cudaSuccess) e = dmalloc(sl, &sl->d_pos, (size_t)cap);
+    if (e == cudaSuccess) e = dmalloc(sl, &sl->d_cap, (size_t)cap);
+    if (e == cudaSuccess) e = dmalloc(sl, &sl->d_list, (size_t)cap * dp::kMaxFanin);
+    if (e == cudaSuccess) e = hmalloc(sl, &sl->h_scen, (size_t)cap);
+    if (e == cudaSuccess) e = hmalloc(sl, &sl->h_pos, (size_t)cap);
+    if (e == cudaSuccess) sl->delta_cap = cap;
+    return e;
+}
+
+dp::SizingDeltas deltas_view(const Slot *sl) {
+    return dp::SizingDeltas{sl->d_cell, sl->d_cap, sl->d_scen, sl->d_pos, sl->d_win, sl->d_dpin,
+                            sl->d_flag, sl->d_list, sl->d_count};
+}
+
+// Batch sizes run as graphs of a few fixed sizes: powers of two up to
+// max_batch, and max_batch itself.
+int64_t bucket_of(int64_t S, int64_t max_batch) {
+    int64_t b = 1;
+    while (b < S) b <<= 1;
+    return b < max_batch ? b : max_batch;
+}
+
+int bucket_index(int64_t Sg) {
+    int i = 0;
+    while ((int64_t)1 << i < Sg) i++;
+    return i;
+}
+
+// Captures the fixed part of a batch of Sg scenarios: inputs to scenario-innermost,
+// forward, power (copied to the pinned power buffer) and, with grad, the reverse
+// pass and the outputs back to request-major.  The per-scenario C_load delta is
+// always bound: where no request changed a cap it is zero, and C + 0 = C exactly.
+cudaError_t capture_batch_graph(dp_server *srv, Slot *sl, int64_t Sg, bool grad, cudaGraphExec_t *out) {
+    dp_design *D = sl->D;
+    dp_batch &B = D->batch;
+    const dp_config &c = srv->cfg.analysis;
+    const cudaStream_t st = sl->stream;
+    const int64_t ns = sl->ns, nc = sl->nc;
+    B.S = Sg;
+    B.b.S = Sg;
+    B.b.dcl = sl->d_dcl;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    dp::launch_transpose(sl->d_in_sp, B.b.sp_in, Sg, ns, st);
+    dp::launch_transpose(sl->d_in_tr, B.b.tr_in, Sg, ns, st);
+    dp::launch_fwdb(D->d, B.b, D->ops, D->lvl_ptr.data(), c.tr_mode, B.fwd_shape, st);
+    dp::launch_powerb(D->d, B.b, c.tr_mode, power_K(c), st);
+    if (grad) {
+        dp::launch_seedb(B.b, power_K(c), nullptr, st);
+        dp::launch_bwdb(D->d, B.b, D->ops, D->lvl_ptr.data(), c.tr_mode, B.bwd_shape, st);
+        dp::launch_transpose(B.b.gsp, sl->d_out_sp, ns, Sg, st);
+        dp::launch_gradb(D->d, B.b, D->ops, c.tr_mode, false, B.stage, nullptr, nullptr, st);
+        dp::launch_transpose(B.stage, sl->d_out_tr, ns, Sg, st);
+        dp::launch_gradb(D->d, B.b, D->ops, c.tr_mode, false, nullptr, B.stage, nullptr, st);
+        dp::launch_transpose(B.stage, sl->d_out_pin, nc, Sg, st);
+    }
+    cudaMemcpyAsync(sl->h_power, B.b.power, sizeof(double) * (size_t)Sg, cudaMemcpyDeviceToHost, st);
+    e = cudaStreamEndCapture(st, &g);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+    if (g) cudaGraphDestroy(g);
+    return e;
+}
+
+// Captures every batch graph of a design (two per batch size: with and without the reverse pass).
+cudaError_t capture_all(dp_server *srv, Slot *sl) {
+    const int64_t m = srv->cfg.max_batch;
+    for (int64_t Sg = 1;; Sg = Sg * 2 < m ? Sg * 2 : m) {
+        const int i = bucket_index(Sg);
+        for (int grad = 0; grad < 2; grad++) {
+            cudaError_t e = capture_batch_graph(srv, sl, Sg, grad != 0, &sl->graphs[(size_t)i][(size_t)grad]);
+            if (e != cudaSuccess) return e;
+        }
+        if (Sg == m) break;
+    }
+    return cudaSuccess;
+}
+
+// Queues one batch on the slot's stream: the requests' inputs and sizing deltas, the
+// captured graph of the batch size, the gradients back into the requests' buffers.  Rows
+// of a padded batch beyond the requests keep earlier (valid) inputs; their results are
+// dropped.  Any CUDA error is returned; the requests are then failed by the caller.
+cudaError_t launch_batch(dp_server *srv, Slot *sl) {
+    const int64_t S = (int64_t)sl->inflight.size(), ns = sl->ns, nc = sl->nc;
+    const int64_t Sg = bucket_of(S, srv->cfg.max_batch);
+    const cudaStream_t st = sl->stream;
+    cudaError_t e = cudaSuccess;
+    bool grad = false;
+    int64_t nd = 0;
+    for (Req *q : sl->inflight) {
+        grad = grad || q->r.want_grad;
+        nd += q->r.n_delta;
+    }
+    for (int64_t s = 0; s < S && e == cudaSuccess; s++) {
+        const Req *q = sl->inflight[(size_t)s];
+        const bool own = q->r.sp != nullptr;
+        if (ns) {
+            e = cudaMemcpyAsync(sl->d_in_sp + s * ns, own ? (const void *)q->r.sp : (const void *)sl->d_ref_sp,
+                                sizeof(float) * (size_t)ns, own ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                                st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(sl->d_in_tr + s * ns, own ? (const void *)q->r.tr : (const void *)sl->d_ref_tr,
+                                    sizeof(float) * (size_t)ns,
+                                    own ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st);
+        }
+    }
+    if (e != cudaSuccess) return e;
+    sl->inflight_deltas = nd;
+    if (nd) {   // the entries go to the device as given; the device resolves them (kern_serve.cu)
+        if ((e = ensure_delta_cap(sl, nd)) != cudaSuccess) return e;
+        int64_t off = 0;
+        for (int64_t s = 0; s < S && e == cudaSuccess; s++) {
+            const dp_request &r = sl->inflight[(size_t)s]->r;
+            if (r.n_delta <= 0) continue;
+            e = cudaMemcpyAsync(sl->d_cell + off, r.cells, sizeof(int32_t) * (size_t)r.n_delta,
+                                cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(sl->d_cap + off, r.pincap, sizeof(float) * (size_t)r.n_delta,
+                                    cudaMemcpyHostToDevice, st);
+            for (int32_t i = 0; i < r.n_delta; i++) {
+                sl->h_scen[off + i] = (int32_t)s;
+                sl->h_pos[off + i] = i;
+            }
+            off += r.n_delta;
+        }
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(sl->d_scen, sl->h_scen, sizeof(int32_t) * (size_t)nd, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(sl->d_pos, sl->h_pos, sizeof(int32_t) * (size_t)nd, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return e;
+        dp::launch_sizing_deltas(sl->D->d, sl->D->ops, deltas_view(sl), nd, Sg, sl->d_dcl, st);
+    }
+    e = cudaGraphLaunch(sl->graphs[(size_t)bucket_index(Sg)][grad ? 1 : 0], st);
+    if (e != cudaSuccess) return e;
+    if (grad)
+        for (int64_t s = 0; s < S && e == cudaSuccess; s++) {
+            const dp_request &r = sl->inflight[(size_t)s]->r;
+            if (!r.want_grad) continue;
+            if (r.grad_sp && ns)
+                e = cudaMemcpyAsync(r.grad_sp, sl->d_out_sp + s * ns, sizeof(float) * (size_t)ns,
+                                    cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess && r.grad_tr && ns)
+                e = cudaMemcpyAsync(r.grad_tr, sl->d_out_tr + s * ns, sizeof(float) * (size_t)ns,
+                                    cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess && r.grad_pincap && nc)
+                e = cudaMemcpyAsync(r.grad_pincap, sl->d_out_pin + s * nc, sizeof(float) * (size_t)nc,
+                                    cudaMemcpyDeviceToHost, st);
+        }
+    if (e != cudaSuccess) return e;
+    if (nd) dp::launch_sizing_clear(sl->D->d, deltas_view(sl), nd, Sg, sl->d_dcl, st);   // back to rest
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return cudaEventRecord(sl->done, st);
+}
+
+// The batch finished (or failed): outputs into the requests, requests done.
+void complete_batch(dp_server *srv, Slot *sl, dp_status status) {
+    const double t = now_s();
+    std::lock_guard<std::mutex> lk(srv->mu);
+    for (size_t s = 0; s < sl->inflight.size(); s++) {
+        Req *q = sl->inflight[s];
+        if (status == DP_OK && q->r.power) *q->r.power = sl->h_power[s];
+        q->status = status;
+        q->t_done = t;
+        q->state = 2;
+    }
+    srv->stats.batches += 1;
+    srv->stats.requests += (int64_t)sl->inflight.size();
+    if ((int64_t)sl->inflight.size() > srv->stats.max_batch_seen) srv->stats.max_batch_seen = (int64_t)sl->inflight.size();
+    sl->inflight.clear();
+    sl->busy = false;
+    srv->cv_done.notify_all();
+}
+
+// Takes the next batch of a free slot (lock held).
+bool take_batch(dp_server *srv, Slot *sl) {
+    if (sl->busy || sl->queue.empty()) return false;
+    const size_t m = (size_t)srv->cfg.max_batch;
+    while (!sl->queue.empty() && sl->inflight.size() < m) {
+        Req *q = sl->queue.front();
+        sl->queue.pop_front();
+        q->state = 1;
+        sl->inflight.push_back(q);
+    }
+    sl->busy = true;
+    return true;
+}
+
+// a failed batch may have left sizing deltas behind: clear them all
+void reset_after_failure(Slot *sl) {
+    cudaGetLastError();
+    cudaStreamSynchronize(sl->stream);
+    const size_t S = (size_t)sl->D->batch.cap;
+    cudaMemsetAsync(sl->d_dcl, 0, sizeof(float) * (size_t)sl->nn * S, sl->stream);
+    cudaMemsetAsync(sl->d_flag, 0, sizeof(unsigned) * (size_t)sl->nn * S, sl->stream);
+    cudaMemsetAsync(sl->d_dpin, 0, sizeof(float) * (size_t)sl->nc * S, sl->stream);
+    cudaMemsetAsync(sl->d_win, 0xFF, sizeof(int) * (size_t)sl->nc * S, sl->stream);
+    cudaStreamSynchronize(sl->stream);
+    cudaGetLastError();
+    sl->D->batch.b.dcl = nullptr;
+}
+
+void run_and_complete(dp_server *srv, Slot *sl) {
+    DeviceGuard g(srv->cfg.device);
+    cudaError_t e = launch_batch(srv, sl);
+    if (e != cudaSuccess) {
+        reset_after_failure(sl);
+        complete_batch(srv, sl, DP_ECUDA);
+    }
+}
+
+// The worker owns the batches in flight (busy, inflight, the events): it polls
+// them without the lock, and takes the lock only to move queued requests into
+// new batches or to mark a finished batch's requests done.
+void worker_main(dp_server *srv) {
+    DeviceGuard g(srv->cfg.device);
+    std::vector<Slot *> launch, slots;
+    for (;;) {
+        launch.clear();
+        bool inflight = false;
+        for (Slot *sl : slots) inflight = inflight || sl->busy;
+        if (srv->queued.load(std::memory_order_acquire) > 0 || !inflight) {
+            std::unique_lock<std::mutex> lk(srv->mu);
+            slots = srv->slots;   // designs may be added meanwhile
+            for (Slot *sl : slots)
+                if (take_batch(srv, sl)) {
+                    srv->queued.fetch_sub((int64_t)sl->inflight.size(), std::memory_order_acq_rel);
+                    launch.push_back(sl);
+                }
+            inflight = false;
+            for (Slot *sl : slots) inflight = inflight || sl->busy;
+            if (launch.empty() && !inflight) {
+                if (srv->stop) return;
+                srv->cv_work.wait(lk);
+                continue;
+            }
+        }
+        for (Slot *sl : launch) run_and_complete(srv, sl);
+        bool any_done = false;
+        for (Slot *sl : slots) {
+            if (!sl->busy || sl->inflight.empty()) continue;
+            const cudaError_t q = cudaEventQuery(sl->done);
+            if (q == cudaSuccess) {
+                complete_batch(srv, sl, DP_OK);
+                any_done = true;
+            } else if (q != cudaErrorNotReady) {
+                reset_after_failure(sl);
+                complete_batch(srv, sl, DP_ECUDA);
+                any_done = true;
+            }
+        }
+        if (launch.empty() && !any_done) std::this_thread::yield();
+    }
+}
+
+// validates a request against its design's sizes (slot found under the lock; the
+// checks themselves run outside it, since resident slots are never removed)
+dp_status check_request(dp_server *srv, const dp_request *r, Slot **out) {
+    if (!r) return srv_err(srv, DP_EINVAL, "NULL request");
+    Slot *sl = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        if (r->design < 0 || (size_t)r->design >= srv->slots.size())
+            return srv_err(srv, DP_EINVAL, "unknown design id " + std::to_string(r->design));
+        sl = srv->slots[(size_t)r->design];
+    }
+    if ((r->sp == nullptr) != (r->tr == nullptr)) return srv_err(srv, DP_EINVAL, "give both sp and tr, or neither");
+    if (r->sp) {   // branch-free scans (NaN fails every comparison)
+        int bad = 0;
+        for (int64_t k = 0; k < sl->ns; k++)
+            bad |= !(r->sp[k] >= 0.f) | !(r->sp[k] <= 1.f) | !(r->tr[k] >= 0.f) | !(r->tr[k] <= 1.f);
+        if (bad) return srv_err(srv, DP_EINVAL, "input SP and TR must lie in [0,1]");
+    }
+    if (r->n_delta < 0 || (r->n_delta > 0 && (!r->cells || !r->pincap)))
+        return srv_err(srv, DP_EINVAL, "bad sizing delta");
+    int bad = 0;
+    const int32_t nc = (int32_t)sl->nc;
+    for (int32_t i = 0; i < r->n_delta; i++)
+        bad |= (r->cells[i] < 0) | (r->cells[i] >= nc) | !(r->pincap[i] >= 0.f) | !(r->pincap[i] < 1e30f);
+    if (bad) return srv_err(srv, DP_EINVAL, "sizing delta: cell index or pin cap out of range");
+    if (!r->power) return srv_err(srv, DP_EINVAL, "NULL power output");
+    *out = sl;
+    return DP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void dp_server_config_default(dp_server_config *c) {
+    if (!c) return;
+    std::memset(c, 0, sizeof *c);
+    c->device = 0;
+    c->max_batch = 64;
+    c->hbm_budget = 0;
+    c->plain = 0;
+    dp_config_default(&c->analysis);
+    c->analysis.grad_mode = 0;
+}
+
+const char *dp_server_last_error(const dp_server *s) { return s ? s->err.c_str() : "NULL server"; }
+
+dp_status dp_server_create(const dp_server_config *cfg, dp_server **out) {
+    if (!cfg || !out) return DP_EINVAL;
+    *out = nullptr;
+    if (cfg->max_batch < 1 || cfg->max_batch > 4096) return DP_EINVAL;
+    if (cfg->analysis.grad_mode != 0 || cfg->analysis.tr_mode < 0 || cfg->analysis.tr_mode > 1) return DP_EINVAL;
+    dp_server *s = new (std::nothrow) dp_server();
+    if (!s) return DP_ENOMEM;
+    s->cfg = *cfg;
+    if (s->cfg.plain) s->cfg.max_batch = 1;
+    dp_status st = dp_create(cfg->device, nullptr, &s->ctx);
+    if (st != DP_OK) {
+        delete s;
+        return st;
+    }
+    if (dp_status e = check_cfg(s->ctx, &s->cfg.analysis); e != DP_OK) {
+        dp_destroy(s->ctx);
+        delete s;
+        return e;
+    }
+    if (s->cfg.hbm_budget == 0) {
+        DeviceGuard g(cfg->device);
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) s->cfg.hbm_budget = fr / 10 * 8;
+        else cudaGetLastError();
+    }
+    if (!s->cfg.plain) s->worker = std::thread(worker_main, s);
+    *out = s;
+    return DP_OK;
+}
+
+void dp_server_destroy(dp_server *s) {
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    for (Slot *sl : s->slots) free_slot(sl);
+    for (auto &kv : s->reqs) delete kv.second;
+    if (s->ctx) dp_destroy(s->ctx);
+    delete s;
+}
+
+dp_status dp_server_add_design(dp_server *srv, const char *netlist, size_t netlist_len, const char *library,
+                               size_t library_len, const float *ref_sp, const float *ref_tr, int32_t *id) {
+    if (!srv || !netlist || !library || !id) return srv_err(srv, DP_EINVAL, "NULL argument");
+    DeviceGuard g(srv->cfg.device);
+    dp_compiled *cp = nullptr;
+    char msg[512] = {0};
+    dp_status st = dp_compile(netlist, netlist_len, library, library_len, &cp, msg, sizeof msg);
+    if (st != DP_OK) return srv_err(srv, st, std::string("compile: ") + msg);
+    const int64_t ns = cp->n_start, nc = cp->n_cells, nn = cp->n_nets, ne = cp->n_edges;
+    const int64_t S = srv->cfg.max_batch;
+    // device bytes: resident netlist (about 24 B per net, 40 per cell, 8 per edge) and batch buffers
+    const double need = 24.0 * nn + 40.0 * nc + 8.0 * ne + 64.0 * nn +
+                        (double)S * (8.0 * nn + 4.0 * ne + 16.0 * ns + 4.0 * nn + 4.0 * std::max(nn, nc) +
+                                     4.0 * (2 * ns + nc) + 8.0 * ns + 8.0 * dp::kBatchPowerChunks + 8.0 * nc +
+                                     4.0 * nn);
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        if ((double)srv->bytes_used + need > (double)srv->cfg.hbm_budget) {
+            dp_compiled_free(cp);
+            return srv_err(srv, DP_ENOMEM, "HBM budget: the design needs about " + std::to_string((long long)need) +
+                                               " bytes, " + std::to_string((long long)(srv->cfg.hbm_budget - srv->bytes_used)) +
+                                               " left");
+        }
+    }
+    Slot *sl = new (std::nothrow) Slot();
+    if (!sl) {
+        dp_compiled_free(cp);
+        return srv_err(srv, DP_ENOMEM, "out of host memory");
+    }
+    sl->ns = ns;
+    sl->nc = nc;
+    sl->nn = nn;
+    cudaError_t e = cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl->done, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        dp_compiled_free(cp);
+        free_slot(sl);
+        return srv_err(srv, DP_ECUDA, std::string("stream: ") + cudaGetErrorString(e));
+    }
+    st = dp_create(srv->cfg.device, sl->stream, &sl->ctx);
+    if (st == DP_OK) st = dp_design_upload(sl->ctx, cp, &sl->D);
+    dp_compiled_free(cp);
+    if (st != DP_OK) {
+        srv_err(srv, st, sl->ctx ? dp_last_error(sl->ctx) : "context");
+        free_slot(sl);
+        return st;
+    }
+    dp_design *D = sl->D;
+    if ((st = batch_reserve(D, S)) != DP_OK) {
+        srv_err(srv, st, dp_last_error(sl->ctx));
+        free_slot(sl);
+        return st;
+    }
+    e = dmalloc(sl, &sl->d_ref_sp, (size_t)ns);
+    if (e == cudaSuccess) e = dmalloc(sl, &sl->d_ref_tr, (size_t)ns);
+    if (e == cudaSuccess) e = dmalloc(sl, &sl->d_in_sp, (size_t)(ns * S));
+    if (e == cudaSuccess) e = dmalloc(sl, &sl->d_in_tr, (size_t)(ns * S));
+    if (e == cudaSuccess) e = dmalloc(sl, &sl->d_dcl, (size_t)(nn * S));
+    if (e == cudaSuccess) e = dmalloc(sl, &sl->d_out_sp, (size_t)(ns * S));
+    if (e == cudaSuccess) e = dmalloc(sl, &sl->d_out_tr, (size_t)(ns * S));
+    if (e == cudaSuccess) e = dmalloc(sl, &sl->d_out_pin, (size_t)(nc * S));
+    if (e == cudaSuccess) e = hmalloc(sl, &sl->h_power, (size_t)S);
+    if (e == cudaSuccess) e = dmalloc(sl, &sl->d_win, (size_t)(nc * S));
+    if (e == cudaSuccess) e = dmalloc(sl, &sl->d_dpin, (size_t)(nc * S));
+    if (e == cudaSuccess) e = dmalloc(sl, &sl->d_flag, (size_t)(nn * S));
+    if (e == cudaSuccess) e = dmalloc(sl, &sl->d_count, 1);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sl->d_dcl, 0, sizeof(float) * (size_t)(nn * S), sl->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sl->d_win, 0xFF, sizeof(int) * (size_t)(nc * S), sl->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sl->d_dpin, 0, sizeof(float) * (size_t)(nc * S), sl->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sl->d_flag, 0, sizeof(unsigned) * (size_t)(nn * S), sl->stream);
+    if (e == cudaSuccess && ns) {
+        std::vector<float> sp(ref_sp ? ref_sp : nullptr, ref_sp ? ref_sp + ns : nullptr);
+        std::vector<float> tr(ref_tr ? ref_tr : nullptr, ref_tr ? ref_tr + ns : nullptr);
+        if (!ref_sp) sp.assign((size_t)ns, 0.5f);
+        if (!ref_tr) tr.assign((size_t)ns, 0.25f);
+        for (int64_t k = 0; k < ns; k++)
+            if (!(sp[(size_t)k] >= 0.f && sp[(size_t)k] <= 1.f && tr[(size_t)k] >= 0.f && tr[(size_t)k] <= 1.f)) {
+                free_slot(sl);
+                return srv_err(srv, DP_EINVAL, "reference SP and TR must lie in [0,1]");
+            }
+        e = cudaMemcpy(sl->d_ref_sp, sp.data(), sizeof(float) * (size_t)ns, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(sl->d_ref_tr, tr.data(), sizeof(float) * (size_t)ns, cudaMemcpyHostToDevice);
+        // the tuner times full batches of the reference inputs, then the shapes stay fixed
+        for (int64_t s = 0; s < S && e == cudaSuccess; s++) {
+            e = cudaMemcpyAsync(sl->d_in_sp + s * ns, sl->d_ref_sp, sizeof(float) * (size_t)ns,
+                                cudaMemcpyDeviceToDevice, sl->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(sl->d_in_tr + s * ns, sl->d_ref_tr, sizeof(float) * (size_t)ns,
+                                    cudaMemcpyDeviceToDevice, sl->stream);
+        }
+    }
+    if (e == cudaSuccess) {
+        dp_batch &B = D->batch;
+        B.S = S;
+        B.b.S = S;
+        dp::launch_transpose(sl->d_in_sp, B.b.sp_in, S, ns, sl->stream);
+        dp::launch_transpose(sl->d_in_tr, B.b.tr_in, S, ns, sl->stream);
+        e = cudaStreamSynchronize(sl->stream);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_slot(sl);
+        return srv_err(srv, DP_ECUDA, std::string("server buffers: ") + cudaGetErrorString(e));
+    }
+    if ((st = batch_tune_and_lock(D)) != DP_OK) {
+        srv_err(srv, st, dp_last_error(sl->ctx));
+        free_slot(sl);
+        return st;
+    }
+    sl->graphs.assign((size_t)bucket_index(S) + 1, std::array<cudaGraphExec_t, 2>{nullptr, nullptr});
+    e = capture_all(srv, sl);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(sl->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_slot(sl);
+        return srv_err(srv, DP_ECUDA, std::string("batch graphs: ") + cudaGetErrorString(e));
+    }
+    sl->bytes += D->bytes + D->batch.bytes;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    sl->id = (int)srv->slots.size();
+    srv->slots.push_back(sl);
+    srv->bytes_used += (size_t)std::max(need, (double)sl->bytes);
+    *id = sl->id;
+    return DP_OK;
+}
+
+dp_status dp_server_design_info(dp_server *srv, int32_t id, dp_info *info) {
+    if (!srv || !info) return DP_EINVAL;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    if (id < 0 || (size_t)id >= srv->slots.size()) return srv_err(srv, DP_EINVAL, "unknown design id");
+    dp_status st = dp_design_info(srv->slots[(size_t)id]->D, info);
+    info->device_bytes = srv->slots[(size_t)id]->bytes;
+    return st;
+}
+
+dp_status dp_server_submit(dp_server *srv, const dp_request *r, uint64_t *ticket) {
+    if (!srv || !ticket) return DP_EINVAL;
+    Slot *sl = nullptr;
+    const dp_status st = check_request(srv, r, &sl);
+    if (st != DP_OK) return st;
+    Req *q = new (std::nothrow) Req();
+    if (!q) return srv_err(srv, DP_ENOMEM, "out of host memory");
+    q->r = *r;
+    q->t_submit = now_s();
+    if (srv->cfg.plain) {   // one request at a time on the calling thread
+        std::unique_lock<std::mutex> lk(srv->mu);
+        q->ticket = srv->next_ticket++;
+        srv->reqs[q->ticket] = q;
+        sl->inflight.push_back(q);
+        q->state = 1;
+        sl->busy = true;
+        lk.unlock();
+        DeviceGuard g(srv->cfg.device);
+        cudaError_t e = launch_batch(srv, sl);
+        if (e == cudaSuccess) e = cudaEventSynchronize(sl->done);
+        if (e != cudaSuccess) reset_after_failure(sl);
+        complete_batch(srv, sl, e == cudaSuccess ? DP_OK : DP_ECUDA);
+        *ticket = q->ticket;
+        return DP_OK;
+    }
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        q->ticket = srv->next_ticket++;
+        srv->reqs[q->ticket] = q;
+        sl->queue.push_back(q);
+        *ticket = q->ticket;
+        srv->queued.fetch_add(1, std::memory_order_acq_rel);
+    }
+    srv->cv_work.notify_one();
+    return DP_OK;
+}
+
+dp_status dp_server_wait(dp_server *srv, uint64_t ticket, double timeout_s, double *latency_ms) {
+    if (!srv) return DP_EINVAL;
+    std::unique_lock<std::mutex> lk(srv->mu);
+    auto it = srv->reqs.find(ticket);
+    if (it == srv->reqs.end()) return srv_err(srv, DP_EINVAL, "unknown ticket");
+    Req *q = it->second;
+    const auto pred = [q] { return q->state == 2; };
+    if (timeout_s > 0) {
+        if (!srv->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), pred))
+            return srv_err(srv, DP_ETIMEOUT, "request not finished within the timeout");
+    } else {
+        srv->cv_done.wait(lk, pred);
+    }
+    if (latency_ms) *latency_ms = 1e3 * (q->t_done - q->t_submit);
+    const dp_status st = q->status;
+    srv->reqs.erase(it);
+    delete q;
+    if (st != DP_OK) return srv_err(srv, st, "the request's batch failed on the device");
+    return DP_OK;
+}
+
+dp_status dp_server_get_stats(dp_server *srv, dp_server_stats *out) {
+    if (!srv || !out) return DP_EINVAL;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    *out = srv->stats;
+    out->device_bytes = srv->bytes_used;
+    out->designs = (int32_t)srv->slots.size();
+    return DP_OK;
+}
+
+}  // extern "C"

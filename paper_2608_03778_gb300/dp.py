@@ -55,6 +55,23 @@ class dp_compiled_view(ctypes.Structure):
                 ("n_bc", ctypes.c_int64)]
 
 
+class dp_server_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("hbm_budget", ctypes.c_size_t),
+                ("plain", ctypes.c_int32), ("analysis", dp_config)]
+
+
+class dp_request(ctypes.Structure):
+    _fields_ = [("design", ctypes.c_int32), ("sp", ctypes.c_void_p), ("tr", ctypes.c_void_p),
+                ("cells", ctypes.c_void_p), ("pincap", ctypes.c_void_p), ("n_delta", ctypes.c_int32),
+                ("want_grad", ctypes.c_int32), ("power", ctypes.c_void_p), ("grad_sp", ctypes.c_void_p),
+                ("grad_tr", ctypes.c_void_p), ("grad_pincap", ctypes.c_void_p)]
+
+
+class dp_server_stats(ctypes.Structure):
+    _fields_ = [("batches", ctypes.c_int64), ("requests", ctypes.c_int64), ("max_batch_seen", ctypes.c_int64),
+                ("device_bytes", ctypes.c_size_t), ("designs", ctypes.c_int32)]
+
+
 _P = ctypes.c_void_p
 _S = ctypes.c_int
 
@@ -96,6 +113,16 @@ _sig("dp_phase_times", [_P, _P])
 _sig("dp_step_kernels", [_P, ctypes.POINTER(ctypes.c_int64)])
 _sig("dp_power_noalloc", [ctypes.c_int, _P, _P, _P, ctypes.c_int64, ctypes.c_double, ctypes.c_double, _P, _P])
 _sig("dp_set_stream", [_P, _P])
+_sig("dp_server_config_default", [ctypes.POINTER(dp_server_config)], None)
+_sig("dp_server_create", [ctypes.POINTER(dp_server_config), ctypes.POINTER(_P)])
+_sig("dp_server_destroy", [_P], None)
+_sig("dp_server_last_error", [_P], ctypes.c_char_p)
+_sig("dp_server_add_design", [_P, ctypes.c_char_p, ctypes.c_size_t, ctypes.c_char_p, ctypes.c_size_t, _P, _P,
+                              ctypes.POINTER(ctypes.c_int32)])
+_sig("dp_server_design_info", [_P, ctypes.c_int32, ctypes.POINTER(dp_info)])
+_sig("dp_server_submit", [_P, ctypes.POINTER(dp_request), ctypes.POINTER(ctypes.c_uint64)])
+_sig("dp_server_wait", [_P, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(ctypes.c_double)])
+_sig("dp_server_get_stats", [_P, ctypes.POINTER(dp_server_stats)])
 _sig("dp_get_power", [_P, _S, _P, _S])
 _sig("dp_set_inputs_batch", [_P, _P, _P, ctypes.c_int32, _S])
 _sig("dp_batch_tuning", [_P, _P, _P])
@@ -109,7 +136,9 @@ EXPORTED = ["dp_config_default", "dp_last_error", "dp_compile", "dp_compiled_fre
             "dp_propagate", "dp_simulate", "dp_total_power", "dp_backward", "dp_get_nets", "dp_step",
             "dp_phase_times", "dp_step_kernels", "dp_power_noalloc", "dp_selftest_wait", "dp_set_stream",
             "dp_get_power", "dp_set_inputs_batch", "dp_batch_tuning", "dp_backward_weighted", "dp_ascent_step",
-            "dp_virus_eval"]
+            "dp_virus_eval", "dp_server_config_default", "dp_server_create", "dp_server_destroy",
+            "dp_server_last_error", "dp_server_add_design", "dp_server_design_info", "dp_server_submit",
+            "dp_server_wait", "dp_server_get_stats"]
 
 
 def _ptr(x):
@@ -346,3 +375,80 @@ def dp_ascent_step(ctx, x, g, n: int, eta: float) -> None:
 
 def dp_virus_eval(ctx, d, sp, n_scen: int, p_virus, v0=None, on_device: int = 0) -> None:
     _check(_lib.dp_virus_eval(d, _ptr(sp), n_scen, _ptr(v0), _ptr(p_virus), on_device), ctx)
+
+
+# ---- request server ----
+
+def _scheck(status: int, srv) -> None:
+    if status != 0:
+        raise DPError(status, _lib.dp_server_last_error(srv).decode() if srv else "")
+
+
+def server_config(**kw) -> dp_server_config:
+    """dp_server_config_default() with fields overridden by keyword (analysis: a dp_config)."""
+    c = dp_server_config()
+    _lib.dp_server_config_default(ctypes.byref(c))
+    for k, v in kw.items():
+        if not hasattr(c, k):
+            raise KeyError(k)
+        setattr(c, k, v)
+    return c
+
+
+def dp_server_create(cfg: dp_server_config):
+    out = _P()
+    st = _lib.dp_server_create(ctypes.byref(cfg), ctypes.byref(out))
+    if st != 0:
+        raise DPError(st, "dp_server_create")
+    return out.value
+
+
+def dp_server_destroy(srv) -> None:
+    _lib.dp_server_destroy(srv)
+
+
+def dp_server_add_design(srv, netlist: str, library: str, ref_sp=None, ref_tr=None) -> int:
+    nb, lb = netlist.encode(), library.encode()
+    i = ctypes.c_int32()
+    _scheck(_lib.dp_server_add_design(srv, nb, len(nb), lb, len(lb), _ptr(ref_sp), _ptr(ref_tr), ctypes.byref(i)),
+            srv)
+    return i.value
+
+
+def dp_server_design_info(srv, design: int) -> dp_info:
+    info = dp_info()
+    _scheck(_lib.dp_server_design_info(srv, design, ctypes.byref(info)), srv)
+    return info
+
+
+def request(design: int, power, sp=None, tr=None, cells=None, pincap=None, want_grad: int = 0, grad_sp=None,
+            grad_tr=None, grad_pincap=None) -> dp_request:
+    """A dp_request over host arrays (kept alive by the caller until the wait returns)."""
+    r = dp_request()
+    r.design = design
+    r.sp, r.tr = _ptr(sp), _ptr(tr)
+    r.cells, r.pincap = _ptr(cells), _ptr(pincap)
+    r.n_delta = 0 if cells is None else len(cells)
+    r.want_grad = want_grad
+    r.power = _ptr(power)
+    r.grad_sp, r.grad_tr, r.grad_pincap = _ptr(grad_sp), _ptr(grad_tr), _ptr(grad_pincap)
+    return r
+
+
+def dp_server_submit(srv, req: dp_request) -> int:
+    t = ctypes.c_uint64()
+    _scheck(_lib.dp_server_submit(srv, ctypes.byref(req), ctypes.byref(t)), srv)
+    return t.value
+
+
+def dp_server_wait(srv, ticket: int, timeout_s: float = 0.0) -> float:
+    """Waits for a request; returns its latency (submission to completion) in ms."""
+    ms = ctypes.c_double()
+    _scheck(_lib.dp_server_wait(srv, ticket, timeout_s, ctypes.byref(ms)), srv)
+    return ms.value
+
+
+def dp_server_get_stats(srv) -> dp_server_stats:
+    s = dp_server_stats()
+    _scheck(_lib.dp_server_get_stats(srv, ctypes.byref(s)), srv)
+    return s

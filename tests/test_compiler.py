@@ -218,3 +218,30 @@ def test_constant_cells_and_empty():
     info = dp.dp_compiled_info(c)
     dp.dp_compiled_free(c)
     assert info.n_nets == 0 and info.n_cells == 0 and info.n_levels == 0
+
+
+def test_abi_struct_layouts_match_the_header(tmp_path):
+    """Every field offset and size of the C-ABI structs as the compiler lays them out,
+    against the ctypes mirrors the binding passes."""
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("gcc missing")
+    structs = {"dp_config": dp.dp_config, "dp_info": dp.dp_info, "dp_server_config": dp.dp_server_config,
+               "dp_request": dp.dp_request, "dp_server_stats": dp.dp_server_stats}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "diffpower.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    for line in filter(None, out):
+        name, field, value = line.split()
+        cls = structs[name]
+        want = ctypes.sizeof(cls) if field == "size" else getattr(cls, field).offset
+        assert int(value) == want, (name, field)
