@@ -769,6 +769,115 @@ int orc_simulate(const void *h, const float *sp_in, const float *tr_in, uint64_t
     return 0;
 }
 
+/* ------------------------------------------------------------------ */
+/* Lag-one mode (an extension of Eq. 2, Sec. II-B): every net carries   */
+/* (P, T), T = P(x_t != x_{t+1}) of a stationary two-state process, so   */
+/* the joint law of two consecutive values is q(1,1) = P - T/2,          */
+/* q(0,0) = P(x=0) - T/2, q(0,1) = q(1,0) = T/2.  Under spatial          */
+/* independence a cell toggles with probability                          */
+/*   T_y = sum over input pairs (a, b) of prod_i q_i(a_i, b_i) [f(a) != f(b)], */
+/* exact on fanout-free circuits; with T = 2P(1-P) at every startpoint   */
+/* (temporal independence) it equals Eq. 2 on every net.                 */
+/* ------------------------------------------------------------------ */
+
+/* q(a, b) of a net, index 2a + b */
+static void lag1_w(double p1, double p0, double t, double w[4]) {
+    w[0] = p0 - 0.5 * t;
+    w[1] = 0.5 * t;
+    w[2] = 0.5 * t;
+    w[3] = p1 - 0.5 * t;
+}
+
+/* sum over (a, b) of prod_i W_i[2 a_i + b_i] [f(a) != f(b)], where input `sub` (if >= 0)
+ * uses the weights dsub instead of its own */
+static double cell_toggle(const LibCell *L, const double (*w)[4], int sub, const double *dsub) {
+    int64_t M = (int64_t)1 << L->k;
+    double s = 0.0;
+    for (int64_t a = 0; a < M; a++)
+        for (int64_t b = 0; b < M; b++) {
+            if (L->tt[a] == L->tt[b]) continue;
+            double p = 1.0;
+            for (int i = 0; i < L->k; i++) {
+                int d = (int)(2 * ((a >> i) & 1) + ((b >> i) & 1));
+                p *= i == sub ? dsub[d] : w[i][d];
+            }
+            s += p;
+        }
+    return s;
+}
+
+/* Forward of the lag-one mode: sp, sq as orc_forward; tr = T of every net. */
+int orc_forward_lag1(const void *h, const double *sp_in, const double *tr_in, double *sp, double *tr, double *sq) {
+    const Orc *o = (const Orc *)h;
+    orc_forward(o, sp_in, tr_in, 0, sp, tr, sq);   /* SP and P(net = 0); tr is rewritten below */
+    for (int64_t k = 0; k < o->ns; k++) tr[o->start_net[k]] = tr_in[k];
+    double w[ORC_MAX_IN][4];
+    for (int64_t t = 0; t < o->nc; t++) {
+        int64_t c = o->topo[t];
+        const LibCell *L = &o->lib[o->cell_lib[c]];
+        for (int i = 0; i < L->k; i++) {
+            int64_t f = o->fin_net[o->fin_ptr[c] + i];
+            lag1_w(sp[f], sq[f], tr[f], w[i]);
+        }
+        tr[o->cell_out[c]] = cell_toggle(L, (const double (*)[4])w, -1, NULL);
+    }
+    return 0;
+}
+
+/* Gradients of P = K sum_n T_n C_n in the lag-one mode: adjoints of P and T
+ * per net, in reverse topological order; outputs as orc_backward. */
+int orc_backward_lag1(const void *h, const double *sp_in, const double *tr_in, double vdd, double fclk,
+                      double *g_sp_in, double *g_tr_in, double *g_pincap, double *g_cload) {
+    const Orc *o = (const Orc *)h;
+    const double K = 0.5 * vdd * vdd * fclk * 1e-15;
+    size_t nb = sizeof(double) * (size_t)(o->nn + 1);
+    double *cl = (double *)malloc(nb), *sp = (double *)malloc(nb), *sq = (double *)malloc(nb);
+    double *tr = (double *)malloc(nb), *gp = (double *)calloc((size_t)o->nn + 1, sizeof(double));
+    double *gt = (double *)calloc((size_t)o->nn + 1, sizeof(double));
+    if (!cl || !sp || !sq || !tr || !gp || !gt) {
+        free(cl); free(sp); free(sq); free(tr); free(gp); free(gt);
+        return -1;
+    }
+    orc_cload(o, cl);
+    orc_forward_lag1(o, sp_in, tr_in, sp, tr, sq);
+    for (int64_t n = 0; n < o->nn; n++) gt[n] = K * cl[n];   /* dP/dT_n, direct */
+    static const double dP[4] = {-1.0, 0.0, 0.0, 1.0};       /* d q(a,b) / dP */
+    static const double dT[4] = {-0.5, 0.5, 0.5, -0.5};      /* d q(a,b) / dT */
+    double w[ORC_MAX_IN][4], a1[ORC_MAX_IN], a0[ORC_MAX_IN];
+    for (int64_t t = o->nc - 1; t >= 0; t--) {
+        int64_t c = o->topo[t];
+        int64_t y = o->cell_out[c];
+        const LibCell *L = &o->lib[o->cell_lib[c]];
+        for (int i = 0; i < L->k; i++) {
+            int64_t f = o->fin_net[o->fin_ptr[c] + i];
+            lag1_w(sp[f], sq[f], tr[f], w[i]);
+            a1[i] = sp[f];
+            a0[i] = sq[f];
+        }
+        for (int i = 0; i < L->k; i++) {
+            int64_t f = o->fin_net[o->fin_ptr[c] + i];
+            double dty_dp = cell_toggle(L, (const double (*)[4])w, i, dP);
+            double dty_dt = cell_toggle(L, (const double (*)[4])w, i, dT);
+            gp[f] += gp[y] * cell_dsp(L, a1, a0, i) + gt[y] * dty_dp;
+            gt[f] += gt[y] * dty_dt;
+        }
+    }
+    for (int64_t k = 0; k < o->ns; k++) {
+        int64_t n = o->start_net[k];
+        if (g_sp_in) g_sp_in[k] = gp[n];
+        if (g_tr_in) g_tr_in[k] = gt[n];
+    }
+    if (g_cload) for (int64_t n = 0; n < o->nn; n++) g_cload[n] = K * tr[n];
+    if (g_pincap)
+        for (int64_t c = 0; c < o->nc; c++) {
+            double s = 0.0;
+            for (int64_t e = o->fin_ptr[c]; e < o->fin_ptr[c + 1]; e++) s += tr[o->fin_net[e]];
+            g_pincap[c] = K * s;
+        }
+    free(cl); free(sp); free(sq); free(tr); free(gp); free(gt);
+    return 0;
+}
+
 /* Logic values of every net for 64 input vectors at once (Eq. 3 needs val_i(v)):
  * bit b of start_words[k] is the value of startpoint k in vector b; each cell, in
  * topological order, ORs the AND-terms of its true minterms over its input words.

@@ -76,6 +76,11 @@ def _load():
             L.orc_simulate.restype = ctypes.c_int
             L.orc_hybrid.argtypes = [_P, _D, _U32, ctypes.c_int, ctypes.c_double, ctypes.c_double, _D, _D]
             L.orc_logic_words.argtypes = [_P, _U64, _U64]
+            L.orc_forward_lag1.argtypes = [_P, _D, _D, _D, _D, _D]
+            L.orc_forward_lag1.restype = ctypes.c_int
+            L.orc_backward_lag1.argtypes = [_P, _D, _D, ctypes.c_double, ctypes.c_double, _opt(_D), _opt(_D),
+                                            _opt(_D), _opt(_D)]
+            L.orc_backward_lag1.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -269,3 +274,27 @@ class Oracle:
         _, tr = self.forward(sp_in, tr_in, tr_mode)
         cl = self.cload()
         return math.fsum((tr * cl).tolist())
+
+    # ---- lag-one mode ----
+
+    def forward_lag1(self, sp_in, tr_in):
+        """Per-net SP and lag-one TR: T_y = sum_(a,b) prod_i q_i(a_i, b_i) [f(a) != f(b)] with
+        q(1,1) = P - T/2, q(0,0) = P(x=0) - T/2, q(0,1) = q(1,0) = T/2 (inputs must satisfy
+        T <= 2 min(P, 1 - P))."""
+        sp = np.zeros(self.n_nets)
+        tr = np.zeros(self.n_nets)
+        sq = np.zeros(self.n_nets)
+        _load().orc_forward_lag1(self._h, np.ascontiguousarray(sp_in, np.float64),
+                                 np.ascontiguousarray(tr_in, np.float64), sp, tr, sq)
+        return sp, tr
+
+    def backward_lag1(self, sp_in, tr_in, vdd: float = 0.8, fclk: float = 1e9) -> dict:
+        """Gradients of K sum_n T_n C_n in the lag-one mode."""
+        out = {"grad_sp_in": np.zeros(self.n_start), "grad_tr_in": np.zeros(self.n_start),
+               "grad_pincap": np.zeros(self.n_cells), "grad_cload": np.zeros(self.n_nets)}
+        rc = _load().orc_backward_lag1(self._h, np.ascontiguousarray(sp_in, np.float64),
+                                       np.ascontiguousarray(tr_in, np.float64), vdd, fclk, out["grad_sp_in"],
+                                       out["grad_tr_in"], out["grad_pincap"], out["grad_cload"])
+        if rc != 0:
+            raise MemoryError("oracle backward_lag1")
+        return out
