@@ -422,6 +422,71 @@ def bench_serving(args, dp, torch, dev) -> dict:
         dp.dp_server_destroy(plain)
 
 
+def bench_adjoint_vs_fd(dp, torch, dev) -> dict:
+    """Gradient of the model power with respect to every startpoint SP of the 120,000-cell
+    netlist: the GPU adjoint (compile + upload + forward + reverse pass, wall clock, as the
+    paper counts graph creation; and the device time of the two passes) against one-sided
+    finite differences on the CPU (one perturbation per startpoint, eps = 1e-4, as in the paper's
+    sweep) with the FP64 oracle, extrapolated from timed forward passes.  Agreement on a stratified
+    sample of startpoints: Pearson r and top-k overlap."""
+    from oracle.oracle import Oracle
+    from paper_2608_03778_gb300 import netgen
+    spec = netgen.WORKLOADS["mid"]
+    lib, text = netgen.library_text(), netgen.netlist_text(spec)
+    sp, tr = netgen.scenario_inputs(spec.n_start, 1000)
+    sp, tr = np.ascontiguousarray(sp[:, 0]), np.ascontiguousarray(tr[:, 0])
+    cfg = dp.config(grad_mode=0)
+    ctx = dp.dp_create(dev.index or 0, torch.cuda.current_stream().cuda_stream)
+    try:
+        g = np.zeros(spec.n_start, np.float32)
+        t0 = time.perf_counter()
+        d = dp.dp_design_load(ctx, text, lib)
+        dp.dp_set_inputs(ctx, d, sp, tr)
+        dp.dp_propagate(ctx, d, cfg)
+        dp.dp_backward(ctx, d, cfg, g)
+        wall = time.perf_counter() - t0
+        for _ in range(3):
+            dp.dp_propagate(ctx, d, cfg)
+            dp.dp_backward(ctx, d, cfg, g)
+        ph = dp.dp_phase_times(ctx, d)
+        dev_ms = float(ph[0] + ph[3])
+        dp.dp_design_free(d)
+    finally:
+        dp.dp_destroy(ctx)
+    o = Oracle(text, lib)
+    sp64, tr64 = sp.astype(np.float64), tr.astype(np.float64)
+    cl = o.cload()
+    K = 0.5 * 0.8 * 0.8 * 1e9 * 1e-15
+
+    def power(x):
+        return K * float(np.sum(o.forward(x, tr64, 0)[1] * cl))
+
+    t0 = time.perf_counter()
+    p0 = power(sp64)
+    n_timed = 3
+    for _ in range(n_timed - 1):
+        power(sp64)
+    t_fwd = (time.perf_counter() - t0) / n_timed
+    rng = np.random.default_rng(7)
+    order = np.argsort(-np.abs(g))
+    idx = np.concatenate([order[:16], rng.choice(order[16:], 32, replace=False)])
+    fd = []
+    for k in idx:
+        x = sp64.copy()
+        x[k] += 1e-4
+        fd.append((power(x) - p0) / 1e-4)
+    fd = np.array(fd)
+    r = float(np.corrcoef(fd, g[idx].astype(np.float64))[0, 1])
+    top = len(set(np.argsort(-np.abs(fd))[:10]) & set(np.argsort(-np.abs(g[idx]))[:10]))
+    fd_all = (spec.n_start + 1) * t_fwd
+    return {"netlist": f"mid: {spec.n_cells} cells, {spec.n_start} startpoints, depth {spec.depth}",
+            "gpu_wall_s": wall, "gpu_device_ms": dev_ms,
+            "cpu_fd_s": fd_all, "cpu_fd": f"({spec.n_start} + 1) oracle forward passes of {t_fwd:.3f} s "
+                                         f"(mean of {n_timed}), single thread, extrapolated",
+            "speedup_vs_gpu_wall": fd_all / wall, "speedup_vs_gpu_device": fd_all / (dev_ms * 1e-3),
+            "sample": {"startpoints": int(len(idx)), "pearson_r": r, "top10_overlap": top}}
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -432,6 +497,7 @@ def main() -> None:
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-scenario measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the request-server measurement")
+    ap.add_argument("--no-fd", action="store_true", help="skip the adjoint-vs-finite-difference timing")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -562,6 +628,8 @@ def main() -> None:
         line["batched"] = bench_batched(args, dp, torch, dev, pk)
     if not args.no_serving:
         line["serving"] = bench_serving(args, dp, torch, dev)
+    if rank == 0 and world == 1 and not args.no_fd:
+        line["adjoint_vs_fd"] = bench_adjoint_vs_fd(dp, torch, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(text, lib, sp, tr, nc, cfg.sim_words)
     if rank == 0:

@@ -81,7 +81,13 @@ typedef struct {
     float beta_min;      /* Eq. 5 clip bounds */
     float beta_max;
     int32_t tr_mode;     /* 0: startpoint TR = given input TR, 2P(1-P) elsewhere;
-                            1: TR = 2P(1-P) on every net (Eq. 2, Algorithm 2 kernel 3) */
+                            1: TR = 2P(1-P) on every net (Eq. 2, Algorithm 2 kernel 3);
+                            2: lag-one - every net carries (SP, TR), consecutive values follow
+                               q(1,1) = P - TR/2, q(0,0) = 1 - P - TR/2, q(0,1) = q(1,0) = TR/2, and
+                               a cell's TR is sum_(a,b) prod_i q_i(a_i, b_i) [f(a) != f(b)] (its
+                               exact toggle rate on fanout-free circuits; Eq. 2 when every input
+                               has TR = 2P(1-P)).  Batched inputs only (dp_set_inputs_batch);
+                               needs TR <= 2 min(P, 1-P) at the startpoints; model gradient only. */
     int32_t grad_mode;   /* 0: gradient of the model power (Eq. 7);
                             1: hybrid, paper rule - each net's accumulated gradient
                                is multiplied by its beta (Eq. 6);

@@ -85,7 +85,7 @@ dp_status check_cfg(dp_ctx *ctx, const dp_config *c) {
         return set_err(ctx, DP_EINVAL, "vdd and fclk must be positive");
     if (!(c->beta_min > 0) || !(c->beta_max >= c->beta_min) || !std::isfinite(c->beta_max))
         return set_err(ctx, DP_EINVAL, "need 0 < beta_min <= beta_max");
-    if (c->tr_mode < 0 || c->tr_mode > 1) return set_err(ctx, DP_EINVAL, "tr_mode must be 0 or 1");
+    if (c->tr_mode < 0 || c->tr_mode > 2) return set_err(ctx, DP_EINVAL, "tr_mode must be 0, 1 or 2");
     if (c->grad_mode < 0 || c->grad_mode > 2) return set_err(ctx, DP_EINVAL, "grad_mode must be 0, 1 or 2");
     if (c->sim_words < 2 || c->sim_words > 4096) return set_err(ctx, DP_EINVAL, "sim_words must be in [2, 4096]");
     if (c->schedule < 0 || c->schedule > 3) return set_err(ctx, DP_EINVAL, "schedule must be 0, 1, 2 or 3");
@@ -530,6 +530,7 @@ dp_status dp_propagate(dp_design *D, const dp_config *cfg) {
     if (s != DP_OK) return s;
     if (!D->inputs_set) return set_err(D->ctx, DP_ESTATE, "dp_propagate before dp_set_inputs");
     if (D->batched) return batch_propagate(D, *cfg);
+    if (cfg->tr_mode == 2) return set_err(D->ctx, DP_EUNSUPPORTED, "the lag-one mode runs on batched inputs");
     DeviceGuard g(D->ctx->device);
     cudaStream_t st = D->ctx->stream;
     rec(D, 0, st);
@@ -547,6 +548,7 @@ dp_status dp_simulate(dp_design *D, const dp_config *cfg) {
     dp_status s = check_cfg(D->ctx, cfg);
     if (s != DP_OK) return s;
     if (D->batched) return set_err(D->ctx, DP_EUNSUPPORTED, "the simulation runs on single-scenario inputs");
+    if (cfg->tr_mode == 2) return set_err(D->ctx, DP_EUNSUPPORTED, "the lag-one mode runs on batched inputs");
     if (!D->fwd_valid || D->fwd_tr_mode != cfg->tr_mode)
         return set_err(D->ctx, DP_ESTATE, "dp_simulate needs dp_propagate with the same tr_mode");
     DeviceGuard g(D->ctx->device);
@@ -652,6 +654,7 @@ dp_status dp_step(dp_design *D, const dp_config *cfg, float *gsp, float *gtr, fl
     if (s != DP_OK) return s;
     if (!D->inputs_set) return set_err(D->ctx, DP_ESTATE, "dp_step before dp_set_inputs");
     if (D->batched) return set_err(D->ctx, DP_EUNSUPPORTED, "dp_step runs on single-scenario inputs");
+    if (cfg->tr_mode == 2) return set_err(D->ctx, DP_EUNSUPPORTED, "the lag-one mode runs on batched inputs");
     DeviceGuard g(D->ctx->device);
     if ((s = ensure_words(D, cfg->sim_words)) != DP_OK) return s;
     cudaStream_t st = D->ctx->stream;

@@ -172,9 +172,27 @@ dp_status batch_tune_and_lock(dp_design *D) {
     return s;
 }
 
+// the lag-one state (every net's TR, two adjoints per edge, the startpoints' TR adjoint),
+// allocated on first use for the current capacity
+dp_status ensure_lag1(dp_design *D) {
+    dp_batch &B = D->batch;
+    if (B.b.tq) return DP_OK;
+    if (capturing(D->ctx->stream))
+        return set_err(D->ctx, DP_ESTATE, "the first lag-one pass allocates: make it before stream capture");
+    const size_t cap = (size_t)B.cap;
+    dp_status s = balloc(D, &B.b.tq, (size_t)D->d.n_nets * cap);
+    if (s == DP_OK) s = balloc(D, &B.b.gfo2, (size_t)D->n_edges * cap);
+    if (s == DP_OK) s = balloc(D, &B.b.gtr, (size_t)D->d.n_start * cap);
+    return s;
+}
+
 dp_status batch_propagate(dp_design *D, const dp_config &c) {
     dp_batch &B = D->batch;
     DeviceGuard g(D->ctx->device);
+    if (c.tr_mode == 2) {
+        dp_status s = ensure_lag1(D);
+        if (s != DP_OK) return s;
+    }
     cudaStream_t st = D->ctx->stream;
     dp::launch_fwdb(D->d, B.b, D->ops, D->lvl_ptr.data(), c.tr_mode, B.fwd_shape, st);
     dp::launch_powerb(D->d, B.b, c.tr_mode, power_K(c), st);

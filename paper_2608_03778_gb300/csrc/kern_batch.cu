@@ -16,65 +16,12 @@
 // the bytes every gather moves.  The gradient is the model gradient (Sec. III-E,
 // Eq. 7) in binary32, scaled per scenario by a seed K * w_s so that a caller
 // can back-propagate any weighted sum of the scenario powers.
-#include "kern_common.cuh"
+#include "kern_batch.cuh"
 
 namespace dp {
 namespace {
 
 __host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
-
-// the stored float-float P of a net and its pair (P, 1 - P)
-__device__ __forceinline__ pair_ff pair_get(const float2 &v) {
-    const ff p{v.x, v.y};
-    const ff t = two_sum(1.f, -v.x);
-    return pair_ff{p, fast_two_sum(t.hi, __fsub_rn(t.lo, v.y))};
-}
-__device__ __forceinline__ float2 p_set(const pair_ff &a) { return make_float2(a.p.hi, a.p.lo); }
-
-__device__ __forceinline__ void gather_ffb(const float2 *pq, const uint4 &r, int k, int64_t S, int64_t s,
-                                           pair_ff (&x)[4]) {
-    const uint32_t n[4] = {r.x & kMask24, r.y, r.z, r.w};
-    float2 v[4];
-#pragma unroll
-    for (int j = 0; j < 4; j++) v[j] = j < k ? pq[(int64_t)n[j] * S + s] : make_float2(0.f, 0.f);
-#pragma unroll
-    for (int j = 0; j < 4; j++) x[j] = pair_get(v[j]);
-}
-
-// binary32 (P, Q) of a cell's inputs for the partial derivatives
-__device__ __forceinline__ void gather32(const float2 *pq, const uint4 &r, int k, int64_t S, int64_t s,
-                                         float (&p)[4], float (&q)[4]) {
-    const uint32_t n[4] = {r.x & kMask24, r.y, r.z, r.w};
-    float2 v[4];
-#pragma unroll
-    for (int j = 0; j < 4; j++) v[j] = j < k ? pq[(int64_t)n[j] * S + s] : make_float2(0.f, 0.f);
-#pragma unroll
-    for (int j = 0; j < 4; j++) {
-        const pair_ff a = pair_get(v[j]);
-        p[j] = a.p.hi + a.p.lo;
-        q[j] = a.q.hi + a.q.lo;
-    }
-}
-
-// Q - P of a stored net, rounded once to binary32
-__device__ __forceinline__ float qmp32(const float2 &v) {
-    const pair_ff a = pair_get(v);
-    const ff d = ff_add(a.q, ff{-a.p.hi, -a.p.lo});
-    return d.hi + d.lo;
-}
-
-// switching activity of net n in scenario s: the input TR at a startpoint in
-// tr_mode 0, else TR_model = 2 P Q (Eq. 2) rounded once to binary32
-__device__ __forceinline__ float alpha32(const float2 *pq, const float *tr_in, int64_t n, int64_t ns, int64_t S,
-                                         int64_t s, int tr_mode) {
-    if (n < ns && tr_mode == 0) return tr_in[n * S + s];
-    return pair_tr(pair_get(pq[n * S + s]));
-}
-
-// the load of net n in scenario s: C_load plus the scenario's sizing delta (if any)
-__device__ __forceinline__ float cl_of(const float *cload, const float *dcl, int64_t n, int64_t S, int64_t s) {
-    return dcl ? cload[n] + dcl[n * S + s] : cload[n];
-}
 
 __global__ void k_fwdb_start(const float *__restrict__ sp_in, float2 *pq, int64_t n) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -204,8 +151,9 @@ __global__ void k_gradb_rows(const uint4 *__restrict__ fanin, const float2 *__re
                              const float *__restrict__ tr_in, const float *__restrict__ cload,
                              const float *__restrict__ dcl,
                              const int32_t *__restrict__ net_of_user, const int32_t *__restrict__ cell_of_user,
-                             const float *__restrict__ ks, float *gcl, float *gpin, float *gtr, int64_t nn,
-                             int64_t nc, int64_t ns, int64_t S, int tr_mode, OpTable ops) {
+                             const float *__restrict__ ks, const float *__restrict__ gtr_lag1, float *gcl,
+                             float *gpin, float *gtr, int64_t nn, int64_t nc, int64_t ns, int64_t S, int tr_mode,
+                             OpTable ops) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S) return;
     const float Ks = ks[s];
@@ -234,7 +182,7 @@ __global__ void k_gradb_rows(const uint4 *__restrict__ fanin, const float2 *__re
             }
             u -= nc;
         }
-        gtr[u * S + s] = tr_mode ? 0.f : Ks * cl_of(cload, dcl, u, S, s);
+        gtr[u * S + s] = tr_mode == 2 ? gtr_lag1[u * S + s] : (tr_mode ? 0.f : Ks * cl_of(cload, dcl, u, S, s));
     }
 }
 
@@ -376,10 +324,6 @@ __global__ void k_transpose(const float *__restrict__ in, float *out, int64_t R,
     }
 }
 
-dim3 bgrid(int64_t S, BatchShape sh, int64_t rows) {
-    const int64_t gy = cdiv(rows > 0 ? rows : 1, sh.by);
-    return dim3((unsigned)cdiv(S, sh.bx), (unsigned)(gy < 65535 ? gy : 65535));
-}
 
 int nchunks_of(int64_t nn, int64_t *chunk) {
     const int64_t m = nn > 0 ? nn : 1;
@@ -391,7 +335,10 @@ int nchunks_of(int64_t nn, int64_t *chunk) {
 
 void launch_fwdb(const DevDesign &d, const BatchBufs &b, const OpTable &ops, const int32_t *lvl, int tr_mode,
                  BatchShape sh, cudaStream_t s) {
-    (void)tr_mode;   // startpoint TR is read from the inputs where it is needed
+    if (tr_mode == 2) {
+        launch_fwdl(d, b, ops, lvl, sh, s);
+        return;
+    }
     const int64_t S = b.S;
     if (d.n_start) k_fwdb_start<<<(unsigned)cdiv(d.n_start * S, 256), 256, 0, s>>>(b.sp_in, b.pq, d.n_start * S);
     const dim3 blk((unsigned)sh.bx, (unsigned)sh.by);
@@ -406,7 +353,8 @@ void launch_powerb(const DevDesign &d, const BatchBufs &b, int tr_mode, double K
     int64_t chunk = 0;
     const int nch = nchunks_of(d.n_nets, &chunk);
     k_powerb_partials<<<dim3((unsigned)cdiv(S, 128), (unsigned)nch), 128, 0, s>>>(
-        b.pq, b.tr_in, d.cload, b.dcl, b.partials, d.n_nets, d.n_start, S, chunk, nch, tr_mode);
+        b.pq, tr_mode == 2 ? b.tq : b.tr_in, d.cload, b.dcl, b.partials, d.n_nets, d.n_start, S, chunk, nch,
+        tr_mode);
     k_sumb_final<<<(unsigned)cdiv(S * 32, 256), 256, 0, s>>>(b.partials, nch, S, K, b.power);
 }
 
@@ -416,6 +364,10 @@ void launch_seedb(const BatchBufs &b, double K, const double *weights, cudaStrea
 
 void launch_bwdb(const DevDesign &d, const BatchBufs &b, const OpTable &ops, const int32_t *lvl, int tr_mode,
                  BatchShape sh, cudaStream_t s) {
+    if (tr_mode == 2) {
+        launch_bwdl(d, b, ops, lvl, sh, s);
+        return;
+    }
     const int64_t S = b.S;
     const dim3 blk((unsigned)sh.bx, (unsigned)sh.by);
     for (int l = d.n_levels; l >= 1; l--) {
@@ -438,8 +390,8 @@ void launch_gradb(const DevDesign &d, const BatchBufs &b, const OpTable &ops, in
         if (rows) {
             const int64_t blocks = cdiv(rows, 8);
             k_gradb_reduce<<<(unsigned)(blocks < 152 * 16 ? blocks : 152 * 16), 256, 0, s>>>(
-                d.fanin, b.pq, b.tr_in, d.net_of_user, d.cell_of_user, b.ks, gcl, gpin, d.n_nets, d.n_cells,
-                d.n_start, S, tr_mode, ops);
+                d.fanin, b.pq, tr_mode == 2 ? b.tq : b.tr_in, d.net_of_user, d.cell_of_user, b.ks, gcl, gpin,
+                d.n_nets, d.n_cells, d.n_start, S, tr_mode, ops);
         }
         gcl = gpin = nullptr;
     }
@@ -447,15 +399,15 @@ void launch_gradb(const DevDesign &d, const BatchBufs &b, const OpTable &ops, in
     if (rows == 0) return;
     const BatchShape sh{S >= 128 ? 128 : 32, S >= 128 ? 1 : 4};
     k_gradb_rows<<<bgrid(S, sh, rows), dim3((unsigned)sh.bx, (unsigned)sh.by), 0, s>>>(
-        d.fanin, b.pq, b.tr_in, d.cload, b.dcl, d.net_of_user, d.cell_of_user, b.ks, gcl, gpin, gtr, d.n_nets,
-        d.n_cells, d.n_start, S, tr_mode, ops);
+        d.fanin, b.pq, tr_mode == 2 ? b.tq : b.tr_in, d.cload, b.dcl, d.net_of_user, d.cell_of_user, b.ks,
+        b.gtr, gcl, gpin, gtr, d.n_nets, d.n_cells, d.n_start, S, tr_mode, ops);
 }
 
 void launch_netb_user(const DevDesign &d, const BatchBufs &b, int tr_mode, float *sp, float *tr, cudaStream_t s) {
     if (!d.n_nets || (!sp && !tr)) return;
     const BatchShape sh{b.S >= 128 ? 128 : 32, b.S >= 128 ? 1 : 4};
     k_netb_user<<<bgrid(b.S, sh, d.n_nets), dim3((unsigned)sh.bx, (unsigned)sh.by), 0, s>>>(
-        b.pq, b.tr_in, d.net_of_user, sp, tr, d.n_nets, d.n_start, b.S, tr_mode);
+        b.pq, tr_mode == 2 ? b.tq : b.tr_in, d.net_of_user, sp, tr, d.n_nets, d.n_start, b.S, tr_mode);
 }
 
 void launch_scatter(float *dcl, const int64_t *at, const float *v, int64_t n, cudaStream_t s) {

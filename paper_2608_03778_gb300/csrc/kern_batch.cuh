@@ -1,0 +1,71 @@
+// Device helpers shared by the batched kernels (kern_batch.cu, kern_lag1.cu):
+// per-net state is stored scenario-innermost, value[n * S + s].
+#pragma once
+#include "kern_common.cuh"
+
+namespace dp {
+
+__host__ __device__ inline int64_t bcdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// the stored float-float P of a net and its pair (P, 1 - P)
+__device__ __forceinline__ pair_ff pair_get(const float2 &v) {
+    const ff p{v.x, v.y};
+    const ff t = two_sum(1.f, -v.x);
+    return pair_ff{p, fast_two_sum(t.hi, __fsub_rn(t.lo, v.y))};
+}
+__device__ __forceinline__ float2 p_set(const pair_ff &a) { return make_float2(a.p.hi, a.p.lo); }
+
+__device__ __forceinline__ void gather_ffb(const float2 *pq, const uint4 &r, int k, int64_t S, int64_t s,
+                                           pair_ff (&x)[4]) {
+    const uint32_t n[4] = {r.x & kMask24, r.y, r.z, r.w};
+    float2 v[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) v[j] = j < k ? pq[(int64_t)n[j] * S + s] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < 4; j++) x[j] = pair_get(v[j]);
+}
+
+// binary32 (P, Q) of a cell's inputs for the partial derivatives
+__device__ __forceinline__ void gather32(const float2 *pq, const uint4 &r, int k, int64_t S, int64_t s,
+                                         float (&p)[4], float (&q)[4]) {
+    const uint32_t n[4] = {r.x & kMask24, r.y, r.z, r.w};
+    float2 v[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) v[j] = j < k ? pq[(int64_t)n[j] * S + s] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        const pair_ff a = pair_get(v[j]);
+        p[j] = a.p.hi + a.p.lo;
+        q[j] = a.q.hi + a.q.lo;
+    }
+}
+
+// Q - P of a stored net, rounded once to binary32
+__device__ __forceinline__ float qmp32(const float2 &v) {
+    const pair_ff a = pair_get(v);
+    const ff d = ff_add(a.q, ff{-a.p.hi, -a.p.lo});
+    return d.hi + d.lo;
+}
+
+// switching activity of net n in scenario s: the input TR at a startpoint in
+// tr_mode 0, else TR_model = 2 P Q (Eq. 2) rounded once to binary32.  In the
+// lag-one mode (tr_mode 2) every net's TR is stored, and the callers pass that
+// array in tr_in's place.
+__device__ __forceinline__ float alpha32(const float2 *pq, const float *tr_in, int64_t n, int64_t ns, int64_t S,
+                                         int64_t s, int tr_mode) {
+    if (tr_mode == 2 || (n < ns && tr_mode == 0)) return tr_in[n * S + s];
+    return pair_tr(pair_get(pq[n * S + s]));
+}
+
+// the load of net n in scenario s: C_load plus the scenario's sizing delta (if any)
+__device__ __forceinline__ float cl_of(const float *cload, const float *dcl, int64_t n, int64_t S, int64_t s) {
+    return dcl ? cload[n] + dcl[n * S + s] : cload[n];
+}
+
+
+inline dim3 bgrid(int64_t S, BatchShape sh, int64_t rows) {
+    const int64_t gy = bcdiv(rows > 0 ? rows : 1, sh.by);
+    return dim3((unsigned)bcdiv(S, sh.bx), (unsigned)(gy < 65535 ? gy : 65535));
+}
+
+}  // namespace dp

@@ -101,6 +101,10 @@ struct BatchBufs {
     double *power;          // [S] model power per scenario
     float *ks;              // [S] per-scenario seed of the backward (K * weight), binary32
     const float *dcl;       // [n_nets * S] per-scenario change of C_load (sizing deltas), or NULL
+    // lag-one mode (tr_mode 2) only, else NULL:
+    float *tq;              // [n_nets * S] TR of every net
+    float2 *gfo2;           // [n_edges * S] edge adjoints of (P, TR)
+    float *gtr;             // [n_start * S] TR adjoint of the startpoints
 };
 constexpr int kBatchPowerChunks = 1024;   // fixed split of the nets -> deterministic FP64 sums
 
@@ -110,6 +114,11 @@ struct BatchShape {
 
 void launch_fwdb(const DevDesign &d, const BatchBufs &b, const OpTable &ops, const int32_t *lvl_host, int tr_mode,
                  BatchShape sh, cudaStream_t s);
+// lag-one mode (kern_lag1.cu): forward of (P, TR) and reverse pass of both adjoints
+void launch_fwdl(const DevDesign &d, const BatchBufs &b, const OpTable &ops, const int32_t *lvl_host, BatchShape sh,
+                 cudaStream_t s);
+void launch_bwdl(const DevDesign &d, const BatchBufs &b, const OpTable &ops, const int32_t *lvl_host, BatchShape sh,
+                 cudaStream_t s);
 void launch_powerb(const DevDesign &d, const BatchBufs &b, int tr_mode, double K, cudaStream_t s);
 // ks[s] = K * weights[s] (weights NULL: K)
 void launch_seedb(const BatchBufs &b, double K, const double *weights, cudaStream_t s);

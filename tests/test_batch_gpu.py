@@ -337,3 +337,95 @@ def test_power_virus_small(dp, small, tr_mode):
     clear = np.all(np.abs(sp_ref - 0.5) > 1e-3, axis=0)
     assert clear.any()
     np.testing.assert_allclose(eager.p_virus.cpu().numpy()[clear], pv_ref[clear], rtol=1e-7)
+
+
+# ---- lag-one mode (tr_mode 2) ----
+
+def check_lag1(o, g, sp, tr, scen, vdd=0.8, fclk=1e9):
+    K = 0.5 * vdd * vdd * fclk * 1e-15
+    cl = o.cload()
+    for s in scen:
+        spf, trf = o.forward_lag1(sp[:, s].astype(np.float64), tr[:, s].astype(np.float64))
+        assert np.abs(g["sp"][:, s] - spf).max(initial=0) <= 1e-5, s
+        assert np.abs(g["tr"][:, s] - trf).max(initial=0) <= 1e-5, s
+        assert g["power"][s] == pytest.approx(K * float(np.sum(trf * cl)), rel=1e-6), s
+        ref = o.backward_lag1(sp[:, s].astype(np.float64), tr[:, s].astype(np.float64), vdd, fclk)
+        for k in ["grad_sp_in", "grad_tr_in", "grad_pincap", "grad_cload"]:
+            assert grad_close(g[k][:, s], ref[k]), (k, s)
+
+
+@pytest.mark.parametrize("S", [1, 37])
+def test_lag1_parity_small(dp, ctx, small, S):
+    text, o = small
+    sp, tr = netgen.scenario_inputs(o.n_start, 3100, S)
+    cfg = dp.config(grad_mode=0, tr_mode=2)
+    d = dp.dp_design_load(ctx, text, netgen.library_text())
+    try:
+        g = run_batch(dp, ctx, d, sp, tr, cfg)
+    finally:
+        dp.dp_design_free(d)
+    check_lag1(o, g, sp, tr, range(S))
+
+
+def test_lag1_custom_cells(dp, ctx):
+    """0- to 4-input cells (constants and a 4-input majority-like function) in the lag-one mode."""
+    lib = ("cell C0 Z 0.8 0\ncell C1 Z 0.8 1\ncell INV ZN 0.8 !A\ncell AOI211 ZN 1.6 !((A1&A2)|B|C)\n"
+           "cell F4 Z 1.2 (A&B)|(C^D)|(A&!D)\ncell MUX2 Z 0.9 (A&!S)|(B&S)\n")
+    rng = np.random.default_rng(8)
+    lines, nid = [], 0
+    for i in range(6):
+        lines += [f"net n{nid} 1.0", f"input n{nid}"]
+        nid += 1
+    cells = [("C0", ["Z"], []), ("C1", ["Z"], []), ("INV", ["ZN"], ["A"]), ("AOI211", ["ZN"], ["A1", "A2", "B", "C"]),
+             ("F4", ["Z"], ["A", "B", "C", "D"]), ("MUX2", ["Z"], ["A", "B", "S"])]
+    for rep in range(3):
+        for ref, (out,), ins in cells:
+            pick = rng.choice(nid, len(ins), replace=False)
+            lines.append(f"net n{nid} {rng.uniform(0.5, 2):.3f}")
+            lines.append(f"cell u{nid} {ref} " + " ".join(f"{p}=n{x}" for p, x in zip(ins, pick)) + f" {out}=n{nid}")
+            nid += 1
+    text = "\n".join(lines) + "\n"
+    o = Oracle(text, lib)
+    S = 33
+    sp, tr = netgen.scenario_inputs(o.n_start, 3300, S)
+    cfg = dp.config(grad_mode=0, tr_mode=2)
+    d = dp.dp_design_load(ctx, text, lib)
+    try:
+        g = run_batch(dp, ctx, d, sp, tr, cfg)
+    finally:
+        dp.dp_design_free(d)
+    check_lag1(o, g, sp, tr, range(S))
+
+
+def test_lag1_with_independent_inputs_is_the_model(dp, ctx, small):
+    """TR = 2P(1-P) at every startpoint: the lag-one mode gives Eq. 2 everywhere (tr_mode 1)."""
+    text, o = small
+    sp, _ = netgen.scenario_inputs(o.n_start, 3200, 16)
+    tr = (2 * sp.astype(np.float64) * (1 - sp.astype(np.float64))).astype(np.float32)
+    d = dp.dp_design_load(ctx, text, netgen.library_text())
+    try:
+        g2 = run_batch(dp, ctx, d, sp, tr, dp.config(grad_mode=0, tr_mode=2))
+        g1 = run_batch(dp, ctx, d, sp, tr, dp.config(grad_mode=0, tr_mode=1))
+    finally:
+        dp.dp_design_free(d)
+    np.testing.assert_array_equal(g2["sp"], g1["sp"])
+    assert np.abs(g2["tr"] - g1["tr"]).max() <= 2e-6
+    np.testing.assert_allclose(g2["power"], g1["power"], rtol=2e-6)
+
+
+def test_lag1_mid_sampled(dp, ctx, library_text):
+    text = netgen.netlist_text(netgen.WORKLOADS["mid"])
+    o = Oracle(text, library_text)
+    S = 64
+    sp, tr = netgen.scenario_inputs(o.n_start, 3400, S)
+    cfg = dp.config(grad_mode=0, tr_mode=2)
+    d = dp.dp_design_load(ctx, text, library_text)
+    try:
+        g = run_batch(dp, ctx, d, sp, tr, cfg)
+        with pytest.raises(dp.DPError) as e:           # the single-scenario path has no lag-one mode
+            dp.dp_set_inputs(ctx, d, np.ascontiguousarray(sp[:, 0]), np.ascontiguousarray(tr[:, 0]), 1)
+            dp.dp_propagate(ctx, d, cfg)
+        assert e.value.name == "DP_EUNSUPPORTED"
+    finally:
+        dp.dp_design_free(d)
+    check_lag1(o, g, sp, tr, [0, 31, 63])
