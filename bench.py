@@ -79,7 +79,13 @@ def batched_algorithmic_bytes(nn: int, ns: int, nc: int, ne: int, S: int) -> int
 # captures and commands are summarised under profiles/).  A figure is reported
 # only while the kernel's source file still hashes to the value it was taken
 # with; otherwise the traffic is unknown (null).
-TRAFFIC = {}
+TRAFFIC = {
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (one pass), 2M-cell step, 4th step
+    "k_sim_wide": {"bytes": 258_320_000 + 986_920_000, "files": ["kern_persist.cu", "kern_common.cuh"],
+                   "sha": "1f0ddf92a7982993"},
+    "k_bwd_persist": {"bytes": 127_290_000 + 11_950_000, "files": ["kern_persist.cu", "kern_common.cuh"],
+                      "sha": "1f0ddf92a7982993"},
+}
 
 
 def kernel_traffic(kernel: str) -> int | None:
@@ -87,10 +93,11 @@ def kernel_traffic(kernel: str) -> int | None:
     t = TRAFFIC.get(kernel)
     if not t:
         return None
-    with open(os.path.join(ROOT, "paper_2608_03778_gb300", "csrc", t["file"]), "rb") as f:
-        if hashlib.sha256(f.read()).hexdigest()[:16] != t["sha"]:
-            return None
-    return int(t["bytes"])
+    m = hashlib.sha256()
+    for name in t["files"]:
+        with open(os.path.join(ROOT, "paper_2608_03778_gb300", "csrc", name), "rb") as f:
+            m.update(f.read())
+    return int(t["bytes"]) if m.hexdigest()[:16] == t["sha"] else None
 
 
 class Clocks:
