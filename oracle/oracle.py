@@ -298,3 +298,24 @@ class Oracle:
         if rc != 0:
             raise MemoryError("oracle backward_lag1")
         return out
+
+    # ---- sizing score (Eq. 8) ----
+
+    def sizing_scores(self, sp_in, tr_in, mode: int = 0, tr_mode: int = 0, vdd: float = 0.8, fclk: float = 1e9,
+                      eps: float = 1e-6):
+        """Per cell line: S = |dP/dP_sw| * P_sw with P_sw = K TR C_load of the cell's output net.
+        mode 0: dP/dP_sw read as the SP adjoint of the output net; mode 1: the chain rule through
+        Eq. 2, adjoint / (2 - 4 SP), with |2 - 4 SP| floored at eps.  Returns (scores, p_sw)."""
+        K = 0.5 * vdd * vdd * fclk * 1e-15
+        sp, tr = self.forward(sp_in, tr_in, tr_mode)
+        g = self.backward(sp_in, tr_in, None, 0, tr_mode, vdd, fclk)["grad_net"]
+        cl = self.cload()
+        y = self.cell_outs()
+        psw = K * tr[y] * cl[y]
+        if mode == 0:
+            sens = np.abs(g[y])
+        else:
+            d = 2.0 - 4.0 * sp[y]
+            d = np.where(np.abs(d) < eps, np.where(d < 0, -eps, eps), d)
+            sens = np.abs(g[y] / d)
+        return sens * psw, psw
