@@ -629,6 +629,15 @@ def main() -> None:
         "clocks": clocks,
         "device_bytes": int(info.device_bytes),
     }
+    # ---- Eq. 8 sizing scores and the top 1,000 cells from the step's adjoint (re-ranking cost)
+    dp.dp_step(ctx, d, cfg, g["sp"], g["tr"], g["pin"], g["cl"], None, 1)
+    top = np.zeros(1000, np.int32)
+    dp.dp_sizing_scores(ctx, d, cfg, 0, None, 1000, top)
+    t0 = time.perf_counter()
+    for _ in range(5):
+        dp.dp_sizing_scores(ctx, d, cfg, 0, None, 1000, top)
+    line["sizing"] = {"cells": int(nc), "k": 1000, "ms_scores_and_top_k": 1e3 * (time.perf_counter() - t0) / 5,
+                      "score": "Eq. 8, mode 0 (SP adjoint of the output net x hybrid P_sw)"}
     dp.dp_design_free(d)
     dp.dp_destroy(ctx)
     if not args.no_batched:

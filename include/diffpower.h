@@ -318,6 +318,19 @@ dp_status dp_ascent_step(dp_ctx *ctx, float *x, const float *g, int64_t n, float
  * Works on any design state.  The first call with a larger n_scen allocates. */
 dp_status dp_virus_eval(dp_design *d, const float *sp, int32_t n_scen, uint8_t *v0, double *p_virus, int on_device);
 
+/* Gradient-weighted sizing score (Eq. 8) of every cell line, S = |dP/dP_sw| * P_sw,
+ * with P_sw = K * alpha * C_load of the cell's output net (alpha = TR_model, or
+ * the hybrid TR when cfg->grad_mode != 0), from the adjoint of the last
+ * dp_backward / dp_step with the same config (DP_ESTATE otherwise).
+ *   mode 0: dP/dP_sw read as the SP adjoint of the output net (global sensitivity);
+ *   mode 1: the chain rule through Eq. 2, SP adjoint / (2 - 4 SP), |2 - 4 SP| >= 1e-6.
+ * scores[n_cells] (may be NULL).  k > 0: the k highest-scoring cell lines, best
+ * first, ties by cell index, into top_cells[k] and top_scores[k] (may be NULL);
+ * found by a radix select on the device, the candidates ordered on the host
+ * (synchronises).  Single-scenario inputs only. */
+dp_status dp_sizing_scores(dp_design *d, const dp_config *cfg, int32_t mode, float *scores, int32_t k,
+                           int32_t *top_cells, float *top_scores, int on_device);
+
 /* Number of kernels the last dp_step launched: the kernel nodes of its CUDA
  * graph plus the output kernels queued after it (0 before the first dp_step). */
 dp_status dp_step_kernels(const dp_design *d, int64_t *kernels);

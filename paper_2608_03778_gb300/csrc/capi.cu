@@ -1,5 +1,6 @@
 // C-ABI of libdiffpower.so: contexts, resident designs, and the call sequence
 // of the hot path (load, set inputs, propagate, simulate, power, backward).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -480,6 +481,7 @@ dp_status dp_set_inputs(dp_design *D, const float *sp, const float *tr, int32_t 
     D->batched = false;
     D->fwd_valid = false;
     D->sim_valid = false;
+    D->bwd_valid = false;
     D->batch.fwd_valid = false;
     return DP_OK;
 }
@@ -515,6 +517,7 @@ dp_status dp_set_pincap(dp_design *D, const int32_t *cells, const float *caps, i
     }
     dp::launch_set_pincap(D->d, dc, dv, n, c->stream);
     dp::launch_cload(D->d, c->stream);
+    D->bwd_valid = false;   // the local gradient terms depend on the loads
     dp_status s = launch_check(c, "dp_set_pincap");
     if (!on_device) {
         if (dc) cudaFreeAsync(dc, c->stream);
@@ -540,6 +543,7 @@ dp_status dp_propagate(dp_design *D, const dp_config *cfg) {
     D->fwd_valid = true;
     D->fwd_tr_mode = cfg->tr_mode;
     D->sim_valid = false;
+    D->bwd_valid = false;
     return DP_OK;
 }
 
@@ -598,6 +602,8 @@ dp_status dp_backward(dp_design *D, const dp_config *cfg, float *gsp, float *gtr
     cudaError_t le = q_backward(D, *cfg, on_device ? gsp : nullptr, st);
     rec(D, 4, st);
     if ((s = cuda_err(D->ctx, le, "dp_backward")) != DP_OK) return s;
+    D->bwd_valid = true;
+    D->bwd_grad_mode = cfg->grad_mode;
     s = q_outputs(D, *cfg, gsp, gtr, gpin, gcl, on_device, on_device != 0);
     rec(D, 5, st);
     return s;
@@ -707,6 +713,8 @@ dp_status dp_step(dp_design *D, const dp_config *cfg, float *gsp, float *gtr, fl
     D->fwd_valid = true;
     D->fwd_tr_mode = cfg->tr_mode;
     D->sim_valid = true;
+    D->bwd_valid = true;
+    D->bwd_grad_mode = cfg->grad_mode;
     s = q_outputs(D, *cfg, gsp, gtr, gpin, gcl, on_device, false);
     rec(D, 5, st);
     D->step_kernels = D->graph_kernels + (gcl && D->d.n_nets ? 1 : 0) + (gpin && D->d.n_cells ? 1 : 0) +
@@ -719,6 +727,82 @@ dp_status dp_step(dp_design *D, const dp_config *cfg, float *gsp, float *gtr, fl
         return check_device_error(D->ctx);
     }
     return DP_OK;
+}
+
+dp_status dp_sizing_scores(dp_design *D, const dp_config *cfg, int32_t mode, float *scores, int32_t k,
+                           int32_t *top_cells, float *top_scores, int on_device) {
+    if (!D) return DP_EINVAL;
+    dp_ctx *c = D->ctx;
+    dp_status s = check_cfg(c, cfg);
+    if (s != DP_OK) return s;
+    if (mode < 0 || mode > 1) return set_err(c, DP_EINVAL, "mode must be 0 or 1");
+    const int64_t nc = D->d.n_cells;
+    if (k < 0 || (k > 0 && !top_cells)) return set_err(c, DP_EINVAL, "bad k or NULL top_cells");
+    if (D->batched) return set_err(c, DP_EUNSUPPORTED, "sizing scores are computed for single-scenario inputs");
+    if (!D->bwd_valid || D->bwd_grad_mode != cfg->grad_mode || D->fwd_tr_mode != cfg->tr_mode)
+        return set_err(c, DP_ESTATE, "sizing scores need dp_backward (or dp_step) with the same config");
+    DeviceGuard g(c->device);
+    cudaStream_t st = c->stream;
+    if (!D->sc_scores) {
+        if ((s = dalloc(D, &D->sc_scores, (size_t)nc)) != DP_OK) return s;
+        if ((s = dalloc(D, &D->sc_idx, (size_t)nc)) != DP_OK) return s;
+        if ((s = dalloc(D, &D->sc_hist, 257)) != DP_OK) return s;
+    }
+    dp::launch_scores(D->d, cfg->grad_mode != 0, (float)power_K(*cfg), mode, D->sc_scores, st);
+    if ((s = launch_check(c, "dp_sizing_scores")) != DP_OK) return s;
+    cudaError_t e = cudaSuccess;
+    if (scores && nc)
+        e = cudaMemcpyAsync(scores, D->sc_scores, sizeof(float) * (size_t)nc,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_err(c, e, "dp_sizing_scores");
+    if (k == 0 || nc == 0) {
+        if (!on_device && (e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_err(c, e, "dp_sizing_scores");
+        return on_device ? DP_OK : check_device_error(c);
+    }
+    const int64_t kk = k < nc ? k : nc;
+    // radix select of the kk-th largest score: 8-bit digits, most significant first
+    uint32_t prefix = 0, mask = 0;
+    int64_t remaining = kk;
+    unsigned hist[256];
+    for (int shift = 24; shift >= 0; shift -= 8) {
+        e = cudaMemsetAsync(D->sc_hist, 0, 256 * sizeof(unsigned), st);
+        if (e == cudaSuccess) dp::launch_radix_hist(D->sc_scores, nc, prefix, mask, shift, D->sc_hist, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hist, D->sc_hist, sizeof hist, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_err(c, e, "dp_sizing_scores (select)");
+        int64_t above = 0;
+        int b = 255;
+        for (; b > 0; b--) {
+            if (above + (int64_t)hist[b] >= remaining) break;
+            above += hist[b];
+        }
+        remaining -= above;
+        prefix |= (uint32_t)b << shift;
+        mask |= 0xFFu << shift;
+    }
+    // every cell at or above the threshold (the kk-th score), then exact ordering on the host
+    unsigned cnt = 0;
+    e = cudaMemsetAsync(D->sc_hist + 256, 0, sizeof(unsigned), st);
+    if (e == cudaSuccess) dp::launch_radix_collect(D->sc_scores, nc, prefix, D->sc_idx, D->sc_hist + 256, nc, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&cnt, D->sc_hist + 256, sizeof cnt, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_err(c, e, "dp_sizing_scores (collect)");
+    std::vector<int32_t> idx(cnt);
+    std::vector<float> all((size_t)nc);
+    if (cnt) e = cudaMemcpy(idx.data(), D->sc_idx, sizeof(int32_t) * cnt, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(all.data(), D->sc_scores, sizeof(float) * (size_t)nc, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_err(c, e, "dp_sizing_scores (collect)");
+    std::sort(idx.begin(), idx.end(), [&](int32_t a, int32_t b) {
+        return all[(size_t)a] != all[(size_t)b] ? all[(size_t)a] > all[(size_t)b] : a < b;
+    });
+    if ((int64_t)idx.size() < kk) return set_err(c, DP_ECUDA, "top-k selection lost candidates");
+    std::vector<float> ts((size_t)kk);
+    for (int64_t i = 0; i < kk; i++) ts[(size_t)i] = all[(size_t)idx[(size_t)i]];
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
+    e = cudaMemcpy(top_cells, idx.data(), sizeof(int32_t) * (size_t)kk, kind);
+    if (e == cudaSuccess && top_scores) e = cudaMemcpy(top_scores, ts.data(), sizeof(float) * (size_t)kk, kind);
+    if (e != cudaSuccess) return cuda_err(c, e, "dp_sizing_scores (top)");
+    return check_device_error(c);
 }
 
 dp_status dp_step_kernels(const dp_design *D, int64_t *k) {

@@ -63,6 +63,12 @@ struct dp_design {
     bool fwd_valid = false;
     int fwd_tr_mode = -1;
     bool sim_valid = false;
+    bool bwd_valid = false;        // gnet holds the adjoint of the current state
+    int bwd_grad_mode = -1;
+    // sizing-score scratch (lazy): scores [n_cells], candidates [n_cells], histogram [256] + count
+    float *sc_scores = nullptr;
+    int32_t *sc_idx = nullptr;
+    unsigned *sc_hist = nullptr;
     dp_batch batch;
     // graph of the whole step for one config
     cudaGraphExec_t graph = nullptr;

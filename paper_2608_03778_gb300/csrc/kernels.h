@@ -158,6 +158,13 @@ void launch_ascent(float *x, const float *g, int64_t n, float eta, cudaStream_t 
 void launch_virus(const DevDesign &d, const OpTable &ops, const int32_t *lvl_host, const float *sp, int64_t S,
                   uint64_t *words, uint8_t *v0, double *partials, double *out, cudaStream_t s);
 
+// sizing score (kern_size.cu): Eq. 8 per cell line, and the radix select of its top k
+void launch_scores(const DevDesign &d, bool hybrid, float K, int mode, float *out, cudaStream_t s);
+void launch_radix_hist(const float *scores, int64_t n, uint32_t prefix, uint32_t mask, int shift, unsigned *hist,
+                       cudaStream_t s);
+void launch_radix_collect(const float *scores, int64_t n, uint32_t thr, int32_t *idx, unsigned *count, int64_t cap,
+                          cudaStream_t s);
+
 // simulation (kern_sim.cu)
 void launch_sim_start(const DevDesign &d, int T, uint64_t seed, cudaStream_t s);
 void launch_sim_level(const DevDesign &d, const OpTable &ops, int32_t c0, int32_t c1, int T, cudaStream_t s);

@@ -113,6 +113,7 @@ _sig("dp_phase_times", [_P, _P])
 _sig("dp_step_kernels", [_P, ctypes.POINTER(ctypes.c_int64)])
 _sig("dp_power_noalloc", [ctypes.c_int, _P, _P, _P, ctypes.c_int64, ctypes.c_double, ctypes.c_double, _P, _P])
 _sig("dp_set_stream", [_P, _P])
+_sig("dp_sizing_scores", [_P, ctypes.POINTER(dp_config), ctypes.c_int32, _P, ctypes.c_int32, _P, _P, _S])
 _sig("dp_server_config_default", [ctypes.POINTER(dp_server_config)], None)
 _sig("dp_server_create", [ctypes.POINTER(dp_server_config), ctypes.POINTER(_P)])
 _sig("dp_server_destroy", [_P], None)
@@ -136,7 +137,7 @@ EXPORTED = ["dp_config_default", "dp_last_error", "dp_compile", "dp_compiled_fre
             "dp_propagate", "dp_simulate", "dp_total_power", "dp_backward", "dp_get_nets", "dp_step",
             "dp_phase_times", "dp_step_kernels", "dp_power_noalloc", "dp_selftest_wait", "dp_set_stream",
             "dp_get_power", "dp_set_inputs_batch", "dp_batch_tuning", "dp_backward_weighted", "dp_ascent_step",
-            "dp_virus_eval", "dp_server_config_default", "dp_server_create", "dp_server_destroy",
+            "dp_virus_eval", "dp_sizing_scores", "dp_server_config_default", "dp_server_create", "dp_server_destroy",
             "dp_server_last_error", "dp_server_add_design", "dp_server_design_info", "dp_server_submit",
             "dp_server_wait", "dp_server_get_stats"]
 
@@ -452,3 +453,10 @@ def dp_server_get_stats(srv) -> dp_server_stats:
     s = dp_server_stats()
     _scheck(_lib.dp_server_get_stats(srv, ctypes.byref(s)), srv)
     return s
+
+
+def dp_sizing_scores(ctx, d, cfg: dp_config, mode: int = 0, scores=None, k: int = 0, top_cells=None,
+                     top_scores=None, on_device: int = 0) -> None:
+    """Eq. 8 scores per cell line and the top-k cells (after dp_backward / dp_step)."""
+    _check(_lib.dp_sizing_scores(d, ctypes.byref(cfg), mode, _ptr(scores), k, _ptr(top_cells), _ptr(top_scores),
+                                 on_device), ctx)
