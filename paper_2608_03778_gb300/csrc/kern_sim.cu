@@ -33,8 +33,10 @@ __global__ void __launch_bounds__(256) k_sim_start(const float *__restrict__ sp_
     const int half = (threadIdx.x >> 4) & 1;
     const int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 4) + (threadIdx.x >> 4);
     const bool valid = k < ns;
+    // the three thresholds of startpoint k, computed by one thread of its half-warp (the
+    // divisions run on the FP64 pipe, slow on this part) and shared with the other fifteen
     uint32_t t_init = 0, t10 = 0, t01 = 0;
-    if (valid) {
+    if (valid && q == 0) {
         const double sp = (double)sp_in[k], tr = (double)tr_in[k];
         const double p10 = sp > 0.0 ? tr / (2.0 * sp) : 0.0;
         const double p01 = sp < 1.0 ? tr / (2.0 * (1.0 - sp)) : 0.0;
@@ -42,6 +44,9 @@ __global__ void __launch_bounds__(256) k_sim_start(const float *__restrict__ sp_
         t10 = threshold16(p10);
         t01 = threshold16(p01);
     }
+    t_init = __shfl_sync(0xFFFFFFFFu, t_init, 0, 16);
+    t10 = __shfl_sync(0xFFFFFFFFu, t10, 0, 16);
+    t01 = __shfl_sync(0xFFFFFFFFu, t01, 0, 16);
     const uint32_t sel = half ? 0x7632u : 0x5410u;  // this half-warp's 16 ballot bits of two ballots
     uint32_t st = 0;                                // bit r = current value of lane 16 r + q
     uint32_t n_flip = 0, n_one = 0;
@@ -81,6 +86,97 @@ __global__ void __launch_bounds__(256) k_sim_start(const float *__restrict__ sp_
     if (valid && q == 0) {
         toggles[k] = n_flip;
         ones[k] = n_one;
+    }
+}
+
+// The same chains for T a multiple of 16, arranged for fewer instructions: one
+// Philox call per two cycles with its low and high halves at fixed positions,
+// sixteen cycles unrolled per block (so the word a thread keeps and the store
+// are fixed at compile time), and the first cycle - the initial draw -
+// peeled off.  Each flip is formed from both threshold tests and the state by
+// one bitwise select.  Identical bits to k_sim_start.
+struct ChainState {
+    uint32_t st, n_flip, n_one;
+};
+
+// one cycle: the four lanes' 16-bit draws d[r]; FIRST draws the initial state
+template <bool FIRST>
+__device__ __forceinline__ uint64_t chain_cycle(ChainState &c, const uint32_t (&d)[4], uint32_t t_init, uint32_t t10,
+                                                uint32_t t01, uint32_t sel) {
+    if (FIRST) {
+        c.st = (uint32_t)(d[0] < t_init) | ((uint32_t)(d[1] < t_init) << 1) | ((uint32_t)(d[2] < t_init) << 2) |
+               ((uint32_t)(d[3] < t_init) << 3);
+    } else {
+        const uint32_t c10 = (uint32_t)(d[0] < t10) | ((uint32_t)(d[1] < t10) << 1) | ((uint32_t)(d[2] < t10) << 2) |
+                             ((uint32_t)(d[3] < t10) << 3);
+        const uint32_t c01 = (uint32_t)(d[0] < t01) | ((uint32_t)(d[1] < t01) << 1) | ((uint32_t)(d[2] < t01) << 2) |
+                             ((uint32_t)(d[3] < t01) << 3);
+        const uint32_t f = (c.st & c10) | (~c.st & c01 & 15u);   // a 1 flips on p10, a 0 on p01
+        c.n_flip += __popc(f);
+        c.st ^= f;
+    }
+    c.n_one += __popc(c.st);
+    const uint32_t b0 = __ballot_sync(0xFFFFFFFFu, c.st & 1u), b1 = __ballot_sync(0xFFFFFFFFu, c.st & 2u);
+    const uint32_t b2 = __ballot_sync(0xFFFFFFFFu, c.st & 4u), b3 = __ballot_sync(0xFFFFFFFFu, c.st & 8u);
+    return (uint64_t)__byte_perm(b0, b1, sel) | ((uint64_t)__byte_perm(b2, b3, sel) << 32);
+}
+
+// sixteen cycles from cycle t0 (a multiple of 16): thread q returns word t0 + q
+template <bool FIRST>
+__device__ __forceinline__ uint64_t chain_block16(ChainState &c, uint32_t k, int t0, int q, uint32_t key0,
+                                                  uint32_t key1, uint32_t t_init, uint32_t t10, uint32_t t01,
+                                                  uint32_t sel) {
+    uint64_t mine = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        const uint4 u = philox4x32_10(make_uint4(k, (uint32_t)((t0 >> 1) + i), (uint32_t)q, 0u), key0, key1);
+        const uint32_t lo[4] = {u.x & 0xFFFFu, u.y & 0xFFFFu, u.z & 0xFFFFu, u.w & 0xFFFFu};
+        const uint32_t hi[4] = {u.x >> 16, u.y >> 16, u.z >> 16, u.w >> 16};
+        const uint64_t w0 = (FIRST && i == 0) ? chain_cycle<true>(c, lo, t_init, t10, t01, sel)
+                                              : chain_cycle<false>(c, lo, t_init, t10, t01, sel);
+        const uint64_t w1 = chain_cycle<false>(c, hi, t_init, t10, t01, sel);
+        if (q == 2 * i) mine = w0;
+        if (q == 2 * i + 1) mine = w1;
+    }
+    return mine;
+}
+
+__global__ void __launch_bounds__(256) k_sim_start16(const float *__restrict__ sp_in, const float *__restrict__ tr_in,
+                                                     uint64_t *words, uint32_t *toggles, uint32_t *ones, int64_t ns,
+                                                     int T, uint32_t key0, uint32_t key1) {
+    const int q = threadIdx.x & 15;
+    const int half = (threadIdx.x >> 4) & 1;
+    const int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 4) + (threadIdx.x >> 4);
+    const bool valid = k < ns;
+    uint32_t t_init = 0, t10 = 0, t01 = 0;
+    if (valid && q == 0) {
+        const double sp = (double)sp_in[k], tr = (double)tr_in[k];
+        const double p10 = sp > 0.0 ? tr / (2.0 * sp) : 0.0;
+        const double p01 = sp < 1.0 ? tr / (2.0 * (1.0 - sp)) : 0.0;
+        t_init = threshold16(sp);
+        t10 = threshold16(p10);
+        t01 = threshold16(p01);
+    }
+    t_init = __shfl_sync(0xFFFFFFFFu, t_init, 0, 16);
+    t10 = __shfl_sync(0xFFFFFFFFu, t10, 0, 16);
+    t01 = __shfl_sync(0xFFFFFFFFu, t01, 0, 16);
+    const uint32_t sel = half ? 0x7632u : 0x5410u;
+    ChainState c{0u, 0u, 0u};
+    uint64_t *out = words + (valid ? k : 0) * T;
+    uint64_t w = chain_block16<true>(c, (uint32_t)k, 0, q, key0, key1, t_init, t10, t01, sel);
+    if (valid) out[q] = w;
+    for (int t0 = 16; t0 < T; t0 += 16) {
+        w = chain_block16<false>(c, (uint32_t)k, t0, q, key0, key1, t_init, t10, t01, sel);
+        if (valid) out[t0 + q] = w;
+    }
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {
+        c.n_flip += __shfl_xor_sync(0xFFFFFFFFu, c.n_flip, o);
+        c.n_one += __shfl_xor_sync(0xFFFFFFFFu, c.n_one, o);
+    }
+    if (valid && q == 0) {
+        toggles[k] = c.n_flip;
+        ones[k] = c.n_one;
     }
 }
 
@@ -169,6 +265,12 @@ __global__ void k_hybrid(const uint32_t *__restrict__ toggles, const float *__re
 
 void launch_sim_start(const DevDesign &d, int T, uint64_t seed, cudaStream_t s) {
     if (d.n_start == 0) return;
+    if (T % 16 == 0) {
+        k_sim_start16<<<(unsigned)cdiv(d.n_start, 16), 256, 0, s>>>(d.sp_in, d.tr_in, d.words, d.toggles, d.ones,
+                                                                    d.n_start, T, (uint32_t)seed,
+                                                                    (uint32_t)(seed >> 32));
+        return;
+    }
     k_sim_start<<<(unsigned)cdiv(d.n_start, 16), 256, 0, s>>>(d.sp_in, d.tr_in, d.words, d.toggles, d.ones,
                                                               d.n_start, T, (uint32_t)seed, (uint32_t)(seed >> 32));
 }
