@@ -629,6 +629,29 @@ def main() -> None:
         "clocks": clocks,
         "device_bytes": int(info.device_bytes),
     }
+    # ---- forward + reverse alone (model gradient, no simulation): N_c / (t_fwd + t_bwd)
+    cfg0 = dp.config(grad_mode=0)
+    for _ in range(3):
+        dp.dp_propagate(ctx, d, cfg0)
+        dp.dp_backward(ctx, d, cfg0, g["sp"], None, None, None, 1)
+    torch.cuda.synchronize()
+    fb = []
+    for i in range(max(args.steps, 5)):
+        flush.fill_(float(i))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dp.dp_propagate(ctx, d, cfg0)
+        dp.dp_backward(ctx, d, cfg0, g["sp"], None, None, None, 1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fb.append(e0.elapsed_time(e1))
+    fb_ms0 = statistics.median(fb)
+    fb_bytes = ab["forward"] + ab["backward"]
+    line["fwd_bwd_model"] = {"ms": fb_ms0, "cell_evals_per_s": nc / (fb_ms0 * 1e-3),
+                             "frac": fb_bytes / (fb_ms0 * 1e-3) / 1e9 / pk["hbm_gbs"],
+                             "what": "dp_propagate + dp_backward (grad_mode 0) alone, L2 flushed, median",
+                             "levels": 2 * int(info.n_levels)}
+
     # ---- Eq. 8 sizing scores and the top 1,000 cells from the step's adjoint (re-ranking cost)
     dp.dp_step(ctx, d, cfg, g["sp"], g["tr"], g["pin"], g["cl"], None, 1)
     top = np.zeros(1000, np.int32)

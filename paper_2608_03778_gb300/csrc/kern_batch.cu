@@ -303,12 +303,6 @@ __global__ void k_virus_partials(const uint64_t *__restrict__ words, const float
     partials[s * nchunks + blockIdx.y] = acc;
 }
 
-// dcl[at[i]] = v[i] (v NULL: 0), at[i] = net * S + scenario, one entry per (net, scenario)
-__global__ void k_scatter(float *dcl, const int64_t *__restrict__ at, const float *__restrict__ v, int64_t n) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) dcl[at[i]] = v ? v[i] : 0.f;
-}
-
 // out[c * ldo + r] = in[r * C + c] for an R x C block, through 32 x 32 tiles in shared memory
 __global__ void k_transpose(const float *__restrict__ in, float *out, int64_t R, int64_t C, int64_t ldo) {
     __shared__ float t[32][33];
@@ -408,10 +402,6 @@ void launch_netb_user(const DevDesign &d, const BatchBufs &b, int tr_mode, float
     const BatchShape sh{b.S >= 128 ? 128 : 32, b.S >= 128 ? 1 : 4};
     k_netb_user<<<bgrid(b.S, sh, d.n_nets), dim3((unsigned)sh.bx, (unsigned)sh.by), 0, s>>>(
         b.pq, tr_mode == 2 ? b.tq : b.tr_in, d.net_of_user, sp, tr, d.n_nets, d.n_start, b.S, tr_mode);
-}
-
-void launch_scatter(float *dcl, const int64_t *at, const float *v, int64_t n, cudaStream_t s) {
-    if (n > 0) k_scatter<<<(unsigned)cdiv(n, 256), 256, 0, s>>>(dcl, at, v, n);
 }
 
 void launch_transpose(const float *in, float *out, int64_t R, int64_t C, cudaStream_t s) {

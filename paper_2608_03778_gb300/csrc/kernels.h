@@ -148,8 +148,6 @@ void launch_sizing_deltas(const DevDesign &d, const OpTable &ops, const SizingDe
 // returns win, dpin, flag and dcl to rest after the batch
 void launch_sizing_clear(const DevDesign &d, const SizingDeltas &z, int64_t ne, int64_t S, float *dcl,
                          cudaStream_t s);
-// dcl[at[i]] = v[i] (v NULL: 0)
-void launch_scatter(float *dcl, const int64_t *at, const float *v, int64_t n, cudaStream_t s);
 // out[c][r] = in[r][c] (row-major R x C in, C x R out)
 void launch_transpose(const float *in, float *out, int64_t R, int64_t C, cudaStream_t s);
 // x <- clip(x + eta g, 0, 1) (Algorithm 4 ascent step with projection)

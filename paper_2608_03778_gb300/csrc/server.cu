@@ -80,7 +80,6 @@ struct Slot {
     size_t bytes = 0;
     std::deque<Req *> queue;
     std::vector<Req *> inflight;
-    int64_t inflight_deltas = 0;
     bool busy = false;
 };
 
@@ -281,7 +280,6 @@ cudaError_t launch_batch(dp_server *srv, Slot *sl) {
         }
     }
     if (e != cudaSuccess) return e;
-    sl->inflight_deltas = nd;
     if (nd) {   // the entries go to the device as given; the device resolves them (kern_serve.cu)
         if ((e = ensure_delta_cap(sl, nd)) != cudaSuccess) return e;
         int64_t off = 0;
