@@ -107,17 +107,21 @@ __global__ void k_bwdb_level(const uint4 *__restrict__ fanin, const int32_t *__r
     const int64_t step = (int64_t)gridDim.y * blockDim.y;
     for (int64_t c = c0 + (int64_t)blockIdx.y * blockDim.y + threadIdx.y; c < c1; c += step) {
         const int64_t n = ns + c;
-        const int32_t e0 = fptr[n], e1 = fptr[n + 1];
-        float acc = 0.f;
-        for (int32_t e = e0; e < e1; e++) acc += gfo[(int64_t)e * S + s];
-        const float g = acc + 2.f * Ks * cl_of(cload, dcl, n, S, s) * qmp32(pq[n * S + s]);
+        // everything that does not depend on the fanout sum goes out first, so its loads
+        // overlap the fanout range's
         const uint4 r = fanin[c];
+        const int4 ep = efpos[c];
+        const int32_t e0 = fptr[n], e1 = fptr[n + 1];
+        const float2 self = pq[n * S + s];
+        const float cl = cl_of(cload, dcl, n, S, s);
         const uint32_t op = r.x >> 24;
         const int k = op_arity(ops, op);
         float p[4], q[4], d[4];
         gather32(pq, r, k, S, s, p, q);
+        float acc = 0.f;
+        for (int32_t e = e0; e < e1; e++) acc += gfo[(int64_t)e * S + s];
+        const float g = acc + 2.f * Ks * cl * qmp32(self);
         cell_partials(k, op_tt(ops, op), p, q, d);
-        const int4 ep = efpos[c];
         if (k > 0) gfo[(int64_t)ep.x * S + s] = g * d[0];
         if (k > 1) gfo[(int64_t)ep.y * S + s] = g * d[1];
         if (k > 2) gfo[(int64_t)ep.z * S + s] = g * d[2];
