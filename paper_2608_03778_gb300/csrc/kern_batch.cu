@@ -6,11 +6,11 @@
 // (cell, scenario) independently of the block shape, so every shape gives
 // bitwise identical results and the shape is free for the autotuner.
 //
-// Each cell evaluates the single-scenario path's float-float (P, Q) pair, P(net=0)
-// its own minterm sum and the pair renormalised by P + Q (the same reading of
-// Eq. 2), but only P is stored, as a float-float value (8 bytes per net and
+// Each cell evaluates P(out = 1) as the multilinear extension of its truth
+// table in float-float (the same reading of Eq. 2 as the single-scenario
+// path), and only P is stored, as a float-float value (8 bytes per net and
 // scenario): Q is re-derived as 1 - P in float-float, exact to about 1e-14
-// absolute.  That loses Q's relative accuracy only for nets within about 1e-9
+// absolute, wherever it is read.  That loses Q's relative accuracy only for nets within about 1e-9
 // of 1, which matters for the hybrid beta (Eq. 5, single-scenario only) and
 // not for the model power, SP, TR or gradients at their tolerances; it halves
 // the bytes every gather moves.  The gradient is the model gradient (Sec. III-E,
@@ -40,7 +40,7 @@ __global__ void k_fwdb_level(const uint4 *__restrict__ fanin, float2 *pq, int32_
         const int k = op_arity(ops, op);
         pair_ff x[4];
         gather_ffb(pq, r, k, S, s, x);
-        pq[(ns + c) * S + s] = p_set(cell_pair(k, op_tt(ops, op), x));
+        pq[(ns + c) * S + s] = cell_p(k, op_tt(ops, op), x);
     }
 }
 

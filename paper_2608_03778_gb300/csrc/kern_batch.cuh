@@ -25,6 +25,40 @@ __device__ __forceinline__ void gather_ffb(const float2 *pq, const uint4 &r, int
     for (int j = 0; j < 4; j++) x[j] = pair_get(v[j]);
 }
 
+// P(out = 1) of a cell alone: the multilinear extension of its truth table over
+// the fanin pairs, folded in float-float.  The batched path stores only P and
+// re-derives each fanin's Q = 1 - P where it is read, so every pair sums to 1
+// to about 4e-15 afresh and no drift of P + Q can build up along paths: the
+// complementary sum and the renormalisation of the single-scenario path would
+// be thrown away here.
+template <int K>
+__device__ __forceinline__ ff ml_p(uint32_t tt, const pair_ff (&x)[4]) {
+    ff v[1 << K];
+#pragma unroll
+    for (int m = 0; m < (1 << (K - 1)); m++) {
+        const bool a1 = (tt >> (2 * m)) & 1u, b1 = (tt >> (2 * m + 1)) & 1u;
+        v[m] = ff_add(a1 ? x[0].q : ff_make(0.f), b1 ? x[0].p : ff_make(0.f));
+    }
+#pragma unroll
+    for (int i = 1; i < K; i++) {
+#pragma unroll
+        for (int m = 0; m < (1 << (K - 1 - i)); m++) v[m] = ff_add(ff_mul(x[i].q, v[2 * m]), ff_mul(x[i].p, v[2 * m + 1]));
+    }
+    return v[0];
+}
+
+__device__ __forceinline__ float2 cell_p(int k, uint32_t tt, const pair_ff (&x)[4]) {
+    ff p;
+    switch (k) {
+        case 0: p = ff_make((tt & 1u) ? 1.f : 0.f); break;
+        case 1: p = ml_p<1>(tt, x); break;
+        case 2: p = ml_p<2>(tt, x); break;
+        case 3: p = ml_p<3>(tt, x); break;
+        default: p = ml_p<4>(tt, x); break;
+    }
+    return make_float2(p.hi, p.lo);
+}
+
 // binary32 (P, Q) of a cell's inputs for the partial derivatives
 __device__ __forceinline__ void gather32(const float2 *pq, const uint4 &r, int k, int64_t S, int64_t s,
                                          float (&p)[4], float (&q)[4]) {

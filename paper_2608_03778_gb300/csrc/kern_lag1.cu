@@ -107,7 +107,7 @@ __global__ void k_fwdl_level(const uint4 *__restrict__ fanin, float2 *pq, float 
         pair_ff x[4];
         float w[4][4];
         gather_lag1(pq, tq, r, k, S, s, x, w);
-        pq[(ns + c) * S + s] = p_set(cell_pair(k, tt, x));
+        pq[(ns + c) * S + s] = cell_p(k, tt, x);
         tq[(ns + c) * S + s] = lag1_t(k, tt, w, -1, none);
     }
 }
