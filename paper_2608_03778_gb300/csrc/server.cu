@@ -549,7 +549,17 @@ dp_status dp_server_add_design(dp_server *srv, const char *netlist, size_t netli
     sl->ns = ns;
     sl->nc = nc;
     sl->nn = nn;
-    cudaError_t e = cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking);
+    // stream priority by size: a small design's short batches are scheduled ahead of a large
+    // design's long ones when both wait for SMs (arithmetic and results are unaffected)
+    int lo_prio = 0, hi_prio = 0;
+    if (cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio) != cudaSuccess) {
+        cudaGetLastError();
+        lo_prio = hi_prio = 0;
+    }
+    const int span = lo_prio - hi_prio;   // greatest priority is the most negative number
+    const int rank = nc < 100000 ? 0 : (nc < 1000000 ? 1 : 2);
+    const int prio = span > 0 ? hi_prio + (rank * span) / 2 : 0;
+    cudaError_t e = cudaStreamCreateWithPriority(&sl->stream, cudaStreamNonBlocking, prio);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl->done, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         dp_compiled_free(cp);
