@@ -46,10 +46,11 @@ __global__ void k_fwdb_level(const uint4 *__restrict__ fanin, float2 *pq, int32_
 
 // Eq. 1 per scenario: chunk b of the nets -> partials[s * nchunks + b], then
 // the chunks of each scenario summed in FP64 in a fixed order (reproducible).
-// Within a chunk a thread forms each term alpha * C as an exact float-float
-// product and adds it with TwoSum (about 48 significant bits), so the FP64
-// pipe, slow on this part, sees one conversion per chunk instead of several
-// operations per term.
+// Within a chunk a thread forms each term alpha * C in binary32 (TR = 2 P Q
+// with Q from the float-float pair, so it keeps its relative accuracy near
+// P = 1; about 1e-7 relative per term) and adds it with TwoSum into a
+// float-float sum (about 48 significant bits), so the FP64 pipe, slow on this
+// part, sees one conversion per chunk instead of several operations per term.
 __global__ void k_powerb_partials(const float2 *__restrict__ pq, const float *__restrict__ tr_in,
                                   const float *__restrict__ cload, const float *__restrict__ dcl, double *partials,
                                   int64_t nn, int64_t ns,
@@ -66,12 +67,20 @@ __global__ void k_powerb_partials(const float2 *__restrict__ pq, const float *__
             a[i] = 0.f;
             c[i] = 0.f;
             if (m < n1) {
-                a[i] = alpha32(pq, tr_in, m, ns, S, s, tr_mode);
+                if (tr_mode == 2 || (m < ns && tr_mode == 0)) {
+                    a[i] = tr_in[m * S + s];
+                } else {
+                    const pair_ff pr = pair_get(pq[m * S + s]);
+                    a[i] = 2.f * (pr.p.hi + pr.p.lo) * (pr.q.hi + pr.q.lo);
+                }
                 c[i] = cl_of(cload, dcl, m, S, s);
             }
         }
 #pragma unroll
-        for (int i = 0; i < 4; i++) acc = ff_add(acc, ff_mul(ff_make(a[i]), ff_make(c[i])));
+        for (int i = 0; i < 4; i++) {
+            const ff t = two_sum(acc.hi, a[i] * c[i]);
+            acc = fast_two_sum(t.hi, t.lo + acc.lo);
+        }
     }
     partials[s * nchunks + blockIdx.y] = (double)acc.hi + (double)acc.lo;
 }
