@@ -141,6 +141,56 @@ __device__ __forceinline__ uint64_t chain_block16(ChainState &c, uint32_t k, int
     return mine;
 }
 
+// Fast form of the same chains when every threshold of the warp is below 2^16
+// (no probability of exactly 1): a 16-bit draw d is compared in the high half
+// of a 32-bit word against thr << 16, which holds whatever the low half is, so
+// the high-half draws need no extraction.  Each lane keeps its state s and the
+// threshold of that state; a flip toggles both (the threshold between t10 and
+// t01 by one XOR).  Ones and toggles are counted from the finished words.
+struct FastChain {
+    uint32_t thr[4];
+    bool s[4];
+};
+
+// one cycle on draws d[r] (in the high half); FIRST draws the initial state
+template <bool FIRST>
+__device__ __forceinline__ uint64_t fast_cycle(FastChain &c, const uint32_t (&d)[4], uint32_t ti16, uint32_t t10_16,
+                                               uint32_t t01_16, uint32_t sel) {
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+        if (FIRST) {
+            c.s[r] = d[r] < ti16;
+            c.thr[r] = c.s[r] ? t10_16 : t01_16;
+        } else {
+            const bool f = d[r] < c.thr[r];
+            c.s[r] ^= f;
+            c.thr[r] ^= f ? (t10_16 ^ t01_16) : 0u;
+        }
+    }
+    const uint32_t b0 = __ballot_sync(0xFFFFFFFFu, c.s[0]), b1 = __ballot_sync(0xFFFFFFFFu, c.s[1]);
+    const uint32_t b2 = __ballot_sync(0xFFFFFFFFu, c.s[2]), b3 = __ballot_sync(0xFFFFFFFFu, c.s[3]);
+    return (uint64_t)__byte_perm(b0, b1, sel) | ((uint64_t)__byte_perm(b2, b3, sel) << 32);
+}
+
+template <bool FIRST>
+__device__ __forceinline__ uint64_t fast_block16(FastChain &c, uint32_t k, int t0, int q, uint32_t key0,
+                                                 uint32_t key1, uint32_t ti16, uint32_t t10_16, uint32_t t01_16,
+                                                 uint32_t sel) {
+    uint64_t mine = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        const uint4 u = philox4x32_10(make_uint4(k, (uint32_t)((t0 >> 1) + i), (uint32_t)q, 0u), key0, key1);
+        const uint32_t lo[4] = {u.x << 16, u.y << 16, u.z << 16, u.w << 16};
+        const uint32_t hi[4] = {u.x, u.y, u.z, u.w};
+        const uint64_t w0 = (FIRST && i == 0) ? fast_cycle<true>(c, lo, ti16, t10_16, t01_16, sel)
+                                              : fast_cycle<false>(c, lo, ti16, t10_16, t01_16, sel);
+        const uint64_t w1 = fast_cycle<false>(c, hi, ti16, t10_16, t01_16, sel);
+        if (q == 2 * i) mine = w0;
+        if (q == 2 * i + 1) mine = w1;
+    }
+    return mine;
+}
+
 __global__ void __launch_bounds__(256) k_sim_start16(const float *__restrict__ sp_in, const float *__restrict__ tr_in,
                                                      uint64_t *words, uint32_t *toggles, uint32_t *ones, int64_t ns,
                                                      int T, uint32_t key0, uint32_t key1) {
@@ -161,8 +211,34 @@ __global__ void __launch_bounds__(256) k_sim_start16(const float *__restrict__ s
     t10 = __shfl_sync(0xFFFFFFFFu, t10, 0, 16);
     t01 = __shfl_sync(0xFFFFFFFFu, t01, 0, 16);
     const uint32_t sel = half ? 0x7632u : 0x5410u;
-    ChainState c{0u, 0u, 0u};
     uint64_t *out = words + (valid ? k : 0) * T;
+    if (!__any_sync(0xFFFFFFFFu, (t_init | t10 | t01) >= 65536u)) {   // warp-uniform
+        FastChain c{};
+        uint32_t n_one = 0, n_flip = 0;
+        uint64_t carry = 0;
+        for (int t0 = 0; t0 < T; t0 += 16) {
+            const uint64_t w = t0 == 0 ? fast_block16<true>(c, (uint32_t)k, 0, q, key0, key1, t_init << 16,
+                                                            t10 << 16, t01 << 16, sel)
+                                       : fast_block16<false>(c, (uint32_t)k, t0, q, key0, key1, t_init << 16,
+                                                             t10 << 16, t01 << 16, sel);
+            if (valid) out[t0 + q] = w;
+            const uint64_t prev = __shfl_up_sync(0xFFFFFFFFu, w, 1, 16);
+            n_one += __popcll(w);
+            if (t0 + q > 0) n_flip += __popcll(w ^ (q > 0 ? prev : carry));
+            carry = __shfl_sync(0xFFFFFFFFu, w, 15, 16);
+        }
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) {
+            n_flip += __shfl_xor_sync(0xFFFFFFFFu, n_flip, o);
+            n_one += __shfl_xor_sync(0xFFFFFFFFu, n_one, o);
+        }
+        if (valid && q == 0) {
+            toggles[k] = n_flip;
+            ones[k] = n_one;
+        }
+        return;
+    }
+    ChainState c{0u, 0u, 0u};
     uint64_t w = chain_block16<true>(c, (uint32_t)k, 0, q, key0, key1, t_init, t10, t01, sel);
     if (valid) out[q] = w;
     for (int t0 = 16; t0 < T; t0 += 16) {

@@ -429,3 +429,39 @@ def test_lag1_mid_sampled(dp, ctx, library_text):
     finally:
         dp.dp_design_free(d)
     check_lag1(o, g, sp, tr, [0, 31, 63])
+
+
+def test_batch_only_startpoints_and_constants(dp, ctx, library_text):
+    """Edge designs in the batched path: no cells at all, and constant cells only."""
+    lib = "cell C0 Z 0.8 0\ncell C1 Z 1.6 1\n"
+    only_start = "net a 1.0\nnet b 2.0\ninput a\ninput b\noutput a\noutput b\n"
+    consts = "net a 1.0\ninput a\nnet y0 0.5\nnet y1 0.7\ncell u0 C0 Z=y0\ncell u1 C1 Z=y1\noutput y0\noutput y1\n"
+    for text in (only_start, consts):
+        o = Oracle(text, lib)
+        S = 5
+        sp, tr = netgen.scenario_inputs(o.n_start, 4400, S)
+        for tr_mode in (0, 1, 2):
+            cfg = dp.config(grad_mode=0, tr_mode=tr_mode)
+            d = dp.dp_design_load(ctx, text, lib)
+            try:
+                g = run_batch(dp, ctx, d, sp, tr, cfg)
+            finally:
+                dp.dp_design_free(d)
+            if tr_mode == 2:
+                check_lag1(o, g, sp, tr, range(S))
+            else:
+                check_scenarios(o, g, sp, tr, cfg, range(S))
+
+
+def test_batch_max_scenarios(dp, ctx, small):
+    """The largest batch the tuner shapes for, 4,096 scenarios, on sampled scenarios."""
+    text, o = small
+    S = 4096
+    sp, tr = netgen.scenario_inputs(o.n_start, 4500, S)
+    cfg = dp.config(grad_mode=0, tr_mode=0)
+    d = dp.dp_design_load(ctx, text, netgen.library_text())
+    try:
+        g = run_batch(dp, ctx, d, sp, tr, cfg)
+    finally:
+        dp.dp_design_free(d)
+    check_scenarios(o, g, sp, tr, cfg, [0, 1, 2047, 4095])

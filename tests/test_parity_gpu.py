@@ -204,6 +204,26 @@ def test_wide_and_constant_cells_ragged_words(dp, ctx, seed, T):
         check_against_oracle(o, g, sp, tr, cfg)
 
 
+@pytest.mark.parametrize("T", [16, 64, 128])
+def test_startpoint_chains_both_forms(dp, ctx, library_text, T):
+    """The startpoint generator's two forms: warps whose thresholds are all below 2^16, and
+    warps (two startpoints each) holding a probability of exactly 1 (SP = 1, or TR = 2 SP so
+    that p10 = 1); toggles and ones of every startpoint equal the oracle's."""
+    n = 997
+    text = "".join(f"net i{i} 1.0\ninput i{i}\n" for i in range(n)) + "output i0\n"
+    o = Oracle(text, library_text)
+    rng = np.random.default_rng(T)
+    sp = rng.uniform(0.01, 0.99, n).astype(np.float32)
+    tr = (rng.uniform(0, 1, n) * 2 * np.minimum(sp, 1 - sp)).astype(np.float32)
+    sp[40], tr[40] = 1.0, 0.0
+    sp[301], tr[301] = np.float32(0.25), np.float32(0.5)
+    sp[302], tr[302] = np.float32(0.75), np.float32(0.5)
+    sp[996], tr[996] = 0.0, 0.0
+    cfg = dp.config(sim_words=T, grad_mode=1, seed=11 + T)
+    g = gpu_run(dp, ctx, text, library_text, sp, tr, cfg)
+    check_against_oracle(o, g, sp, tr, cfg)
+
+
 def test_boolean_inputs_exact(dp, ctx, library_text):
     text = netgen.netlist_text(netgen.WORKLOADS["small"])
     o = Oracle(text, library_text)
