@@ -77,21 +77,24 @@ def batched_algorithmic_bytes(nn: int, ns: int, nc: int, ne: int, S: int) -> int
 # DRAM traffic per launch of the dominant kernels, from `ncu --metrics
 # dram__bytes_read.sum,dram__bytes_write.sum` on the 2,000,000-cell step (the
 # captures and commands are summarised under profiles/).  A figure is reported
-# only while the kernel's source file still hashes to the value it was taken
-# with; otherwise the traffic is unknown (null).
+# only for the workload it was taken on, and while the kernel's source files
+# still hash to the value it was taken with; otherwise the traffic is unknown
+# (null).
 TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (one pass), 2M-cell step, 4th step
-    "k_sim_wide": {"bytes": 258_320_000 + 986_920_000, "files": ["kern_persist.cu", "kern_common.cuh"],
+    "k_sim_wide": {"bytes": 258_320_000 + 986_920_000, "workload": "roofline",
+                   "files": ["kern_persist.cu", "kern_common.cuh"],
                    "sha": "1f0ddf92a7982993"},
-    "k_bwd_persist": {"bytes": 127_290_000 + 11_950_000, "files": ["kern_persist.cu", "kern_common.cuh"],
+    "k_bwd_persist": {"bytes": 127_290_000 + 11_950_000, "workload": "roofline",
+                      "files": ["kern_persist.cu", "kern_common.cuh"],
                       "sha": "1f0ddf92a7982993"},
 }
 
 
-def kernel_traffic(kernel: str) -> int | None:
+def kernel_traffic(kernel: str, workload: str) -> int | None:
     import hashlib
     t = TRAFFIC.get(kernel)
-    if not t:
+    if not t or t["workload"] != workload:
         return None
     m = hashlib.sha256()
     for name in t["files"]:
@@ -617,7 +620,7 @@ def main() -> None:
         },
         "roofline": {"bound": "hbm", "kernel": f"{kernel_of[dom]} ({dom}, one cooperative launch per step)",
                      "achieved": per_phase[dom]["achieved_gbs"], "peak": pk["hbm_gbs"], "unit": "GB/s",
-                     "frac": per_phase[dom]["frac"], "traffic": kernel_traffic(kernel_of[dom]),
+                     "frac": per_phase[dom]["frac"], "traffic": kernel_traffic(kernel_of[dom], args.workload),
                      "algorithmic_bytes": ab[dom], "peak_source": pk["source"]},
         "phases": per_phase,
         "fwd_bwd": {"ms": fb_ms, "cell_evals_per_s": nc / (fb_ms / 1e3),

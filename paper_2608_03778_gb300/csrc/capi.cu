@@ -132,6 +132,14 @@ dp_status ensure_words(dp_design *D, int T) {
     }
     dp_status s = dalloc(D, &D->d.words, (size_t)D->d.n_nets * (size_t)T);
     if (s == DP_OK) D->words_T = T;
+    if (s == DP_OK && !D->d.simdone) {   // flags of the dataflow simulation: pass number 0 = none
+        s = dalloc(D, &D->d.simdone, (size_t)D->d.n_cells);
+        if (s == DP_OK) {
+            const cudaError_t e = cudaMemsetAsync(D->d.simdone, 0, sizeof(unsigned) * (size_t)D->d.n_cells,
+                                                  D->ctx->stream);
+            if (e != cudaSuccess) s = cuda_err(D->ctx, e, "cudaMemsetAsync");
+        }
+    }
     return s;
 }
 
@@ -182,7 +190,10 @@ void q_sim_start(dp_design *D, const dp_config &c, cudaStream_t s) {
 
 // the simulation levels, beta and the hybrid power (after the generator and the forward pass)
 cudaError_t q_sim_levels(dp_design *D, const dp_config &c, cudaStream_t s) {
-    if (persistent(D, c, 3) && dp::wide_ok(c.sim_words)) {
+    if (dataflow(D, c, 1) && dp::wide_ok(c.sim_words) && D->d.simdone) {
+        cudaError_t e = dp::launch_sim_flow(D->d, D->ops, c.sim_words, D->flow_grid[1], s);
+        if (e != cudaSuccess) return e;
+    } else if (persistent(D, c, 3) && dp::wide_ok(c.sim_words)) {
         cudaError_t e = dp::launch_sim_wide(D->d, D->ops, c.sim_words, D->grid[3], s);
         if (e != cudaSuccess) return e;
     } else if (persistent(D, c, 1)) {
@@ -357,6 +368,11 @@ dp_status dp_design_upload(dp_ctx *ctx, const dp_compiled *cp, dp_design **out) 
     chunk_ptr[1] = (int32_t)((cp->n_start + 31) / 32);
     for (int l = 1; l <= cp->n_levels; l++)
         chunk_ptr[l + 1] = chunk_ptr[l] + (cp->lvl_ptr[l] - cp->lvl_ptr[l - 1] + 31) / 32;
+    // level-aligned cell pairs (the dataflow simulation's unit of work)
+    std::vector<int32_t> pair_ptr((size_t)cp->n_levels + 1, 0);
+    for (int l = 1; l <= cp->n_levels; l++)
+        pair_ptr[l] = pair_ptr[l - 1] + (cp->lvl_ptr[l] - cp->lvl_ptr[l - 1] + 1) / 2;
+    int32_t *pairs = nullptr;
     float *base = nullptr;
 #define TRY(x) do { if ((s = (x)) != DP_OK) { free_design(D); return s; } } while (0)
     TRY(dalloc(D, &fanin, nc));
@@ -382,6 +398,7 @@ dp_status dp_design_upload(dp_ctx *ctx, const dp_compiled *cp, dp_design **out) 
     TRY(dalloc(D, &d.bar, dp::persist_bar_words(cp->n_levels)));
     TRY(dalloc(D, &d.epoch, 4));
     TRY(dalloc(D, &chunks, chunk_ptr.size()));
+    TRY(dalloc(D, &pairs, pair_ptr.size()));
     TRY(dalloc(D, &d.partials, (size_t)dp::kPowerBlocks));
     TRY(dalloc(D, &d.power, 4));
     d.fanin = fanin;
@@ -390,6 +407,7 @@ dp_status dp_design_upload(dp_ctx *ctx, const dp_compiled *cp, dp_design **out) 
     d.edge_fpos = efpos;
     d.lvl = lvl;
     d.chunk_ptr = chunks;
+    d.pair_ptr = pairs;
     d.err = ctx->d_err;
     d.net_of_user = nou;
     d.cell_of_user = cou;
@@ -405,6 +423,7 @@ dp_status dp_design_upload(dp_ctx *ctx, const dp_compiled *cp, dp_design **out) 
     up(efpos, cp->edge_fpos.data(), sizeof(int32_t) * cp->edge_fpos.size());
     up(lvl, cp->lvl_ptr.data(), sizeof(int32_t) * cp->lvl_ptr.size());
     up(chunks, chunk_ptr.data(), sizeof(int32_t) * chunk_ptr.size());
+    up(pairs, pair_ptr.data(), sizeof(int32_t) * pair_ptr.size());
     up(nou, cp->net_of_user.data(), sizeof(int32_t) * nn);
     up(cou, cp->cell_of_user.data(), sizeof(int32_t) * nc);
     up(base, cp->base_cap.data(), sizeof(float) * nn);
@@ -418,6 +437,7 @@ dp_status dp_design_upload(dp_ctx *ctx, const dp_compiled *cp, dp_design **out) 
     if (const char *v = std::getenv("DP_FLOW_BLOCKS")) D->flow_blocks_per_sm = std::atoi(v);
     if (const char *v = std::getenv("DP_FLOW_SLEEP")) D->flow_sleep = (unsigned)std::atoi(v);
     D->flow_grid[0] = dp::flow_grid(0, ctx->sm_count, D->flow_blocks_per_sm);
+    D->flow_grid[1] = dp::flow_grid(1, ctx->sm_count, 2);
     if (e != cudaSuccess) { s = cuda_err(ctx, e, "upload"); free_design(D); return s; }
     dp::launch_cload(d, st);
     for (auto &ev : D->ev)

@@ -76,7 +76,7 @@ struct dp_design {
     cudaStream_t cap_stream = nullptr, cap_stream2 = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
     int grid[4] = {0, 0, 0, 0};   // persistent grids: forward, simulation, backward, wide simulation
-    int flow_grid[1] = {0};        // dataflow grids: forward
+    int flow_grid[2] = {0, 0};     // dataflow grids: forward, simulation
     // launch-shape tuning (defaults, overridable by DP_FLOW_BLOCKS / DP_FLOW_SLEEP for sweeps)
     int flow_blocks_per_sm = 2;
     unsigned flow_sleep = 0;

@@ -32,10 +32,14 @@ __global__ void k_fwdb_start(const float *__restrict__ sp_in, float2 *pq, int64_
 __global__ void k_fwdb_level(const uint4 *__restrict__ fanin, float2 *pq, int32_t c0, int32_t c1, int64_t ns,
                              int64_t S, OpTable ops) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    pdl_trigger();
     if (s >= S) return;
     const int64_t step = (int64_t)gridDim.y * blockDim.y;
-    for (int64_t c = c0 + (int64_t)blockIdx.y * blockDim.y + threadIdx.y; c < c1; c += step) {
-        const uint4 r = fanin[c];
+    const int64_t cf = c0 + (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
+    uint4 r = cf < c1 ? fanin[cf] : make_uint4(0, 0, 0, 0);   // static: before the wait
+    pdl_wait();
+    for (int64_t c = cf; c < c1; c += step) {
+        if (c != cf) r = fanin[c];
         const uint32_t op = r.x >> 24;
         const int k = op_arity(ops, op);
         pair_ff x[4];
@@ -111,14 +115,18 @@ __global__ void k_bwdb_level(const uint4 *__restrict__ fanin, const int32_t *__r
                              const float *__restrict__ ks, float *gfo, int32_t c0, int32_t c1, int64_t ns, int64_t S,
                              OpTable ops) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    pdl_trigger();
     if (s >= S) return;
-    const float Ks = ks[s];
     const int64_t step = (int64_t)gridDim.y * blockDim.y;
-    for (int64_t c = c0 + (int64_t)blockIdx.y * blockDim.y + threadIdx.y; c < c1; c += step) {
+    const int64_t cf = c0 + (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
+    uint4 rf = cf < c1 ? fanin[cf] : make_uint4(0, 0, 0, 0);   // static: before the wait
+    pdl_wait();
+    const float Ks = ks[s];
+    for (int64_t c = cf; c < c1; c += step) {
         const int64_t n = ns + c;
         // everything that does not depend on the fanout sum goes out first, so its loads
         // overlap the fanout range's
-        const uint4 r = fanin[c];
+        const uint4 r = c == cf ? rf : fanin[c];
         const int4 ep = efpos[c];
         const int32_t e0 = fptr[n], e1 = fptr[n + 1];
         const float2 self = pq[n * S + s];
@@ -144,7 +152,9 @@ __global__ void k_bwdb_start(const int32_t *__restrict__ fptr, const float2 *__r
                              const float *__restrict__ ks,
                              const float *__restrict__ gfo, float *gsp, int64_t ns, int64_t S, int tr_mode) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    pdl_trigger();
     if (s >= S) return;
+    pdl_wait();
     const float Ks = ks[s];
     const int64_t step = (int64_t)gridDim.y * blockDim.y;
     for (int64_t k = (int64_t)blockIdx.y * blockDim.y + threadIdx.y; k < ns; k += step) {
@@ -351,7 +361,7 @@ void launch_fwdb(const DevDesign &d, const BatchBufs &b, const OpTable &ops, con
     const dim3 blk((unsigned)sh.bx, (unsigned)sh.by);
     for (int l = 1; l <= d.n_levels; l++) {
         const int32_t c0 = lvl[l - 1], c1 = lvl[l];
-        if (c1 > c0) k_fwdb_level<<<bgrid(S, sh, c1 - c0), blk, 0, s>>>(d.fanin, b.pq, c0, c1, d.n_start, S, ops);
+        if (c1 > c0) launch_pdl(k_fwdb_level, bgrid(S, sh, c1 - c0), blk, s, d.fanin, b.pq, c0, c1, d.n_start, S, ops);
     }
 }
 
@@ -380,13 +390,12 @@ void launch_bwdb(const DevDesign &d, const BatchBufs &b, const OpTable &ops, con
     for (int l = d.n_levels; l >= 1; l--) {
         const int32_t c0 = lvl[l - 1], c1 = lvl[l];
         if (c1 > c0)
-            k_bwdb_level<<<bgrid(S, sh, c1 - c0), blk, 0, s>>>(d.fanin, d.fout_ptr, (const int4 *)d.edge_fpos, b.pq,
-                                                               d.cload, b.dcl, b.ks, b.gfo, c0, c1, d.n_start, S,
-                                                               ops);
+            launch_pdl(k_bwdb_level, bgrid(S, sh, c1 - c0), blk, s, d.fanin, d.fout_ptr, (const int4 *)d.edge_fpos,
+                       b.pq, d.cload, b.dcl, b.ks, b.gfo, c0, c1, d.n_start, S, ops);
     }
     if (d.n_start)
-        k_bwdb_start<<<bgrid(S, sh, d.n_start), blk, 0, s>>>(d.fout_ptr, b.pq, d.cload, b.dcl, b.ks, b.gfo, b.gsp,
-                                                             d.n_start, S, tr_mode);
+        launch_pdl(k_bwdb_start, bgrid(S, sh, d.n_start), blk, s, d.fout_ptr, b.pq, d.cload, b.dcl, b.ks, b.gfo, b.gsp,
+                   d.n_start, S, tr_mode);
 }
 
 void launch_gradb(const DevDesign &d, const BatchBufs &b, const OpTable &ops, int tr_mode, bool reduce, float *gtr,

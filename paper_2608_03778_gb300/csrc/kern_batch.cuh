@@ -10,7 +10,7 @@ __host__ __device__ inline int64_t bcdiv(int64_t a, int64_t b) { return (a + b -
 // the stored float-float P of a net and its pair (P, 1 - P)
 __device__ __forceinline__ pair_ff pair_get(const float2 &v) {
     const ff p{v.x, v.y};
-    const ff t = two_sum(1.f, -v.x);
+    const ff t = fast_two_sum(1.f, -v.x);   // exact: 0 <= P.hi <= 1
     return pair_ff{p, fast_two_sum(t.hi, __fsub_rn(t.lo, v.y))};
 }
 __device__ __forceinline__ float2 p_set(const pair_ff &a) { return make_float2(a.p.hi, a.p.lo); }
@@ -31,18 +31,34 @@ __device__ __forceinline__ void gather_ffb(const float2 *pq, const uint4 &r, int
 // to about 4e-15 afresh and no drift of P + Q can build up along paths: the
 // complementary sum and the renormalisation of the single-scenario path would
 // be thrown away here.
+// one fold step, q v0 + p v1 (all terms non-negative): the two products' rounding
+// errors and every low-part product are gathered in one binary32 sum, then a
+// single renormalisation
+__device__ __forceinline__ ff fold_pq(const pair_ff &x, const ff &v0, const ff &v1) {
+    const float a = __fmul_rn(x.q.hi, v0.hi), b = __fmul_rn(x.p.hi, v1.hi);
+    const float ea = fmaf(x.q.hi, v0.hi, -a), eb = fmaf(x.p.hi, v1.hi, -b);
+    const ff s = two_sum(a, b);
+    float lo = __fadd_rn(s.lo, __fadd_rn(ea, eb));
+    lo = fmaf(x.q.hi, v0.lo, lo);
+    lo = fmaf(x.q.lo, v0.hi, lo);
+    lo = fmaf(x.p.hi, v1.lo, lo);
+    lo = fmaf(x.p.lo, v1.hi, lo);
+    return fast_two_sum(s.hi, lo);
+}
+
 template <int K>
 __device__ __forceinline__ ff ml_p(uint32_t tt, const pair_ff (&x)[4]) {
     ff v[1 << K];
+    // input 0 over a pair of table entries (f(0), f(1)): 0, Q, P, or exactly 1
 #pragma unroll
     for (int m = 0; m < (1 << (K - 1)); m++) {
         const bool a1 = (tt >> (2 * m)) & 1u, b1 = (tt >> (2 * m + 1)) & 1u;
-        v[m] = ff_add(a1 ? x[0].q : ff_make(0.f), b1 ? x[0].p : ff_make(0.f));
+        v[m] = a1 ? (b1 ? ff_make(1.f) : x[0].q) : (b1 ? x[0].p : ff_make(0.f));
     }
 #pragma unroll
     for (int i = 1; i < K; i++) {
 #pragma unroll
-        for (int m = 0; m < (1 << (K - 1 - i)); m++) v[m] = ff_add(ff_mul(x[i].q, v[2 * m]), ff_mul(x[i].p, v[2 * m + 1]));
+        for (int m = 0; m < (1 << (K - 1 - i)); m++) v[m] = fold_pq(x[i], v[2 * m], v[2 * m + 1]);
     }
     return v[0];
 }
@@ -96,6 +112,29 @@ __device__ __forceinline__ float cl_of(const float *cload, const float *dcl, int
     return dcl ? cload[n] + dcl[n * S + s] : cload[n];
 }
 
+
+// Programmatic dependent launch of the level chains: a level kernel lets the
+// next kernel's blocks be scheduled as soon as all of its own blocks have
+// started (they fill the SMs during its tail), and waits for the previous
+// kernel in the stream to complete, with its writes visible, before reading
+// anything but static design structures.  Kernels launched without the
+// attribute are unaffected: the wait returns at once.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <class... KArgs, class... Args>
+inline void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);   // errors surface via cudaGetLastError
+}
 
 inline dim3 bgrid(int64_t S, BatchShape sh, int64_t rows) {
     const int64_t gy = bcdiv(rows > 0 ? rows : 1, sh.by);

@@ -96,11 +96,15 @@ __global__ void k_fwdl_start(const float *__restrict__ sp_in, const float *__res
 __global__ void k_fwdl_level(const uint4 *__restrict__ fanin, float2 *pq, float *tq, int32_t c0, int32_t c1,
                              int64_t ns, int64_t S, OpTable ops) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    pdl_trigger();
     if (s >= S) return;
     const float none[4] = {0.f, 0.f, 0.f, 0.f};
     const int64_t step = (int64_t)gridDim.y * blockDim.y;
-    for (int64_t c = c0 + (int64_t)blockIdx.y * blockDim.y + threadIdx.y; c < c1; c += step) {
-        const uint4 r = fanin[c];
+    const int64_t cf = c0 + (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
+    const uint4 rf = cf < c1 ? fanin[cf] : make_uint4(0, 0, 0, 0);   // static: before the wait
+    pdl_wait();
+    for (int64_t c = cf; c < c1; c += step) {
+        const uint4 r = c == cf ? rf : fanin[c];
         const uint32_t op = r.x >> 24;
         const int k = op_arity(ops, op);
         const uint32_t tt = op_tt(ops, op);
@@ -121,7 +125,9 @@ __global__ void k_bwdl_level(const uint4 *__restrict__ fanin, const int32_t *__r
                              const float *__restrict__ dcl, const float *__restrict__ ks, float2 *gfo2, int32_t c0,
                              int32_t c1, int64_t ns, int64_t S, OpTable ops) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    pdl_trigger();
     if (s >= S) return;
+    pdl_wait();
     const float Ks = ks[s];
     const float dP[4] = {-1.f, 0.f, 0.f, 1.f};
     const float dT[4] = {-0.5f, 0.5f, 0.5f, -0.5f};
@@ -163,7 +169,9 @@ __global__ void k_bwdl_start(const int32_t *__restrict__ fptr, const float *__re
                              const float *__restrict__ dcl, const float *__restrict__ ks,
                              const float2 *__restrict__ gfo2, float *gsp, float *gtr, int64_t ns, int64_t S) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    pdl_trigger();
     if (s >= S) return;
+    pdl_wait();
     const float Ks = ks[s];
     const int64_t step = (int64_t)gridDim.y * blockDim.y;
     for (int64_t k = (int64_t)blockIdx.y * blockDim.y + threadIdx.y; k < ns; k += step) {
@@ -188,7 +196,8 @@ void launch_fwdl(const DevDesign &d, const BatchBufs &b, const OpTable &ops, con
     const dim3 blk((unsigned)sh.bx, (unsigned)sh.by);
     for (int l = 1; l <= d.n_levels; l++) {
         const int32_t c0 = lvl[l - 1], c1 = lvl[l];
-        if (c1 > c0) k_fwdl_level<<<bgrid(S, sh, c1 - c0), blk, 0, s>>>(d.fanin, b.pq, b.tq, c0, c1, d.n_start, S, ops);
+        if (c1 > c0)
+            launch_pdl(k_fwdl_level, bgrid(S, sh, c1 - c0), blk, s, d.fanin, b.pq, b.tq, c0, c1, d.n_start, S, ops);
     }
 }
 
@@ -199,13 +208,12 @@ void launch_bwdl(const DevDesign &d, const BatchBufs &b, const OpTable &ops, con
     for (int l = d.n_levels; l >= 1; l--) {
         const int32_t c0 = lvl[l - 1], c1 = lvl[l];
         if (c1 > c0)
-            k_bwdl_level<<<bgrid(S, sh, c1 - c0), blk, 0, s>>>(d.fanin, d.fout_ptr, (const int4 *)d.edge_fpos, b.pq,
-                                                               b.tq, d.cload, b.dcl, b.ks, b.gfo2, c0, c1, d.n_start,
-                                                               S, ops);
+            launch_pdl(k_bwdl_level, bgrid(S, sh, c1 - c0), blk, s, d.fanin, d.fout_ptr, (const int4 *)d.edge_fpos,
+                       b.pq, b.tq, d.cload, b.dcl, b.ks, b.gfo2, c0, c1, d.n_start, S, ops);
     }
     if (d.n_start)
-        k_bwdl_start<<<bgrid(S, sh, d.n_start), blk, 0, s>>>(d.fout_ptr, d.cload, b.dcl, b.ks, b.gfo2, b.gsp, b.gtr,
-                                                             d.n_start, S);
+        launch_pdl(k_bwdl_start, bgrid(S, sh, d.n_start), blk, s, d.fout_ptr, d.cload, b.dcl, b.ks, b.gfo2, b.gsp,
+                   b.gtr, d.n_start, S);
 }
 
 }  // namespace dp

@@ -46,6 +46,8 @@ struct DevDesign {
     unsigned *bar;             // level-barrier arrival counters of the persistent passes (128-byte lines)
     uint32_t *epoch;           // [4] pass counters: [0] forward (its parity tags the stored pairs)
     const int32_t *chunk_ptr;  // [n_levels+2] level-aligned chunks of 32 (level 0 = startpoints)
+    const int32_t *pair_ptr;   // [n_levels+1] level-aligned cell pairs: pairs of level l are [pair_ptr[l-1], pair_ptr[l])
+    unsigned *simdone;         // [n_cells] pass number of the simulation pass that last wrote the cell's words
     int *err;                  // device error word of the context (bounded wait gave up)
 };
 
@@ -74,9 +76,11 @@ void launch_bwd_start(const DevDesign &d, int grad_mode, int tr_mode, float K, f
 
 // pass counters and the dataflow schedule (kern_flow.cu)
 void launch_bump(uint32_t *counter, cudaStream_t s);
-int flow_grid(int which, int sm_count, int blocks_per_sm);   // which: 0 forward; 0 = unavailable
+int flow_grid(int which, int sm_count, int blocks_per_sm);   // which: 0 forward, 1 simulation; 0 = unavailable
 cudaError_t launch_fwd_flow(const DevDesign &d, const OpTable &ops, int tr_mode, int grid, unsigned sleep_max,
                             cudaStream_t s);
+// simulation levels without barriers (T % 4 == 0), bumps epoch[1] first
+cudaError_t launch_sim_flow(const DevDesign &d, const OpTable &ops, int T, int grid, cudaStream_t s);
 
 // persistent schedule (kern_persist.cu): one cooperative launch per pass
 int persist_grid(int which, int sm_count);   // which: 0 forward, 1 simulation, 2 backward, 3 wide simulation
