@@ -189,7 +189,7 @@ def custom_case(rng, n_in=6, n_cells=40, lib_extra=""):
 
 
 @pytest.mark.parametrize("seed", [1, 2, 3])
-@pytest.mark.parametrize("T", [2, 33, 64, 97])
+@pytest.mark.parametrize("T", [2, 12, 33, 64, 97, 128])
 def test_wide_and_constant_cells_ragged_words(dp, ctx, seed, T):
     rng = np.random.default_rng(seed)
     text, lib = custom_case(rng)
