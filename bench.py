@@ -82,12 +82,12 @@ def batched_algorithmic_bytes(nn: int, ns: int, nc: int, ne: int, S: int) -> int
 # (null).
 TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (one pass), 2M-cell step, 4th step
-    "k_sim_wide": {"bytes": 258_320_000 + 986_920_000, "workload": "roofline",
+    "k_sim_wide": {"bytes": 258_193_152 + 987_000_832, "workload": "roofline",
                    "files": ["kern_persist.cu", "kern_common.cuh"],
-                   "sha": "1f0ddf92a7982993"},
-    "k_bwd_persist": {"bytes": 127_290_000 + 11_950_000, "workload": "roofline",
+                   "sha": "b8d6164d41989cea"},
+    "k_bwd_persist": {"bytes": 127_327_744 + 11_744_768, "workload": "roofline",
                       "files": ["kern_persist.cu", "kern_common.cuh"],
-                      "sha": "1f0ddf92a7982993"},
+                      "sha": "b8d6164d41989cea"},
 }
 
 

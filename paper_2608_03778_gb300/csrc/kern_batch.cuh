@@ -31,21 +31,6 @@ __device__ __forceinline__ void gather_ffb(const float2 *pq, const uint4 &r, int
 // to about 4e-15 afresh and no drift of P + Q can build up along paths: the
 // complementary sum and the renormalisation of the single-scenario path would
 // be thrown away here.
-// one fold step, q v0 + p v1 (all terms non-negative): the two products' rounding
-// errors and every low-part product are gathered in one binary32 sum, then a
-// single renormalisation
-__device__ __forceinline__ ff fold_pq(const pair_ff &x, const ff &v0, const ff &v1) {
-    const float a = __fmul_rn(x.q.hi, v0.hi), b = __fmul_rn(x.p.hi, v1.hi);
-    const float ea = fmaf(x.q.hi, v0.hi, -a), eb = fmaf(x.p.hi, v1.hi, -b);
-    const ff s = two_sum(a, b);
-    float lo = __fadd_rn(s.lo, __fadd_rn(ea, eb));
-    lo = fmaf(x.q.hi, v0.lo, lo);
-    lo = fmaf(x.q.lo, v0.hi, lo);
-    lo = fmaf(x.p.hi, v1.lo, lo);
-    lo = fmaf(x.p.lo, v1.hi, lo);
-    return fast_two_sum(s.hi, lo);
-}
-
 template <int K>
 __device__ __forceinline__ ff ml_p(uint32_t tt, const pair_ff (&x)[4]) {
     ff v[1 << K];

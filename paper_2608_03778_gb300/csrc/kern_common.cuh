@@ -110,23 +110,38 @@ __device__ __forceinline__ pair_ff pair_renorm(const ff &p, const ff &q) {
                    fast_two_sum(q.hi, __fsub_rn(q.lo, __fmul_rn(q.hi, d)))};
 }
 
+// one fold step, q v0 + p v1 (all terms non-negative): the two products' rounding
+// errors and every low-part product are gathered in one binary32 sum, then a
+// single renormalisation
+__device__ __forceinline__ ff fold_pq(const pair_ff &x, const ff &v0, const ff &v1) {
+    const float a = __fmul_rn(x.q.hi, v0.hi), b = __fmul_rn(x.p.hi, v1.hi);
+    const float ea = fmaf(x.q.hi, v0.hi, -a), eb = fmaf(x.p.hi, v1.hi, -b);
+    const ff s = two_sum(a, b);
+    float lo = __fadd_rn(s.lo, __fadd_rn(ea, eb));
+    lo = fmaf(x.q.hi, v0.lo, lo);
+    lo = fmaf(x.q.lo, v0.hi, lo);
+    lo = fmaf(x.p.hi, v1.lo, lo);
+    lo = fmaf(x.p.lo, v1.hi, lo);
+    return fast_two_sum(s.hi, lo);
+}
+
 template <int K>
 __device__ __forceinline__ pair_ff ml_pair(uint32_t tt, const pair_ff (&x)[4]) {
     ff v1[1 << K], v0[1 << K];
-    // first fold: leaves are 0/1, so each term is Q_0, P_0, both or neither
+    // first fold: leaves are 0/1, so each term is 0, Q_0, P_0, or Q_0 + P_0 = 1
 #pragma unroll
     for (int m = 0; m < (1 << (K - 1)); m++) {
         const bool a1 = (tt >> (2 * m)) & 1u, b1 = (tt >> (2 * m + 1)) & 1u;
-        const ff z = ff_make(0.f);
-        v1[m] = ff_add(a1 ? x[0].q : z, b1 ? x[0].p : z);
-        v0[m] = ff_add(a1 ? z : x[0].q, b1 ? z : x[0].p);
+        const ff z = ff_make(0.f), o = ff_make(1.f);
+        v1[m] = a1 ? (b1 ? o : x[0].q) : (b1 ? x[0].p : z);
+        v0[m] = a1 ? (b1 ? z : x[0].p) : (b1 ? x[0].q : o);
     }
 #pragma unroll
     for (int i = 1; i < K; i++) {
 #pragma unroll
         for (int m = 0; m < (1 << (K - 1 - i)); m++) {
-            v1[m] = ff_add(ff_mul(x[i].q, v1[2 * m]), ff_mul(x[i].p, v1[2 * m + 1]));
-            v0[m] = ff_add(ff_mul(x[i].q, v0[2 * m]), ff_mul(x[i].p, v0[2 * m + 1]));
+            v1[m] = fold_pq(x[i], v1[2 * m], v1[2 * m + 1]);
+            v0[m] = fold_pq(x[i], v0[2 * m], v0[2 * m + 1]);
         }
     }
     return pair_renorm(v1[0], v0[0]);
