@@ -58,10 +58,12 @@ def algorithmic_bytes(nn: int, ns: int, nc: int, ne: int, T: int) -> dict:
         "simulation": fanin + 8 * T * nn + 8 * T * nc + 8 * nc,
         # TR_model and toggles read, beta and hybrid TR written, C_load read for the power
         "hybrid": 4 * nn * 5,
-        # fanin + fanout structure, SP, C_load, beta read; adjoint per net written
-        "backward": fanin + fanout + 4 * nn * 3 + 4 * nn,
-        # outputs: grad_cload (TR, beta in, out), grad_pincap (structure, out), grad_tr_in, grad_sp_in
-        "outputs": 12 * nn + fanin + 4 * nc + 8 * ns + 8 * ns,
+        # fanin + fanout structure, SP, C_load, beta read; adjoint per net written; beside it the
+        # gradient outputs into staging: grad_cload (TR, beta in, out), grad_pincap (structure,
+        # out), grad_tr_in (beta, C_load in, out)
+        "backward": fanin + fanout + 4 * nn * 3 + 4 * nn + 12 * nn + fanin + 4 * nc + 12 * ns,
+        # outputs: the four gradient arrays copied into the caller's buffers (read + write)
+        "outputs": 8 * (2 * ns + nc + nn),
     }
 
 

@@ -108,6 +108,9 @@ void free_design(dp_design *D) {
     if (D->cap_stream2) cudaStreamDestroy(D->cap_stream2);
     if (D->fork) cudaEventDestroy(D->fork);
     if (D->join) cudaEventDestroy(D->join);
+    if (D->out_stream) cudaStreamDestroy(D->out_stream);
+    if (D->ev_grads) cudaEventDestroy(D->ev_grads);
+    if (D->ev_copies) cudaEventDestroy(D->ev_copies);
     for (auto &e : D->ev)
         if (e) cudaEventDestroy(e);
     free_batch(D);
@@ -250,6 +253,37 @@ dp_status q_outputs(dp_design *D, const dp_config &c, float *gsp, float *gtr, fl
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_err(D->ctx, e, "gradient copy");
     return check_device_error(D->ctx);
+}
+
+// the step's outputs from its staging buffers (and the startpoint adjoints) into the
+// caller's buffers, and both powers into watts (host); host buffers are complete on
+// return, after one synchronisation
+dp_status q_step_copies(dp_design *D, float *gsp, float *gtr, float *gpin, float *gcl, double *watts,
+                        int on_device) {
+    cudaStream_t s = D->ctx->stream, o = D->out_stream;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    cudaError_t e = cudaSuccess;
+    // the staged gradients go out on the side stream while the backward pass still runs
+    // (the graph records ev_grads when its gradient branch is done); the stream joins
+    // back before anything else is queued on s, so the next step cannot overwrite the
+    // staging buffers under these copies
+    const bool side = (gtr && D->d.n_start) || (gpin && D->d.n_cells) || (gcl && D->d.n_nets);
+    if (side) e = cudaStreamWaitEvent(o, D->ev_grads, 0);
+    if (e == cudaSuccess && gtr && D->d.n_start)
+        e = cudaMemcpyAsync(gtr, D->st_gtr, sizeof(float) * (size_t)D->d.n_start, kind, o);
+    if (e == cudaSuccess && gpin && D->d.n_cells)
+        e = cudaMemcpyAsync(gpin, D->st_gpin, sizeof(float) * (size_t)D->d.n_cells, kind, o);
+    if (e == cudaSuccess && gcl && D->d.n_nets)
+        e = cudaMemcpyAsync(gcl, D->st_gcl, sizeof(float) * (size_t)D->d.n_nets, kind, o);
+    if (e == cudaSuccess && side) e = cudaEventRecord(D->ev_copies, o);
+    if (e == cudaSuccess && gsp && D->d.n_start)
+        e = cudaMemcpyAsync(gsp, D->d.gnet, sizeof(float) * (size_t)D->d.n_start, kind, s);
+    if (e == cudaSuccess && side) e = cudaStreamWaitEvent(s, D->ev_copies, 0);
+    if (e == cudaSuccess && watts) e = cudaMemcpyAsync(watts, D->d.power, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    rec(D, 5, s);   // the outputs phase: these copies (the gradient kernels ran beside the backward pass)
+    if (e != cudaSuccess) return cuda_err(D->ctx, e, "dp_step outputs");
+    if (on_device && !watts) return DP_OK;
+    return check_device_error(D->ctx);   // synchronises the stream
 }
 
 }  // namespace
@@ -446,6 +480,9 @@ dp_status dp_design_upload(dp_ctx *ctx, const dp_compiled *cp, dp_design **out) 
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&D->cap_stream2, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&D->fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&D->join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&D->out_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&D->ev_grads, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&D->ev_copies, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) { s = cuda_err(ctx, e, "upload"); free_design(D); return s; }
@@ -487,10 +524,17 @@ dp_status dp_set_inputs(dp_design *D, const float *sp, const float *tr, int32_t 
     if (n_scen > 1) return dp_set_inputs_batch(D, sp, tr, n_scen, on_device);
     const int64_t ns = D->d.n_start;
     if (ns && (!sp || !tr)) return set_err(c, DP_EINVAL, "NULL input");
-    if (!on_device)
+    if (!on_device) {
+        // a branch-free pass (vectorisable) first; the offending index only on failure
+        int bad = 0;
         for (int64_t k = 0; k < ns; k++)
-            if (!(sp[k] >= 0.f && sp[k] <= 1.f && tr[k] >= 0.f && tr[k] <= 1.f))
-                return set_err(c, DP_EINVAL, "input SP and TR must lie in [0,1] (startpoint " + std::to_string(k) + ")");
+            bad |= !(sp[k] >= 0.f) | !(sp[k] <= 1.f) | !(tr[k] >= 0.f) | !(tr[k] <= 1.f);
+        if (bad)
+            for (int64_t k = 0; k < ns; k++)
+                if (!(sp[k] >= 0.f && sp[k] <= 1.f && tr[k] >= 0.f && tr[k] <= 1.f))
+                    return set_err(c, DP_EINVAL,
+                                   "input SP and TR must lie in [0,1] (startpoint " + std::to_string(k) + ")");
+    }
     DeviceGuard g(c->device);
     cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     cudaError_t e = cudaSuccess;
@@ -683,6 +727,7 @@ dp_status dp_step(dp_design *D, const dp_config *cfg, float *gsp, float *gtr, fl
     if (cfg->tr_mode == 2) return set_err(D->ctx, DP_EUNSUPPORTED, "the lag-one mode runs on batched inputs");
     DeviceGuard g(D->ctx->device);
     if ((s = ensure_words(D, cfg->sim_words)) != DP_OK) return s;
+    if ((s = ensure_stage(D)) != DP_OK) return s;
     cudaStream_t st = D->ctx->stream;
     if (!D->graph || std::memcmp(&D->graph_cfg, cfg, sizeof *cfg) != 0) {
         if (D->graph) { cudaGraphExecDestroy(D->graph); D->graph = nullptr; }
@@ -706,7 +751,16 @@ dp_status dp_step(dp_design *D, const dp_config *cfg, float *gsp, float *gtr, fl
         cudaEventRecordWithFlags(D->ev[2], cs, cudaEventRecordExternal);
         if (le == cudaSuccess) le = q_hybrid(D, *cfg, cs);
         cudaEventRecordWithFlags(D->ev[3], cs, cudaEventRecordExternal);
+        // the cap and TR gradients need only the hybrid activities: a second branch
+        // writes them to the staging buffers beside the (latency-bound) backward pass
+        cudaEventRecord(D->fork, cs);
+        cudaStreamWaitEvent(D->cap_stream2, D->fork, 0);
+        dp::launch_cap_grads(D->d, D->ops, cfg->grad_mode != 0, cfg->tr_mode, power_K(*cfg), D->st_gcl, D->st_gpin,
+                             D->st_gtr, D->cap_stream2);
+        cudaEventRecordWithFlags(D->ev_grads, D->cap_stream2, cudaEventRecordExternal);
+        cudaEventRecord(D->join, D->cap_stream2);
         if (le == cudaSuccess) le = q_backward(D, *cfg, nullptr, cs);
+        cudaStreamWaitEvent(cs, D->join, 0);
         cudaEventRecordWithFlags(D->ev[4], cs, cudaEventRecordExternal);
         e = cudaStreamEndCapture(cs, &graph);
         if (e == cudaSuccess && le != cudaSuccess) e = le;
@@ -735,18 +789,8 @@ dp_status dp_step(dp_design *D, const dp_config *cfg, float *gsp, float *gtr, fl
     D->sim_valid = true;
     D->bwd_valid = true;
     D->bwd_grad_mode = cfg->grad_mode;
-    s = q_outputs(D, *cfg, gsp, gtr, gpin, gcl, on_device, false);
-    rec(D, 5, st);
-    D->step_kernels = D->graph_kernels + (gcl && D->d.n_nets ? 1 : 0) + (gpin && D->d.n_cells ? 1 : 0) +
-                      (gtr && D->d.n_start ? 1 : 0);
-    if (s != DP_OK) return s;
-    if (watts) {
-        e = cudaMemcpyAsync(watts, D->d.power, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) return cuda_err(D->ctx, e, "dp_step power");
-        return check_device_error(D->ctx);
-    }
-    return DP_OK;
+    D->step_kernels = D->graph_kernels;
+    return q_step_copies(D, gsp, gtr, gpin, gcl, watts, on_device);
 }
 
 dp_status dp_sizing_scores(dp_design *D, const dp_config *cfg, int32_t mode, float *scores, int32_t k,

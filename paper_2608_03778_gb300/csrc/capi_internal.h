@@ -75,6 +75,10 @@ struct dp_design {
     dp_config graph_cfg{};
     cudaStream_t cap_stream = nullptr, cap_stream2 = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
+    // the step's output copies: a side stream that starts them when the gradient branch of
+    // the step graph is done (ev_grads, recorded by the graph), and their completion
+    cudaStream_t out_stream = nullptr;
+    cudaEvent_t ev_grads = nullptr, ev_copies = nullptr;
     int grid[4] = {0, 0, 0, 0};   // persistent grids: forward, simulation, backward, wide simulation
     int flow_grid[2] = {0, 0};     // dataflow grids: forward, simulation
     // launch-shape tuning (defaults, overridable by DP_FLOW_BLOCKS / DP_FLOW_SLEEP for sweeps)
