@@ -83,6 +83,18 @@ __global__ void k_delta_clear_cells(const int32_t *__restrict__ cell, const int3
     dpin[at] = 0.f;
 }
 
+// every scenario column of a batch gets the reference inputs' forward state:
+// the float-float P of every net and the input TR of every startpoint
+__global__ void k_bcast_ref(const float2 *__restrict__ ref_pq, const float *__restrict__ ref_tr, float2 *pq,
+                            float *tr_in, int64_t nn, int64_t ns, int64_t S) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    for (int64_t n = blockIdx.y; n < nn; n += gridDim.y) {
+        pq[n * S + s] = ref_pq[n];
+        if (n < ns) tr_in[n * S + s] = ref_tr[n];
+    }
+}
+
 }  // namespace
 
 void launch_sizing_deltas(const DevDesign &d, const OpTable &ops, const SizingDeltas &z, int64_t ne, int64_t S,
@@ -103,6 +115,14 @@ void launch_sizing_clear(const DevDesign &d, const SizingDeltas &z, int64_t ne, 
     k_delta_clear_nets<<<(unsigned)cdiv(cap, 256), 256, 0, s>>>(z.list, z.count, z.flag, dcl, cap);
     k_delta_clear_cells<<<(unsigned)cdiv(ne, 256), 256, 0, s>>>(z.cell, z.scen, d.cell_of_user, z.win, z.dpin, ne,
                                                                 S);
+}
+
+void launch_bcast_ref(const float2 *ref_pq, const float *ref_tr, float2 *pq, float *tr_in, int64_t nn, int64_t ns,
+                      int64_t S, cudaStream_t s) {
+    if (nn <= 0 || S <= 0) return;
+    const unsigned bx = S >= 128 ? 128u : 32u;
+    k_bcast_ref<<<dim3((unsigned)cdiv(S, bx), (unsigned)(nn < 8192 ? nn : 8192)), bx, 0, s>>>(ref_pq, ref_tr, pq,
+                                                                                              tr_in, nn, ns, S);
 }
 
 }  // namespace dp

@@ -150,6 +150,10 @@ struct SizingDeltas {
 void launch_sizing_deltas(const DevDesign &d, const OpTable &ops, const SizingDeltas &z, int64_t ne, int64_t S,
                           float *dcl, cudaStream_t s);
 // returns win, dpin, flag and dcl to rest after the batch
+// the reference inputs' forward state (P of every net, TR of every startpoint) into every
+// scenario column of a batch: a batch of requests on the reference inputs skips the forward pass
+void launch_bcast_ref(const float2 *ref_pq, const float *ref_tr, float2 *pq, float *tr_in, int64_t nn, int64_t ns,
+                      int64_t S, cudaStream_t s);
 void launch_sizing_clear(const DevDesign &d, const SizingDeltas &z, int64_t ne, int64_t S, float *dcl,
                          cudaStream_t s);
 // out[c][r] = in[r][c] (row-major R x C in, C x R out)

@@ -13,7 +13,12 @@
 //
 // A request carries either new startpoint SP/TR or the design's reference
 // inputs, and optionally a sizing delta (new input pin caps of some cells,
-// relative to the design's own caps).  The delta enters the batch as a
+// relative to the design's own caps).  A batch holds requests of one kind.
+// Caps do not enter SP or TR, so a batch on the reference inputs skips the
+// forward pass: the forward state of the reference inputs, computed once when
+// the design is added, is copied into every scenario column, and only the
+// power and the reverse pass run (the columns are the ones the forward pass
+// would write, bit for bit).  The delta enters the batch as a
 // per-scenario change of C_load on the nets those cells load, so requests with
 // different deltas share a batch.  Every (cell, scenario) is computed alone,
 // the power sums of a scenario run in a fixed order, and the launch shapes are
@@ -60,6 +65,7 @@ struct Slot {
     dp_design *D = nullptr;
     int64_t ns = 0, nc = 0, nn = 0;
     float *d_ref_sp = nullptr, *d_ref_tr = nullptr;   // [ns]
+    float2 *d_ref_pq = nullptr;                        // [nn] float-float P of the reference inputs
     float *d_in_sp = nullptr, *d_in_tr = nullptr;     // [max_batch][ns] request-major inputs
     float *d_dcl = nullptr;                            // [nn * max_batch], zero between batches
     // sizing-delta entries of a batch (capacity delta_cap) and the device work arrays
@@ -75,12 +81,13 @@ struct Slot {
     double *h_power = nullptr;                         // [max_batch], pinned
     float *d_out_sp = nullptr, *d_out_tr = nullptr, *d_out_pin = nullptr;   // [max_batch][rows]
     cudaEvent_t done = nullptr;
-    std::vector<std::array<cudaGraphExec_t, 2>> graphs;   // [log2 batch size][with reverse pass]
+    std::vector<std::array<cudaGraphExec_t, 4>> graphs;   // [log2 batch size][reverse pass + 2 reference inputs]
     std::vector<void *> dev, pinned;
     size_t bytes = 0;
     std::deque<Req *> queue;
     std::vector<Req *> inflight;
     bool busy = false;
+    bool batch_ref = false;   // the batch in flight is on the reference inputs
 };
 
 }  // namespace
@@ -201,11 +208,12 @@ int bucket_index(int64_t Sg) {
     return i;
 }
 
-// Captures the fixed part of a batch of Sg scenarios: inputs to scenario-innermost,
-// forward, power (copied to the pinned power buffer) and, with grad, the reverse
+// Captures the fixed part of a batch of Sg scenarios: inputs to scenario-innermost
+// and the forward pass (or, on the reference inputs, their forward state copied into
+// every column), power (copied to the pinned power buffer) and, with grad, the reverse
 // pass and the outputs back to request-major.  The per-scenario C_load delta is
 // always bound: where no request changed a cap it is zero, and C + 0 = C exactly.
-cudaError_t capture_batch_graph(dp_server *srv, Slot *sl, int64_t Sg, bool grad, cudaGraphExec_t *out) {
+cudaError_t capture_batch_graph(dp_server *srv, Slot *sl, int64_t Sg, bool grad, bool ref, cudaGraphExec_t *out) {
     dp_design *D = sl->D;
     dp_batch &B = D->batch;
     const dp_config &c = srv->cfg.analysis;
@@ -217,9 +225,13 @@ cudaError_t capture_batch_graph(dp_server *srv, Slot *sl, int64_t Sg, bool grad,
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
-    dp::launch_transpose(sl->d_in_sp, B.b.sp_in, Sg, ns, st);
-    dp::launch_transpose(sl->d_in_tr, B.b.tr_in, Sg, ns, st);
-    dp::launch_fwdb(D->d, B.b, D->ops, D->lvl_ptr.data(), c.tr_mode, B.fwd_shape, st);
+    if (ref) {
+        dp::launch_bcast_ref(sl->d_ref_pq, sl->d_ref_tr, B.b.pq, B.b.tr_in, sl->nn, ns, Sg, st);
+    } else {
+        dp::launch_transpose(sl->d_in_sp, B.b.sp_in, Sg, ns, st);
+        dp::launch_transpose(sl->d_in_tr, B.b.tr_in, Sg, ns, st);
+        dp::launch_fwdb(D->d, B.b, D->ops, D->lvl_ptr.data(), c.tr_mode, B.fwd_shape, st);
+    }
     dp::launch_powerb(D->d, B.b, c.tr_mode, power_K(c), st);
     if (grad) {
         dp::launch_seedb(B.b, power_K(c), nullptr, st);
@@ -237,13 +249,14 @@ cudaError_t capture_batch_graph(dp_server *srv, Slot *sl, int64_t Sg, bool grad,
     return e;
 }
 
-// Captures every batch graph of a design (two per batch size: with and without the reverse pass).
+// Captures every batch graph of a design (four per batch size: with and without the
+// reverse pass, on new or on the reference inputs).
 cudaError_t capture_all(dp_server *srv, Slot *sl) {
     const int64_t m = srv->cfg.max_batch;
     for (int64_t Sg = 1;; Sg = Sg * 2 < m ? Sg * 2 : m) {
         const int i = bucket_index(Sg);
-        for (int grad = 0; grad < 2; grad++) {
-            cudaError_t e = capture_batch_graph(srv, sl, Sg, grad != 0, &sl->graphs[(size_t)i][(size_t)grad]);
+        for (int v = 0; v < 4; v++) {
+            cudaError_t e = capture_batch_graph(srv, sl, Sg, (v & 1) != 0, (v & 2) != 0, &sl->graphs[(size_t)i][(size_t)v]);
             if (e != cudaSuccess) return e;
         }
         if (Sg == m) break;
@@ -266,17 +279,13 @@ cudaError_t launch_batch(dp_server *srv, Slot *sl) {
         grad = grad || q->r.want_grad;
         nd += q->r.n_delta;
     }
-    for (int64_t s = 0; s < S && e == cudaSuccess; s++) {
+    for (int64_t s = 0; s < S && e == cudaSuccess && !sl->batch_ref; s++) {   // a batch of new inputs
         const Req *q = sl->inflight[(size_t)s];
-        const bool own = q->r.sp != nullptr;
         if (ns) {
-            e = cudaMemcpyAsync(sl->d_in_sp + s * ns, own ? (const void *)q->r.sp : (const void *)sl->d_ref_sp,
-                                sizeof(float) * (size_t)ns, own ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
-                                st);
+            e = cudaMemcpyAsync(sl->d_in_sp + s * ns, q->r.sp, sizeof(float) * (size_t)ns, cudaMemcpyHostToDevice, st);
             if (e == cudaSuccess)
-                e = cudaMemcpyAsync(sl->d_in_tr + s * ns, own ? (const void *)q->r.tr : (const void *)sl->d_ref_tr,
-                                    sizeof(float) * (size_t)ns,
-                                    own ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st);
+                e = cudaMemcpyAsync(sl->d_in_tr + s * ns, q->r.tr, sizeof(float) * (size_t)ns,
+                                    cudaMemcpyHostToDevice, st);
         }
     }
     if (e != cudaSuccess) return e;
@@ -304,7 +313,7 @@ cudaError_t launch_batch(dp_server *srv, Slot *sl) {
         if (e != cudaSuccess) return e;
         dp::launch_sizing_deltas(sl->D->d, sl->D->ops, deltas_view(sl), nd, Sg, sl->d_dcl, st);
     }
-    e = cudaGraphLaunch(sl->graphs[(size_t)bucket_index(Sg)][grad ? 1 : 0], st);
+    e = cudaGraphLaunch(sl->graphs[(size_t)bucket_index(Sg)][(grad ? 1 : 0) + (sl->batch_ref ? 2 : 0)], st);
     if (e != cudaSuccess) return e;
     if (grad)
         for (int64_t s = 0; s < S && e == cudaSuccess; s++) {
@@ -345,16 +354,23 @@ void complete_batch(dp_server *srv, Slot *sl, dp_status status) {
     srv->cv_done.notify_all();
 }
 
-// Takes the next batch of a free slot (lock held).
+// Takes the next batch of a free slot (lock held): the oldest waiting request and,
+// in arrival order, up to max_batch - 1 more of its kind (new or reference inputs).
 bool take_batch(dp_server *srv, Slot *sl) {
     if (sl->busy || sl->queue.empty()) return false;
     const size_t m = (size_t)srv->cfg.max_batch;
-    while (!sl->queue.empty() && sl->inflight.size() < m) {
-        Req *q = sl->queue.front();
-        sl->queue.pop_front();
+    const bool ref = sl->queue.front()->r.sp == nullptr;
+    for (auto it = sl->queue.begin(); it != sl->queue.end() && sl->inflight.size() < m;) {
+        Req *q = *it;
+        if ((q->r.sp == nullptr) != ref) {
+            ++it;
+            continue;
+        }
+        it = sl->queue.erase(it);
         q->state = 1;
         sl->inflight.push_back(q);
     }
+    sl->batch_ref = ref;
     sl->busy = true;
     return true;
 }
@@ -528,7 +544,7 @@ dp_status dp_server_add_design(dp_server *srv, const char *netlist, size_t netli
     const int64_t ns = cp->n_start, nc = cp->n_cells, nn = cp->n_nets, ne = cp->n_edges;
     const int64_t S = srv->cfg.max_batch;
     // device bytes: resident netlist (about 24 B per net, 40 per cell, 8 per edge) and batch buffers
-    const double need = 24.0 * nn + 40.0 * nc + 8.0 * ne + 64.0 * nn +
+    const double need = 24.0 * nn + 40.0 * nc + 8.0 * ne + 72.0 * nn +
                         (double)S * (8.0 * nn + 4.0 * ne + 16.0 * ns + 4.0 * nn + 4.0 * std::max(nn, nc) +
                                      4.0 * (2 * ns + nc) + 8.0 * ns + 8.0 * dp::kBatchPowerChunks + 8.0 * nc +
                                      4.0 * nn);
@@ -636,8 +652,26 @@ dp_status dp_server_add_design(dp_server *srv, const char *netlist, size_t netli
         free_slot(sl);
         return st;
     }
-    sl->graphs.assign((size_t)bucket_index(S) + 1, std::array<cudaGraphExec_t, 2>{nullptr, nullptr});
-    e = capture_all(srv, sl);
+    // the forward state of the reference inputs, for batches that use them: one column
+    e = dmalloc(sl, &sl->d_ref_pq, (size_t)nn);
+    if (e == cudaSuccess) {
+        dp_batch &B = D->batch;
+        B.S = 1;
+        B.b.S = 1;
+        if (ns) e = cudaMemcpyAsync(B.b.sp_in, sl->d_ref_sp, sizeof(float) * (size_t)ns, cudaMemcpyDeviceToDevice, sl->stream);
+        if (e == cudaSuccess && ns)
+            e = cudaMemcpyAsync(B.b.tr_in, sl->d_ref_tr, sizeof(float) * (size_t)ns, cudaMemcpyDeviceToDevice, sl->stream);
+        if (e == cudaSuccess) {
+            dp::launch_fwdb(D->d, B.b, D->ops, D->lvl_ptr.data(), srv->cfg.analysis.tr_mode, B.fwd_shape, sl->stream);
+            e = cudaMemcpyAsync(sl->d_ref_pq, B.b.pq, sizeof(float2) * (size_t)nn, cudaMemcpyDeviceToDevice, sl->stream);
+        }
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(sl->stream);
+    }
+    if (e == cudaSuccess) {
+        sl->graphs.assign((size_t)bucket_index(S) + 1, std::array<cudaGraphExec_t, 4>{nullptr, nullptr, nullptr, nullptr});
+        e = capture_all(srv, sl);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(sl->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -677,6 +711,7 @@ dp_status dp_server_submit(dp_server *srv, const dp_request *r, uint64_t *ticket
         srv->reqs[q->ticket] = q;
         sl->inflight.push_back(q);
         q->state = 1;
+        sl->batch_ref = r->sp == nullptr;
         sl->busy = true;
         lk.unlock();
         DeviceGuard g(srv->cfg.device);

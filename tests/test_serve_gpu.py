@@ -148,6 +148,30 @@ def test_alone_equals_in_mix(dp, server):
             np.testing.assert_array_equal(x, y)
 
 
+def test_reference_batches_skip_the_forward_with_the_same_bits(dp, server):
+    """Requests on the reference inputs run as their own batches, from the forward state
+    cached when the design was added; the same requests with the reference inputs given
+    explicitly run the forward pass.  Both give the same bits (sizing deltas and gradients
+    included)."""
+    srv, ids, infos, refs = server
+    rng = np.random.default_rng(31)
+    implicit, explicit = [], []
+    for i in range(12):
+        k = i % len(ids)
+        ns, nc = infos[k].n_start, infos[k].n_cells
+        m = max(1, nc // 50)
+        cells = rng.choice(nc, m, replace=False).astype(np.int32)
+        caps = rng.choice(np.array([1.6, 3.2], np.float32), m)
+        implicit.append(Job(dp, ids[k], ns, nc, cells=cells, caps=caps, grad=1))
+        explicit.append(Job(dp, ids[k], ns, nc, refs[k][0], refs[k][1], cells=cells, caps=caps, grad=1))
+    before = dp.dp_server_get_stats(srv).batches
+    run(dp, srv, [x for pair in zip(implicit, explicit) for x in pair])   # interleaved kinds
+    assert dp.dp_server_get_stats(srv).batches > before
+    for a, b in zip(implicit, explicit):
+        for x, y in zip(a.result(), b.result()):
+            np.testing.assert_array_equal(x, y)
+
+
 def test_plain_mode_gives_the_same_bits(dp, server, texts):
     srv, ids, infos, refs = server
     jobs = make_jobs(dp, ids, infos, 12, 21, refs)
