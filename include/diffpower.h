@@ -365,10 +365,14 @@ dp_status dp_power_noalloc(int device, const float *tr, const float *beta, const
 /* ------------------------------ request server ------------------------------
  * Several designs resident on one GPU; power and gradient requests of any of
  * them are served by continuous batching: a worker thread takes the requests
- * waiting for a design whose batch slot is free (up to max_batch, in arrival
- * order) and runs them as the scenarios of one batched pass on that design's
- * own stream, so batches of different designs overlap on the device and
- * requests that arrive meanwhile join the design's next batch.  A request's
+ * waiting for a design whose batch slot is free (the oldest one and up to
+ * max_batch - 1 more of its kind - new inputs or the reference inputs - in
+ * arrival order) and runs them as the scenarios of one batched pass on that
+ * design's own stream, so batches of different designs overlap on the device
+ * and requests that arrive meanwhile join the design's next batch.  A batch on
+ * the reference inputs (sizing deltas) skips the forward pass: caps do not
+ * enter SP or TR, so it starts from the reference inputs' forward state,
+ * computed once by dp_server_add_design.  A request's
  * results do not depend on the requests it shares a batch with: they are
  * bitwise the same alone and in any mix.  Model power and model gradient
  * (Eq. 1, Eq. 2, Eq. 7); no simulation. */
@@ -417,7 +421,7 @@ void dp_server_destroy(dp_server *srv);
 const char *dp_server_last_error(const dp_server *srv);
 /* Compiles and uploads a design, reserves its batch buffers for max_batch
  * requests, tunes its launch shapes once (on max_batch copies of the reference
- * inputs) and keeps them.  ref_sp / ref_tr (n_start each, may be NULL: 0.5 and
+ * inputs) and keeps them, and computes the reference inputs' forward state.  ref_sp / ref_tr (n_start each, may be NULL: 0.5 and
  * 0.25) are the inputs of requests that give none.  Admission: DP_ENOMEM when
  * the design would exceed the HBM budget. */
 dp_status dp_server_add_design(dp_server *srv, const char *netlist, size_t netlist_len, const char *library,
