@@ -365,14 +365,13 @@ dp_status dp_power_noalloc(int device, const float *tr, const float *beta, const
 /* ------------------------------ request server ------------------------------
  * Several designs resident on one GPU; power and gradient requests of any of
  * them are served by continuous batching: a worker thread takes the requests
- * waiting for a design whose batch slot is free (the oldest one and up to
- * max_batch - 1 more of its kind - new inputs or the reference inputs - in
- * arrival order) and runs them as the scenarios of one batched pass on that
- * design's own stream, so batches of different designs overlap on the device
- * and requests that arrive meanwhile join the design's next batch.  A batch on
- * the reference inputs (sizing deltas) skips the forward pass: caps do not
- * enter SP or TR, so it starts from the reference inputs' forward state,
- * computed once by dp_server_add_design.  A request's
+ * waiting for a design whose batch slot is free (up to max_batch, in arrival
+ * order) and runs them as the scenarios of one batched pass on that design's
+ * own stream, so batches of different designs overlap on the device and
+ * requests that arrive meanwhile join the design's next batch.  A batch whose
+ * requests all use the reference inputs (sizing deltas) skips the forward
+ * pass: caps do not enter SP or TR, so it starts from the reference inputs'
+ * forward state, computed once by dp_server_add_design.  A request's
  * results do not depend on the requests it shares a batch with: they are
  * bitwise the same alone and in any mix.  Model power and model gradient
  * (Eq. 1, Eq. 2, Eq. 7); no simulation. */

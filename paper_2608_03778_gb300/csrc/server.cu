@@ -13,12 +13,12 @@
 //
 // A request carries either new startpoint SP/TR or the design's reference
 // inputs, and optionally a sizing delta (new input pin caps of some cells,
-// relative to the design's own caps).  A batch holds requests of one kind.
-// Caps do not enter SP or TR, so a batch on the reference inputs skips the
-// forward pass: the forward state of the reference inputs, computed once when
-// the design is added, is copied into every scenario column, and only the
-// power and the reverse pass run (the columns are the ones the forward pass
-// would write, bit for bit).  The delta enters the batch as a
+// relative to the design's own caps).  Caps do not enter SP or TR, so a batch
+// whose requests all use the reference inputs (sizing deltas) skips the forward
+// pass: the forward state of the reference inputs, computed once when the
+// design is added, is copied into every scenario column, and only the power and
+// the reverse pass run (the columns are the ones the forward pass would write,
+// bit for bit).  The delta enters the batch as a
 // per-scenario change of C_load on the nets those cells load, so requests with
 // different deltas share a batch.  Every (cell, scenario) is computed alone,
 // the power sums of a scenario run in a fixed order, and the launch shapes are
@@ -87,7 +87,7 @@ struct Slot {
     std::deque<Req *> queue;
     std::vector<Req *> inflight;
     bool busy = false;
-    bool batch_ref = false;   // the batch in flight is on the reference inputs
+    bool batch_ref = false;   // every request of the batch in flight is on the reference inputs
 };
 
 }  // namespace
@@ -279,13 +279,17 @@ cudaError_t launch_batch(dp_server *srv, Slot *sl) {
         grad = grad || q->r.want_grad;
         nd += q->r.n_delta;
     }
-    for (int64_t s = 0; s < S && e == cudaSuccess && !sl->batch_ref; s++) {   // a batch of new inputs
+    for (int64_t s = 0; s < S && e == cudaSuccess && !sl->batch_ref; s++) {   // the batch runs the forward pass
         const Req *q = sl->inflight[(size_t)s];
+        const bool own = q->r.sp != nullptr;
         if (ns) {
-            e = cudaMemcpyAsync(sl->d_in_sp + s * ns, q->r.sp, sizeof(float) * (size_t)ns, cudaMemcpyHostToDevice, st);
+            e = cudaMemcpyAsync(sl->d_in_sp + s * ns, own ? (const void *)q->r.sp : (const void *)sl->d_ref_sp,
+                                sizeof(float) * (size_t)ns, own ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                                st);
             if (e == cudaSuccess)
-                e = cudaMemcpyAsync(sl->d_in_tr + s * ns, q->r.tr, sizeof(float) * (size_t)ns,
-                                    cudaMemcpyHostToDevice, st);
+                e = cudaMemcpyAsync(sl->d_in_tr + s * ns, own ? (const void *)q->r.tr : (const void *)sl->d_ref_tr,
+                                    sizeof(float) * (size_t)ns,
+                                    own ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st);
         }
     }
     if (e != cudaSuccess) return e;
@@ -354,20 +358,17 @@ void complete_batch(dp_server *srv, Slot *sl, dp_status status) {
     srv->cv_done.notify_all();
 }
 
-// Takes the next batch of a free slot (lock held): the oldest waiting request and,
-// in arrival order, up to max_batch - 1 more of its kind (new or reference inputs).
+// Takes the next batch of a free slot (lock held): up to max_batch waiting requests in
+// arrival order.
 bool take_batch(dp_server *srv, Slot *sl) {
     if (sl->busy || sl->queue.empty()) return false;
     const size_t m = (size_t)srv->cfg.max_batch;
-    const bool ref = sl->queue.front()->r.sp == nullptr;
-    for (auto it = sl->queue.begin(); it != sl->queue.end() && sl->inflight.size() < m;) {
-        Req *q = *it;
-        if ((q->r.sp == nullptr) != ref) {
-            ++it;
-            continue;
-        }
-        it = sl->queue.erase(it);
+    bool ref = true;
+    while (!sl->queue.empty() && sl->inflight.size() < m) {
+        Req *q = sl->queue.front();
+        sl->queue.pop_front();
         q->state = 1;
+        ref = ref && q->r.sp == nullptr;
         sl->inflight.push_back(q);
     }
     sl->batch_ref = ref;
