@@ -84,12 +84,12 @@ def batched_algorithmic_bytes(nn: int, ns: int, nc: int, ne: int, S: int) -> int
 # (null).
 TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (one pass), 2M-cell step, 4th step
-    "k_sim_wide": {"bytes": 258_193_152 + 987_000_832, "workload": "roofline",
+    "k_sim_wide": {"bytes": 258_525_696 + 987_099_136, "workload": "roofline",
                    "files": ["kern_persist.cu", "kern_common.cuh"],
-                   "sha": "b8d6164d41989cea"},
-    "k_bwd_persist": {"bytes": 127_327_744 + 11_744_768, "workload": "roofline",
+                   "sha": "4d74eb6225d0a7a1"},
+    "k_bwd_persist": {"bytes": 127_273_472 + 11_897_344, "workload": "roofline",
                       "files": ["kern_persist.cu", "kern_common.cuh"],
-                      "sha": "b8d6164d41989cea"},
+                      "sha": "4d74eb6225d0a7a1"},
 }
 
 

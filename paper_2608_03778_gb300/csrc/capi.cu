@@ -169,15 +169,19 @@ bool dataflow(const dp_design *D, const dp_config &c, int which) {
 }
 
 // each q_* returns the first launch error (a cooperative launch reports it directly)
-cudaError_t q_forward(dp_design *D, const dp_config &c, cudaStream_t s) {
+// The forward pass and the model power.  ready (may be null) is recorded on s just before
+// the first forward kernel: a branch forked there becomes ready with that kernel.
+cudaError_t q_forward(dp_design *D, const dp_config &c, cudaStream_t s, cudaEvent_t ready = nullptr) {
     dp::launch_bump(D->d.epoch, s);   // new parity for the stored (P, Q) pairs
     if (dataflow(D, c, 0)) {
+        if (ready) cudaEventRecord(ready, s);
         cudaError_t e = dp::launch_fwd_flow(D->d, D->ops, c.tr_mode, D->flow_grid[0], D->flow_sleep, s);
         if (e != cudaSuccess) return e;
     } else if (persistent(D, c, 0)) {
-        cudaError_t e = dp::launch_fwd_persist(D->d, D->ops, c.tr_mode, D->grid[0], s);
+        cudaError_t e = dp::launch_fwd_persist(D->d, D->ops, c.tr_mode, D->grid[0], s, ready);
         if (e != cudaSuccess) return e;
     } else {
+        if (ready) cudaEventRecord(ready, s);
         dp::launch_init_start(D->d, c.tr_mode, s);
         for (int l = 1; l <= D->d.n_levels; l++)
             dp::launch_fwd_level(D->d, D->ops, D->lvl_ptr[l - 1], D->lvl_ptr[l], s);
@@ -738,12 +742,14 @@ dp_status dp_step(dp_design *D, const dp_config *cfg, float *gsp, float *gtr, fl
         // external event records become timing nodes of the graph (a plain record
         // inside a capture only expresses a dependency).  The startpoint generator
         // (ALU-bound) runs on a second branch, concurrently with the forward pass
-        // (latency-bound); the simulation levels wait for both.
+        // (latency-bound); the simulation levels wait for both.  The branch forks right
+        // before the forward kernel, so that the two become ready together: forked
+        // earlier, the generator's blocks fill the SMs first when the GPU is idle at the
+        // launch, and the cooperative forward kernel waits for room.
         cudaEventRecordWithFlags(D->ev[0], cs, cudaEventRecordExternal);
-        cudaEventRecord(D->fork, cs);
-        cudaStreamWaitEvent(D->cap_stream2, D->fork, 0);
-        cudaError_t le = q_forward(D, *cfg, cs);
+        cudaError_t le = q_forward(D, *cfg, cs, D->fork);
         cudaEventRecordWithFlags(D->ev[1], cs, cudaEventRecordExternal);
+        cudaStreamWaitEvent(D->cap_stream2, D->fork, 0);
         q_sim_start(D, *cfg, D->cap_stream2);
         cudaEventRecord(D->join, D->cap_stream2);
         cudaStreamWaitEvent(cs, D->join, 0);

@@ -404,9 +404,11 @@ int persist_grid(int which, int sm_count) {
 
 size_t persist_bar_words(int n_levels) { return 3 * 32 * ((size_t)n_levels + 2); }
 
-cudaError_t launch_fwd_persist(const DevDesign &d, const OpTable &ops, int tr_mode, int grid, cudaStream_t s) {
+cudaError_t launch_fwd_persist(const DevDesign &d, const OpTable &ops, int tr_mode, int grid, cudaStream_t s,
+                               cudaEvent_t ready) {
     unsigned *bar = d.bar;
     cudaMemsetAsync(bar, 0, bar_bytes(d), s);
+    if (ready) cudaEventRecord(ready, s);   // work forked here becomes ready together with the kernel
     return launch_coop(k_fwd_persist, grid, kPersistThreads, s, d.fanin, d.pq, d.tr, (const float *)d.sp_in,
                        (const float *)d.tr_in, d.lvl, d.n_levels, d.n_start, tr_mode, ops, bar, d.err,
                        kWaitLimitCycles, (const uint32_t *)d.epoch);

@@ -87,7 +87,10 @@ int persist_grid(int which, int sm_count);   // which: 0 forward, 1 simulation, 
 bool wide_ok(int T);                         // the wide simulation handles this word count
 cudaError_t launch_sim_wide(const DevDesign &d, const OpTable &ops, int T, int grid, cudaStream_t s);
 size_t persist_bar_words(int n_levels);      // counters needed by the three passes
-cudaError_t launch_fwd_persist(const DevDesign &d, const OpTable &ops, int tr_mode, int grid, cudaStream_t s);
+// ready (may be null) is recorded on s just before the kernel: a branch forked there becomes
+// ready with it rather than ahead of it
+cudaError_t launch_fwd_persist(const DevDesign &d, const OpTable &ops, int tr_mode, int grid, cudaStream_t s,
+                               cudaEvent_t ready = nullptr);
 cudaError_t launch_sim_persist(const DevDesign &d, const OpTable &ops, int T, int grid, cudaStream_t s);
 cudaError_t launch_bwd_persist(const DevDesign &d, const OpTable &ops, int grad_mode, int tr_mode, float K,
                                float *out_gsp, int grid, cudaStream_t s);
