@@ -84,12 +84,12 @@ def batched_algorithmic_bytes(nn: int, ns: int, nc: int, ne: int, S: int) -> int
 # (null).
 TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (one pass), 2M-cell step, 4th step
-    "k_sim_wide": {"bytes": 258_525_696 + 987_099_136, "workload": "roofline",
+    "k_sim_wide": {"bytes": 257_115_136 + 985_070_336, "workload": "roofline",
                    "files": ["kern_persist.cu", "kern_common.cuh"],
-                   "sha": "4d74eb6225d0a7a1"},
-    "k_bwd_persist": {"bytes": 127_273_472 + 11_897_344, "workload": "roofline",
+                   "sha": "2eee32781a24a2e0"},
+    "k_bwd_persist": {"bytes": 127_266_048 + 11_657_984, "workload": "roofline",
                       "files": ["kern_persist.cu", "kern_common.cuh"],
-                      "sha": "4d74eb6225d0a7a1"},
+                      "sha": "2eee32781a24a2e0"},
 }
 
 

@@ -7,7 +7,8 @@
 // Data written by other blocks during the launch is read through L2
 // (ld.global.cg); the barrier's release/acquire pair orders it.  Static data
 // of the next level (fanin records, fanout ranges, forward results) is loaded
-// before a block waits at the barrier, so the wait hides its latency.
+// between a block's arrival at the barrier and its wait, so the wait hides its
+// latency.
 #include "kern_common.cuh"
 
 namespace dp {
@@ -24,18 +25,25 @@ __device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned *p) {
     return v;
 }
 
-// Level barrier over all blocks of the grid.  Each barrier of a launch has
-// its own arrival counter (own 128-byte line, zeroed before the launch):
-// thread 0 of every block arrives with a release reduction (no round trip)
-// and polls the counter with acquire loads until every block has arrived.
-// Returns false, identically in every thread of the block, when the wait
-// gave up (limit reached, or another block reported an error).
-__device__ bool level_barrier(unsigned *ctr, int *err, unsigned nblocks, long long limit) {
-    __shared__ int s_ok;
+// Level barrier over all blocks of the grid, in two halves.  Each barrier of a
+// launch has its own arrival counter (own 128-byte line, zeroed before the
+// launch).  barrier_arrive: once every thread of the block is done with the
+// level, thread 0 arrives with a release reduction (no round trip).
+// barrier_wait: thread 0 polls the counter with acquire loads until every
+// block has arrived; returns false, identically in every thread of the block,
+// when the wait gave up (limit reached, or another block reported an error).
+// Between the two a block may load whatever does not depend on the other
+// blocks' work of the level (the next level's static data), so those loads
+// overlap the barrier's latency instead of delaying the block's arrival.
+__device__ __forceinline__ void barrier_arrive(unsigned *ctr) {
     __syncthreads();
+    if (threadIdx.x == 0) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(ctr) : "memory");
+}
+
+__device__ bool barrier_wait(unsigned *ctr, int *err, unsigned nblocks, long long limit) {
+    __shared__ int s_ok;
     if (threadIdx.x == 0) {
         int ok = 1;
-        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(ctr) : "memory");
         const long long t0 = clock64();
         unsigned spins = 0;
         while (ld_acquire_u32(ctr) < nblocks) {
@@ -52,6 +60,11 @@ __device__ bool level_barrier(unsigned *ctr, int *err, unsigned nblocks, long lo
     }
     __syncthreads();
     return s_ok != 0;
+}
+
+__device__ bool level_barrier(unsigned *ctr, int *err, unsigned nblocks, long long limit) {
+    barrier_arrive(ctr);
+    return barrier_wait(ctr, err, nblocks, limit);
 }
 
 // thread index that spreads consecutive 32-element groups over all blocks
@@ -88,9 +101,10 @@ __global__ void __launch_bounds__(kPersistThreads) k_fwd_persist(
     for (int l = 1; l <= L; l++) {
         const int32_t c0 = lvl[l - 1], c1 = lvl[l];
         const int64_t c = c0 + tid;
+        barrier_arrive(bar + 32 * (l - 1));
         uint4 r = make_uint4(0, 0, 0, 0);
-        if (c < c1) r = fanin[c];   // static: loaded before the wait
-        if (!level_barrier(bar + 32 * (l - 1), err, gridDim.x, limit)) return;
+        if (c < c1) r = fanin[c];   // static: loaded between arrival and wait
+        if (!barrier_wait(bar + 32 * (l - 1), err, gridDim.x, limit)) return;
         if (c < c1) fwd_cell(r, c, pq, tr, ns, ops, par);
         for (int64_t cc = c + T; cc < c1; cc += T) fwd_cell(fanin[cc], cc, pq, tr, ns, ops, par);
     }
@@ -152,10 +166,13 @@ __global__ void __launch_bounds__(kPersistThreads) k_bwd_persist(
     for (int l = L; l >= 1; l--) {
         const int32_t c0 = lvl[l - 1], c1 = lvl[l];
         const int64_t c = c0 + tid;
+        // the top level has no fanout inside the pass: no barrier before it.  Below it the
+        // block arrives for the level above, then gathers this level's static part (its
+        // loads do not depend on the level above) while the other blocks arrive.
+        if (l < L) barrier_arrive(bar + 32 * (L - 1 - l));
         BwdStatic s;
         if (c < c1) s = bwd_static(fanin, fptr, efpos, pq, cload, beta, c, ns, grad_mode, K, ops);
-        // the top level has no fanout inside the pass: no wait before it
-        if (l < L && !level_barrier(bar + 32 * (L - 1 - l), err, gridDim.x, limit)) return;
+        if (l < L && !barrier_wait(bar + 32 * (L - 1 - l), err, gridDim.x, limit)) return;
         if (c < c1) bwd_finish(s, ns + c, gnet, gfo, grad_mode);
         for (int64_t cc = c + T; cc < c1; cc += T)
             bwd_finish(bwd_static(fanin, fptr, efpos, pq, cload, beta, cc, ns, grad_mode, K, ops), ns + cc, gnet,
@@ -248,10 +265,11 @@ __global__ void __launch_bounds__(kSimThreads) k_sim_persist(const uint4 *__rest
     for (int l = 1; l <= L; l++) {
         const int32_t c0 = lvl[l - 1], c1 = lvl[l];
         const int64_t c = c0 + gw;
+        // level 1 reads only startpoint words, written by the previous launch
+        if (l > 1) barrier_arrive(bar + 32 * (l - 2));
         uint4 r = make_uint4(0, 0, 0, 0);
         if (c < c1) r = fanin[c];
-        // level 1 reads only startpoint words, written by the previous launch
-        if (l > 1 && !level_barrier(bar + 32 * (l - 2), err, gridDim.x, limit)) return;
+        if (l > 1 && !barrier_wait(bar + 32 * (l - 2), err, gridDim.x, limit)) return;
         if (c < c1) sim_cell(r, c, words, toggles, ones, ns, T, ops, lane);
         for (int64_t cc = c + W; cc < c1; cc += W) sim_cell(fanin[cc], cc, words, toggles, ones, ns, T, ops, lane);
     }
@@ -275,9 +293,10 @@ __global__ void __launch_bounds__(kSimThreads, 2) k_sim_wide(const uint4 *__rest
     for (int l = 1; l <= L; l++) {
         const int32_t c0 = lvl[l - 1], c1 = lvl[l];
         const int64_t cfirst = c0 + 2 * gw + half;
+        if (l > 1) barrier_arrive(bar + 32 * (l - 2));
         uint4 r = make_uint4(0, 0, 0, 0);
-        if (cfirst < c1) r = fanin[cfirst];   // static: loaded before the wait
-        if (l > 1 && !level_barrier(bar + 32 * (l - 2), err, gridDim.x, limit)) return;
+        if (cfirst < c1) r = fanin[cfirst];   // static: loaded between arrival and wait
+        if (l > 1 && !barrier_wait(bar + 32 * (l - 2), err, gridDim.x, limit)) return;
         for (int64_t c = cfirst;; c += step) {
             const bool valid = c < c1;
             if (!__any_sync(0xFFFFFFFFu, valid)) break;
