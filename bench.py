@@ -84,12 +84,12 @@ def batched_algorithmic_bytes(nn: int, ns: int, nc: int, ne: int, S: int) -> int
 # (null).
 TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (one pass), 2M-cell step, 4th step
-    "k_sim_wide": {"bytes": 257_115_136 + 985_070_336, "workload": "roofline",
+    "k_sim_wide": {"bytes": 257_035_520 + 985_288_704, "workload": "roofline",
                    "files": ["kern_persist.cu", "kern_common.cuh"],
-                   "sha": "2eee32781a24a2e0"},
-    "k_bwd_persist": {"bytes": 127_266_048 + 11_657_984, "workload": "roofline",
+                   "sha": "ed76965506855319"},
+    "k_bwd_persist": {"bytes": 127_249_152 + 11_665_664, "workload": "roofline",
                       "files": ["kern_persist.cu", "kern_common.cuh"],
-                      "sha": "2eee32781a24a2e0"},
+                      "sha": "ed76965506855319"},
 }
 
 

@@ -86,7 +86,7 @@ __device__ __forceinline__ void fwd_cell(const uint4 &r, int64_t c, float4 *pq, 
     tr[ns + c] = pair_tr(o);
 }
 
-__global__ void __launch_bounds__(kPersistThreads) k_fwd_persist(
+__global__ void __launch_bounds__(kFwdThreads) k_fwd_persist(
     const uint4 *__restrict__ fanin, float4 *pq, float *tr, const float *__restrict__ sp_in,
     const float *__restrict__ tr_in, const int32_t *__restrict__ lvl, int L, int64_t ns, int tr_mode, OpTable ops,
     unsigned *bar, int *err, long long limit, const uint32_t *epoch) {
@@ -410,7 +410,7 @@ int persist_grid(int which, int sm_count) {
     int per = 0;
     cudaError_t e;
     if (which == 3) return wide_grid(sm_count);
-    if (which == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fwd_persist, kPersistThreads, 0);
+    if (which == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fwd_persist, kFwdThreads, 0);
     else if (which == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sim_persist, kSimThreads, 0);
     else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bwd_persist, kPersistThreads, 0);
     if (e != cudaSuccess) {
@@ -428,7 +428,7 @@ cudaError_t launch_fwd_persist(const DevDesign &d, const OpTable &ops, int tr_mo
     unsigned *bar = d.bar;
     cudaMemsetAsync(bar, 0, bar_bytes(d), s);
     if (ready) cudaEventRecord(ready, s);   // work forked here becomes ready together with the kernel
-    return launch_coop(k_fwd_persist, grid, kPersistThreads, s, d.fanin, d.pq, d.tr, (const float *)d.sp_in,
+    return launch_coop(k_fwd_persist, grid, kFwdThreads, s, d.fanin, d.pq, d.tr, (const float *)d.sp_in,
                        (const float *)d.tr_in, d.lvl, d.n_levels, d.n_start, tr_mode, ops, bar, d.err,
                        kWaitLimitCycles, (const uint32_t *)d.epoch);
 }

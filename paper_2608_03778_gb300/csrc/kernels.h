@@ -15,6 +15,10 @@ struct OpTable {
 };
 
 constexpr int kPersistThreads = 512;
+// the persistent forward pass runs beside the startpoint generator: a smaller block leaves
+// the generator more registers on every SM (one block of 256 threads per SM still gives one
+// thread per cell of a 38,912-cell level)
+constexpr int kFwdThreads = 256;
 constexpr int kSimThreads = 512;
 // bounded waits give up after this many SM cycles (about 2 s at 2 GHz)
 constexpr long long kWaitLimitCycles = 4000000000LL;
