@@ -84,12 +84,12 @@ def batched_algorithmic_bytes(nn: int, ns: int, nc: int, ne: int, S: int) -> int
 # (null).
 TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (one pass), 2M-cell step, 4th step
-    "k_sim_wide": {"bytes": 257_035_520 + 985_288_704, "workload": "roofline",
+    "k_sim_wide": {"bytes": 232_209_920 + 174_487_808, "workload": "roofline",
                    "files": ["kern_persist.cu", "kern_common.cuh"],
-                   "sha": "ed76965506855319"},
-    "k_bwd_persist": {"bytes": 127_249_152 + 11_665_664, "workload": "roofline",
+                   "sha": "3f98159b756effd3"},
+    "k_bwd_persist": {"bytes": 127_277_568 + 11_832_832, "workload": "roofline",
                       "files": ["kern_persist.cu", "kern_common.cuh"],
-                      "sha": "ed76965506855319"},
+                      "sha": "3f98159b756effd3"},
 }
 
 

@@ -406,6 +406,26 @@ dp_status dp_design_upload(dp_ctx *ctx, const dp_compiled *cp, dp_design **out) 
     chunk_ptr[1] = (int32_t)((cp->n_start + 31) / 32);
     for (int l = 1; l <= cp->n_levels; l++)
         chunk_ptr[l + 1] = chunk_ptr[l] + (cp->lvl_ptr[l] - cp->lvl_ptr[l - 1] + 31) / 32;
+    // nets by death level: the highest level of a cell reading the net, else the net's own level
+    std::vector<int32_t> dead_ptr((size_t)cp->n_levels + 2, 0), dead_net((size_t)cp->n_nets);
+    {
+        std::vector<int32_t> death((size_t)cp->n_nets, 0);
+        for (int l = 1; l <= cp->n_levels; l++)
+            for (int32_t c = cp->lvl_ptr[l - 1]; c < cp->lvl_ptr[l]; c++) {
+                death[(size_t)(cp->n_start + c)] = l;
+                const uint32_t *r = &cp->fanin[4 * (size_t)c];
+                const int k = cp->op_arity[r[0] >> 24];
+                for (int j = 0; j < k; j++) {
+                    const uint32_t n = j == 0 ? (r[0] & dp::kNetMask) : r[j];
+                    death[n] = std::max(death[n], l);
+                }
+            }
+        for (int32_t d : death) dead_ptr[(size_t)d + 1]++;
+        for (size_t l = 1; l < dead_ptr.size(); l++) dead_ptr[l] += dead_ptr[l - 1];
+        std::vector<int32_t> at(dead_ptr.begin(), dead_ptr.end() - 1);
+        for (size_t n = 0; n < death.size(); n++) dead_net[(size_t)at[(size_t)death[n]]++] = (int32_t)n;
+    }
+    int32_t *dptr = nullptr, *dnet = nullptr;
     // level-aligned cell pairs (the dataflow simulation's unit of work)
     std::vector<int32_t> pair_ptr((size_t)cp->n_levels + 1, 0);
     for (int l = 1; l <= cp->n_levels; l++)
@@ -437,6 +457,8 @@ dp_status dp_design_upload(dp_ctx *ctx, const dp_compiled *cp, dp_design **out) 
     TRY(dalloc(D, &d.epoch, 4));
     TRY(dalloc(D, &chunks, chunk_ptr.size()));
     TRY(dalloc(D, &pairs, pair_ptr.size()));
+    TRY(dalloc(D, &dptr, dead_ptr.size()));
+    TRY(dalloc(D, &dnet, dead_net.size()));
     TRY(dalloc(D, &d.partials, (size_t)dp::kPowerBlocks));
     TRY(dalloc(D, &d.power, 4));
     d.fanin = fanin;
@@ -446,6 +468,8 @@ dp_status dp_design_upload(dp_ctx *ctx, const dp_compiled *cp, dp_design **out) 
     d.lvl = lvl;
     d.chunk_ptr = chunks;
     d.pair_ptr = pairs;
+    d.dead_ptr = dptr;
+    d.dead_net = dnet;
     d.err = ctx->d_err;
     d.net_of_user = nou;
     d.cell_of_user = cou;
@@ -462,6 +486,8 @@ dp_status dp_design_upload(dp_ctx *ctx, const dp_compiled *cp, dp_design **out) 
     up(lvl, cp->lvl_ptr.data(), sizeof(int32_t) * cp->lvl_ptr.size());
     up(chunks, chunk_ptr.data(), sizeof(int32_t) * chunk_ptr.size());
     up(pairs, pair_ptr.data(), sizeof(int32_t) * pair_ptr.size());
+    up(dptr, dead_ptr.data(), sizeof(int32_t) * dead_ptr.size());
+    up(dnet, dead_net.data(), sizeof(int32_t) * dead_net.size());
     up(nou, cp->net_of_user.data(), sizeof(int32_t) * nn);
     up(cou, cp->cell_of_user.data(), sizeof(int32_t) * nc);
     up(base, cp->base_cap.data(), sizeof(float) * nn);

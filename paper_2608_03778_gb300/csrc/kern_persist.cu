@@ -282,20 +282,40 @@ __global__ void __launch_bounds__(kSimThreads) k_sim_persist(const uint4 *__rest
 // cells are sorted by it inside a level).  Every lane issues its two 16-byte
 // loads per fanin before using any of them, which keeps several kilobytes in
 // flight per warp; toggle and ones counts are reduced over the half-warp.
+// The words are scratch of the pass: once the last level that reads a net is
+// complete, its words are dead, and when T is a multiple of 16 (whole 128-byte
+// lines per net) they are dropped from L2 without a write-back
+// (discard.global.L2).  A net dies at its death level (the highest level of
+// the cells it feeds, else its own); the nets of death level d, listed in
+// dead_net[dead_ptr[d] .. dead_ptr[d+1]), are discarded by the whole grid during
+// level d + 2, between a block's arrival and its wait (every block passed the
+// barrier that ended level d before it worked on level d + 1).  Without it the
+// pass writes every cell's words back to DRAM as L2 fills with them.
+__device__ __forceinline__ void discard_l2(const void *p) {
+    asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
+}
+
 __global__ void __launch_bounds__(kSimThreads, 2) k_sim_wide(const uint4 *__restrict__ fanin, uint64_t *words,
                                                             uint32_t *toggles, uint32_t *ones,
                                                             const int32_t *__restrict__ lvl, int L, int64_t ns,
-                                                            int T, OpTable ops, unsigned *bar, int *err,
-                                                            long long limit) {
+                                                            int T, OpTable ops, const int32_t *__restrict__ dead_ptr,
+                                                            const int32_t *__restrict__ dead_net, unsigned *bar,
+                                                            int *err, long long limit) {
     const int lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
     const int64_t gw = spread_warp();
     const int64_t step = 2 * (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int lines = (T & 15) == 0 && dead_ptr ? T / 16 : 0;   // 128-byte lines per net
     for (int l = 1; l <= L; l++) {
         const int32_t c0 = lvl[l - 1], c1 = lvl[l];
         const int64_t cfirst = c0 + 2 * gw + half;
         if (l > 1) barrier_arrive(bar + 32 * (l - 2));
         uint4 r = make_uint4(0, 0, 0, 0);
         if (cfirst < c1) r = fanin[cfirst];   // static: loaded between arrival and wait
+        if (lines && l >= 2) {
+            const int64_t d0 = dead_ptr[l - 2], nd = (int64_t)(dead_ptr[l - 1] - d0) * lines;
+            for (int64_t i = spread_tid(); i < nd; i += (int64_t)gridDim.x * blockDim.x)
+                discard_l2(words + (size_t)dead_net[d0 + i / lines] * T + (size_t)(i % lines) * 16);
+        }
         if (l > 1 && !barrier_wait(bar + 32 * (l - 2), err, gridDim.x, limit)) return;
         for (int64_t c = cfirst;; c += step) {
             const bool valid = c < c1;
@@ -446,7 +466,7 @@ cudaError_t launch_sim_wide(const DevDesign &d, const OpTable &ops, int T, int g
     unsigned *bar = d.bar + 32 * ((size_t)d.n_levels + 2);
     cudaMemsetAsync(bar, 0, bar_bytes(d), s);
     return launch_coop(k_sim_wide, grid, kSimThreads, s, d.fanin, d.words, d.toggles, d.ones, d.lvl, d.n_levels,
-                       d.n_start, T, ops, bar, d.err, kWaitLimitCycles);
+                       d.n_start, T, ops, d.dead_ptr, d.dead_net, bar, d.err, kWaitLimitCycles);
 }
 
 cudaError_t launch_bwd_persist(const DevDesign &d, const OpTable &ops, int grad_mode, int tr_mode, float K,

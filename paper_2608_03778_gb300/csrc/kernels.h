@@ -52,6 +52,8 @@ struct DevDesign {
     const int32_t *chunk_ptr;  // [n_levels+2] level-aligned chunks of 32 (level 0 = startpoints)
     const int32_t *pair_ptr;   // [n_levels+1] level-aligned cell pairs: pairs of level l are [pair_ptr[l-1], pair_ptr[l])
     unsigned *simdone;         // [n_cells] pass number of the simulation pass that last wrote the cell's words
+    const int32_t *dead_ptr;   // [n_levels+2] nets by death level d (the highest level reading the net, else
+    const int32_t *dead_net;   // [n_nets]      its own): dead_net[dead_ptr[d] .. dead_ptr[d+1])
     int *err;                  // device error word of the context (bounded wait gave up)
 };
 
