@@ -97,20 +97,18 @@ __global__ void __launch_bounds__(kPowerThreads) k_power_final(const double *__r
 }
 
 // d P / d C_load (user net order) = K alpha
-__global__ void k_grad_cload(const float *__restrict__ tr, const float *__restrict__ beta,
-                             const int32_t *__restrict__ net_of_user, float K, float *out, int64_t nn) {
+// alpha: TR_model, or the hybrid TR beta * TR_model as k_hybrid stores it (one gather per net)
+__global__ void k_grad_cload(const float *__restrict__ alpha, const int32_t *__restrict__ net_of_user, float K,
+                             float *out, int64_t nn) {
     int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= nn) return;
-    int32_t n = net_of_user[u];
-    float a = tr[n];
-    if (beta) a *= beta[n];
-    out[u] = K * a;
+    out[u] = K * alpha[net_of_user[u]];
 }
 
 // d P / d pincap (user cell order) = K * sum over the cell's inputs of alpha
-__global__ void k_grad_pincap(const uint4 *__restrict__ fanin, const float *__restrict__ tr,
-                              const float *__restrict__ beta, const int32_t *__restrict__ cell_of_user, float K,
-                              float *out, int64_t nc, OpTable ops) {
+__global__ void k_grad_pincap(const uint4 *__restrict__ fanin, const float *__restrict__ alpha,
+                              const int32_t *__restrict__ cell_of_user, float K, float *out, int64_t nc,
+                              OpTable ops) {
     int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= nc) return;
     const uint4 r = fanin[cell_of_user[u]];
@@ -119,7 +117,7 @@ __global__ void k_grad_pincap(const uint4 *__restrict__ fanin, const float *__re
     float s = 0.f;
 #pragma unroll
     for (int j = 0; j < 4; j++)
-        if (j < k) s += beta ? beta[n[j]] * tr[n[j]] : tr[n[j]];
+        if (j < k) s += alpha[n[j]];
     out[u] = K * s;
 }
 
@@ -192,11 +190,12 @@ void launch_power(const DevDesign &d, bool hybrid, double K, int slot, cudaStrea
 void launch_cap_grads(const DevDesign &d, const OpTable &ops, bool hybrid, int tr_mode, double K,
                           float *grad_cload, float *grad_pincap, float *grad_tr_in, cudaStream_t s) {
     const float *beta = hybrid ? d.beta : nullptr;
+    const float *alpha = hybrid ? d.trh : d.tr;   // trh = beta * TR_model, the same binary32 product
     if (grad_cload && d.n_nets)
-        k_grad_cload<<<(unsigned)cdiv(d.n_nets, 256), 256, 0, s>>>(d.tr, beta, d.net_of_user, (float)K, grad_cload,
+        k_grad_cload<<<(unsigned)cdiv(d.n_nets, 256), 256, 0, s>>>(alpha, d.net_of_user, (float)K, grad_cload,
                                                                    d.n_nets);
     if (grad_pincap && d.n_cells)
-        k_grad_pincap<<<(unsigned)cdiv(d.n_cells, 256), 256, 0, s>>>(d.fanin, d.tr, beta, d.cell_of_user, (float)K,
+        k_grad_pincap<<<(unsigned)cdiv(d.n_cells, 256), 256, 0, s>>>(d.fanin, alpha, d.cell_of_user, (float)K,
                                                                      grad_pincap, d.n_cells, ops);
     if (grad_tr_in && d.n_start)
         k_grad_tr_in<<<(unsigned)cdiv(d.n_start, 256), 256, 0, s>>>(beta, d.cload, (float)K, tr_mode, grad_tr_in,
