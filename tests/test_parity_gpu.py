@@ -1,6 +1,6 @@
 """GPU path vs the FP64 oracle, element by element, through the C-ABI.
 
-Tolerances (spec bar):
+Tolerances (the bar the hot path is held to):
 * SP and TR of every net: 1e-5 absolute;
 * toggle and ones counts: bit-exact;
 * gradients: |g - g*| <= 1e-4 max(|g*|, 1e-3 max|g*|) (relative, near-zero floor);
