@@ -135,6 +135,19 @@ dp_status dp_compile(const char *netlist, size_t netlist_len, const char *librar
 void dp_compiled_free(dp_compiled *c);
 dp_status dp_compiled_info(const dp_compiled *c, dp_info *info);
 
+/* A compiled netlist as a self-contained byte blob (host memory, little-endian):
+ * compile once, store, load later without the netlist text.  dp_compiled_save
+ * writes the blob into buf when cap is large enough (buf may be NULL to ask for
+ * the size) and always sets *len to the blob's size; DP_EINVAL when buf is too
+ * small.  dp_compiled_load reads a blob (borrowed for the call) into a new
+ * compiled netlist owned by the caller; every size and every structural
+ * property the device code relies on (levels, fanin ids below the cell's own
+ * level, fanout CSR and edge positions, user-order permutations, finite
+ * non-negative caps, bytecode ranges) is checked, and a damaged blob returns
+ * DP_EPARSE with a message in err. */
+dp_status dp_compiled_save(const dp_compiled *c, void *buf, size_t cap, size_t *len);
+dp_status dp_compiled_load(const void *blob, size_t len, dp_compiled **out, char *err, size_t errlen);
+
 /* Read-only views into a compiled netlist, for inspection and tests.  All
  * pointers are host memory owned by *c and valid until dp_compiled_free.
  * Internal numbering: nets [0, n_start) are the startpoints in input order;
@@ -194,6 +207,8 @@ dp_status dp_design_load(dp_ctx *ctx, const char *netlist, size_t netlist_len, c
                          size_t library_len, dp_design **out);
 /* Uploads an already compiled netlist (the compiled object is not consumed). */
 dp_status dp_design_upload(dp_ctx *ctx, const dp_compiled *c, dp_design **out);
+/* Loads (as dp_compiled_load) and uploads a compiled-netlist blob. */
+dp_status dp_design_load_blob(dp_ctx *ctx, const void *blob, size_t len, dp_design **out);
 void dp_design_free(dp_design *d);
 dp_status dp_design_info(const dp_design *d, dp_info *info);
 

@@ -533,6 +533,17 @@ dp_status dp_design_load(dp_ctx *ctx, const char *netlist, size_t netlist_len, c
     return s;
 }
 
+dp_status dp_design_load_blob(dp_ctx *ctx, const void *blob, size_t len, dp_design **out) {
+    if (!ctx || !out) return set_err(ctx, DP_EINVAL, "NULL argument");
+    dp_compiled *cp = nullptr;
+    char msg[256] = {0};
+    dp_status s = dp_compiled_load(blob, len, &cp, msg, sizeof msg);
+    if (s != DP_OK) return set_err(ctx, s, msg);
+    s = dp_design_upload(ctx, cp, out);
+    dp_compiled_free(cp);
+    return s;
+}
+
 void dp_design_free(dp_design *D) { free_design(D); }
 
 dp_status dp_design_info(const dp_design *D, dp_info *info) {

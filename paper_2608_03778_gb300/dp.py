@@ -131,7 +131,12 @@ _sig("dp_backward_weighted", [_P, ctypes.POINTER(dp_config), _P, ctypes.c_int32,
 _sig("dp_ascent_step", [_P, _P, _P, ctypes.c_int64, ctypes.c_float])
 _sig("dp_virus_eval", [_P, _P, ctypes.c_int32, _P, _P, _S])
 
+_sig("dp_compiled_save", [_P, _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)])
+_sig("dp_compiled_load", [_P, ctypes.c_size_t, ctypes.POINTER(_P), ctypes.c_char_p, ctypes.c_size_t])
+_sig("dp_design_load_blob", [_P, _P, ctypes.c_size_t, ctypes.POINTER(_P)])
+
 EXPORTED = ["dp_config_default", "dp_last_error", "dp_compile", "dp_compiled_free", "dp_compiled_info",
+            "dp_compiled_save", "dp_compiled_load", "dp_design_load_blob",
             "dp_compiled_view_get", "dp_compile_function", "dp_create", "dp_destroy", "dp_sync", "dp_design_load",
             "dp_design_upload", "dp_design_free", "dp_design_info", "dp_set_inputs", "dp_set_pincap",
             "dp_propagate", "dp_simulate", "dp_total_power", "dp_backward", "dp_get_nets", "dp_step",
@@ -193,6 +198,24 @@ def dp_compile(netlist: str, library: str):
 
 def dp_compiled_free(c) -> None:
     _lib.dp_compiled_free(c)
+
+
+def dp_compiled_save(c) -> bytes:
+    """The compiled netlist as a blob."""
+    n = ctypes.c_size_t(0)
+    _check(_lib.dp_compiled_save(c, None, 0, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value)
+    _check(_lib.dp_compiled_save(c, buf, n.value, ctypes.byref(n)))
+    return buf.raw[:n.value]
+
+
+def dp_compiled_load(blob: bytes):
+    out = _P()
+    err = ctypes.create_string_buffer(256)
+    st = _lib.dp_compiled_load(blob, len(blob), ctypes.byref(out), err, 256)
+    if st != 0:
+        raise DPError(st, err.value.decode())
+    return out.value
 
 
 def dp_compiled_info(c) -> dp_info:
@@ -259,6 +282,12 @@ def dp_design_load(ctx, netlist: str, library: str):
     nb, lb = netlist.encode(), library.encode()
     out = _P()
     _check(_lib.dp_design_load(ctx, nb, len(nb), lb, len(lb), ctypes.byref(out)), ctx)
+    return out.value
+
+
+def dp_design_load_blob(ctx, blob: bytes):
+    out = _P()
+    _check(_lib.dp_design_load_blob(ctx, blob, len(blob), ctypes.byref(out)), ctx)
     return out.value
 
 

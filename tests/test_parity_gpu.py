@@ -224,6 +224,38 @@ def test_startpoint_chains_both_forms(dp, ctx, library_text, T):
     check_against_oracle(o, g, sp, tr, cfg)
 
 
+def test_blob_design_gives_the_same_bits(dp, ctx, library_text):
+    """A design loaded from a compiled-netlist blob runs exactly as one compiled from text."""
+    text = netgen.netlist_text(netgen.WORKLOADS["small"])
+    c = dp.dp_compile(text, library_text)
+    try:
+        blob = dp.dp_compiled_save(c)
+    finally:
+        dp.dp_compiled_free(c)
+    sp, tr = netgen.scenario_inputs(netgen.WORKLOADS["small"].n_start, 77, 1)
+    sp, tr = np.ascontiguousarray(sp[:, 0]), np.ascontiguousarray(tr[:, 0])
+    cfg = dp.config()
+    outs = []
+    for load in (lambda: dp.dp_design_load(ctx, text, library_text), lambda: dp.dp_design_load_blob(ctx, blob)):
+        d = load()
+        try:
+            info = dp.dp_design_info(d)
+            dp.dp_set_inputs(ctx, d, sp, tr)
+            g = {k: np.zeros(n, np.float32) for k, n in [("sp", info.n_start), ("tr", info.n_start),
+                                                          ("pin", info.n_cells), ("cl", info.n_nets)]}
+            w = np.zeros(2)
+            dp.dp_step(ctx, d, cfg, g["sp"], g["tr"], g["pin"], g["cl"], w, 0)
+            outs.append((g, w))
+        finally:
+            dp.dp_design_free(d)
+    for k in outs[0][0]:
+        np.testing.assert_array_equal(outs[0][0][k], outs[1][0][k])
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])
+    with pytest.raises(dp.DPError) as e:
+        dp.dp_design_load_blob(ctx, blob[:-3])
+    assert e.value.name == "DP_EPARSE"
+
+
 def test_boolean_inputs_exact(dp, ctx, library_text):
     text = netgen.netlist_text(netgen.WORKLOADS["small"])
     o = Oracle(text, library_text)
