@@ -428,7 +428,8 @@ typedef struct {
 
 void dp_server_config_default(dp_server_config *cfg);
 /* Creates a server (and its worker thread unless cfg->plain).  DP_EINVAL for a
- * bad max_batch or grad_mode != 0. */
+ * bad max_batch, grad_mode != 0, or a tr_mode other than 0 and 1 (the lag-one
+ * mode runs through dp_set_inputs_batch only). */
 dp_status dp_server_create(const dp_server_config *cfg, dp_server **out);
 /* Stops the worker after the batches in flight, frees every design. */
 void dp_server_destroy(dp_server *srv);
