@@ -127,7 +127,7 @@ class VirusResult:
     p_virus: torch.Tensor     # [S] float64, fF (Eq. 3)
     proxy_start: torch.Tensor # [S] float64, fF: sum C TR at the start
     proxy_end: torch.Tensor   # [S] float64, fF: at the end
-    ms_ascent: float          # device time of the ascent steps
+    ms_ascent: float          # device time of the ascent steps (the replays, with a graph)
     graph: bool
 
 
@@ -140,8 +140,8 @@ def power_virus(design: Design, sp0: torch.Tensor, tr0: torch.Tensor, steps: int
     K = 1/2 Vdd^2 f; Eq. 9 in tr_mode 1) through :class:`DiffPowerFunction`
     and moves SP (and TR in tr_mode 0) by eta times its gradient, projected
     onto [0, 1].  With ``graph`` the step - forward, backward and update - is
-    captured once in a CUDA graph after ``warmup`` eager steps and replayed for
-    the rest.  Then the final SP is thresholded (v0 = [SP >= 0.5], v1 = not v0)
+    captured once in a CUDA graph (after ``warmup`` eager steps whose effect on
+    the inputs is undone) and replayed ``steps`` times.  Then the final SP is thresholded (v0 = [SP >= 0.5], v1 = not v0)
     and P_virus (Eq. 3) is evaluated by two bitwise forward passes.
     """
     if steps < 0:
@@ -169,20 +169,28 @@ def power_virus(design: Design, sp0: torch.Tensor, tr0: torch.Tensor, steps: int
             dp.dp_ascent_step(design.ctx, t, t.grad, n, eta_tr)
 
     p_start = proxy()
-    use_graph = graph and steps > warmup
+    use_graph = graph and steps > 0
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if use_graph:
+        # warm-up steps on the side stream (first-use allocations, autograd state), then the
+        # starting point restored: all `steps` steps are replays of the captured step, and
+        # the timing holds their device time alone
+        with torch.no_grad():
+            x0, t0 = x.detach().clone(), t.detach().clone()
         side = torch.cuda.Stream(sp0.device)
         side.wait_stream(torch.cuda.current_stream(sp0.device))
         with torch.cuda.stream(side):
-            ev0.record()
             for _ in range(warmup):
                 step()
         torch.cuda.current_stream(sp0.device).wait_stream(side)
+        with torch.no_grad():
+            x.copy_(x0)
+            t.copy_(t0)
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
             step()
-        for _ in range(steps - warmup):
+        ev0.record()
+        for _ in range(steps):
             g.replay()
         ev1.record()
     else:
