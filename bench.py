@@ -117,7 +117,7 @@ class Clocks:
         self.p = None
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                       "-lms", "200", "-i", str(gpu)], stdout=self.f, stderr=subprocess.DEVNULL)
+                                       "-lms", "50", "-i", str(gpu)], stdout=self.f, stderr=subprocess.DEVNULL)
         except (FileNotFoundError, OSError):
             self.p = None
 
@@ -193,16 +193,38 @@ def cpu_baseline(text: str, lib: str, sp, tr, n_cells: int, T: int) -> dict:
                       f"netlist, {dt:.1f} s, single thread"}
 
 
+REFERENCE_BUDGET_S = 150.0   # the whole --impl reference run, warm-up included
+
+
 def run_reference(args, rank: int, world: int) -> None:
-    """Reference arm: the FP64 CPU oracle on the host cores, rank 0 only."""
+    """Reference arm: the FP64 CPU oracle on the host cores, rank 0 only.
+
+    Each step is a bounded sample of the workload: the same generator recipe (startpoint
+    shares, depth, fanout cap, seed) at a cell count chosen so that the warm-up and timed
+    steps together take about REFERENCE_BUDGET_S on this host (the oracle's rate, measured
+    on a 20,000-cell draw first, sets it).  The oracle's work per cell does not grow with the
+    netlist, so cells/s on the sample stands for the full workload; a smaller draw fits the
+    host caches better, so the sample if anything flatters the oracle (about 1.6x against the
+    full 2M-cell netlist)."""
     if rank != 0:
         return
+    from dataclasses import replace
+
     from oracle.oracle import Oracle
-    spec, lib, text, sp, tr = workload(args.workload)
-    o = Oracle(text, lib)
+    from paper_2608_03778_gb300 import netgen
+    full = netgen.WORKLOADS[args.workload]
+    lib = netgen.library_text()
     T, T_sample = 64, 8
 
-    def one():
+    def draw(n_cells: int):
+        f = n_cells / full.n_cells
+        spec = replace(full, n_cells=n_cells, n_pi=max(8, round(full.n_pi * f)), n_dff=max(8, round(full.n_dff * f)),
+                       depth=max(2, min(full.depth, n_cells // 16)))
+        text = netgen.netlist_text(spec)
+        sp, tr = netgen.scenario_inputs(spec.n_start, 1000)
+        return spec, Oracle(text, lib), np.ascontiguousarray(sp[:, 0]), np.ascontiguousarray(tr[:, 0])
+
+    def one(o, sp, tr):
         t0 = time.perf_counter()
         s, t = o.forward(sp, tr, 0)
         o.power(t)
@@ -215,21 +237,29 @@ def run_reference(args, rank: int, world: int) -> None:
         t3 = time.perf_counter()
         return (t1 - t0) + (t3 - t2) + (t2 - t1) * (T / T_sample)
 
+    probe_spec, o, sp, tr = draw(min(20_000, full.n_cells))
+    rate = probe_spec.n_cells / one(o, sp, tr)
+    per_step = REFERENCE_BUDGET_S / max(1, args.steps + args.warmup)
+    n = int(min(full.n_cells, max(probe_spec.n_cells, rate * per_step)))
+    spec, o, sp, tr = (probe_spec, o, sp, tr) if n == probe_spec.n_cells else draw(n)
+
     for _ in range(args.warmup):
-        one()
-    ts = [one() for _ in range(args.steps)]
+        one(o, sp, tr)
+    ts = [one(o, sp, tr) for _ in range(args.steps)]
     ms = 1e3 * sum(ts) / len(ts)
     val = spec.n_cells / (ms / 1e3)
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{args.workload}: {spec.n_cells} cells, {spec.n_start} startpoints, depth "
-                               f"{spec.depth}", "sim_vectors": 64 * T},
+        "config": {"workload": f"{args.workload}: {full.n_cells} cells, {full.n_start} startpoints, depth "
+                               f"{full.depth}", "sim_vectors": 64 * T},
         "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"per step: forward, power and adjoint of the full netlist plus the simulation "
-                                   f"at {64 * T_sample} vectors, its time scaled by {T // T_sample} to "
-                                   f"{64 * T} vectors; single thread"},
+                         "sample": f"per step: forward, power and adjoint of a {spec.n_cells}-cell draw of the same "
+                                   f"recipe ({spec.n_start} startpoints, depth {spec.depth}), plus its simulation "
+                                   f"at {64 * T_sample} vectors with the time scaled by {T // T_sample} to "
+                                   f"{64 * T} vectors; sized for about {REFERENCE_BUDGET_S:.0f} s in all; "
+                                   f"single thread"},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -502,7 +532,7 @@ def bench_adjoint_vs_fd(dp, torch, dev) -> dict:
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="roofline")
