@@ -358,6 +358,7 @@ void launch_fwdb(const DevDesign &d, const BatchBufs &b, const OpTable &ops, con
     }
     const int64_t S = b.S;
     if (d.n_start) k_fwdb_start<<<(unsigned)cdiv(d.n_start * S, 256), 256, 0, s>>>(b.sp_in, b.pq, d.n_start * S);
+    sh = fit_shape(sh, S);
     const dim3 blk((unsigned)sh.bx, (unsigned)sh.by);
     for (int l = 1; l <= d.n_levels; l++) {
         const int32_t c0 = lvl[l - 1], c1 = lvl[l];
@@ -386,6 +387,7 @@ void launch_bwdb(const DevDesign &d, const BatchBufs &b, const OpTable &ops, con
         return;
     }
     const int64_t S = b.S;
+    sh = fit_shape(sh, S);
     const dim3 blk((unsigned)sh.bx, (unsigned)sh.by);
     for (int l = d.n_levels; l >= 1; l--) {
         const int32_t c0 = lvl[l - 1], c1 = lvl[l];
@@ -413,7 +415,7 @@ void launch_gradb(const DevDesign &d, const BatchBufs &b, const OpTable &ops, in
     }
     const int64_t rows = (gcl ? d.n_nets : 0) + (gpin ? d.n_cells : 0) + (gtr ? d.n_start : 0);
     if (rows == 0) return;
-    const BatchShape sh{S >= 128 ? 128 : 32, S >= 128 ? 1 : 4};
+    const BatchShape sh = fit_shape(BatchShape{S >= 128 ? 128 : 32, S >= 128 ? 1 : 4}, S);
     k_gradb_rows<<<bgrid(S, sh, rows), dim3((unsigned)sh.bx, (unsigned)sh.by), 0, s>>>(
         d.fanin, b.pq, tr_mode == 2 ? b.tq : b.tr_in, d.cload, b.dcl, d.net_of_user, d.cell_of_user, b.ks,
         b.gtr, gcl, gpin, gtr, d.n_nets, d.n_cells, d.n_start, S, tr_mode, ops);
@@ -421,7 +423,7 @@ void launch_gradb(const DevDesign &d, const BatchBufs &b, const OpTable &ops, in
 
 void launch_netb_user(const DevDesign &d, const BatchBufs &b, int tr_mode, float *sp, float *tr, cudaStream_t s) {
     if (!d.n_nets || (!sp && !tr)) return;
-    const BatchShape sh{b.S >= 128 ? 128 : 32, b.S >= 128 ? 1 : 4};
+    const BatchShape sh = fit_shape(BatchShape{b.S >= 128 ? 128 : 32, b.S >= 128 ? 1 : 4}, b.S);
     k_netb_user<<<bgrid(b.S, sh, d.n_nets), dim3((unsigned)sh.bx, (unsigned)sh.by), 0, s>>>(
         b.pq, tr_mode == 2 ? b.tq : b.tr_in, d.net_of_user, sp, tr, d.n_nets, d.n_start, b.S, tr_mode);
 }

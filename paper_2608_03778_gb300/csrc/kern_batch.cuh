@@ -121,6 +121,17 @@ inline void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream
     cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);   // errors surface via cudaGetLastError
 }
 
+// A shape for S scenarios: when S is below the shape's scenario width, the width
+// shrinks to the power of two covering S and the block takes more cells instead
+// (same threads per block), so a small batch does not leave most lanes of every
+// warp idle.  Each (cell, scenario) is computed the same way in any shape.
+inline BatchShape fit_shape(BatchShape sh, int64_t S) {
+    if (S <= 0 || S >= sh.bx) return sh;
+    int bx = 1;
+    while (bx < S) bx <<= 1;
+    return BatchShape{bx, sh.bx / bx * sh.by};
+}
+
 inline dim3 bgrid(int64_t S, BatchShape sh, int64_t rows) {
     const int64_t gy = bcdiv(rows > 0 ? rows : 1, sh.by);
     return dim3((unsigned)bcdiv(S, sh.bx), (unsigned)(gy < 65535 ? gy : 65535));

@@ -193,6 +193,7 @@ void launch_fwdl(const DevDesign &d, const BatchBufs &b, const OpTable &ops, con
     const int64_t S = b.S;
     if (d.n_start)
         k_fwdl_start<<<(unsigned)bcdiv(d.n_start * S, 256), 256, 0, s>>>(b.sp_in, b.tr_in, b.pq, b.tq, d.n_start * S);
+    sh = fit_shape(sh, S);
     const dim3 blk((unsigned)sh.bx, (unsigned)sh.by);
     for (int l = 1; l <= d.n_levels; l++) {
         const int32_t c0 = lvl[l - 1], c1 = lvl[l];
@@ -204,6 +205,7 @@ void launch_fwdl(const DevDesign &d, const BatchBufs &b, const OpTable &ops, con
 void launch_bwdl(const DevDesign &d, const BatchBufs &b, const OpTable &ops, const int32_t *lvl, BatchShape sh,
                  cudaStream_t s) {
     const int64_t S = b.S;
+    sh = fit_shape(sh, S);
     const dim3 blk((unsigned)sh.bx, (unsigned)sh.by);
     for (int l = d.n_levels; l >= 1; l--) {
         const int32_t c0 = lvl[l - 1], c1 = lvl[l];

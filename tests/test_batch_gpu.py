@@ -149,6 +149,27 @@ def test_shapes_give_identical_bits(dp, ctx, small):
             np.testing.assert_array_equal(g[k], results[0][k], err_msg=k)
 
 
+@pytest.mark.parametrize("tr_mode", [0, 1, 2])
+def test_narrow_batches_match_wide_ones(dp, ctx, small, tr_mode):
+    """A batch narrower than the tuned scenario width runs with the width cut to the power of
+    two covering it (more cells per block); each scenario gives the same bits as the same
+    scenario inside a wide batch."""
+    text, o = small
+    S = 70
+    sp, tr = netgen.scenario_inputs(o.n_start, 3100, S)
+    cfg = dp.config(grad_mode=0, tr_mode=tr_mode)
+    d = dp.dp_design_load(ctx, text, netgen.library_text())
+    try:
+        wide = run_batch(dp, ctx, d, sp, tr, cfg)
+        for cols in ([0], [69], [3, 4, 5], list(range(10, 27))):
+            g = run_batch(dp, ctx, d, np.ascontiguousarray(sp[:, cols]), np.ascontiguousarray(tr[:, cols]), cfg)
+            for k in g:
+                want = wide[k][:, cols] if wide[k].ndim == 2 else wide[k][cols]
+                np.testing.assert_array_equal(g[k], want, err_msg=f"{k} {cols}")
+    finally:
+        dp.dp_design_free(d)
+
+
 def test_autotuner_picks_a_candidate(dp, ctx, small):
     text, o = small
     sp, tr = netgen.scenario_inputs(o.n_start, 4000, 96)
