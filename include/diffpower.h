@@ -380,10 +380,11 @@ dp_status dp_power_noalloc(int device, const float *tr, const float *beta, const
 /* ------------------------------ request server ------------------------------
  * Several designs resident on one GPU; power and gradient requests of any of
  * them are served by continuous batching: a worker thread takes the requests
- * waiting for a design whose batch slot is free (up to max_batch, in arrival
- * order) and runs them as the scenarios of one batched pass on that design's
- * own stream, so batches of different designs overlap on the device and
- * requests that arrive meanwhile join the design's next batch.  A batch whose
+ * waiting for a design that has a free batch slot (up to max_batch, in arrival
+ * order) and runs them as the scenarios of one batched pass on that slot's
+ * own stream, so batches of different designs, and of the slots of one
+ * design, overlap on the device, and requests that arrive while every slot of
+ * their design is busy join its next batch.  A batch whose
  * requests all use the reference inputs (sizing deltas) skips the forward
  * pass: caps do not enter SP or TR, so it starts from the reference inputs'
  * forward state, computed once by dp_server_add_design.  A request's
@@ -400,6 +401,11 @@ typedef struct {
     int32_t plain;        /* 1: no worker and no batching - dp_server_submit runs the request on the
                              calling thread and returns when it is done (the one-at-a-time loop) */
     dp_config analysis;   /* vdd, fclk, tr_mode; grad_mode must be 0 */
+    int32_t slots_per_design;   /* batch slots per design, 1..8 (default 1; 0 also means 1; plain: 1).
+                                   Each slot holds its own copy of the design's device state and batch
+                                   buffers and its own stream, so batches of one design overlap (one
+                                   batch's copies beside the next one's kernels); the HBM budget is
+                                   charged for every slot */
 } dp_server_config;
 
 /* One request.  Every pointer is host memory borrowed until dp_server_wait

@@ -1,15 +1,18 @@
 // Request server: several designs resident on one GPU, analysis and gradient
 // requests of any of them served by continuous batching.
 //
-// Each design owns a CUDA stream and one batch slot.  A worker thread takes
-// the requests waiting for a design whose slot is free - up to max_batch of
-// them, in arrival order - and runs them as the scenarios of one batched pass
-// (forward, power, and the reverse pass when any of them wants gradients);
-// batches of different designs overlap on the device.  Requests that arrive
-// while a design's batch runs wait for its slot and join the next batch.
+// Each design has one request queue and one or more batch slots (one by
+// default), each slot with its own copy of the design's device state, batch buffers and
+// CUDA stream.  A worker thread takes the requests waiting for a design that
+// has a free slot - up to max_batch of them, in arrival order - and runs them
+// as the scenarios of one batched pass (forward, power, and the reverse pass
+// when any of them wants gradients); batches of different designs, and the
+// slots of one design, overlap on the device, so one batch's copies run beside
+// the next batch's kernels.  Requests that arrive while every slot of their
+// design is busy join the next batch.
 // Admission: a design is accepted only while the device bytes it needs (the
 // resident netlist plus its batch buffers for max_batch scenarios) fit in the
-// server's HBM budget.
+// server's HBM budget (for every slot of the design).
 //
 // A request carries either new startpoint SP/TR or the design's reference
 // inputs, and optionally a sizing delta (new input pin caps of some cells,
@@ -58,8 +61,11 @@ struct Req {
     dp_status status = DP_OK;
 };
 
+struct Design;
+
+// One executor of a design: its device state, batch buffers, stream and graphs.
 struct Slot {
-    int id = 0;
+    Design *des = nullptr;
     dp_ctx *ctx = nullptr;                  // owns this design's stream
     cudaStream_t stream = nullptr;
     dp_design *D = nullptr;
@@ -84,10 +90,18 @@ struct Slot {
     std::vector<std::array<cudaGraphExec_t, 4>> graphs;   // [log2 batch size][reverse pass + 2 reference inputs]
     std::vector<void *> dev, pinned;
     size_t bytes = 0;
-    std::deque<Req *> queue;
     std::vector<Req *> inflight;
     bool busy = false;
     bool batch_ref = false;   // every request of the batch in flight is on the reference inputs
+};
+
+// A resident design: its request queue and the slots that serve it.
+struct Design {
+    int id = 0;
+    int64_t ns = 0, nc = 0, nn = 0;
+    size_t bytes = 0;            // device bytes of all its slots
+    std::deque<Req *> queue;     // waiting requests, arrival order
+    std::vector<Slot *> slots;
 };
 
 }  // namespace
@@ -95,7 +109,8 @@ struct Slot {
 struct dp_server {
     dp_server_config cfg{};
     dp_ctx *ctx = nullptr;                  // for allocation bookkeeping and messages
-    std::vector<Slot *> slots;
+    std::vector<Design *> designs;
+    std::vector<Slot *> slots;          // every slot of every design
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::unordered_map<uint64_t, Req *> reqs;
@@ -358,15 +373,16 @@ void complete_batch(dp_server *srv, Slot *sl, dp_status status) {
     srv->cv_done.notify_all();
 }
 
-// Takes the next batch of a free slot (lock held): up to max_batch waiting requests in
-// arrival order.
+// Takes the next batch of a free slot (lock held): up to max_batch requests waiting for
+// its design, in arrival order.
 bool take_batch(dp_server *srv, Slot *sl) {
-    if (sl->busy || sl->queue.empty()) return false;
+    std::deque<Req *> &queue = sl->des->queue;
+    if (sl->busy || queue.empty()) return false;
     const size_t m = (size_t)srv->cfg.max_batch;
     bool ref = true;
-    while (!sl->queue.empty() && sl->inflight.size() < m) {
-        Req *q = sl->queue.front();
-        sl->queue.pop_front();
+    while (!queue.empty() && sl->inflight.size() < m) {
+        Req *q = queue.front();
+        queue.pop_front();
         q->state = 1;
         ref = ref && q->r.sp == nullptr;
         sl->inflight.push_back(q);
@@ -443,16 +459,16 @@ void worker_main(dp_server *srv) {
     }
 }
 
-// validates a request against its design's sizes (slot found under the lock; the
-// checks themselves run outside it, since resident slots are never removed)
-dp_status check_request(dp_server *srv, const dp_request *r, Slot **out) {
+// validates a request against its design's sizes (design found under the lock; the
+// checks themselves run outside it, since resident designs are never removed)
+dp_status check_request(dp_server *srv, const dp_request *r, Design **out) {
     if (!r) return srv_err(srv, DP_EINVAL, "NULL request");
-    Slot *sl = nullptr;
+    Design *sl = nullptr;
     {
         std::lock_guard<std::mutex> lk(srv->mu);
-        if (r->design < 0 || (size_t)r->design >= srv->slots.size())
+        if (r->design < 0 || (size_t)r->design >= srv->designs.size())
             return srv_err(srv, DP_EINVAL, "unknown design id " + std::to_string(r->design));
-        sl = srv->slots[(size_t)r->design];
+        sl = srv->designs[(size_t)r->design];
     }
     if ((r->sp == nullptr) != (r->tr == nullptr)) return srv_err(srv, DP_EINVAL, "give both sp and tr, or neither");
     if (r->sp) {   // branch-free scans (NaN fails every comparison)
@@ -486,6 +502,7 @@ void dp_server_config_default(dp_server_config *c) {
     c->plain = 0;
     dp_config_default(&c->analysis);
     c->analysis.grad_mode = 0;
+    c->slots_per_design = 1;
 }
 
 const char *dp_server_last_error(const dp_server *s) { return s ? s->err.c_str() : "NULL server"; }
@@ -494,11 +511,16 @@ dp_status dp_server_create(const dp_server_config *cfg, dp_server **out) {
     if (!cfg || !out) return DP_EINVAL;
     *out = nullptr;
     if (cfg->max_batch < 1 || cfg->max_batch > 4096) return DP_EINVAL;
+    if (cfg->slots_per_design < 0 || cfg->slots_per_design > 8) return DP_EINVAL;
     if (cfg->analysis.grad_mode != 0 || cfg->analysis.tr_mode < 0 || cfg->analysis.tr_mode > 1) return DP_EINVAL;
     dp_server *s = new (std::nothrow) dp_server();
     if (!s) return DP_ENOMEM;
     s->cfg = *cfg;
-    if (s->cfg.plain) s->cfg.max_batch = 1;
+    if (s->cfg.slots_per_design == 0) s->cfg.slots_per_design = 1;
+    if (s->cfg.plain) {
+        s->cfg.max_batch = 1;
+        s->cfg.slots_per_design = 1;
+    }
     dp_status st = dp_create(cfg->device, nullptr, &s->ctx);
     if (st != DP_OK) {
         delete s;
@@ -529,40 +551,26 @@ void dp_server_destroy(dp_server *s) {
     s->cv_work.notify_all();
     if (s->worker.joinable()) s->worker.join();
     for (Slot *sl : s->slots) free_slot(sl);
+    for (Design *d : s->designs) delete d;
     for (auto &kv : s->reqs) delete kv.second;
     if (s->ctx) dp_destroy(s->ctx);
     delete s;
 }
 
-dp_status dp_server_add_design(dp_server *srv, const char *netlist, size_t netlist_len, const char *library,
-                               size_t library_len, const float *ref_sp, const float *ref_tr, int32_t *id) {
-    if (!srv || !netlist || !library || !id) return srv_err(srv, DP_EINVAL, "NULL argument");
-    DeviceGuard g(srv->cfg.device);
-    dp_compiled *cp = nullptr;
-    char msg[512] = {0};
-    dp_status st = dp_compile(netlist, netlist_len, library, library_len, &cp, msg, sizeof msg);
-    if (st != DP_OK) return srv_err(srv, st, std::string("compile: ") + msg);
-    const int64_t ns = cp->n_start, nc = cp->n_cells, nn = cp->n_nets, ne = cp->n_edges;
+}  // extern "C"
+
+namespace {
+
+// Builds one slot of a design from its compiled netlist (which stays the caller's):
+// device state, batch buffers, tuned shapes, the reference inputs' forward state and
+// the batch graphs.  On failure the slot is freed and the error recorded.
+dp_status make_slot(dp_server *srv, const dp_compiled *cp, const float *ref_sp, const float *ref_tr, Slot **out) {
+    *out = nullptr;
+    const int64_t ns = cp->n_start, nc = cp->n_cells, nn = cp->n_nets;
     const int64_t S = srv->cfg.max_batch;
-    // device bytes: resident netlist (about 24 B per net, 40 per cell, 8 per edge) and batch buffers
-    const double need = 24.0 * nn + 40.0 * nc + 8.0 * ne + 72.0 * nn +
-                        (double)S * (8.0 * nn + 4.0 * ne + 16.0 * ns + 4.0 * nn + 4.0 * std::max(nn, nc) +
-                                     4.0 * (2 * ns + nc) + 8.0 * ns + 8.0 * dp::kBatchPowerChunks + 8.0 * nc +
-                                     4.0 * nn);
-    {
-        std::lock_guard<std::mutex> lk(srv->mu);
-        if ((double)srv->bytes_used + need > (double)srv->cfg.hbm_budget) {
-            dp_compiled_free(cp);
-            return srv_err(srv, DP_ENOMEM, "HBM budget: the design needs about " + std::to_string((long long)need) +
-                                               " bytes, " + std::to_string((long long)(srv->cfg.hbm_budget - srv->bytes_used)) +
-                                               " left");
-        }
-    }
+    dp_status st = DP_OK;
     Slot *sl = new (std::nothrow) Slot();
-    if (!sl) {
-        dp_compiled_free(cp);
-        return srv_err(srv, DP_ENOMEM, "out of host memory");
-    }
+    if (!sl) return srv_err(srv, DP_ENOMEM, "out of host memory");
     sl->ns = ns;
     sl->nc = nc;
     sl->nn = nn;
@@ -579,13 +587,11 @@ dp_status dp_server_add_design(dp_server *srv, const char *netlist, size_t netli
     cudaError_t e = cudaStreamCreateWithPriority(&sl->stream, cudaStreamNonBlocking, prio);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl->done, cudaEventDisableTiming);
     if (e != cudaSuccess) {
-        dp_compiled_free(cp);
         free_slot(sl);
         return srv_err(srv, DP_ECUDA, std::string("stream: ") + cudaGetErrorString(e));
     }
     st = dp_create(srv->cfg.device, sl->stream, &sl->ctx);
     if (st == DP_OK) st = dp_design_upload(sl->ctx, cp, &sl->D);
-    dp_compiled_free(cp);
     if (st != DP_OK) {
         srv_err(srv, st, sl->ctx ? dp_last_error(sl->ctx) : "context");
         free_slot(sl);
@@ -680,33 +686,95 @@ dp_status dp_server_add_design(dp_server *srv, const char *netlist, size_t netli
         return srv_err(srv, DP_ECUDA, std::string("batch graphs: ") + cudaGetErrorString(e));
     }
     sl->bytes += D->bytes + D->batch.bytes;
+    *out = sl;
+    return DP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dp_status dp_server_add_design(dp_server *srv, const char *netlist, size_t netlist_len, const char *library,
+                               size_t library_len, const float *ref_sp, const float *ref_tr, int32_t *id) {
+    if (!srv || !netlist || !library || !id) return srv_err(srv, DP_EINVAL, "NULL argument");
+    DeviceGuard g(srv->cfg.device);
+    dp_compiled *cp = nullptr;
+    char msg[512] = {0};
+    dp_status st = dp_compile(netlist, netlist_len, library, library_len, &cp, msg, sizeof msg);
+    if (st != DP_OK) return srv_err(srv, st, std::string("compile: ") + msg);
+    const int64_t ns = cp->n_start, nc = cp->n_cells, nn = cp->n_nets, ne = cp->n_edges;
+    const int64_t S = srv->cfg.max_batch;
+    const int nslots = srv->cfg.slots_per_design;
+    // device bytes per slot: resident netlist (about 24 B per net, 40 per cell, 8 per edge) and
+    // batch buffers
+    const double need = 24.0 * nn + 40.0 * nc + 8.0 * ne + 72.0 * nn +
+                        (double)S * (8.0 * nn + 4.0 * ne + 16.0 * ns + 4.0 * nn + 4.0 * std::max(nn, nc) +
+                                     4.0 * (2 * ns + nc) + 8.0 * ns + 8.0 * dp::kBatchPowerChunks + 8.0 * nc +
+                                     4.0 * nn);
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        if ((double)srv->bytes_used + nslots * need > (double)srv->cfg.hbm_budget) {
+            dp_compiled_free(cp);
+            return srv_err(srv, DP_ENOMEM, "HBM budget: the design needs about " +
+                                               std::to_string((long long)(nslots * need)) + " bytes, " +
+                                               std::to_string((long long)(srv->cfg.hbm_budget - srv->bytes_used)) +
+                                               " left");
+        }
+    }
+    Design *des = new (std::nothrow) Design();
+    if (!des) {
+        dp_compiled_free(cp);
+        return srv_err(srv, DP_ENOMEM, "out of host memory");
+    }
+    des->ns = ns;
+    des->nc = nc;
+    des->nn = nn;
+    size_t charged = 0;
+    for (int k = 0; k < nslots && st == DP_OK; k++) {
+        Slot *sl = nullptr;
+        st = make_slot(srv, cp, ref_sp, ref_tr, &sl);
+        if (st != DP_OK) break;
+        sl->des = des;
+        des->slots.push_back(sl);
+        des->bytes += sl->bytes;
+        charged += (size_t)std::max(need, (double)sl->bytes);
+    }
+    dp_compiled_free(cp);
+    if (st != DP_OK) {
+        for (Slot *sl : des->slots) free_slot(sl);
+        delete des;
+        return st;
+    }
     std::lock_guard<std::mutex> lk(srv->mu);
-    sl->id = (int)srv->slots.size();
-    srv->slots.push_back(sl);
-    srv->bytes_used += (size_t)std::max(need, (double)sl->bytes);
-    *id = sl->id;
+    des->id = (int)srv->designs.size();
+    srv->designs.push_back(des);
+    for (Slot *sl : des->slots) srv->slots.push_back(sl);
+    srv->bytes_used += charged;
+    *id = des->id;
     return DP_OK;
 }
 
 dp_status dp_server_design_info(dp_server *srv, int32_t id, dp_info *info) {
     if (!srv || !info) return DP_EINVAL;
     std::lock_guard<std::mutex> lk(srv->mu);
-    if (id < 0 || (size_t)id >= srv->slots.size()) return srv_err(srv, DP_EINVAL, "unknown design id");
-    dp_status st = dp_design_info(srv->slots[(size_t)id]->D, info);
-    info->device_bytes = srv->slots[(size_t)id]->bytes;
+    if (id < 0 || (size_t)id >= srv->designs.size()) return srv_err(srv, DP_EINVAL, "unknown design id");
+    const Design *des = srv->designs[(size_t)id];
+    dp_status st = dp_design_info(des->slots[0]->D, info);
+    info->device_bytes = des->bytes;
     return st;
 }
 
 dp_status dp_server_submit(dp_server *srv, const dp_request *r, uint64_t *ticket) {
     if (!srv || !ticket) return DP_EINVAL;
-    Slot *sl = nullptr;
-    const dp_status st = check_request(srv, r, &sl);
+    Design *des = nullptr;
+    const dp_status st = check_request(srv, r, &des);
     if (st != DP_OK) return st;
     Req *q = new (std::nothrow) Req();
     if (!q) return srv_err(srv, DP_ENOMEM, "out of host memory");
     q->r = *r;
     q->t_submit = now_s();
     if (srv->cfg.plain) {   // one request at a time on the calling thread
+        Slot *sl = des->slots[0];
         std::unique_lock<std::mutex> lk(srv->mu);
         q->ticket = srv->next_ticket++;
         srv->reqs[q->ticket] = q;
@@ -727,7 +795,7 @@ dp_status dp_server_submit(dp_server *srv, const dp_request *r, uint64_t *ticket
         std::lock_guard<std::mutex> lk(srv->mu);
         q->ticket = srv->next_ticket++;
         srv->reqs[q->ticket] = q;
-        sl->queue.push_back(q);
+        des->queue.push_back(q);
         *ticket = q->ticket;
         srv->queued.fetch_add(1, std::memory_order_acq_rel);
     }
@@ -761,7 +829,7 @@ dp_status dp_server_get_stats(dp_server *srv, dp_server_stats *out) {
     std::lock_guard<std::mutex> lk(srv->mu);
     *out = srv->stats;
     out->device_bytes = srv->bytes_used;
-    out->designs = (int32_t)srv->slots.size();
+    out->designs = (int32_t)srv->designs.size();
     return DP_OK;
 }
 

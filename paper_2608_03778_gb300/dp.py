@@ -57,7 +57,7 @@ class dp_compiled_view(ctypes.Structure):
 
 class dp_server_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("hbm_budget", ctypes.c_size_t),
-                ("plain", ctypes.c_int32), ("analysis", dp_config)]
+                ("plain", ctypes.c_int32), ("analysis", dp_config), ("slots_per_design", ctypes.c_int32)]
 
 
 class dp_request(ctypes.Structure):

@@ -194,6 +194,32 @@ def test_plain_mode_gives_the_same_bits(dp, server, texts):
             np.testing.assert_array_equal(x, y)
 
 
+def test_two_slots_per_design_give_the_same_bits(dp, server, texts):
+    """Two batch slots per design (two copies of its device state, batches of one design
+    overlapping): every result bitwise equal to the one-slot server's."""
+    srv1, ids, infos, refs = server
+    srv2 = dp.dp_server_create(dp.server_config(max_batch=16, slots_per_design=2))
+    try:
+        lib = netgen.library_text()
+        for k, ref in zip(DESIGNS, refs):
+            dp.dp_server_add_design(srv2, texts[k], lib, *ref)
+        st = dp.dp_server_get_stats(srv2)
+        assert st.designs == len(DESIGNS)
+        info2 = dp.dp_server_design_info(srv2, ids[0])
+        assert info2.device_bytes > infos[0].device_bytes
+        jobs = make_jobs(dp, ids, infos, 120, 77, refs)
+        run(dp, srv2, jobs)
+        two = [j.result() for j in jobs]
+        run(dp, srv1, jobs, together=False)
+        for a, b in zip(two, [j.result() for j in jobs]):
+            for x, y in zip(a, b):
+                np.testing.assert_array_equal(x, y)
+    finally:
+        dp.dp_server_destroy(srv2)
+    with pytest.raises(dp.DPError):
+        dp.dp_server_create(dp.server_config(slots_per_design=9))
+
+
 def test_budget_admission_and_errors(dp, texts):
     lib = netgen.library_text()
     srv = dp.dp_server_create(dp.server_config(max_batch=8, hbm_budget=32 << 20))
