@@ -24,9 +24,9 @@
 // bit for bit).  The delta enters the batch as a
 // per-scenario change of C_load on the nets those cells load, so requests with
 // different deltas share a batch.  Every (cell, scenario) is computed alone,
-// the power sums of a scenario run in a fixed order, and the launch shapes are
-// fixed per design, so a request's results do not depend on the requests it
-// is batched with.
+// by the same arithmetic in any launch shape, and the power sums of a scenario
+// run in a fixed order, so a request's results do not depend on the requests
+// it is batched with, nor on the batch size.
 #include <algorithm>
 #include <array>
 #include <atomic>
