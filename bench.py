@@ -464,6 +464,24 @@ def bench_serving(args, dp, torch, dev) -> dict:
         dp.dp_server_destroy(plain)
 
 
+def serving_in_child(device: int) -> dict:
+    """The serving measurement in a fresh interpreter on the same GPU: its own CUDA
+    context, threads and host allocations, so that nothing the earlier measurements
+    leave in this process enters its latencies (repeated in one process, the Poisson
+    latencies grew from run to run)."""
+    drop = {"RANK", "WORLD_SIZE", "LOCAL_RANK", "LOCAL_WORLD_SIZE", "GROUP_RANK", "ROLE_RANK",
+            "MASTER_ADDR", "MASTER_PORT", "TORCHELASTIC_RUN_ID"}
+    env = {k: v for k, v in os.environ.items() if k not in drop}
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--serving-only", "--device", str(device)],
+                       env=env, capture_output=True, text=True, timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError(f"serving measurement failed ({r.returncode}): {r.stderr[-2000:]}")
+    for line in r.stdout.splitlines():
+        if line.startswith("{"):
+            return json.loads(line)
+    raise RuntimeError("serving measurement printed no result")
+
+
 def bench_adjoint_vs_fd(dp, torch, dev) -> dict:
     """Gradient of the model power with respect to every startpoint SP of the 120,000-cell
     netlist: the GPU adjoint (compile + upload + forward + reverse pass, wall clock, as the
@@ -540,7 +558,15 @@ def main() -> None:
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-scenario measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the request-server measurement")
     ap.add_argument("--no-fd", action="store_true", help="skip the adjoint-vs-finite-difference timing")
+    ap.add_argument("--serving-only", action="store_true", help=argparse.SUPPRESS)   # the child of serving_in_child
+    ap.add_argument("--device", type=int, default=0, help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.serving_only:
+        import torch
+        torch.cuda.set_device(args.device)
+        from paper_2608_03778_gb300 import dp
+        print(json.dumps(bench_serving(args, dp, torch, torch.device("cuda", args.device))), flush=True)
+        return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local = int(os.environ.get("LOCAL_RANK", 0))
@@ -700,8 +726,8 @@ def main() -> None:
     dp.dp_destroy(ctx)
     if not args.no_batched:
         line["batched"] = bench_batched(args, dp, torch, dev, pk)
-    if not args.no_serving:
-        line["serving"] = bench_serving(args, dp, torch, dev)
+    if rank == 0 and not args.no_serving:
+        line["serving"] = serving_in_child(local)
     if rank == 0 and world == 1 and not args.no_fd:
         line["adjoint_vs_fd"] = bench_adjoint_vs_fd(dp, torch, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
