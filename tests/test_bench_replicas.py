@@ -55,3 +55,14 @@ def test_single_rank_is_identity():
     import bench
     assert bench.max_over_ranks(3.25, 1) == 3.25
     bench.barrier(1)
+
+
+def test_serving_child_failure_is_reported():
+    """The serving measurement runs in a child interpreter; without a GPU that child exits
+    non-zero, and the parent raises with the child's error instead of returning a result."""
+    import bench
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present: the child would run the real measurement")
+    with pytest.raises(RuntimeError, match="serving measurement failed"):
+        bench.serving_in_child(0)
