@@ -686,7 +686,8 @@ def main() -> None:
         "power_w": {"model": float(watts[0]), "hybrid": float(watts[1])},
         "e2e": {"value": nc * world / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": int(kernels),
+        "gpu_launches": int(kernels) * args.steps,   # kernel nodes of the step graph x timed steps
+        "gpu_launches_per_step": int(kernels),
         "clocks": clocks,
         "device_bytes": int(info.device_bytes),
     }
