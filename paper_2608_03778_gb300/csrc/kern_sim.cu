@@ -144,32 +144,36 @@ __device__ __forceinline__ uint64_t chain_block16(ChainState &c, uint32_t k, int
 // Fast form of the same chains when every threshold of the warp is below 2^16
 // (no probability of exactly 1): a 16-bit draw d is compared in the high half
 // of a 32-bit word against thr << 16, which holds whatever the low half is, so
-// the high-half draws need no extraction.  Each lane keeps its state s and the
-// threshold of that state; a flip toggles both (the threshold between t10 and
-// t01 by one XOR).  Ones and toggles are counted from the finished words.
+// the high-half draws need no extraction.  Each lane keeps only the threshold
+// of its current state (t10 in state 1, t01 in state 0; a flip toggles it by
+// one XOR).  The warp votes on the flips, and the cycle's word is the previous
+// word XOR the flip word, so no lane state is formed.  Ones and toggles are
+// counted from the finished words.
 struct FastChain {
     uint32_t thr[4];
-    bool s[4];
+    uint64_t word;   // lane states of the previous cycle (this half-warp's startpoint)
 };
 
 // one cycle on draws d[r] (in the high half); FIRST draws the initial state
 template <bool FIRST>
 __device__ __forceinline__ uint64_t fast_cycle(FastChain &c, const uint32_t (&d)[4], uint32_t ti16, uint32_t t10_16,
                                                uint32_t t01_16, uint32_t sel) {
+    bool b[4];   // FIRST: the initial state; else: a flip
 #pragma unroll
     for (int r = 0; r < 4; r++) {
         if (FIRST) {
-            c.s[r] = d[r] < ti16;
-            c.thr[r] = c.s[r] ? t10_16 : t01_16;
+            b[r] = d[r] < ti16;
+            c.thr[r] = b[r] ? t10_16 : t01_16;
         } else {
-            const bool f = d[r] < c.thr[r];
-            c.s[r] ^= f;
-            c.thr[r] ^= f ? (t10_16 ^ t01_16) : 0u;
+            b[r] = d[r] < c.thr[r];
+            c.thr[r] ^= b[r] ? (t10_16 ^ t01_16) : 0u;
         }
     }
-    const uint32_t b0 = __ballot_sync(0xFFFFFFFFu, c.s[0]), b1 = __ballot_sync(0xFFFFFFFFu, c.s[1]);
-    const uint32_t b2 = __ballot_sync(0xFFFFFFFFu, c.s[2]), b3 = __ballot_sync(0xFFFFFFFFu, c.s[3]);
-    return (uint64_t)__byte_perm(b0, b1, sel) | ((uint64_t)__byte_perm(b2, b3, sel) << 32);
+    const uint32_t b0 = __ballot_sync(0xFFFFFFFFu, b[0]), b1 = __ballot_sync(0xFFFFFFFFu, b[1]);
+    const uint32_t b2 = __ballot_sync(0xFFFFFFFFu, b[2]), b3 = __ballot_sync(0xFFFFFFFFu, b[3]);
+    const uint64_t w = (uint64_t)__byte_perm(b0, b1, sel) | ((uint64_t)__byte_perm(b2, b3, sel) << 32);
+    c.word = FIRST ? w : c.word ^ w;
+    return c.word;
 }
 
 template <bool FIRST>
@@ -177,7 +181,9 @@ __device__ __forceinline__ uint64_t fast_block16(FastChain &c, uint32_t k, int t
                                                  uint32_t key1, uint32_t ti16, uint32_t t10_16, uint32_t t01_16,
                                                  uint32_t sel) {
     uint64_t mine = 0;
-#pragma unroll
+    // unrolled by 4, not 8: fully unrolled, the compiler keeps several calls' draws live
+    // (124 registers); at 4 the kernel needs 48 and more warps fit on an SM
+#pragma unroll 4
     for (int i = 0; i < 8; i++) {
         const uint4 u = philox4x32_10(make_uint4(k, (uint32_t)((t0 >> 1) + i), (uint32_t)q, 0u), key0, key1);
         const uint32_t lo[4] = {u.x << 16, u.y << 16, u.z << 16, u.w << 16};
