@@ -245,3 +245,15 @@ def test_abi_struct_layouts_match_the_header(tmp_path):
         cls = structs[name]
         want = ctypes.sizeof(cls) if field == "size" else getattr(cls, field).offset
         assert int(value) == want, (name, field)
+
+
+def test_server_config_checked_before_any_device_call():
+    """dp_server_create rejects a bad configuration with DP_EINVAL before it touches a device
+    (so this runs without a GPU); the defaults are 64 requests per batch and one slot."""
+    c = dp.server_config()
+    assert c.max_batch == 64 and c.slots_per_design == 1 and c.plain == 0 and c.analysis.grad_mode == 0
+    for bad in [dict(max_batch=0), dict(max_batch=4097), dict(slots_per_design=9), dict(slots_per_design=-1),
+                dict(analysis=dp.config(grad_mode=1)), dict(analysis=dp.config(tr_mode=2))]:
+        with pytest.raises(dp.DPError) as e:
+            dp.dp_server_create(dp.server_config(**bad))
+        assert e.value.name == "DP_EINVAL", bad
