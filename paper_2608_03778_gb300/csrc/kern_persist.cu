@@ -352,7 +352,9 @@ __global__ void __launch_bounds__(kSimThreads, 2) k_sim_wide(const uint4 *__rest
                     cell_bits_lop3(lut, a0, a1, w[0], w[1]);
                     cell_bits_lop3(lut, b0, b1, w[2], w[3]);
                 } else {
-                    // 4-input cells: two words at a time through the multiplexer tree
+                    // 4-input cells: the two cofactors in x3 by LOP3 (tables tt & 0xFF and
+                    // tt >> 8 over x2, x1, x0), then a select by x3.  No leaf words: the
+                    // multiplexer tree's 16 leaves made the kernel spill at its 64 registers
 #pragma unroll
                     for (int h2 = 0; h2 < 2; h2++) {
                         uint64_t x0[4] = {0, 0, 0, 0}, x1[4] = {0, 0, 0, 0};
@@ -364,8 +366,11 @@ __global__ void __launch_bounds__(kSimThreads, 2) k_sim_wide(const uint4 *__rest
                                 x0[j] = a.x;
                                 x1[j] = a.y;
                             }
-                        w[2 * h2] = bits_eval<4>(tt, x0);
-                        w[2 * h2 + 1] = bits_eval<4>(tt, x1);
+                        uint64_t f00, f01, f10, f11;
+                        cell_bits_lop3(tt & 0xFFu, x0, x1, f00, f01);
+                        cell_bits_lop3((tt >> 8) & 0xFFu, x0, x1, f10, f11);
+                        w[2 * h2] = (x0[3] & f10) | (~x0[3] & f00);
+                        w[2 * h2 + 1] = (x1[3] & f11) | (~x1[3] & f01);
                     }
                 }
                 const uint64_t prev = __shfl_up_sync(0xFFFFFFFFu, w[3], 1, 16);
