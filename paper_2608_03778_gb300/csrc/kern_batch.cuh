@@ -129,7 +129,8 @@ inline BatchShape fit_shape(BatchShape sh, int64_t S) {
     if (S <= 0 || S >= sh.bx) return sh;
     int bx = 1;
     while (bx < S) bx <<= 1;
-    return BatchShape{bx, sh.bx / bx * sh.by};
+    if (bx >= sh.bx) return sh;   // a width that is no power of two (set by hand) and S above its half
+    return BatchShape{bx, sh.bx * sh.by / bx};
 }
 
 inline dim3 bgrid(int64_t S, BatchShape sh, int64_t rows) {
