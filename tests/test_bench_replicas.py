@@ -66,3 +66,21 @@ def test_serving_child_failure_is_reported():
         pytest.skip("a GPU is present: the child would run the real measurement")
     with pytest.raises(RuntimeError, match="serving measurement failed"):
         bench.serving_in_child(0)
+
+
+def test_traffic_is_reported_only_for_its_workload_and_sources():
+    """A stored DRAM-traffic figure comes back only for the workload it was captured on and
+    while its kernel's source files still hash to the recorded value; otherwise null."""
+    import hashlib
+
+    import bench
+    assert bench.TRAFFIC, "no stored traffic figures"
+    for kernel, t in bench.TRAFFIC.items():
+        m = hashlib.sha256()
+        for name in t["files"]:
+            with open(os.path.join(bench.ROOT, "paper_2608_03778_gb300", "csrc", name), "rb") as f:
+                m.update(f.read())
+        current = m.hexdigest()[:16] == t["sha"]
+        assert bench.kernel_traffic(kernel, t["workload"]) == (t["bytes"] if current else None)
+        assert bench.kernel_traffic(kernel, t["workload"] + "_other") is None
+    assert bench.kernel_traffic("no_such_kernel", "roofline") is None
