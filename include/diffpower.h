@@ -201,6 +201,15 @@ dp_status dp_sync(dp_ctx *ctx);
  * No GPU fault is involved. */
 dp_status dp_selftest_wait(dp_ctx *ctx, double seconds);
 
+/* Test hook on the calling thread's CUDA runtime error state (the library's
+ * own runtime, linked statically).  action 1 plants a launch-configuration
+ * error: a kernel launch with zero threads per block, which the runtime
+ * rejects on the host, so no work reaches the GPU.  action 2 takes (reads and
+ * clears) the pending error; action 0 only reads it.  *pending (may be NULL)
+ * receives the cudaError_t code pending after the action (before the clear,
+ * for action 2).  Any other action returns DP_EINVAL. */
+dp_status dp_selftest_pending_error(int action, int32_t *pending);
+
 /* Compiles (as dp_compile) and uploads a netlist; the design keeps its whole
  * graph and per-net state resident in device memory (Sec. III). */
 dp_status dp_design_load(dp_ctx *ctx, const char *netlist, size_t netlist_len, const char *library,
@@ -368,11 +377,16 @@ dp_status dp_step_kernels(const dp_design *d, int64_t *kernels);
  *    bad device or non-positive vdd/fclk return DP_EINVAL.
  *  - The first call on a device looks up the scratch array's device address
  *    (with that device made current) and caches it; make that first call
- *    before any stream capture.
+ *    before any stream capture.  The cached address belongs to the device's
+ *    primary context: do not call this after cudaDeviceReset() of that device
+ *    in the same process.
  *  - Every call shares the scratch and overwrites the partials it reads
  *    (nothing needs clearing); calls that overlap on the GPU (other streams,
  *    other threads) race on it and must be serialised by the caller.
  *  - The summation order is fixed, so results are reproducible.
+ *  - DP_ECUDA comes only from this call's own runtime calls and launches: a
+ *    launch error the caller left pending on the calling thread is neither
+ *    reported as this call's result nor cleared.
  *  - There is no context, so dp_last_error() has no message for this call. */
 dp_status dp_power_noalloc(int device, const float *tr, const float *beta, const float *cload, int64_t n,
                            double vdd, double fclk, double *watts, void *cuda_stream);

@@ -114,8 +114,47 @@ void free_design(dp_design *D) {
     for (auto &e : D->ev)
         if (e) cudaEventDestroy(e);
     free_batch(D);
+    if (D->pc_done) cudaEventDestroy(D->pc_done);
+    if (D->pc_cells) cudaFree(D->pc_cells);
+    if (D->pc_caps) cudaFree(D->pc_caps);
     for (void *p : D->allocs) cudaFree(p);
     delete D;
+}
+
+// Staging for n host sizing-delta entries: grows (with headroom) only when n exceeds what is
+// held; the old buffers are freed after the stream that last read them is done.
+dp_status reserve_pincap_staging(dp_design *D, int64_t n) {
+    dp_ctx *c = D->ctx;
+    if (!D->pc_done) {
+        cudaError_t e = cudaEventCreateWithFlags(&D->pc_done, cudaEventDisableTiming);
+        if (e != cudaSuccess) { D->pc_done = nullptr; return cuda_err(c, e, "dp_set_pincap"); }
+    }
+    if (n <= D->pc_cap) return DP_OK;
+    int64_t want = std::max<int64_t>(n, std::max<int64_t>(1024, 2 * D->pc_cap));
+    want = std::min<int64_t>(want, std::max<int64_t>(n, D->d.n_cells));
+    if (D->pc_cells || D->pc_caps) {
+        cudaEventSynchronize(D->pc_done);
+        cudaFree(D->pc_cells);
+        cudaFree(D->pc_caps);
+        D->bytes -= (sizeof(int32_t) + sizeof(float)) * (size_t)D->pc_cap;
+        D->pc_cells = nullptr;
+        D->pc_caps = nullptr;
+        D->pc_cap = 0;
+    }
+    std::vector<void *> got;
+    size_t bytes = 0;
+    void *a = nullptr, *b = nullptr;
+    dp_status s = alloc_into(c, &a, sizeof(int32_t) * (size_t)want, &got, &bytes);
+    if (s == DP_OK) s = alloc_into(c, &b, sizeof(float) * (size_t)want, &got, &bytes);
+    if (s != DP_OK) {
+        for (void *p : got) cudaFree(p);
+        return s;
+    }
+    D->pc_cells = static_cast<int32_t *>(a);
+    D->pc_caps = static_cast<float *>(b);
+    D->pc_cap = want;
+    D->bytes += bytes;
+    return DP_OK;
 }
 
 dp_status ensure_words(dp_design *D, int T) {
@@ -374,6 +413,18 @@ dp_status dp_selftest_wait(dp_ctx *c, double seconds) {
     return check_device_error(c);
 }
 
+namespace {
+__global__ void k_zero_threads() {}
+}  // namespace
+
+dp_status dp_selftest_pending_error(int action, int32_t *pending) {
+    if (action < 0 || action > 2) return DP_EINVAL;
+    if (action == 1) k_zero_threads<<<1, 0>>>();   // invalid configuration, rejected on the host
+    const cudaError_t e = action == 2 ? cudaGetLastError() : cudaPeekAtLastError();
+    if (pending) *pending = (int32_t)e;
+    return DP_OK;
+}
+
 dp_status dp_design_upload(dp_ctx *ctx, const dp_compiled *cp, dp_design **out) {
     if (!ctx || !cp || !out) return set_err(ctx, DP_EINVAL, "NULL argument");
     *out = nullptr;
@@ -600,22 +651,22 @@ dp_status dp_set_pincap(dp_design *D, const int32_t *cells, const float *caps, i
     DeviceGuard g(c->device);
     int32_t *dc = nullptr;
     float *dv = nullptr;
-    std::vector<void *> tmp;
     cudaError_t e = cudaSuccess;
     if (!on_device) {
         for (int32_t i = 0; i < n; i++)
             if ((cells && (cells[i] < 0 || cells[i] >= D->d.n_cells)) || !(caps[i] >= 0.f) || !std::isfinite(caps[i]))
                 return set_err(c, DP_EINVAL, "cell index or pin cap out of range");
-        if (cells) e = cudaMallocAsync((void **)&dc, sizeof(int32_t) * (size_t)n, c->stream);
-        if (e == cudaSuccess) e = cudaMallocAsync((void **)&dv, sizeof(float) * (size_t)n, c->stream);
+        // the design's own staging, grown on demand: a sizing loop allocates nothing per call
+        dp_status rs = reserve_pincap_staging(D, n);
+        if (rs != DP_OK) return rs;
+        e = cudaStreamWaitEvent(c->stream, D->pc_done, 0);   // the previous delta's kernels are done
         if (e == cudaSuccess && cells)
-            e = cudaMemcpyAsync(dc, cells, sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, c->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(dv, caps, sizeof(float) * (size_t)n, cudaMemcpyHostToDevice, c->stream);
-        if (e != cudaSuccess) {
-            if (dc) cudaFreeAsync(dc, c->stream);
-            if (dv) cudaFreeAsync(dv, c->stream);
-            return cuda_err(c, e, "dp_set_pincap");
-        }
+            e = cudaMemcpyAsync(D->pc_cells, cells, sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(D->pc_caps, caps, sizeof(float) * (size_t)n, cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess) return cuda_err(c, e, "dp_set_pincap");
+        dc = cells ? D->pc_cells : nullptr;
+        dv = D->pc_caps;
     } else {
         dc = const_cast<int32_t *>(cells);
         dv = const_cast<float *>(caps);
@@ -624,9 +675,9 @@ dp_status dp_set_pincap(dp_design *D, const int32_t *cells, const float *caps, i
     dp::launch_cload(D->d, c->stream);
     D->bwd_valid = false;   // the local gradient terms depend on the loads
     dp_status s = launch_check(c, "dp_set_pincap");
-    if (!on_device) {
-        if (dc) cudaFreeAsync(dc, c->stream);
-        cudaFreeAsync(dv, c->stream);
+    if (!on_device && s == DP_OK) {
+        e = cudaEventRecord(D->pc_done, c->stream);
+        if (e != cudaSuccess) s = cuda_err(c, e, "dp_set_pincap");
     }
     // loads changed: the powers and gradients must be recomputed (SP and TR stay valid)
     return s;

@@ -65,6 +65,12 @@ struct dp_design {
     bool sim_valid = false;
     bool bwd_valid = false;        // gnet holds the adjoint of the current state
     int bwd_grad_mode = -1;
+    // staging of host sizing deltas (dp_set_pincap): grown on demand, never shrunk; pc_done is
+    // recorded after the kernels that read it, so a later call waits for them on any stream
+    int32_t *pc_cells = nullptr;
+    float *pc_caps = nullptr;
+    int64_t pc_cap = 0;
+    cudaEvent_t pc_done = nullptr;
     // sizing-score scratch (lazy): scores [n_cells], candidates [n_cells], histogram [256] + count
     float *sc_scores = nullptr;
     int32_t *sc_idx = nullptr;

@@ -80,11 +80,11 @@ extern "C" dp_status dp_power_noalloc(int device, const float *tr, const float *
     if (!(vdd > 0) || !(fclk > 0) || !std::isfinite(vdd) || !std::isfinite(fclk)) return DP_EINVAL;
     if (n > (int64_t)kMaxBlocks * kChunk) return DP_EUNSUPPORTED;  // beyond the scratch capacity
     int ndev = 0;
-    if (cudaGetDeviceCount(&ndev) != cudaSuccess) { cudaGetLastError(); return DP_ECUDA; }
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) return DP_ECUDA;
     if (device < 0 || device >= ndev || device >= kMaxDevices) return DP_EINVAL;
     int prev = -1;
-    if (cudaGetDevice(&prev) != cudaSuccess) { cudaGetLastError(); return DP_ECUDA; }
-    if (prev != device && cudaSetDevice(device) != cudaSuccess) { cudaGetLastError(); return DP_ECUDA; }
+    if (cudaGetDevice(&prev) != cudaSuccess) return DP_ECUDA;
+    if (prev != device && cudaSetDevice(device) != cudaSuccess) return DP_ECUDA;
     dp_status st = DP_OK;
     double *scratch = nullptr;
     {
@@ -94,7 +94,6 @@ extern "C" dp_status dp_power_noalloc(int device, const float *tr, const float *
         if (!g_scratch[device]) {
             void *p = nullptr;
             if (cudaGetSymbolAddress(&p, g_partials) != cudaSuccess) {
-                cudaGetLastError();
                 st = DP_ECUDA;
             } else {
                 g_scratch[device] = static_cast<double *>(p);
@@ -103,11 +102,24 @@ extern "C" dp_status dp_power_noalloc(int device, const float *tr, const float *
         scratch = g_scratch[device];
     }
     if (st == DP_OK) {
+        // Each launch's own status decides the result.  An error the caller left pending on
+        // this thread is neither reported as this call's nor cleared, so the caller still
+        // finds it with cudaGetLastError().
         cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
         const int nb = (int)((n + kChunk - 1) / kChunk);
-        if (nb > 0) k_partials<<<nb, kThreads, 0, s>>>(tr, beta, cload, n, scratch);
-        k_final<<<1, kThreads, 0, s>>>(scratch, nb, 0.5 * vdd * vdd * fclk * 1e-15, watts);
-        if (cudaGetLastError() != cudaSuccess) st = DP_ECUDA;
+        const double K = 0.5 * vdd * vdd * fclk * 1e-15;
+        if (nb > 0) {
+            void *args[] = {(void *)&tr, (void *)&beta, (void *)&cload, (void *)&n, (void *)&scratch};
+            if (cudaLaunchKernel((const void *)k_partials, dim3(nb), dim3(kThreads), args, 0, s) != cudaSuccess)
+                st = DP_ECUDA;
+        }
+        if (st == DP_OK) {
+            const double *partials = scratch;
+            int nblocks = nb;
+            void *args[] = {(void *)&partials, (void *)&nblocks, (void *)&K, (void *)&watts};
+            if (cudaLaunchKernel((const void *)k_final, dim3(1), dim3(kThreads), args, 0, s) != cudaSuccess)
+                st = DP_ECUDA;
+        }
     }
     if (prev >= 0 && prev != device) cudaSetDevice(prev);
     return st;

@@ -97,6 +97,7 @@ _sig("dp_create", [ctypes.c_int, _P, ctypes.POINTER(_P)])
 _sig("dp_destroy", [_P], None)
 _sig("dp_sync", [_P])
 _sig("dp_selftest_wait", [_P, ctypes.c_double])
+_sig("dp_selftest_pending_error", [ctypes.c_int, ctypes.POINTER(ctypes.c_int32)])
 _sig("dp_design_load", [_P, ctypes.c_char_p, ctypes.c_size_t, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(_P)])
 _sig("dp_design_upload", [_P, _P, ctypes.POINTER(_P)])
 _sig("dp_design_free", [_P], None)
@@ -140,7 +141,8 @@ EXPORTED = ["dp_config_default", "dp_last_error", "dp_compile", "dp_compiled_fre
             "dp_compiled_view_get", "dp_compile_function", "dp_create", "dp_destroy", "dp_sync", "dp_design_load",
             "dp_design_upload", "dp_design_free", "dp_design_info", "dp_set_inputs", "dp_set_pincap",
             "dp_propagate", "dp_simulate", "dp_total_power", "dp_backward", "dp_get_nets", "dp_step",
-            "dp_phase_times", "dp_step_kernels", "dp_power_noalloc", "dp_selftest_wait", "dp_set_stream",
+            "dp_phase_times", "dp_step_kernels", "dp_power_noalloc", "dp_selftest_wait",
+            "dp_selftest_pending_error", "dp_set_stream",
             "dp_get_power", "dp_set_inputs_batch", "dp_batch_tuning", "dp_backward_weighted", "dp_ascent_step",
             "dp_virus_eval", "dp_sizing_scores", "dp_server_config_default", "dp_server_create", "dp_server_destroy",
             "dp_server_last_error", "dp_server_add_design", "dp_server_design_info", "dp_server_submit",
@@ -276,6 +278,14 @@ def dp_sync(ctx) -> None:
 
 def dp_selftest_wait(ctx, seconds: float) -> None:
     _check(_lib.dp_selftest_wait(ctx, seconds), ctx)
+
+
+def dp_selftest_pending_error(action: int) -> int:
+    """0: read the library runtime's pending CUDA error code; 1: plant a host-side launch
+    configuration error first; 2: read and clear it."""
+    code = ctypes.c_int32(0)
+    _check(_lib.dp_selftest_pending_error(action, ctypes.byref(code)))
+    return int(code.value)
 
 
 def dp_design_load(ctx, netlist: str, library: str):

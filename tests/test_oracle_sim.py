@@ -141,3 +141,38 @@ def test_hybrid_special_cases(library_text):
     assert beta[0] == 10.0 and trh[0] == 0.0
     assert beta[1] == 0.1                       # clipped below
     assert beta[2] == 4.0 and trh[2] == 1.0     # TR_acc / TR_model = 1 / 0.25
+
+
+def test_flip_probabilities_below_the_draw_resolution(library_text):
+    """Reading R7 draws 16-bit numbers against floor(p 2^16): a flip probability in (0, 2^-16)
+    rounds to threshold 0 and never fires, so a chain whose p10 and p01 both lie there keeps its
+    initial bits (toggles 0) and its beta is beta_min (TR_model > 0, TR_acc = 0); a probability of
+    exactly 2^-16 keeps threshold 1, i.e. fires with probability 2^-16 per draw (binomial count
+    over 4,096 chains)."""
+    n = 4096
+    lines = [f"net i{k} 1" for k in range(n)] + ["net y 1"] + [f"input i{k}" for k in range(n)]
+    lines.append("cell u BUF_X1 A=i0 Z=y")
+    o = Oracle("\n".join(lines) + "\n", library_text)
+    sn = o.start_nets()
+    below = np.nextafter(np.float32(2.0 ** -16), np.float32(0))
+    sp = np.full(n, 0.5, np.float32)
+    tr = np.full(n, below, np.float32)          # p10 = p01 = tr / (2 * 0.5) = tr < 2^-16
+    tg, on, words = o.simulate(sp, tr, 5, 64, want_words=True)
+    assert (tg[sn] == 0).all()
+    assert (words[sn] == words[sn][:, :1]).all()     # every lane keeps its initial bit
+    z = zscores(on[sn].astype(float) / 64, np.full(n, 64.0), np.full(n, 0.5))
+    assert np.abs(z).max() < 5.5                 # initial states still Bernoulli(SP)
+    _, trm = o.forward(sp, tr)
+    beta, trh = o.hybrid(trm, tg, 64, 0.1, 10.0)
+    np.testing.assert_array_equal(beta[sn], 0.1)
+    # exactly 2^-16: 4,096 chains x 64 lanes x 63 steps draws, each a flip with probability 2^-16
+    tr[:] = np.float32(2.0 ** -16)
+    tg, on = o.simulate(sp, tr, 5, 64)
+    draws = n * 64 * 63
+    z = (tg[sn].sum() - draws * 2.0 ** -16) / np.sqrt(draws * 2.0 ** -16)
+    assert tg[sn].sum() > 0 and abs(z) < 5.5
+    # SP below 2^-16: the initial state is always 0 as well
+    sp[:] = np.float32(1e-5)
+    tr[:] = np.float32(1e-5)                     # p01 = 5e-6
+    tg, on = o.simulate(sp, tr, 5, 64)
+    assert (tg[sn] == 0).all() and (on[sn] == 0).all()

@@ -142,6 +142,82 @@ def test_roofline_full_size(dp, ctx, library_text):
     check_against_oracle(o, g, sp[:, 0], tr[:, 0], cfg)
 
 
+def test_roofline_fwd_bwd_model(dp, ctx, library_text):
+    """The 2M-cell netlist through dp_propagate + dp_backward with the model gradient (grad_mode 0)
+    on device buffers: the forward + reverse pass the benchmark times alone (first with the
+    startpoint SP gradient only, as timed, then with every gradient output)."""
+    text = netgen.netlist_text(netgen.WORKLOADS["roofline"])
+    o = Oracle(text, library_text)
+    sp, tr = netgen.scenario_inputs(o.n_start, 1000)
+    sp, tr = np.ascontiguousarray(sp[:, 0]), np.ascontiguousarray(tr[:, 0])
+    cfg = dp.config(grad_mode=0)
+    dev = torch.device("cuda")
+    d = dp.dp_design_load(ctx, text, library_text)
+    try:
+        info = dp.dp_design_info(d)
+        ns, nc, nn = info.n_start, info.n_cells, info.n_nets
+        dp.dp_set_inputs(ctx, d, torch.from_numpy(sp).to(dev), torch.from_numpy(tr).to(dev), 1, 1)
+        g = {k: torch.zeros(n, device=dev) for k, n in
+             [("grad_sp_in", ns), ("grad_tr_in", ns), ("grad_pincap", nc), ("grad_cload", nn)]}
+        for _ in range(2):
+            dp.dp_propagate(ctx, d, cfg)
+            dp.dp_backward(ctx, d, cfg, g["grad_sp_in"], None, None, None, 1)
+        torch.cuda.synchronize()
+        only_sp = g["grad_sp_in"].cpu().numpy()
+        p_model = dp.dp_total_power(ctx, d, 0)
+        dp.dp_backward(ctx, d, cfg, g["grad_sp_in"], g["grad_tr_in"], g["grad_pincap"], g["grad_cload"], 1)
+        torch.cuda.synchronize()
+        out = {k: v.cpu().numpy() for k, v in g.items()}
+        net_sp, net_tr = np.zeros(nn, np.float32), np.zeros(nn, np.float32)
+        dp.dp_get_nets(ctx, d, net_sp, net_tr, None, None, None, None)
+    finally:
+        dp.dp_design_free(d)
+    sp_ref, tr_ref = o.forward(sp, tr, 0)
+    assert np.abs(net_sp - sp_ref).max() <= 1e-5
+    assert np.abs(net_tr - tr_ref).max() <= 1e-5
+    assert p_model == pytest.approx(o.power(tr_ref), rel=1e-6)
+    ref = o.backward(sp, tr, None, 0, 0)
+    np.testing.assert_array_equal(only_sp, out["grad_sp_in"])
+    for k in ["grad_sp_in", "grad_tr_in", "grad_pincap", "grad_cload"]:
+        assert grad_close(out[k], ref[k]), k
+
+
+def test_mid_exact_hybrid_gradient(dp, ctx, library_text):
+    """grad_mode 2 (exact gradient of the hybrid power with beta held fixed) on the 120K-cell
+    netlist through dp_step with device buffers."""
+    text = netgen.netlist_text(netgen.WORKLOADS["mid"])
+    o = Oracle(text, library_text)
+    sp, tr = netgen.scenario_inputs(o.n_start, 1000)
+    cfg = dp.config(grad_mode=2)
+    g = gpu_run(dp, ctx, text, library_text, sp[:, 0], tr[:, 0], cfg, use_step=True, on_device=True)
+    check_against_oracle(o, g, sp[:, 0], tr[:, 0], cfg)
+
+
+def test_flip_probabilities_below_the_draw_resolution(dp, ctx, library_text):
+    """Startpoints whose p10 or p01 lies in (0, 2^-16) get a zero threshold (reading R7): their
+    chains never flip that way, so a startpoint with both below never toggles and its beta is
+    beta_min (TR_model > 0, TR_acc = 0).  A probability of exactly 2^-16 keeps threshold 1.  GPU
+    and oracle agree bit for bit on the counts and on beta."""
+    text = netgen.netlist_text(netgen.WORKLOADS["small"])
+    o = Oracle(text, library_text)
+    sp, tr = netgen.scenario_inputs(o.n_start, 1000)
+    sp, tr = sp[:, 0].copy(), tr[:, 0].copy()
+    tiny = [(0.5, 1e-5),                     # p10 = p01 = 1e-5
+            (1e-5, 1e-5),                    # initial state always 0, p01 = 5e-6
+            (0.99999, 1e-5),                 # p10 = 5e-6, p01 = 0.5
+            (0.5, 2.0 ** -16),               # p10 = p01 = 2^-16 exactly: threshold 1
+            (0.5, np.nextafter(np.float32(2.0 ** -16), np.float32(0)))]   # just below: threshold 0
+    for k, (a, b) in enumerate(tiny):
+        sp[k], tr[k] = np.float32(a), np.float32(b)
+    cfg = dp.config()
+    g = gpu_run(dp, ctx, text, library_text, sp, tr, cfg)
+    ref = check_against_oracle(o, g, sp, tr, cfg)
+    nets = o.start_nets()
+    for k in (0, 1, 4):
+        assert ref["toggles"][nets[k]] == 0 and g["toggles"][nets[k]] == 0
+        assert g["beta"][nets[k]] == pytest.approx(cfg.beta_min)
+
+
 @pytest.mark.parametrize("other_schedule", [0, 1, 3])
 def test_step_is_deterministic(dp, ctx, library_text, other_schedule):
     """Two runs, and the persistent and per-level schedules, agree bit for bit."""
@@ -287,12 +363,19 @@ def test_sizing_delta(dp, ctx, library_text):
     sp, tr = netgen.scenario_inputs(o.n_start, 1000)
     cfg = dp.config(grad_mode=0)
     rng = np.random.default_rng(8)
-    cells = rng.choice(o.n_cells, 20, replace=False).astype(np.int32)
-    caps = rng.choice([1.6, 3.2], 20).astype(np.float32)
+    # deltas in several calls; the third outgrows the design's staging, the fourth reuses it
+    deltas = []
+    for m in (5, 15, 1500, 40):
+        cells = rng.choice(o.n_cells, m, replace=False).astype(np.int32)
+        deltas.append((cells, rng.choice([0.8, 1.6, 3.2], m).astype(np.float32)))
     d = dp.dp_design_load(ctx, text, library_text)
     try:
         dp.dp_set_inputs(ctx, d, sp[:, 0].copy(), tr[:, 0].copy())
-        dp.dp_set_pincap(ctx, d, cells, caps)
+        sizes = []
+        for cells, caps in deltas:
+            dp.dp_set_pincap(ctx, d, cells, caps)
+            sizes.append(dp.dp_design_info(d).device_bytes)
+        assert sizes[0] == sizes[1] and sizes[2] > sizes[1] and sizes[3] == sizes[2]
         dp.dp_propagate(ctx, d, cfg)
         p = dp.dp_total_power(ctx, d, 0)
         gsp = np.zeros(o.n_start, np.float32)
@@ -300,8 +383,9 @@ def test_sizing_delta(dp, ctx, library_text):
         dp.dp_backward(ctx, d, cfg, gsp, None, gpin, None)
     finally:
         dp.dp_design_free(d)
-    for c, v in zip(cells, caps):
-        o.set_pincap(int(c), float(v))
+    for cells, caps in deltas:
+        for c, v in zip(cells, caps):
+            o.set_pincap(int(c), float(v))
     rsp, rtr = o.forward(sp[:, 0], tr[:, 0])
     assert p == pytest.approx(o.power(rtr), rel=1e-6)
     ref = o.backward(sp[:, 0], tr[:, 0])

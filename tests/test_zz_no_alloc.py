@@ -1,14 +1,17 @@
 """dp_power_noalloc: the power reduction for callers that cannot allocate device memory (a host
 framework that owns every device byte through its own pool, or a service that plans its memory
 ahead and must not let a cudaMalloc synchronise the device).  Its scratch is a fixed array in the
-library's device memory.  Checked through the C-ABI against dp_total_power on the same nets, on
-two calls in a row, within the power tolerance of the other GPU tests (1e-6 relative).
+library's device memory.  Checked through the C-ABI on two calls in a row, within the power
+tolerance of the other GPU tests (1e-6 relative), against dp_total_power on the same nets and
+against the FP64 oracle's power (Eq. 1) of the oracle's own TR and beta; device free memory must
+not change across calls after the first, and an error the caller left pending must survive a call.
 
 This file is collected last on purpose: if it fails, a run that stops at the first failure has
 already run every other test."""
 import numpy as np
 import pytest
 
+from oracle.oracle import Oracle
 from paper_2608_03778_gb300 import netgen
 from tests import _gates as G
 
@@ -62,7 +65,13 @@ def test_noalloc_power_matches_total_power(name, library_text):
         dp.dp_get_nets(ctx, d, None, tr_d, beta_d, None, None, None, 1)
         cl_d = torch.from_numpy(cload_user(text, library_text)).to(dev)
         watts = torch.zeros(2, dtype=torch.float64, device=dev)
-        for _ in range(2):   # two calls in a row share the scratch
+        # the oracle's powers (Eq. 1) from its own forward pass, simulation and beta
+        o = Oracle(text, library_text)
+        ref = o.step(np.ascontiguousarray(sp[:, 0]), np.ascontiguousarray(tr[:, 0]), seed=cfg.seed,
+                     T=cfg.sim_words, grad_mode=0)
+        np.testing.assert_allclose(cl_d.cpu().numpy(), o.cload(), rtol=1e-6)
+        free_after_first = None
+        for i in range(4):   # calls in a row share the scratch
             watts.fill_(-1.0)
             dp.dp_power_noalloc(0, tr_d, None, cl_d, nn, cfg.vdd, cfg.fclk, watts[0:1], stream)
             dp.dp_power_noalloc(0, tr_d, beta_d, cl_d, nn, cfg.vdd, cfg.fclk, watts[1:2], stream)
@@ -70,6 +79,13 @@ def test_noalloc_power_matches_total_power(name, library_text):
             got = watts.cpu().numpy()
             assert got[0] == pytest.approx(want_model, rel=1e-6)
             assert got[1] == pytest.approx(want_hyb, rel=1e-6)
+            assert got[0] == pytest.approx(ref["power_model"], rel=1e-6)
+            assert got[1] == pytest.approx(ref["power_hybrid"], rel=1e-6)
+            # after the first call (which may load the kernels' code) no call takes device memory
+            free = torch.cuda.mem_get_info(0)[0]
+            if free_after_first is None:
+                free_after_first = free
+            assert free == free_after_first
     finally:
         dp.dp_design_free(d)
         dp.dp_destroy(ctx)
@@ -90,3 +106,24 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     dp.dp_power_noalloc(0, x, None, x, 0, 0.8, 1e9, w)   # empty: writes 0
     torch.cuda.synchronize()
     assert w.item() == 0.0
+
+
+def test_noalloc_leaves_a_pending_error_alone():
+    """An error the caller left pending on this thread (a launch the runtime rejected on the host;
+    nothing reached the GPU) is neither this call's result nor cleared by it."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2608_03778_gb300 import dp
+    w = torch.zeros(1, dtype=torch.float64, device="cuda")
+    x = torch.ones(1000, device="cuda")
+    dp.dp_selftest_pending_error(2)
+    code = dp.dp_selftest_pending_error(1)
+    try:
+        assert code != 0
+        dp.dp_power_noalloc(0, x, None, x, 1000, 0.8, 1e9, w)   # must not raise
+        torch.cuda.synchronize()
+        assert w.item() == pytest.approx(0.5 * 0.8 * 0.8 * 1e9 * 1e-15 * 1000, rel=1e-12)
+        assert dp.dp_selftest_pending_error(0) == code
+    finally:
+        dp.dp_selftest_pending_error(2)
+    assert dp.dp_selftest_pending_error(0) == 0
