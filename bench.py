@@ -44,27 +44,49 @@ def peaks() -> dict:
     return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
+def fanin_bytes(nc: int, ne: int) -> int:
+    """Compact fanin CSR: row pointers, fanin net ids, one opcode byte per cell."""
+    return 4 * (nc + 1) + 4 * ne + nc
+
+
+def fanout_bytes(nn: int, ne: int) -> int:
+    """Compact fanout CSR: row pointers and edge ids."""
+    return 4 * (nn + 1) + 4 * ne
+
+
+def fwd_bwd_bytes(nn: int, ns: int, nc: int, ne: int) -> dict:
+    """Compulsory bytes of one forward + reverse pass with the model gradient, every structure or
+    value array read or written once (int32 indices, binary32 values; repeated gathers and the edge
+    adjoints not counted).  Forward: fanin CSR, startpoint SP and TR in, C_load in, SP and TR of
+    every net out.  Reverse: fanin CSR, SP and C_load in, fanout CSR, the adjoint of every net
+    written, the pin-cap gradient of every cell and the SP and TR gradients of every startpoint out."""
+    fwd = fanin_bytes(nc, ne) + 8 * ns + 4 * nn + 8 * nn
+    bwd = fanin_bytes(nc, ne) + 4 * nn + 4 * nn + fanout_bytes(nn, ne) + 4 * nn + 4 * nc + 8 * ns
+    return {"forward": fwd, "backward": bwd, "total": fwd + bwd}
+
+
 def algorithmic_bytes(nn: int, ns: int, nc: int, ne: int, T: int) -> dict:
-    """Compulsory bytes per phase: every structure or value array read or written once,
-    int32 indices, binary32 values, compact CSR (4(nc+1) + 4E + nc bytes of fanin structure);
-    repeated gathers and intermediates (edge adjoints) not counted."""
-    fanin = 4 * (nc + 1) + 4 * ne + nc
-    fanout = 4 * (nn + 1) + 4 * ne
+    """Compulsory bytes per phase of the step (same counting as fwd_bwd_bytes)."""
+    fb = fwd_bwd_bytes(nn, ns, nc, ne)
     return {
-        # inputs, fanin structure, C_load, SP and TR out
-        "forward": fanin + 8 * ns + 4 * nn + 8 * nn,
-        # the bitwise cells: fanin structure, every net's words read once, every cell's words
-        # written once, toggles + ones of every cell written
-        "simulation": fanin + 8 * T * nn + 8 * T * nc + 8 * nc,
+        "forward": fb["forward"],
+        # generator: startpoint SP and TR in, their words out; cells: fanin CSR, every fanin word
+        # read once, every cell's words written once; toggles + ones of every net written
+        "simulation": 8 * ns + 8 * T * ns + fanin_bytes(nc, ne) + 8 * T * nn + 8 * T * nc + 8 * nn,
         # TR_model and toggles read, beta and hybrid TR written, C_load read for the power
         "hybrid": 4 * nn * 5,
-        # fanin + fanout structure, SP, C_load, beta read; adjoint per net written; beside it the
-        # gradient outputs into staging: grad_cload (TR, beta in, out), grad_pincap (structure,
-        # out), grad_tr_in (beta, C_load in, out)
-        "backward": fanin + fanout + 4 * nn * 3 + 4 * nn + 12 * nn + fanin + 4 * nc + 12 * ns,
+        # the reverse pass with the paper's beta rule (beta read) and the gradient outputs of the step:
+        # the pass's compulsory bytes, beta, and the C_load gradient (hybrid TR in, gradient out)
+        "backward": fb["backward"] + 4 * nn + 8 * nn,
         # outputs: the four gradient arrays copied into the caller's buffers (read + write)
         "outputs": 8 * (2 * ns + nc + nn),
     }
+
+
+def sim_bytes(nn: int, ns: int, nc: int, ne: int, T: int) -> int:
+    """The simulation pass alone: every net's words written once and read once (T uint64 per
+    net), the fanin CSR, and toggles + ones of every net written."""
+    return 2 * 8 * T * nn + fanin_bytes(nc, ne) + 8 * nn
 
 
 def batched_algorithmic_bytes(nn: int, ns: int, nc: int, ne: int, S: int) -> int:
@@ -83,14 +105,27 @@ def batched_algorithmic_bytes(nn: int, ns: int, nc: int, ne: int, S: int) -> int
 # still hash to the value it was taken with; otherwise the traffic is unknown
 # (null).
 TRAFFIC = {
-    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (one pass), 2M-cell step, 4th step
-    "k_sim_wide": {"bytes": 232_209_920 + 174_487_808, "workload": "roofline",
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,lts__t_bytes.sum,... (one launch),
+    # 2M-cell step, 4th step (profiles/roofline_step_k_sim_wide_traffic.md)
+    "k_sim_wide": {"bytes": 224_548_608 + 162_620_416, "l2_bytes": 7_807_160_736, "workload": "roofline",
                    "files": ["kern_persist.cu", "kern_common.cuh"],
-                   "sha": "3f98159b756effd3"},
-    "k_bwd_persist": {"bytes": 127_277_568 + 11_832_832, "workload": "roofline",
-                      "files": ["kern_persist.cu", "kern_common.cuh"],
-                      "sha": "3f98159b756effd3"},
+                   "sha": "f0daa1842f2960d9"},
 }
+
+
+# L2 <-> SM throughput ceiling for the L2 fraction of the dominant kernel: ncu's peak of
+# lts__t_bytes on this part (summarised with the capture under profiles/); None until measured.
+L2_PEAK_GBS = 36_205.0
+L2_PEAK_SOURCE = ("ncu on k_sim_wide, 2M-cell step: lts__t_bytes.sum.per_second 11,466 GB/s at "
+                  "lts__t_bytes.sum.pct_of_peak_sustained_elapsed 31.67 %")
+
+
+def kernel_l2_bytes(kernel: str, workload: str) -> int | None:
+    """lts__t_bytes of one launch, under the same conditions as kernel_traffic."""
+    t = TRAFFIC.get(kernel)
+    if not t or "l2_bytes" not in t or L2_PEAK_GBS is None or kernel_traffic(kernel, workload) is None:
+        return None
+    return int(t["l2_bytes"])
 
 
 def kernel_traffic(kernel: str, workload: str) -> int | None:
@@ -181,31 +216,77 @@ def workload(name: str):
     return spec, lib, text, np.ascontiguousarray(sp[:, 0]), np.ascontiguousarray(tr[:, 0])
 
 
-def cpu_baseline(text: str, lib: str, sp, tr, n_cells: int, T: int) -> dict:
-    """The FP64 oracle, as it stands, single-threaded, on one full step of the same workload."""
-    from oracle.oracle import Oracle
+def host_cpu() -> dict:
+    """Host cores and CPU model of this machine (nproc and /proc/cpuinfo)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k = line.split(":")[0].strip().lower()
+                if k in ("model name", "cpu model", "hardware") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if model is None:
+        import platform
+        model = platform.processor() or platform.machine()
+    return {"nproc": os.cpu_count(), "cpu_model": model}
+
+
+def bench_config(name: str, spec, world: int) -> dict:
+    """The `config` object of both arms: the workload and what one step does."""
+    return {
+        "workload": f"{name}: {spec.n_cells} cells, {spec.n_start} startpoints ({spec.n_pi} PI + {spec.n_dff} "
+                    f"DFF), depth {spec.depth}, fanout cap {spec.fanout_cap}, seed {spec.seed}",
+        "step": "forward SP/TR + power, 4,096-vector simulation, hybrid beta + power, adjoint "
+                "(grad_mode 1) with all gradient outputs",
+        "global_batch": 1, "parallelism": f"replicas x{world}",
+        "l2": "256 MB buffer written before every timed step (outside the step's events)",
+    }
+
+
+def oracle_step_times(o, sp, tr, T: int, reps: int, parallel: bool) -> list[float]:
+    """Seconds of `reps` full steps of the FP64 oracle (forward, power, simulation, hybrid, adjoint
+    with the paper's beta rule and every gradient output), timed outright."""
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        o.step(sp, tr, seed=42, T=T, grad_mode=1, parallel=parallel)
+        ts.append(time.perf_counter() - t0)
+    return ts
+
+
+def cpu_baseline(text: str, lib: str, sp, tr, n_cells: int, T: int, reps: int = 5) -> dict:
+    """The FP64 oracle, as it stands, on full steps of the same workload: single-threaded (the
+    paper's CPU comparator), median of `reps`; beside it the oracle's level-parallel variant on all
+    host cores (OpenMP), median of `reps`."""
+    from oracle.oracle import Oracle, threads
     o = Oracle(text, lib)
-    t0 = time.perf_counter()
-    o.step(sp, tr, seed=42, T=T, grad_mode=1)
-    dt = time.perf_counter() - t0
-    return {"value": n_cells / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one full step (forward, power, {64 * T}-vector simulation, hybrid, adjoint) of the same "
-                      f"netlist, {dt:.1f} s, single thread"}
+    t1 = oracle_step_times(o, sp, tr, T, reps, parallel=False)
+    tp = oracle_step_times(o, sp, tr, T, reps, parallel=True)
+    m1, mp = statistics.median(t1), statistics.median(tp)
+    host = host_cpu()
+    return {"value": n_cells / m1, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"full steps (forward, power, {64 * T}-vector simulation, hybrid, adjoint) of the same "
+                      f"netlist, median of {reps}: {m1:.2f} s, single thread",
+            "step_s": t1, **host,
+            "all_cores": {"value": n_cells / mp, "unit": UNIT, "cores": threads(), "kind": "oracle, level-parallel",
+                          "sample": f"the same full steps with the oracle's level-parallel variant (OpenMP), "
+                                    f"median of {reps}: {mp:.2f} s", "step_s": tp}}
 
 
-REFERENCE_BUDGET_S = 150.0   # the whole --impl reference run, warm-up included
+REFERENCE_BUDGET_S = 120.0   # the whole --impl reference run, warm-up included
 
 
 def run_reference(args, rank: int, world: int) -> None:
-    """Reference arm: the FP64 CPU oracle on the host cores, rank 0 only.
+    """Reference arm: the FP64 CPU oracle as it stands, single-threaded, rank 0 only.
 
-    Each step is a bounded sample of the workload: the same generator recipe (startpoint
-    shares, depth, fanout cap, seed) at a cell count chosen so that the warm-up and timed
-    steps together take about REFERENCE_BUDGET_S on this host (the oracle's rate, measured
-    on a 20,000-cell draw first, sets it).  The oracle's work per cell does not grow with the
-    netlist, so cells/s on the sample stands for the full workload; a smaller draw fits the
-    host caches better, so the sample if anything flatters the oracle (about 1.6x against the
-    full 2M-cell netlist)."""
+    Each step is one full step of the oracle (forward, power, 4,096-vector simulation, hybrid,
+    adjoint with every gradient output), timed outright, on a bounded sample of the workload: the
+    same generator recipe (startpoint shares, depth, fanout cap, seed) at a cell count chosen so
+    that the warm-up and timed steps together take about REFERENCE_BUDGET_S on this host (the
+    oracle's rate on a 20,000-cell draw sets it; the full netlist when it fits)."""
     if rank != 0:
         return
     from dataclasses import replace
@@ -214,55 +295,149 @@ def run_reference(args, rank: int, world: int) -> None:
     from paper_2608_03778_gb300 import netgen
     full = netgen.WORKLOADS[args.workload]
     lib = netgen.library_text()
-    T, T_sample = 64, 8
+    T = 64
 
     def draw(n_cells: int):
-        f = n_cells / full.n_cells
-        spec = replace(full, n_cells=n_cells, n_pi=max(8, round(full.n_pi * f)), n_dff=max(8, round(full.n_dff * f)),
-                       depth=max(2, min(full.depth, n_cells // 16)))
+        if n_cells >= full.n_cells:
+            spec = full
+        else:
+            f = n_cells / full.n_cells
+            spec = replace(full, n_cells=n_cells, n_pi=max(8, round(full.n_pi * f)),
+                           n_dff=max(8, round(full.n_dff * f)), depth=max(2, min(full.depth, n_cells // 16)))
         text = netgen.netlist_text(spec)
         sp, tr = netgen.scenario_inputs(spec.n_start, 1000)
         return spec, Oracle(text, lib), np.ascontiguousarray(sp[:, 0]), np.ascontiguousarray(tr[:, 0])
 
-    def one(o, sp, tr):
-        t0 = time.perf_counter()
-        s, t = o.forward(sp, tr, 0)
-        o.power(t)
-        t1 = time.perf_counter()
-        tg, _ = o.simulate(sp, tr, 42, T_sample)
-        beta, trh = o.hybrid(t, tg, T_sample)
-        o.power(trh)
-        t2 = time.perf_counter()
-        o.backward(sp, tr, beta, 1, 0)
-        t3 = time.perf_counter()
-        return (t1 - t0) + (t3 - t2) + (t2 - t1) * (T / T_sample)
-
     probe_spec, o, sp, tr = draw(min(20_000, full.n_cells))
-    rate = probe_spec.n_cells / one(o, sp, tr)
+    rate = probe_spec.n_cells / min(oracle_step_times(o, sp, tr, T, 2, parallel=False))
     per_step = REFERENCE_BUDGET_S / max(1, args.steps + args.warmup)
-    n = int(min(full.n_cells, max(probe_spec.n_cells, rate * per_step)))
+    n = int(min(full.n_cells, max(probe_spec.n_cells, 0.9 * rate * per_step)))
     spec, o, sp, tr = (probe_spec, o, sp, tr) if n == probe_spec.n_cells else draw(n)
 
-    for _ in range(args.warmup):
-        one(o, sp, tr)
-    ts = [one(o, sp, tr) for _ in range(args.steps)]
+    oracle_step_times(o, sp, tr, T, args.warmup, parallel=False)
+    ts = oracle_step_times(o, sp, tr, T, args.steps, parallel=False)
     ms = 1e3 * sum(ts) / len(ts)
     val = spec.n_cells / (ms / 1e3)
+    sample = "the full netlist" if spec is full else (
+        f"a {spec.n_cells}-cell draw of the same recipe ({spec.n_start} startpoints, depth {spec.depth})")
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{args.workload}: {full.n_cells} cells, {full.n_start} startpoints, depth "
-                               f"{full.depth}", "sim_vectors": 64 * T},
+        "config": bench_config(args.workload, full, world),
         "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"per step: forward, power and adjoint of a {spec.n_cells}-cell draw of the same "
-                                   f"recipe ({spec.n_start} startpoints, depth {spec.depth}), plus its simulation "
-                                   f"at {64 * T_sample} vectors with the time scaled by {T // T_sample} to "
-                                   f"{64 * T} vectors; sized for about {REFERENCE_BUDGET_S:.0f} s in all; "
-                                   f"single thread"},
+                         "sample": f"per step: one full step of the FP64 oracle (forward, power, {64 * T}-vector "
+                                   f"simulation, hybrid, adjoint with every gradient output) on {sample}, timed "
+                                   f"outright; sized for about {REFERENCE_BUDGET_S:.0f} s in all; single thread",
+                         "step_ms_median": 1e3 * statistics.median(ts), **host_cpu()},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def pct(ts, q: float) -> float:
+    return float(np.percentile(np.asarray(ts, np.float64), q))
+
+
+def timed_reps(fn, stream, flush, reps: int) -> list[float]:
+    """CUDA-event milliseconds of `reps` calls of fn on `stream`; with a flush buffer, L2 is flushed
+    by writing it before each call, outside the events."""
+    import torch
+    out = []
+    for i in range(reps):
+        if flush is not None:
+            flush.fill_(float(i))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return out
+
+
+def rep_stats(ts) -> dict:
+    return {"median_ms": statistics.median(ts), "p10_ms": pct(ts, 10), "p90_ms": pct(ts, 90), "reps": len(ts)}
+
+
+def fwd_bwd_record(dp, ctx, d, stream, flush, reps: int, pk: dict) -> dict:
+    """dp_propagate + dp_backward with the model gradient and the compulsory outputs (SP and TR
+    gradients of the startpoints, pin-cap gradients), L2 flushed and warm, median of `reps`."""
+    import torch
+    info = dp.dp_design_info(d)
+    nn, ns, nc, ne = info.n_nets, info.n_start, info.n_cells, info.n_edges
+    dev = torch.device("cuda", torch.cuda.current_device())
+    gsp, gtr, gpin = (torch.zeros(n, device=dev) for n in (ns, ns, nc))
+    cfg0 = dp.config(grad_mode=0)
+
+    def fn():
+        dp.dp_propagate(ctx, d, cfg0)
+        dp.dp_backward(ctx, d, cfg0, gsp, gtr, gpin, None, 1)
+
+    for _ in range(5):
+        fn()
+    torch.cuda.synchronize()
+    cold = timed_reps(fn, stream, flush, reps)
+    warm = timed_reps(fn, stream, None, reps)
+    fb = fwd_bwd_bytes(nn, ns, nc, ne)
+    ms, wms = statistics.median(cold), statistics.median(warm)
+    return {"ms": ms, **{k: v for k, v in rep_stats(cold).items() if k != "median_ms"},
+            "cell_evals_per_s": nc / (ms * 1e-3),
+            "algorithmic_bytes": fb["total"], "achieved_gbs": fb["total"] / (ms * 1e-3) / 1e9,
+            "frac": fb["total"] / (ms * 1e-3) / 1e9 / pk["hbm_gbs"],
+            "warm_l2": {**rep_stats(warm), "cell_evals_per_s": nc / (wms * 1e-3),
+                        "frac": fb["total"] / (wms * 1e-3) / 1e9 / pk["hbm_gbs"]},
+            "levels": 2 * int(info.n_levels),
+            "what": "dp_propagate + dp_backward (grad_mode 0; startpoint SP/TR and pin-cap gradients out); "
+                    "L2 flushed before each repetition (warm_l2: not flushed); median"}
+
+
+def bench_config_passes(dp, torch, dev, name: str, reps: int, pk: dict, with_sim: bool) -> dict:
+    """One single-scenario workload: forward + reverse pass (fwd_bwd_record), and with `with_sim`
+    the 4,096-vector simulation alone (generator + bitwise levels, then beta + hybrid power) with
+    its own roofline; L2 flushed and warm."""
+    spec, lib, text, sp, tr = workload(name)
+    stream = torch.cuda.current_stream()
+    ctx = dp.dp_create(dev.index or 0, stream.cuda_stream)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    try:
+        d = dp.dp_design_load(ctx, text, lib)
+        try:
+            info = dp.dp_design_info(d)
+            nn, ns, nc, ne = info.n_nets, info.n_start, info.n_cells, info.n_edges
+            dp.dp_set_inputs(ctx, d, sp, tr)
+            out = {"workload": f"{name}: {nc} cells, {ns} startpoints ({spec.n_pi} PI + {spec.n_dff} DFF), depth "
+                               f"{info.n_levels}, seed {spec.seed}",
+                   "fwd_bwd": fwd_bwd_record(dp, ctx, d, stream, flush, reps, pk)}
+            out["fwd_bwd"]["us"] = 1e3 * out["fwd_bwd"]["ms"]
+            if with_sim:
+                cfg = dp.config()
+                dp.dp_propagate(ctx, d, cfg)
+                sim = lambda: dp.dp_simulate(ctx, d, cfg)  # noqa: E731
+                for _ in range(5):
+                    sim()
+                torch.cuda.synchronize()
+                res = {}
+                for key, fl in (("cold", flush), ("warm_l2", None)):
+                    ts, ph = [], []
+                    for i in range(reps):
+                        ts += timed_reps(sim, stream, fl, 1)
+                        ph.append(dp.dp_phase_times(ctx, d))
+                    ph = np.median(np.stack(ph), axis=0)
+                    b = sim_bytes(nn, ns, nc, ne, cfg.sim_words)
+                    res[key] = {**rep_stats(ts), "levels_ms": float(ph[1]), "hybrid_ms": float(ph[2]),
+                                "achieved_gbs": b / (float(ph[1]) * 1e-3) / 1e9,
+                                "frac": b / (float(ph[1]) * 1e-3) / 1e9 / pk["hbm_gbs"]}
+                out["simulation"] = {"vectors": 64 * cfg.sim_words, "algorithmic_bytes": b,
+                                     "roofline": "hbm, on the generator + bitwise levels time (levels_ms)",
+                                     **res["cold"], "warm_l2": res["warm_l2"],
+                                     "what": "dp_simulate: Philox Markov startpoints + bitwise levels with PopCount "
+                                             "(levels_ms), then beta + hybrid power (hybrid_ms)"}
+        finally:
+            dp.dp_design_free(d)
+    finally:
+        dp.dp_destroy(ctx)
+    return out
 
 
 def bench_batched(args, dp, torch, dev, pk: dict) -> dict:
@@ -299,15 +474,9 @@ def bench_batched(args, dp, torch, dev, pk: dict) -> dict:
         for _ in range(args.warmup):
             fwd_bwd()
         torch.cuda.synchronize()
-        ts = []
-        for i in range(max(args.steps, 5)):
-            flush.fill_(float(i))
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            fwd_bwd()
-            e1.record()
-            torch.cuda.synchronize()
-            ts.append(e0.elapsed_time(e1))
+        stream = torch.cuda.current_stream()
+        ts = timed_reps(fwd_bwd, stream, flush, max(args.steps, 20))
+        warm = timed_reps(fwd_bwd, stream, None, max(args.steps, 20))
         ms = statistics.median(ts)
         fwd_shape, bwd_shape, tune_ms = dp.dp_batch_tuning(des.d)
         ab = batched_algorithmic_bytes(nn, ns, nc, ne, S)
@@ -324,8 +493,10 @@ def bench_batched(args, dp, torch, dev, pk: dict) -> dict:
         out = {
             "workload": f"mid: {nc} cells, {ns} startpoints, depth {L}, seed {spec.seed}; {S} scenarios "
                         f"(SP ~ U[0.1, 0.9], TR ~ U[0, 2 min(SP, 1-SP)], seeds 1000..{1000 + S - 1})",
-            "fwd_bwd_ms": ms, "fwd_bwd_ms_p10_p90": [float(np.percentile(ts, 10)), float(np.percentile(ts, 90))],
+            "fwd_bwd_ms": ms, "fwd_bwd_ms_p10_p90": [pct(ts, 10), pct(ts, 90)],
             "cell_evals_per_s": nc * S / (ms * 1e-3),
+            "warm_l2": {**rep_stats(warm), "cell_evals_per_s": nc * S / (statistics.median(warm) * 1e-3),
+                        "frac": ab / (statistics.median(warm) * 1e-3) / 1e9 / pk["hbm_gbs"]},
             "roofline": {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
                          "frac": ach / pk["hbm_gbs"], "algorithmic_bytes": ab, "traffic": None,
                          "kernels": "k_fwdb_level / k_bwdb_level per level, k_powerb_*"},
@@ -558,6 +729,8 @@ def main() -> None:
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-scenario measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the request-server measurement")
     ap.add_argument("--no-fd", action="store_true", help="skip the adjoint-vs-finite-difference timing")
+    ap.add_argument("--no-configs", action="store_true", help="skip the 2K- and 120K-cell single-scenario timings")
+    ap.add_argument("--no-probe", action="store_true", help="skip the level-latency probe")
     ap.add_argument("--serving-only", action="store_true", help=argparse.SUPPRESS)   # the child of serving_in_child
     ap.add_argument("--device", type=int, default=0, help=argparse.SUPPRESS)
     args = ap.parse_args()
@@ -620,6 +793,8 @@ def main() -> None:
     ms = max_over_ranks(sum(step_ms) / len(step_ms), world)
     ph = np.median(np.stack(phases), axis=0)
     kernels = dp.dp_step_kernels(d)
+    # the same steps with L2 warm (no flush between them): what a re-propagation loop sees
+    warm_ms = timed_reps(step, stream, None, max(args.steps, 5))
     dp.dp_step(ctx, d, cfg, g["sp"], g["tr"], g["pin"], g["cl"], watts, 1)
 
     # ---- end to end through the C-ABI with pinned host buffers
@@ -654,7 +829,16 @@ def main() -> None:
         per_phase[n] = {"ms": float(ph[i]), "algorithmic_bytes": ab[n], "achieved_gbs": ach,
                         "frac": ach / pk["hbm_gbs"]}
     dom = max(["forward", "simulation", "backward"], key=lambda n: per_phase[n]["ms"])
-    fb_ms = max(per_phase["forward"]["ms"] + per_phase["backward"]["ms"], 1e-9)
+    roof = {"bound": "hbm", "kernel": f"{kernel_of[dom]} ({dom}, one cooperative launch per step)",
+            "achieved": per_phase[dom]["achieved_gbs"], "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": per_phase[dom]["frac"], "traffic": kernel_traffic(kernel_of[dom], args.workload),
+            "algorithmic_bytes": ab[dom], "peak_source": pk["source"]}
+    l2b = kernel_l2_bytes(kernel_of[dom], args.workload)
+    if l2b is not None:
+        # L2 <-> SM bytes of the same launch against the L2 bandwidth measured on this part
+        roof["l2"] = {"bytes": l2b, "achieved_gbs": l2b / (per_phase[dom]["ms"] * 1e-3) / 1e9,
+                      "peak_gbs": L2_PEAK_GBS, "frac": l2b / (per_phase[dom]["ms"] * 1e-3) / 1e9 / L2_PEAK_GBS,
+                      "peak_source": L2_PEAK_SOURCE}
     line = {
         "metric": METRIC,
         "value": nc * world / (ms / 1e3),
@@ -668,21 +852,10 @@ def main() -> None:
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": {
-            "workload": f"{args.workload}: {nc} cells, {ns} startpoints ({spec.n_pi} PI + {spec.n_dff} DFF), "
-                        f"depth {info.n_levels}, fanout cap {spec.fanout_cap}, seed {spec.seed}",
-            "step": "forward SP/TR + power, 4,096-vector simulation, hybrid beta + power, adjoint "
-                    "(grad_mode 1) with all gradient outputs",
-            "global_batch": 1, "parallelism": f"replicas x{world}",
-            "l2": "256 MB buffer written before every timed step (outside the step's events)",
-        },
-        "roofline": {"bound": "hbm", "kernel": f"{kernel_of[dom]} ({dom}, one cooperative launch per step)",
-                     "achieved": per_phase[dom]["achieved_gbs"], "peak": pk["hbm_gbs"], "unit": "GB/s",
-                     "frac": per_phase[dom]["frac"], "traffic": kernel_traffic(kernel_of[dom], args.workload),
-                     "algorithmic_bytes": ab[dom], "peak_source": pk["source"]},
+        "config": bench_config(args.workload, spec, world),
+        "roofline": roof,
         "phases": per_phase,
-        "fwd_bwd": {"ms": fb_ms, "cell_evals_per_s": nc / (fb_ms / 1e3),
-                    "frac": (ab["forward"] + ab["backward"]) / (fb_ms / 1e3) / 1e9 / pk["hbm_gbs"]},
+        "warm_l2_step": {**rep_stats(warm_ms), "cell_evals_per_s": nc / (statistics.median(warm_ms) * 1e-3)},
         "power_w": {"model": float(watts[0]), "hybrid": float(watts[1])},
         "e2e": {"value": nc * world / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -692,27 +865,20 @@ def main() -> None:
         "device_bytes": int(info.device_bytes),
     }
     # ---- forward + reverse alone (model gradient, no simulation): N_c / (t_fwd + t_bwd)
-    cfg0 = dp.config(grad_mode=0)
-    for _ in range(3):
-        dp.dp_propagate(ctx, d, cfg0)
-        dp.dp_backward(ctx, d, cfg0, g["sp"], None, None, None, 1)
-    torch.cuda.synchronize()
-    fb = []
-    for i in range(max(args.steps, 5)):
-        flush.fill_(float(i))
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        dp.dp_propagate(ctx, d, cfg0)
-        dp.dp_backward(ctx, d, cfg0, g["sp"], None, None, None, 1)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        fb.append(e0.elapsed_time(e1))
-    fb_ms0 = statistics.median(fb)
-    fb_bytes = ab["forward"] + ab["backward"]
-    line["fwd_bwd_model"] = {"ms": fb_ms0, "cell_evals_per_s": nc / (fb_ms0 * 1e-3),
-                             "frac": fb_bytes / (fb_ms0 * 1e-3) / 1e9 / pk["hbm_gbs"],
-                             "what": "dp_propagate + dp_backward (grad_mode 0) alone, L2 flushed, median",
-                             "levels": 2 * int(info.n_levels)}
+    fbm = fwd_bwd_record(dp, ctx, d, stream, flush, max(args.steps, 50), pk)
+    line["fwd_bwd_model"] = fbm
+    # ---- the latency floor of the level-synchronous passes, measured with the library's barrier
+    if not args.no_probe:
+        lat = dp.dp_probe_latency(ctx, 1000)
+        L = int(info.n_levels)
+        floor_ms = L * (lat["level_us_256"] + lat["level_us_512"]) * 1e-3
+        line["latency_floor"] = {
+            **lat, "levels_forward": L, "levels_reverse": L, "floor_ms": floor_ms,
+            "fwd_bwd_frac_of_floor": floor_ms / fbm["ms"],
+            "fwd_us_per_level": 1e3 * per_phase["forward"]["ms"] / L if per_phase["forward"]["ms"] else None,
+            "what": "dp_probe_latency: per level, a grid barrier plus three loads through L2 of values other "
+                    "blocks stored in the level before and one store, on the forward (256-thread) and reverse "
+                    "(512-thread) grids; floor = L x both; fwd_bwd_model's time against it"}
 
     # ---- Eq. 8 sizing scores and the top 1,000 cells from the step's adjoint (re-ranking cost)
     dp.dp_step(ctx, d, cfg, g["sp"], g["tr"], g["pin"], g["cl"], None, 1)
@@ -725,6 +891,10 @@ def main() -> None:
                       "score": "Eq. 8, mode 0 (SP adjoint of the output net x hybrid P_sw)"}
     dp.dp_design_free(d)
     dp.dp_destroy(ctx)
+    del flush
+    if not args.no_configs:
+        line["configs"] = {"small": bench_config_passes(dp, torch, dev, "small", max(args.steps, 50), pk, False),
+                           "mid": bench_config_passes(dp, torch, dev, "mid", max(args.steps, 50), pk, True)}
     if not args.no_batched:
         line["batched"] = bench_batched(args, dp, torch, dev, pk)
     if rank == 0 and not args.no_serving:

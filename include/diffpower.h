@@ -210,6 +210,21 @@ dp_status dp_selftest_wait(dp_ctx *ctx, double seconds);
  * for action 2).  Any other action returns DP_EINVAL. */
 dp_status dp_selftest_pending_error(int action, int32_t *pending);
 
+/* Latency probes of the level-synchronous schedule on this GPU: the cost per
+ * level that bounds the persistent passes (Algorithm 2 and 3 walk the levels
+ * in order, so each level waits for the one before it).  Each figure is the
+ * difference of two timed launches (n and 3n units, CUDA events), divided by
+ * 2n, so launch costs cancel.  out[6] (host):
+ *   [0] us per level barrier on one block of 256 threads per SM (the forward
+ *       pass's grid), [1] us per level of its skeleton: barrier, then three
+ *       loads through L2 of values other blocks stored in the previous level
+ *       and one store, [2], [3] the same on 512-thread blocks (the reverse
+ *       pass's grid), [4] us per dependent L2 load (one thread chasing a
+ *       pointer cycle through 8 MB resident in L2), [5] blocks of the grid.
+ * levels in [16, 20000] (DP_EINVAL otherwise).  Every wait is bounded
+ * (DP_ETIMEOUT).  Allocates and frees its own buffers; synchronises. */
+dp_status dp_probe_latency(dp_ctx *ctx, int32_t levels, double *out);
+
 /* Compiles (as dp_compile) and uploads a netlist; the design keeps its whole
  * graph and per-net state resident in device memory (Sec. III). */
 dp_status dp_design_load(dp_ctx *ctx, const char *netlist, size_t netlist_len, const char *library,

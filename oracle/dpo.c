@@ -222,6 +222,10 @@ typedef struct {
     int64_t *sink_cell;
     int64_t *topo;      /* cells in a topological order (Kahn) */
     int32_t depth;
+    /* cells by level (1 + the deepest fanin's level), for the level-parallel CPU baseline:
+     * level l holds lvl_cell[lvl_ptr[l - 1] .. lvl_ptr[l]), in cell order */
+    int64_t *lvl_ptr;
+    int64_t *lvl_cell;
 } Orc;
 
 static void orc_destroy(Orc *o) {
@@ -230,6 +234,7 @@ static void orc_destroy(Orc *o) {
     free(o->lib); free(o->wire); free(o->drv); free(o->start_of); free(o->ppo_cap);
     free(o->start_net); free(o->cell_lib); free(o->cell_out); free(o->fin_ptr); free(o->fin_net);
     free(o->pincap); free(o->sink_ptr); free(o->sink_cell); free(o->topo);
+    free(o->lvl_ptr); free(o->lvl_cell);
     free(o);
 }
 
@@ -493,8 +498,20 @@ void *orc_load(const char *netlist, const char *library, char *err, int errlen) 
         for (int64_t s = o->sink_ptr[n]; s < o->sink_ptr[n + 1]; s++)
             if (--indeg[o->sink_cell[s]] == 0) o->topo[tail++] = o->sink_cell[s];
     }
+    if (tail != o->nc) { free(fill); free(indeg); free(lev); seterr(err, errlen, "combinational cycle", 0); orc_destroy(o); return 0; }
+    /* level buckets (counting sort by level, stable in cell order) */
+    o->lvl_ptr = (int64_t *)calloc((size_t)o->depth + 2, sizeof(int64_t));
+    o->lvl_cell = (int64_t *)malloc((size_t)(o->nc + 1) * sizeof(int64_t));
+    if (!o->lvl_ptr || !o->lvl_cell) {
+        free(fill); free(indeg); free(lev); seterr(err, errlen, "out of memory", 0); orc_destroy(o); return 0;
+    }
+    for (int64_t c = 0; c < o->nc; c++) o->lvl_ptr[lev[o->cell_out[c]]]++;
+    for (int32_t l = 1; l <= o->depth; l++) o->lvl_ptr[l] += o->lvl_ptr[l - 1];
+    for (int64_t c = o->nc - 1; c >= 0; c--) o->lvl_cell[--o->lvl_ptr[lev[o->cell_out[c]]]] = c;
+    /* now lvl_ptr[l] = first cell of level l; shift so level l spans [lvl_ptr[l-1], lvl_ptr[l]) */
+    for (int32_t l = 0; l < o->depth; l++) o->lvl_ptr[l] = o->lvl_ptr[l + 1];
+    o->lvl_ptr[o->depth] = o->nc;
     free(fill); free(indeg); free(lev);
-    if (tail != o->nc) { seterr(err, errlen, "combinational cycle", 0); orc_destroy(o); return 0; }
     return o;
 }
 
@@ -923,4 +940,213 @@ void orc_hybrid(const void *h, const double *tr_model, const uint32_t *toggles, 
         beta[n] = b;
         tr_hyb[n] = b * tr_model[n];
     }
+}
+
+
+/* ------------------------------------------------------------------ */
+/* Level-parallel variants (OpenMP) for the CPU baseline of the        */
+/* benchmark: the same per-cell arithmetic as orc_forward, orc_simulate */
+/* and orc_backward, with the cells of one level processed in parallel  */
+/* (all fanins of a cell lie on lower levels).  The forward pass and   */
+/* the simulation give bitwise the same results as the serial ones;    */
+/* the adjoint gathers each net's contributions over its sinks instead  */
+/* of scattering them, so it agrees to rounding.                       */
+/* ------------------------------------------------------------------ */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+int orc_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+static void par_fwd_cell(const Orc *o, int64_t c, double *sp, double *tr, double *sq) {
+    const LibCell *L = &o->lib[o->cell_lib[c]];
+    double a1[ORC_MAX_IN], a0[ORC_MAX_IN];
+    for (int i = 0; i < L->k; i++) {
+        int64_t f = o->fin_net[o->fin_ptr[c] + i];
+        a1[i] = sp[f];
+        a0[i] = sq[f];
+    }
+    int64_t n = o->cell_out[c];
+    double p1 = cell_prob(L, a1, a0, 1), p0 = cell_prob(L, a1, a0, 0), s = p1 + p0;
+    sp[n] = p1 / s;
+    sq[n] = p0 / s;
+    tr[n] = 2.0 * sp[n] * sq[n];
+}
+
+int orc_forward_par(const void *h, const double *sp_in, const double *tr_in, int tr_mode, double *sp, double *tr,
+                    double *sq) {
+    const Orc *o = (const Orc *)h;
+    #pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < o->ns; k++) {
+        int64_t n = o->start_net[k];
+        sp[n] = sp_in[k];
+        sq[n] = 1.0 - sp_in[k];
+        tr[n] = tr_mode == 0 ? tr_in[k] : 2.0 * sp[n] * sq[n];
+    }
+    for (int32_t l = 1; l <= o->depth; l++) {
+        const int64_t i0 = o->lvl_ptr[l - 1], i1 = o->lvl_ptr[l];
+        #pragma omp parallel for schedule(static)
+        for (int64_t i = i0; i < i1; i++) par_fwd_cell(o, o->lvl_cell[i], sp, tr, sq);
+    }
+    return 0;
+}
+
+/* the Markov chains of startpoint k (the serial simulation's startpoint loop body) */
+static void par_sim_start(const Orc *o, int64_t k, const float *sp_in, const float *tr_in, const uint32_t key[2],
+                          int T, uint64_t *w) {
+    uint64_t *wk = w + (size_t)o->start_net[k] * (size_t)T;
+    double sp = (double)sp_in[k], tr = (double)tr_in[k];
+    double p10 = sp > 0.0 ? tr / (2.0 * sp) : 0.0;
+    double p01 = sp < 1.0 ? tr / (2.0 * (1.0 - sp)) : 0.0;
+    uint32_t t_init = thr(sp), t10 = thr(p10), t01 = thr(p01);
+    for (int q = 0; q < 16; q++) {
+        int bit[4] = {0, 0, 0, 0};
+        uint32_t u[4] = {0, 0, 0, 0};
+        for (int t = 0; t < T; t++) {
+            if ((t & 1) == 0) {
+                uint32_t ctr[4] = {(uint32_t)k, (uint32_t)(t / 2), (uint32_t)q, 0u};
+                orc_philox4x32_10(ctr, key, u);
+            }
+            for (int r = 0; r < 4; r++) {
+                uint32_t d = (t & 1) ? (u[r] >> 16) : (u[r] & 0xFFFFu);
+                if (t == 0) bit[r] = d < t_init;
+                else if (d < (bit[r] ? t10 : t01)) bit[r] ^= 1;
+                if (bit[r]) wk[t] |= 1ull << (16 * r + q);
+            }
+        }
+    }
+}
+
+static void par_sim_cell(const Orc *o, int64_t c, int T, uint64_t *w) {
+    const LibCell *L = &o->lib[o->cell_lib[c]];
+    uint64_t *wo = w + (size_t)o->cell_out[c] * (size_t)T;
+    int64_t M = (int64_t)1 << L->k;
+    for (int t = 0; t < T; t++) {
+        uint64_t acc = 0;
+        for (int64_t m = 0; m < M; m++) {
+            if (!L->tt[m]) continue;
+            uint64_t term = ~0ull;
+            for (int i = 0; i < L->k; i++) {
+                uint64_t x = w[(size_t)o->fin_net[o->fin_ptr[c] + i] * (size_t)T + (size_t)t];
+                term &= ((m >> i) & 1) ? x : ~x;
+            }
+            acc |= term;
+        }
+        wo[t] = acc;
+    }
+}
+
+int orc_simulate_par(const void *h, const float *sp_in, const float *tr_in, uint64_t seed, int T,
+                     uint64_t *words_out, uint32_t *toggles, uint32_t *ones) {
+    const Orc *o = (const Orc *)h;
+    if (T < 1) return -1;
+    uint64_t *w = words_out ? words_out : (uint64_t *)malloc(sizeof(uint64_t) * (size_t)o->nn * (size_t)T + 8);
+    if (!w) return -1;
+    memset(w, 0, sizeof(uint64_t) * (size_t)o->nn * (size_t)T);
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    #pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t k = 0; k < o->ns; k++) par_sim_start(o, k, sp_in, tr_in, key, T, w);
+    for (int32_t l = 1; l <= o->depth; l++) {
+        const int64_t i0 = o->lvl_ptr[l - 1], i1 = o->lvl_ptr[l];
+        #pragma omp parallel for schedule(static)
+        for (int64_t i = i0; i < i1; i++) par_sim_cell(o, o->lvl_cell[i], T, w);
+    }
+    #pragma omp parallel for schedule(static)
+    for (int64_t n = 0; n < o->nn; n++) {
+        const uint64_t *wn = w + (size_t)n * (size_t)T;
+        uint32_t tg = 0, on = 0;
+        for (int t = 0; t < T; t++) {
+            on += (uint32_t)popc64(wn[t]);
+            if (t > 0) tg += (uint32_t)popc64(wn[t] ^ wn[t - 1]);
+        }
+        if (toggles) toggles[n] = tg;
+        if (ones) ones[n] = on;
+    }
+    if (!words_out) free(w);
+    return 0;
+}
+
+/* sum over the sink pins (c, j) of net n of tot[out(c)] * d SP_out(c) / d a_j */
+static double par_sink_sum(const Orc *o, int64_t n, const double *tot, const double *sp, const double *sq) {
+    double s = 0.0;
+    int64_t prev = -1;
+    double a1[ORC_MAX_IN], a0[ORC_MAX_IN];
+    for (int64_t e = o->sink_ptr[n]; e < o->sink_ptr[n + 1]; e++) {
+        int64_t c = o->sink_cell[e];
+        if (c == prev) continue;   /* a cell reading n on several pins is listed once per pin */
+        prev = c;
+        const LibCell *L = &o->lib[o->cell_lib[c]];
+        for (int i = 0; i < L->k; i++) {
+            int64_t f = o->fin_net[o->fin_ptr[c] + i];
+            a1[i] = sp[f];
+            a0[i] = sq[f];
+        }
+        for (int j = 0; j < L->k; j++)
+            if (o->fin_net[o->fin_ptr[c] + j] == n) s += tot[o->cell_out[c]] * cell_dsp(L, a1, a0, j);
+    }
+    return s;
+}
+
+int orc_backward_par(const void *h, const double *sp_in, const double *tr_in, const double *beta, int grad_mode,
+                     int tr_mode, double vdd, double fclk, double *g_sp_in, double *g_tr_in, double *g_pincap,
+                     double *g_cload, double *g_net) {
+    const Orc *o = (const Orc *)h;
+    const double K = 0.5 * vdd * vdd * fclk * 1e-15;
+    size_t nb = sizeof(double) * (size_t)(o->nn + 1);
+    double *cl = (double *)malloc(nb), *tot = (double *)calloc((size_t)o->nn + 1, sizeof(double));
+    double *sp = (double *)malloc(nb), *sq = (double *)malloc(nb), *tr = (double *)malloc(nb);
+    if (!cl || !tot || !sp || !sq || !tr) {
+        free(cl); free(tot); free(sp); free(sq); free(tr);
+        return -1;
+    }
+    orc_cload(o, cl);
+    orc_forward_par(o, sp_in, tr_in, tr_mode, sp, tr, sq);
+    #define LOCAL(n) ((o->drv[n] >= 0 || (o->drv[n] == -1 && tr_mode == 1)) ? 2.0 * K * cl[n] * (sq[n] - sp[n]) : 0.0)
+    #define COMBINE(acc, l, b) (grad_mode == 1 ? (b) * ((acc) + (l)) : (grad_mode == 2 ? (acc) + (b) * (l) : (acc) + (l)))
+    for (int32_t l = o->depth; l >= 1; l--) {
+        const int64_t i0 = o->lvl_ptr[l - 1], i1 = o->lvl_ptr[l];
+        #pragma omp parallel for schedule(static)
+        for (int64_t i = i0; i < i1; i++) {
+            int64_t n = o->cell_out[o->lvl_cell[i]];
+            double b = grad_mode ? beta[n] : 1.0;
+            tot[n] = COMBINE(par_sink_sum(o, n, tot, sp, sq), LOCAL(n), b);
+        }
+    }
+    #pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < o->ns; k++) {
+        int64_t n = o->start_net[k];
+        double b = grad_mode ? beta[n] : 1.0;
+        tot[n] = COMBINE(par_sink_sum(o, n, tot, sp, sq), LOCAL(n), b);
+    }
+    #undef COMBINE
+    #undef LOCAL
+    for (int64_t k = 0; k < o->ns; k++) {
+        int64_t n = o->start_net[k];
+        double b = grad_mode ? beta[n] : 1.0;
+        if (g_sp_in) g_sp_in[k] = tot[n];
+        if (g_tr_in) g_tr_in[k] = tr_mode == 0 ? K * b * cl[n] : 0.0;
+    }
+    #define ALPHA(n) (grad_mode ? beta[n] * tr[n] : tr[n])
+    if (g_cload) {
+        #pragma omp parallel for schedule(static)
+        for (int64_t n = 0; n < o->nn; n++) g_cload[n] = K * ALPHA(n);
+    }
+    if (g_pincap) {
+        #pragma omp parallel for schedule(static)
+        for (int64_t c = 0; c < o->nc; c++) {
+            double s = 0.0;
+            for (int64_t e = o->fin_ptr[c]; e < o->fin_ptr[c + 1]; e++) s += ALPHA(o->fin_net[e]);
+            g_pincap[c] = K * s;
+        }
+    }
+    #undef ALPHA
+    if (g_net) memcpy(g_net, tot, sizeof(double) * (size_t)o->nn);
+    free(cl); free(tot); free(sp); free(sq); free(tr);
+    return 0;
 }

@@ -37,7 +37,10 @@ def build(force: bool = False) -> str:
     os.makedirs(_OUT, exist_ok=True)
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        # OpenMP only for the level-parallel baseline; without it those functions run serially
+        if subprocess.run(cmd[:1] + ["-fopenmp"] + cmd[1:], capture_output=True).returncode != 0:
+            subprocess.check_call(cmd)
         os.replace(tmp, _SO)
     return _SO
 
@@ -81,8 +84,20 @@ def _load():
             L.orc_backward_lag1.argtypes = [_P, _D, _D, ctypes.c_double, ctypes.c_double, _opt(_D), _opt(_D),
                                             _opt(_D), _opt(_D)]
             L.orc_backward_lag1.restype = ctypes.c_int
+            L.orc_threads.restype = ctypes.c_int
+            L.orc_forward_par.argtypes = L.orc_forward.argtypes
+            L.orc_forward_par.restype = ctypes.c_int
+            L.orc_backward_par.argtypes = L.orc_backward.argtypes
+            L.orc_backward_par.restype = ctypes.c_int
+            L.orc_simulate_par.argtypes = L.orc_simulate.argtypes
+            L.orc_simulate_par.restype = ctypes.c_int
             _lib = L
     return _lib
+
+
+def threads() -> int:
+    """Host threads the level-parallel variants use (1 when built without OpenMP)."""
+    return int(_load().orc_threads())
 
 
 def philox4x32_10(ctr, key) -> np.ndarray:
@@ -130,15 +145,16 @@ class Oracle:
         _load().orc_cload(self._h, out)
         return out
 
-    def forward(self, sp_in, tr_in, tr_mode: int = 0, want_sq: bool = False):
+    def forward(self, sp_in, tr_in, tr_mode: int = 0, want_sq: bool = False, parallel: bool = False):
         """Per-net SP and TR (Algorithm 2, Eq. 2) from startpoint inputs (binary32 inputs
         convert exactly; binary64 inputs allow finite differences).  With ``want_sq`` also
         P(net = 0), evaluated as its own probability sum rather than as 1 - SP."""
         sp = np.zeros(self.n_nets, np.float64)
         tr = np.zeros(self.n_nets, np.float64)
         sq = np.zeros(self.n_nets, np.float64)
-        _load().orc_forward(self._h, np.ascontiguousarray(sp_in, np.float64),
-                            np.ascontiguousarray(tr_in, np.float64), int(tr_mode), sp, tr, sq)
+        f = _load().orc_forward_par if parallel else _load().orc_forward
+        f(self._h, np.ascontiguousarray(sp_in, np.float64), np.ascontiguousarray(tr_in, np.float64), int(tr_mode),
+          sp, tr, sq)
         return (sp, tr, sq) if want_sq else (sp, tr)
 
     def power(self, alpha, vdd: float = 0.8, fclk: float = 1e9) -> float:
@@ -146,9 +162,10 @@ class Oracle:
         return float(_load().orc_power(self._h, np.ascontiguousarray(alpha, np.float64), vdd, fclk))
 
     def backward(self, sp_in, tr_in, beta=None, grad_mode: int = 0, tr_mode: int = 0,
-                 vdd: float = 0.8, fclk: float = 1e9) -> dict:
+                 vdd: float = 0.8, fclk: float = 1e9, parallel: bool = False) -> dict:
         """Gradients of Eq. 1 at the startpoint inputs (Eq. 7; Eq. 6 for grad_mode 1).  The
-        hybrid modes (grad_mode 1, 2) differentiate sum K beta TR C with the given beta."""
+        hybrid modes (grad_mode 1, 2) differentiate sum K beta TR C with the given beta.
+        ``parallel``: the level-parallel variant (each net gathers over its sinks)."""
         out = {
             "grad_sp_in": np.zeros(self.n_start), "grad_tr_in": np.zeros(self.n_start),
             "grad_pincap": np.zeros(self.n_cells), "grad_cload": np.zeros(self.n_nets),
@@ -156,7 +173,8 @@ class Oracle:
         }
         if grad_mode and beta is None:
             raise ValueError("beta required for hybrid gradient modes")
-        rc = _load().orc_backward(self._h, np.ascontiguousarray(sp_in, np.float64),
+        f = _load().orc_backward_par if parallel else _load().orc_backward
+        rc = f(self._h, np.ascontiguousarray(sp_in, np.float64),
                                   np.ascontiguousarray(tr_in, np.float64),
                                   None if beta is None else np.ascontiguousarray(beta, np.float64),
                                   int(grad_mode), int(tr_mode), vdd, fclk, out["grad_sp_in"],
@@ -165,12 +183,14 @@ class Oracle:
             raise MemoryError("oracle backward")
         return out
 
-    def simulate(self, sp_in, tr_in, seed: int = 42, T: int = 64, want_words: bool = False):
+    def simulate(self, sp_in, tr_in, seed: int = 42, T: int = 64, want_words: bool = False,
+                 parallel: bool = False):
         """Bit-packed Markov simulation: (toggles, ones[, words[n_nets, T]])."""
         tg = np.zeros(self.n_nets, np.uint32)
         on = np.zeros(self.n_nets, np.uint32)
         words = np.zeros((self.n_nets, T), np.uint64) if want_words else None
-        rc = _load().orc_simulate(self._h, np.ascontiguousarray(sp_in, np.float32),
+        f = _load().orc_simulate_par if parallel else _load().orc_simulate
+        rc = f(self._h, np.ascontiguousarray(sp_in, np.float32),
                                   np.ascontiguousarray(tr_in, np.float32), int(seed), int(T), words, tg, on)
         if rc != 0:
             raise MemoryError("oracle simulate")
@@ -185,14 +205,17 @@ class Oracle:
         return beta, trh
 
     def step(self, sp_in, tr_in, *, seed: int = 42, T: int = 64, grad_mode: int = 1, tr_mode: int = 0,
-             vdd: float = 0.8, fclk: float = 1e9, beta_min: float = 0.1, beta_max: float = 10.0) -> dict:
-        """The whole hot path once: forward, power, simulation, hybrid, adjoint."""
-        sp, tr = self.forward(sp_in, tr_in, tr_mode)
+             vdd: float = 0.8, fclk: float = 1e9, beta_min: float = 0.1, beta_max: float = 10.0,
+             parallel: bool = False) -> dict:
+        """The whole hot path once: forward, power, simulation, hybrid, adjoint (``parallel``:
+        the level-parallel variants of the forward pass, simulation and adjoint)."""
+        sp, tr = self.forward(sp_in, tr_in, tr_mode, parallel=parallel)
         p_model = self.power(tr, vdd, fclk)
-        tg, on = self.simulate(sp_in, tr_in, seed, T)
+        tg, on = self.simulate(sp_in, tr_in, seed, T, parallel=parallel)
         beta, trh = self.hybrid(tr, tg, T, beta_min, beta_max)
         p_hyb = self.power(trh, vdd, fclk)
-        g = self.backward(sp_in, tr_in, beta if grad_mode else None, grad_mode, tr_mode, vdd, fclk)
+        g = self.backward(sp_in, tr_in, beta if grad_mode else None, grad_mode, tr_mode, vdd, fclk,
+                          parallel=parallel)
         g.update(sp=sp, tr=tr, toggles=tg, ones=on, beta=beta, tr_hyb=trh, power_model=p_model,
                  power_hybrid=p_hyb)
         return g

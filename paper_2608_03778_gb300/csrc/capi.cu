@@ -415,7 +415,89 @@ dp_status dp_selftest_wait(dp_ctx *c, double seconds) {
 
 namespace {
 __global__ void k_zero_threads() {}
+
+struct ProbeBufs {
+    float *buf = nullptr;
+    unsigned *bar = nullptr;
+    uint32_t *next = nullptr, *sink = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ~ProbeBufs() {
+        cudaFree(buf);
+        cudaFree(bar);
+        cudaFree(next);
+        cudaFree(sink);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    }
+};
 }  // namespace
+
+dp_status dp_probe_latency(dp_ctx *c, int32_t levels, double *out) {
+    if (!c || !out || levels < 16 || levels > 20000)
+        return set_err(c, DP_EINVAL, "dp_probe_latency: levels must be in [16, 20000]");
+    DeviceGuard g(c->device);
+    const int grid = c->sm_count, max_threads = dp::kPersistThreads;
+    const int M = 65536, stride = 32;   // chain entries, one per 128-byte line: 8 MB, resident in L2
+    ProbeBufs p;
+    cudaError_t e = cudaMalloc((void **)&p.buf, sizeof(float) * 2 * (size_t)grid * max_threads);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&p.bar, sizeof(unsigned) * 32 * 3 * (size_t)levels);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&p.next, sizeof(uint32_t) * (size_t)M * stride);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&p.sink, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaEventCreate(&p.e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&p.e1);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p.buf, 0, sizeof(float) * 2 * (size_t)grid * max_threads, c->stream);
+    if (e != cudaSuccess) return cuda_err(c, e, "dp_probe_latency");
+    {
+        // one cycle through all M entries (Sattolo's shuffle, SplitMix64 draws)
+        std::vector<uint32_t> perm(M), host((size_t)M * stride, 0u);
+        for (int i = 0; i < M; i++) perm[i] = (uint32_t)i;
+        uint64_t x = 0x5EEDu;
+        for (int i = M - 1; i > 0; i--) {
+            uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+            z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+            z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+            z ^= z >> 31;
+            std::swap(perm[i], perm[(size_t)(z % (uint64_t)i)]);
+        }
+        for (int i = 0; i < M; i++) host[(size_t)perm[i] * stride] = perm[(i + 1) % M] * (uint32_t)stride;
+        e = cudaMemcpy(p.next, host.data(), sizeof(uint32_t) * host.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_err(c, e, "dp_probe_latency");
+    }
+    float ms = 0.f;
+    // milliseconds of one probe launch, its barrier counters zeroed outside the timed region
+    auto timed = [&](int kind, int n, int threads) -> dp_status {
+        cudaError_t le = cudaSuccess;
+        if (kind != 2) le = cudaMemsetAsync(p.bar, 0, sizeof(unsigned) * 32 * (size_t)n, c->stream);   // n <= 3 levels
+        if (le == cudaSuccess) le = cudaEventRecord(p.e0, c->stream);
+        if (le == cudaSuccess)
+            le = kind == 2 ? dp::launch_probe_chase(p.next, n, p.sink, c->stream)
+                           : dp::launch_probe_levels(p.buf, n, kind, grid, threads, p.bar, c->d_err, c->stream);
+        if (le == cudaSuccess) le = cudaEventRecord(p.e1, c->stream);
+        if (le == cudaSuccess) le = cudaEventSynchronize(p.e1);
+        if (le == cudaSuccess) le = cudaEventElapsedTime(&ms, p.e0, p.e1);
+        if (le != cudaSuccess) return cuda_err(c, le, "dp_probe_latency");
+        return check_device_error(c);
+    };
+    // microseconds per unit from launches of n and 3n units (launch costs cancel)
+    auto per_unit = [&](int kind, int n, int threads, double *r) -> dp_status {
+        dp_status s = timed(kind, n, threads);   // warm-up
+        if (s != DP_OK) return s;
+        if ((s = timed(kind, n, threads)) != DP_OK) return s;
+        const double t1 = ms;
+        if ((s = timed(kind, 3 * n, threads)) != DP_OK) return s;
+        *r = 1e3 * ((double)ms - t1) / (2.0 * n);
+        return DP_OK;
+    };
+    dp_status s = DP_OK;
+    if (s == DP_OK) s = per_unit(0, levels, dp::kFwdThreads, &out[0]);
+    if (s == DP_OK) s = per_unit(1, levels, dp::kFwdThreads, &out[1]);
+    if (s == DP_OK) s = per_unit(0, levels, dp::kPersistThreads, &out[2]);
+    if (s == DP_OK) s = per_unit(1, levels, dp::kPersistThreads, &out[3]);
+    if (s == DP_OK) s = timed(2, M, 1);   // the first pass brings the chain into L2
+    if (s == DP_OK) s = per_unit(2, 8 * levels, 1, &out[4]);
+    out[5] = (double)grid;
+    return s;
+}
 
 dp_status dp_selftest_pending_error(int action, int32_t *pending) {
     if (action < 0 || action > 2) return DP_EINVAL;

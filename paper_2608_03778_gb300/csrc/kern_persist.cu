@@ -397,6 +397,34 @@ __global__ void __launch_bounds__(kSimThreads, 2) k_sim_wide(const uint4 *__rest
     }
 }
 
+// ---------------------------------------------------------- latency probes
+// The level-synchronous skeleton of the persistent passes without their
+// arithmetic: `levels` levels, each ended by the same level barrier.
+// gather = 0: the barriers alone.  gather = 1: after each barrier every thread
+// loads, through L2, three values that threads of three other blocks stored in
+// the previous level, and stores one value: the barrier plus one dependent L2
+// round trip and a store per level, the least a level of the forward pass does.
+__global__ void k_probe_levels(float *buf, int levels, int gather, unsigned *bar, int *err, long long limit) {
+    const int64_t N = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t b = blockDim.x, g = gridDim.x;
+    const int64_t s0 = (t + b * (g / 4 + 1)) % N, s1 = (t + b * (g / 2 + 1)) % N, s2 = (t + b * (3 * g / 4 + 1)) % N;
+    for (int l = 0; l < levels; l++) {
+        const float *prev = buf + (l & 1) * N;
+        float *cur = buf + ((l + 1) & 1) * N;
+        if (gather) cur[t] = (__ldcg(prev + s0) + __ldcg(prev + s1) + __ldcg(prev + s2)) * (1.f / 3.f);
+        if (!level_barrier(bar + 32 * l, err, gridDim.x, limit)) return;
+    }
+}
+
+// one thread follows a chain of dependent loads through L2 (ld.global.cg):
+// the latency of one dependent L2 access
+__global__ void k_probe_chase(const uint32_t *next, int hops, uint32_t *sink) {
+    uint32_t i = 0;
+    for (int h = 0; h < hops; h++) i = __ldcg(next + i);
+    *sink = i;
+}
+
 // self-test of the bounded wait: the barrier expects one arrival more than
 // the grid has blocks, so it can only end by giving up
 __global__ void k_wait_selftest(unsigned *bar, int *err, long long limit) {
@@ -481,6 +509,16 @@ cudaError_t launch_bwd_persist(const DevDesign &d, const OpTable &ops, int grad_
     return launch_coop(k_bwd_persist, grid, kPersistThreads, s, d.fanin, d.fout_ptr, (const int4 *)d.edge_fpos,
                        (const float4 *)d.pq, (const float *)d.cload, (const float *)d.beta, d.gnet, d.gfo, d.lvl,
                        d.n_levels, d.n_start, grad_mode, tr_mode, K, out_gsp, ops, bar, d.err, kWaitLimitCycles);
+}
+
+cudaError_t launch_probe_levels(float *buf, int levels, int gather, int grid, int threads, unsigned *bar, int *err,
+                                cudaStream_t s) {
+    return launch_coop(k_probe_levels, grid, threads, s, buf, levels, gather, bar, err, kWaitLimitCycles);
+}
+
+cudaError_t launch_probe_chase(const uint32_t *next, int hops, uint32_t *sink, cudaStream_t s) {
+    k_probe_chase<<<1, 1, 0, s>>>(next, hops, sink);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_wait_selftest(unsigned *bar, int *err, long long limit, cudaStream_t s) {

@@ -101,6 +101,10 @@ cudaError_t launch_sim_persist(const DevDesign &d, const OpTable &ops, int T, in
 cudaError_t launch_bwd_persist(const DevDesign &d, const OpTable &ops, int grad_mode, int tr_mode, float K,
                                float *out_gsp, int grid, cudaStream_t s);
 cudaError_t launch_wait_selftest(unsigned *bar, int *err, long long limit, cudaStream_t s);
+// latency probes (buffers owned by the caller; bar zeroed by the caller, 32 words per level)
+cudaError_t launch_probe_levels(float *buf, int levels, int gather, int grid, int threads, unsigned *bar, int *err,
+                                cudaStream_t s);
+cudaError_t launch_probe_chase(const uint32_t *next, int hops, uint32_t *sink, cudaStream_t s);
 
 // Batched scenarios (kern_batch.cu): S scenarios of one design, every per-net
 // value stored scenario-innermost (value[n * S + s]).

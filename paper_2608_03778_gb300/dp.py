@@ -98,6 +98,7 @@ _sig("dp_destroy", [_P], None)
 _sig("dp_sync", [_P])
 _sig("dp_selftest_wait", [_P, ctypes.c_double])
 _sig("dp_selftest_pending_error", [ctypes.c_int, ctypes.POINTER(ctypes.c_int32)])
+_sig("dp_probe_latency", [_P, ctypes.c_int32, _P])
 _sig("dp_design_load", [_P, ctypes.c_char_p, ctypes.c_size_t, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(_P)])
 _sig("dp_design_upload", [_P, _P, ctypes.POINTER(_P)])
 _sig("dp_design_free", [_P], None)
@@ -142,7 +143,7 @@ EXPORTED = ["dp_config_default", "dp_last_error", "dp_compile", "dp_compiled_fre
             "dp_design_upload", "dp_design_free", "dp_design_info", "dp_set_inputs", "dp_set_pincap",
             "dp_propagate", "dp_simulate", "dp_total_power", "dp_backward", "dp_get_nets", "dp_step",
             "dp_phase_times", "dp_step_kernels", "dp_power_noalloc", "dp_selftest_wait",
-            "dp_selftest_pending_error", "dp_set_stream",
+            "dp_selftest_pending_error", "dp_probe_latency", "dp_set_stream",
             "dp_get_power", "dp_set_inputs_batch", "dp_batch_tuning", "dp_backward_weighted", "dp_ascent_step",
             "dp_virus_eval", "dp_sizing_scores", "dp_server_config_default", "dp_server_create", "dp_server_destroy",
             "dp_server_last_error", "dp_server_add_design", "dp_server_design_info", "dp_server_submit",
@@ -278,6 +279,14 @@ def dp_sync(ctx) -> None:
 
 def dp_selftest_wait(ctx, seconds: float) -> None:
     _check(_lib.dp_selftest_wait(ctx, seconds), ctx)
+
+
+def dp_probe_latency(ctx, levels: int = 1000) -> dict:
+    """Per-level latency figures of the level-synchronous schedule (microseconds)."""
+    out = np.zeros(6, np.float64)
+    _check(_lib.dp_probe_latency(ctx, levels, out.ctypes.data), ctx)
+    return {"barrier_us_256": float(out[0]), "level_us_256": float(out[1]), "barrier_us_512": float(out[2]),
+            "level_us_512": float(out[3]), "l2_load_us": float(out[4]), "grid_blocks": int(out[5])}
 
 
 def dp_selftest_pending_error(action: int) -> int:

@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 from paper_2608_03778_gb300 import dp, netgen
-from tests.test_parity_gpu import custom_case
+from tests._netlists import custom_case
 
 ARRAYS = [("lvl_ptr", "i4"), ("fanin", "u4"), ("fout_ptr", "i4"), ("fout_edge", "i4"), ("edge_fpos", "i4"),
           ("net_of_user", "i4"), ("user_of_net", "i4"), ("cell_of_user", "i4"), ("user_of_cell", "i4"),
