@@ -217,17 +217,26 @@ def workload(name: str):
 
 
 def host_cpu() -> dict:
-    """Host cores and CPU model of this machine (nproc and /proc/cpuinfo)."""
+    """Host cores and CPU model of this machine (nproc; the model from lscpu, else /proc/cpuinfo)."""
     model = None
     try:
-        with open("/proc/cpuinfo") as f:
-            for line in f:
-                k = line.split(":")[0].strip().lower()
-                if k in ("model name", "cpu model", "hardware") and ":" in line:
-                    model = line.split(":", 1)[1].strip()
-                    break
-    except OSError:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip().lower() == "model name" and ":" in line:
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
         pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    k = line.split(":")[0].strip().lower()
+                    if k in ("model name", "cpu model", "hardware") and ":" in line:
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
     if model is None:
         import platform
         model = platform.processor() or platform.machine()
@@ -377,7 +386,11 @@ def fwd_bwd_record(dp, ctx, d, stream, flush, reps: int, pk: dict) -> dict:
     for _ in range(5):
         fn()
     torch.cuda.synchronize()
-    cold = timed_reps(fn, stream, flush, reps)
+    cold, ph = [], []
+    for _ in range(reps):
+        cold += timed_reps(fn, stream, flush, 1)
+        ph.append(dp.dp_phase_times(ctx, d))   # library events around the forward and the reverse pass
+    ph = np.median(np.stack(ph), axis=0)
     warm = timed_reps(fn, stream, None, reps)
     fb = fwd_bwd_bytes(nn, ns, nc, ne)
     ms, wms = statistics.median(cold), statistics.median(warm)
@@ -388,6 +401,7 @@ def fwd_bwd_record(dp, ctx, d, stream, flush, reps: int, pk: dict) -> dict:
             "warm_l2": {**rep_stats(warm), "cell_evals_per_s": nc / (wms * 1e-3),
                         "frac": fb["total"] / (wms * 1e-3) / 1e9 / pk["hbm_gbs"]},
             "levels": 2 * int(info.n_levels),
+            "forward_ms": float(ph[0]), "backward_ms": float(ph[3]),
             "what": "dp_propagate + dp_backward (grad_mode 0; startpoint SP/TR and pin-cap gradients out); "
                     "L2 flushed before each repetition (warm_l2: not flushed); median"}
 
@@ -585,20 +599,27 @@ def bench_serving(args, dp, torch, dev) -> dict:
                 dp.dp_server_wait(srv, dp.dp_server_submit(srv, j["req"]), 120.0)
                 dp.dp_server_wait(plain, dp.dp_server_submit(plain, j["req"]), 120.0)
 
-        # Poisson arrivals
+        # Poisson arrivals, three runs in a row on the same (long-running) server
         gaps = rng.exponential(1.0 / rate, n_req)
         arrive = np.cumsum(gaps) - gaps[0]
-        st0 = dp.dp_server_get_stats(srv)
-        tickets = []
-        t0 = time.perf_counter()
-        for j, ta in zip(jobs, arrive):
-            while time.perf_counter() - t0 < ta:
-                pass
-            tickets.append(dp.dp_server_submit(srv, j["req"]))
-        lat = np.array([dp.dp_server_wait(srv, t, 600.0) for t in tickets])
-        t_poisson = time.perf_counter() - t0
-        st1 = dp.dp_server_get_stats(srv)
-        served = results()
+        runs = []
+        for _ in range(3):
+            st0 = dp.dp_server_get_stats(srv)
+            tickets = []
+            t0 = time.perf_counter()
+            for j, ta in zip(jobs, arrive):
+                while time.perf_counter() - t0 < ta:
+                    pass
+                tickets.append(dp.dp_server_submit(srv, j["req"]))
+            lat = np.array([dp.dp_server_wait(srv, t, 600.0) for t in tickets])
+            t_poisson = time.perf_counter() - t0
+            st1 = dp.dp_server_get_stats(srv)
+            nb = st1.batches - st0.batches
+            runs.append({"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                         "throughput_rps": n_req / t_poisson, "batches": int(nb),
+                         "mean_batch": (st1.requests - st0.requests) / max(nb, 1),
+                         "host_launch_us_per_batch": 1e6 * (st1.host_launch_s - st0.host_launch_s) / max(nb, 1)})
+            served = results()
         # saturated
         t0 = time.perf_counter()
         tickets = [dp.dp_server_submit(srv, j["req"]) for j in jobs]
@@ -613,14 +634,11 @@ def bench_serving(args, dp, torch, dev) -> dict:
         base = results()
         same = all(all(np.array_equal(x, y) for x, y in zip(a, b)) for a, b in zip(served, base)) and all(
             all(np.array_equal(x, y) for x, y in zip(a, b)) for a, b in zip(saturated, base))
-        nb = st1.batches - st0.batches
         return {
             "workload": "8 resident netlists serve_5000 ... serve_2000000 (seeds 1-8); 2,000 requests, half new "
                         "input SP/TR, half sizing deltas (1 % of X1 cells to X2/X4); gradients on half",
             "max_batch": max_batch,
-            "poisson": {"rate_per_s": rate, "p50_ms": float(np.percentile(lat, 50)),
-                        "p99_ms": float(np.percentile(lat, 99)), "throughput_rps": n_req / t_poisson,
-                        "batches": int(nb), "mean_batch": (st1.requests - st0.requests) / max(nb, 1)},
+            "poisson": {"rate_per_s": rate, **runs[0], "runs": runs},
             "saturated": {"throughput_rps": n_req / t_sat, "p50_ms": float(np.percentile(lat_sat, 50)),
                           "p99_ms": float(np.percentile(lat_sat, 99)),
                           "mean_batch": (st2.requests - st1.requests) / max(st2.batches - st1.batches, 1)},
@@ -875,7 +893,7 @@ def main() -> None:
         line["latency_floor"] = {
             **lat, "levels_forward": L, "levels_reverse": L, "floor_ms": floor_ms,
             "fwd_bwd_frac_of_floor": floor_ms / fbm["ms"],
-            "fwd_us_per_level": 1e3 * per_phase["forward"]["ms"] / L if per_phase["forward"]["ms"] else None,
+            "forward_us_per_level": 1e3 * fbm["forward_ms"] / L, "reverse_us_per_level": 1e3 * fbm["backward_ms"] / L,
             "what": "dp_probe_latency: per level, a grid barrier plus three loads through L2 of values other "
                     "blocks stored in the level before and one store, on the forward (256-thread) and reverse "
                     "(512-thread) grids; floor = L x both; fwd_bwd_model's time against it"}

@@ -459,6 +459,7 @@ typedef struct {
     int64_t max_batch_seen;   /* largest batch */
     size_t device_bytes;      /* device bytes charged against the budget */
     int32_t designs;          /* resident designs */
+    double host_launch_s;     /* host seconds spent queuing batches (copies, graph launches) */
 } dp_server_stats;
 
 void dp_server_config_default(dp_server_config *cfg);

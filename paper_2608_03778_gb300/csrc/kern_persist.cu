@@ -67,6 +67,11 @@ __device__ bool level_barrier(unsigned *ctr, int *err, unsigned nblocks, long lo
     return barrier_wait(ctr, err, nblocks, limit);
 }
 
+// L2 prefetch of one line; the persistent passes fetch a level's static data two
+// levels ahead, so its DRAM latency is hidden by a whole level instead of by the
+// part of one barrier that follows a block's arrival
+__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 // thread index that spreads consecutive 32-element groups over all blocks
 // (and so over all SMs) before giving any block a second warp of work
 __device__ __forceinline__ int64_t spread_tid() {
@@ -104,6 +109,10 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd_persist(
         barrier_arrive(bar + 32 * (l - 1));
         uint4 r = make_uint4(0, 0, 0, 0);
         if (c < c1) r = fanin[c];   // static: loaded between arrival and wait
+        if (l + 2 <= L) {
+            const int64_t cp = lvl[l + 1] + tid;
+            if (cp < lvl[l + 2]) prefetch_l2(fanin + cp);
+        }
         if (!barrier_wait(bar + 32 * (l - 1), err, gridDim.x, limit)) return;
         if (c < c1) fwd_cell(r, c, pq, tr, ns, ops, par);
         for (int64_t cc = c + T; cc < c1; cc += T) fwd_cell(fanin[cc], cc, pq, tr, ns, ops, par);
@@ -172,6 +181,16 @@ __global__ void __launch_bounds__(kPersistThreads) k_bwd_persist(
         if (l < L) barrier_arrive(bar + 32 * (L - 1 - l));
         BwdStatic s;
         if (c < c1) s = bwd_static(fanin, fptr, efpos, pq, cload, beta, c, ns, grad_mode, K, ops);
+        if (l >= 3) {
+            const int64_t cp = lvl[l - 3] + tid;
+            if (cp < lvl[l - 2]) {
+                prefetch_l2(fanin + cp);
+                prefetch_l2(efpos + cp);
+                prefetch_l2(fptr + ns + cp);
+                prefetch_l2(cload + ns + cp);
+                if (grad_mode) prefetch_l2(beta + ns + cp);
+            }
+        }
         if (l < L && !barrier_wait(bar + 32 * (L - 1 - l), err, gridDim.x, limit)) return;
         if (c < c1) bwd_finish(s, ns + c, gnet, gfo, grad_mode);
         for (int64_t cc = c + T; cc < c1; cc += T)

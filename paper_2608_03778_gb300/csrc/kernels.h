@@ -151,8 +151,8 @@ constexpr int kMaxFanin = 4;
 struct SizingDeltas {
     const int32_t *cell;        // [ne] cell-line index of each entry
     const float *cap;           // [ne] its new input pin cap, fF
-    const int32_t *scen;        // [ne] scenario of the entry
-    const int32_t *pos;         // [ne] position of the entry within its request (the last one counts)
+    const int32_t *off;         // [n_req + 1] entries of request (scenario) s: [off[s], off[s+1]); an entry's
+    int32_t n_req;              //   position within its request (the last one counts) is its index - off[s]
     int *win;                   // [n_cells * S] -1 at rest
     float *dpin;                // [n_cells * S] 0 at rest
     unsigned *flag;             // [n_nets * S] 0 at rest

@@ -74,12 +74,13 @@ struct Slot {
     float2 *d_ref_pq = nullptr;                        // [nn] float-float P of the reference inputs
     float *d_in_sp = nullptr, *d_in_tr = nullptr;     // [max_batch][ns] request-major inputs
     float *d_dcl = nullptr;                            // [nn * max_batch], zero between batches
-    // sizing-delta entries of a batch (capacity delta_cap) and the device work arrays
+    // sizing-delta entries of a batch (capacity delta_cap, reserved at admission and grown in
+    // stream order only when a batch brings more) and the device work arrays
     int64_t delta_cap = 0;
-    int32_t *d_cell = nullptr, *d_scen = nullptr, *d_pos = nullptr;
+    int32_t *d_cell = nullptr;
     float *d_cap = nullptr;
-    int32_t *h_scen = nullptr, *h_pos = nullptr;
     int64_t *d_list = nullptr;
+    int32_t *h_off = nullptr, *d_off = nullptr;        // [max_batch + 1] entry offsets of the requests
     int *d_win = nullptr;                              // [nc * max_batch]
     float *d_dpin = nullptr;                           // [nc * max_batch]
     unsigned *d_flag = nullptr;                        // [nn * max_batch]
@@ -155,9 +156,12 @@ cudaError_t hmalloc(Slot *sl, T **p, size_t n) {
     return e;
 }
 
+void free_delta_arrays(Slot *sl, bool stream_ordered);
+
 void free_slot(Slot *sl) {
     if (!sl) return;
     if (sl->stream) cudaStreamSynchronize(sl->stream);
+    free_delta_arrays(sl, false);
     for (void *p : sl->dev) cudaFree(p);
     for (void *p : sl->pinned) cudaFreeHost(p);
     if (sl->done) cudaEventDestroy(sl->done);
@@ -170,42 +174,58 @@ void free_slot(Slot *sl) {
     delete sl;
 }
 
-// (growing) room for the sizing-delta entries of one batch
-cudaError_t ensure_delta_cap(Slot *sl, int64_t n) {
+// bytes of device work arrays per sizing-delta entry: cell, cap, kMaxFanin claimed slots
+constexpr int64_t kDeltaEntryBytes = 4 + 4 + 8 * dp::kMaxFanin;
+
+// entries reserved at admission: max_batch requests that each resize 2 % of the cells
+int64_t initial_delta_cap(int64_t max_batch, int64_t nc) {
+    return std::max<int64_t>(4096, max_batch * std::max<int64_t>(1, nc / 50));
+}
+
+void free_delta_arrays(Slot *sl, bool stream_ordered) {
+    for (void *p : {(void *)sl->d_cell, (void *)sl->d_cap, (void *)sl->d_list})
+        if (p) {
+            if (stream_ordered) cudaFreeAsync(p, sl->stream);
+            else cudaFree(p);
+        }
+    sl->bytes -= (size_t)(kDeltaEntryBytes * sl->delta_cap);
+    sl->d_cell = nullptr;
+    sl->d_cap = nullptr;
+    sl->d_list = nullptr;
+    sl->delta_cap = 0;
+}
+
+// Room for the sizing-delta entries of one batch.  The arrays are reserved at admission;
+// a batch that brings more entries grows them in stream order (cudaMallocAsync /
+// cudaFreeAsync on the slot's stream), so the serving path never allocates pinned host
+// memory, never waits for the device and never synchronises other streams.
+cudaError_t ensure_delta_cap(Slot *sl, int64_t n, bool stream_ordered) {
     if (n <= sl->delta_cap) return cudaSuccess;
     int64_t cap = sl->delta_cap ? sl->delta_cap : 4096;
     while (cap < n) cap *= 2;
-    cudaStreamSynchronize(sl->stream);
-    auto drop = [](std::vector<void *> &l, void *p, bool host) {
-        auto it = std::find(l.begin(), l.end(), p);
-        if (it != l.end()) {
-            if (host) cudaFreeHost(p);
-            else cudaFree(p);
-            l.erase(it);
-        }
-    };
-    for (void *p : {(void *)sl->d_cell, (void *)sl->d_scen, (void *)sl->d_pos, (void *)sl->d_cap, (void *)sl->d_list})
-        if (p) drop(sl->dev, p, false);
-    for (void *p : {(void *)sl->h_scen, (void *)sl->h_pos})
-        if (p) drop(sl->pinned, p, true);
-    sl->d_cell = sl->d_scen = sl->d_pos = nullptr;
-    sl->d_cap = nullptr;
-    sl->d_list = nullptr;
-    sl->h_scen = sl->h_pos = nullptr;
-    sl->delta_cap = 0;
-    cudaError_t e = dmalloc(sl, &sl->d_cell, (size_t)cap);
-    if (e == cudaSuccess) e = dmalloc(sl, &sl->d_scen, (size_t)cap);
-    if (e == cudaSuccess) e = dmalloc(sl, &sl->d_pos, (size_t)cap);
-    if (e == cudaSuccess) e = dmalloc(sl, &sl->d_cap, (size_t)cap);
-    if (e == cudaSuccess) e = dmalloc(sl, &sl->d_list, (size_t)cap * dp::kMaxFanin);
-    if (e == cudaSuccess) e = hmalloc(sl, &sl->h_scen, (size_t)cap);
-    if (e == cudaSuccess) e = hmalloc(sl, &sl->h_pos, (size_t)cap);
-    if (e == cudaSuccess) sl->delta_cap = cap;
+    if (sl->delta_cap) free_delta_arrays(sl, stream_ordered);
+    cudaError_t e = cudaSuccess;
+    void *a = nullptr, *b = nullptr, *c = nullptr;
+    if (stream_ordered) {
+        e = cudaMallocAsync(&a, sizeof(int32_t) * (size_t)cap, sl->stream);
+        if (e == cudaSuccess) e = cudaMallocAsync(&b, sizeof(float) * (size_t)cap, sl->stream);
+        if (e == cudaSuccess) e = cudaMallocAsync(&c, sizeof(int64_t) * (size_t)cap * dp::kMaxFanin, sl->stream);
+    } else {
+        e = cudaMalloc(&a, sizeof(int32_t) * (size_t)cap);
+        if (e == cudaSuccess) e = cudaMalloc(&b, sizeof(float) * (size_t)cap);
+        if (e == cudaSuccess) e = cudaMalloc(&c, sizeof(int64_t) * (size_t)cap * dp::kMaxFanin);
+    }
+    sl->d_cell = static_cast<int32_t *>(a);
+    sl->d_cap = static_cast<float *>(b);
+    sl->d_list = static_cast<int64_t *>(c);
+    sl->delta_cap = cap;
+    sl->bytes += (size_t)(kDeltaEntryBytes * cap);
+    if (e != cudaSuccess) free_delta_arrays(sl, stream_ordered);
     return e;
 }
 
-dp::SizingDeltas deltas_view(const Slot *sl) {
-    return dp::SizingDeltas{sl->d_cell, sl->d_cap, sl->d_scen, sl->d_pos, sl->d_win, sl->d_dpin,
+dp::SizingDeltas deltas_view(const Slot *sl, int32_t n_req) {
+    return dp::SizingDeltas{sl->d_cell, sl->d_cap, sl->d_off, n_req, sl->d_win, sl->d_dpin,
                             sl->d_flag, sl->d_list, sl->d_count};
 }
 
@@ -309,28 +329,24 @@ cudaError_t launch_batch(dp_server *srv, Slot *sl) {
     }
     if (e != cudaSuccess) return e;
     if (nd) {   // the entries go to the device as given; the device resolves them (kern_serve.cu)
-        if ((e = ensure_delta_cap(sl, nd)) != cudaSuccess) return e;
+        if ((e = ensure_delta_cap(sl, nd, true)) != cudaSuccess) return e;
         int64_t off = 0;
         for (int64_t s = 0; s < S && e == cudaSuccess; s++) {
             const dp_request &r = sl->inflight[(size_t)s]->r;
+            sl->h_off[s] = (int32_t)off;
             if (r.n_delta <= 0) continue;
             e = cudaMemcpyAsync(sl->d_cell + off, r.cells, sizeof(int32_t) * (size_t)r.n_delta,
                                 cudaMemcpyHostToDevice, st);
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(sl->d_cap + off, r.pincap, sizeof(float) * (size_t)r.n_delta,
                                     cudaMemcpyHostToDevice, st);
-            for (int32_t i = 0; i < r.n_delta; i++) {
-                sl->h_scen[off + i] = (int32_t)s;
-                sl->h_pos[off + i] = i;
-            }
             off += r.n_delta;
         }
+        sl->h_off[S] = (int32_t)off;
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(sl->d_scen, sl->h_scen, sizeof(int32_t) * (size_t)nd, cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(sl->d_pos, sl->h_pos, sizeof(int32_t) * (size_t)nd, cudaMemcpyHostToDevice, st);
+            e = cudaMemcpyAsync(sl->d_off, sl->h_off, sizeof(int32_t) * (size_t)(S + 1), cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return e;
-        dp::launch_sizing_deltas(sl->D->d, sl->D->ops, deltas_view(sl), nd, Sg, sl->d_dcl, st);
+        dp::launch_sizing_deltas(sl->D->d, sl->D->ops, deltas_view(sl, (int32_t)S), nd, Sg, sl->d_dcl, st);
     }
     e = cudaGraphLaunch(sl->graphs[(size_t)bucket_index(Sg)][(grad ? 1 : 0) + (sl->batch_ref ? 2 : 0)], st);
     if (e != cudaSuccess) return e;
@@ -349,7 +365,7 @@ cudaError_t launch_batch(dp_server *srv, Slot *sl) {
                                     cudaMemcpyDeviceToHost, st);
         }
     if (e != cudaSuccess) return e;
-    if (nd) dp::launch_sizing_clear(sl->D->d, deltas_view(sl), nd, Sg, sl->d_dcl, st);   // back to rest
+    if (nd) dp::launch_sizing_clear(sl->D->d, deltas_view(sl, (int32_t)S), nd, Sg, sl->d_dcl, st);   // back to rest
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return cudaEventRecord(sl->done, st);
 }
@@ -408,7 +424,12 @@ void reset_after_failure(Slot *sl) {
 
 void run_and_complete(dp_server *srv, Slot *sl) {
     DeviceGuard g(srv->cfg.device);
+    const double t0 = now_s();
     cudaError_t e = launch_batch(srv, sl);
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        srv->stats.host_launch_s += now_s() - t0;
+    }
     if (e != cudaSuccess) {
         reset_after_failure(sl);
         complete_batch(srv, sl, DP_ECUDA);
@@ -616,6 +637,9 @@ dp_status make_slot(dp_server *srv, const dp_compiled *cp, const float *ref_sp, 
     if (e == cudaSuccess) e = dmalloc(sl, &sl->d_dpin, (size_t)(nc * S));
     if (e == cudaSuccess) e = dmalloc(sl, &sl->d_flag, (size_t)(nn * S));
     if (e == cudaSuccess) e = dmalloc(sl, &sl->d_count, 1);
+    if (e == cudaSuccess) e = dmalloc(sl, &sl->d_off, (size_t)(S + 1));
+    if (e == cudaSuccess) e = hmalloc(sl, &sl->h_off, (size_t)(S + 1));
+    if (e == cudaSuccess) e = ensure_delta_cap(sl, initial_delta_cap(S, nc), false);
     if (e == cudaSuccess) e = cudaMemsetAsync(sl->d_dcl, 0, sizeof(float) * (size_t)(nn * S), sl->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(sl->d_win, 0xFF, sizeof(int) * (size_t)(nc * S), sl->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(sl->d_dpin, 0, sizeof(float) * (size_t)(nc * S), sl->stream);
@@ -710,7 +734,8 @@ dp_status dp_server_add_design(dp_server *srv, const char *netlist, size_t netli
     const double need = 24.0 * nn + 40.0 * nc + 8.0 * ne + 72.0 * nn +
                         (double)S * (8.0 * nn + 4.0 * ne + 16.0 * ns + 4.0 * nn + 4.0 * std::max(nn, nc) +
                                      4.0 * (2 * ns + nc) + 8.0 * ns + 8.0 * dp::kBatchPowerChunks + 8.0 * nc +
-                                     4.0 * nn);
+                                     4.0 * nn) +
+                        (double)(kDeltaEntryBytes * initial_delta_cap(S, nc));
     {
         std::lock_guard<std::mutex> lk(srv->mu);
         if ((double)srv->bytes_used + nslots * need > (double)srv->cfg.hbm_budget) {
@@ -784,7 +809,12 @@ dp_status dp_server_submit(dp_server *srv, const dp_request *r, uint64_t *ticket
         sl->busy = true;
         lk.unlock();
         DeviceGuard g(srv->cfg.device);
+        const double t0 = now_s();
         cudaError_t e = launch_batch(srv, sl);
+        {
+            std::lock_guard<std::mutex> lk2(srv->mu);
+            srv->stats.host_launch_s += now_s() - t0;
+        }
         if (e == cudaSuccess) e = cudaEventSynchronize(sl->done);
         if (e != cudaSuccess) reset_after_failure(sl);
         complete_batch(srv, sl, e == cudaSuccess ? DP_OK : DP_ECUDA);

@@ -69,7 +69,7 @@ class dp_request(ctypes.Structure):
 
 class dp_server_stats(ctypes.Structure):
     _fields_ = [("batches", ctypes.c_int64), ("requests", ctypes.c_int64), ("max_batch_seen", ctypes.c_int64),
-                ("device_bytes", ctypes.c_size_t), ("designs", ctypes.c_int32)]
+                ("device_bytes", ctypes.c_size_t), ("designs", ctypes.c_int32), ("host_launch_s", ctypes.c_double)]
 
 
 _P = ctypes.c_void_p
