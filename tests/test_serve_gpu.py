@@ -250,3 +250,48 @@ def test_budget_admission_and_errors(dp, texts):
         dp.dp_server_destroy(srv)
     with pytest.raises(dp.DPError):
         dp.dp_server_create(dp.server_config(max_batch=0))
+
+
+def test_sizing_deltas_beyond_the_reserved_capacity(dp, texts):
+    """Batches whose sizing deltas outgrow the entries reserved at admission (the arrays grow
+    in stream order), with requests without deltas and cells listed twice in between: results
+    match the oracle and the plain loop bit for bit."""
+    lib = netgen.library_text()
+    text = texts["small"]
+    ns = netgen.WORKLOADS["small"].n_start
+    sp, tr = netgen.scenario_inputs(ns, 42, 1)
+    ref = (np.ascontiguousarray(sp[:, 0]), np.ascontiguousarray(tr[:, 0]))
+    srv = dp.dp_server_create(dp.server_config(max_batch=4))
+    plain = dp.dp_server_create(dp.server_config(plain=1))
+    try:
+        i = dp.dp_server_add_design(srv, text, lib, *ref)
+        assert dp.dp_server_add_design(plain, text, lib, *ref) == i
+        nc = dp.dp_server_design_info(srv, i).n_cells
+        rng = np.random.default_rng(5)
+        jobs = []
+        for r in range(8):
+            if r % 3 == 1:
+                jobs.append(Job(dp, i, ns, nc, grad=1))                   # no delta
+                continue
+            cells = np.concatenate([rng.permutation(nc), rng.permutation(nc)]).astype(np.int32)
+            caps = rng.choice(np.array([0.8, 1.6, 3.2], np.float32), cells.size)
+            jobs.append(Job(dp, i, ns, nc, cells=cells, caps=caps, grad=1))   # 2 entries per cell
+        run(dp, srv, jobs)
+        assert dp.dp_server_get_stats(srv).max_batch_seen > 1
+        served = [j.result() for j in jobs]
+        run(dp, plain, jobs, together=False)
+        for j, a in zip(jobs, served):
+            for x, y in zip(j.result(), a):
+                np.testing.assert_array_equal(x, y)
+        for j in jobs[:3]:
+            o = Oracle(text, lib)
+            if j.cells is not None:
+                for c, cap in zip(j.cells, j.caps):   # the last entry of a cell counts
+                    o.set_pincap(int(c), float(cap))
+            _, trf = o.forward(*ref, 0)
+            assert j.power[0] == pytest.approx(o.power(trf), rel=1e-6)
+            g = o.backward(*ref, None, 0, 0)
+            assert grad_close(j.gsp, g["grad_sp_in"]) and grad_close(j.gpin, g["grad_pincap"])
+    finally:
+        dp.dp_server_destroy(srv)
+        dp.dp_server_destroy(plain)
