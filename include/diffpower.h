@@ -324,10 +324,12 @@ dp_status dp_phase_times(dp_design *d, float *ms5);
  * Every shape gives bitwise identical results. */
 dp_status dp_set_inputs_batch(dp_design *d, const float *sp, const float *tr, int32_t n_scen, int on_device);
 
-/* Shapes in use (bx threads over scenarios x by cells per block) for the
- * forward (shape4[0..1]) and the reverse pass (shape4[2..3]), and the tuner's
- * best times in ms (ms2, may be NULL; 0 when fixed by the environment). */
-dp_status dp_batch_tuning(const dp_design *d, int32_t *shape4, float *ms2);
+/* Shapes in use (bx threads over scenarios x by cells per block x v scenarios
+ * per thread, v = 1 or 2; v = 2 applies to even n_scen) for the forward
+ * (shape6[0..2]) and the reverse pass (shape6[3..5]), and the tuner's best
+ * times in ms (ms2, may be NULL; 0 when fixed by the environment).  Every
+ * shape gives bitwise the same results. */
+dp_status dp_batch_tuning(const dp_design *d, int32_t *shape6, float *ms2);
 
 /* Reverse pass of the model power (Sec. III-E, Eq. 7) for every scenario,
  * scaled by weights[n_scen] (NULL: all 1): the gradient of

@@ -17,8 +17,11 @@ namespace {
 
 int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-// launch shapes the tuner tries: bx threads over scenarios x by cells per block
-const dp::BatchShape kShapes[] = {{32, 4}, {32, 8}, {64, 2}, {64, 4}, {128, 1}, {128, 2}, {256, 1}, {512, 1}};
+// launch shapes the tuner tries: bx threads over scenarios x by cells per block, v scenarios
+// per thread (two only where S is even)
+const dp::BatchShape kShapes[] = {{32, 4, 1}, {32, 8, 1},  {64, 2, 1},  {64, 4, 1},  {128, 1, 1}, {128, 2, 1},
+                                  {256, 1, 1}, {512, 1, 1}, {32, 8, 2},  {64, 2, 2},  {64, 4, 2},  {128, 1, 2},
+                                  {128, 2, 2}, {256, 1, 2}};
 
 template <class T>
 dp_status balloc(dp_design *D, T **p, size_t count) {
@@ -81,17 +84,34 @@ dp_status ensure_stage_batch(dp_design *D) {
     return balloc(D, &B.stage, (size_t)rows * (size_t)B.cap);
 }
 
+// DP_BATCH_SHAPE = "bx,by" | "bx,by,v" (both passes) | "bx,by,bx,by" | "bx,by,v,bx,by,v" (forward, reverse)
 bool parse_shape_env(dp::BatchShape *f, dp::BatchShape *b) {
     const char *v = std::getenv("DP_BATCH_SHAPE");
     if (!v) return false;
-    int a[4] = {0, 0, 0, 0};
-    int n = std::sscanf(v, "%d,%d,%d,%d", &a[0], &a[1], &a[2], &a[3]);
-    if (n != 2 && n != 4) return false;
-    if (n == 2) { a[2] = a[0]; a[3] = a[1]; }
-    for (int i = 0; i < 4; i += 2)
-        if (a[i] < 32 || a[i] > 1024 || (a[i] & 31) || a[i + 1] < 1 || a[i] * a[i + 1] > 1024) return false;
-    *f = dp::BatchShape{a[0], a[1]};
-    *b = dp::BatchShape{a[2], a[3]};
+    int a[6] = {0, 0, 0, 0, 0, 0};
+    const int n = std::sscanf(v, "%d,%d,%d,%d,%d,%d", &a[0], &a[1], &a[2], &a[3], &a[4], &a[5]);
+    int s[2][3];
+    if (n == 2 || n == 3) {
+        for (int i = 0; i < 2; i++) {
+            s[i][0] = a[0];
+            s[i][1] = a[1];
+            s[i][2] = n == 3 ? a[2] : 1;
+        }
+    } else if (n == 4) {
+        s[0][0] = a[0]; s[0][1] = a[1]; s[0][2] = 1;
+        s[1][0] = a[2]; s[1][1] = a[3]; s[1][2] = 1;
+    } else if (n == 6) {
+        for (int i = 0; i < 2; i++)
+            for (int j = 0; j < 3; j++) s[i][j] = a[3 * i + j];
+    } else {
+        return false;
+    }
+    for (int i = 0; i < 2; i++)
+        if (s[i][0] < 32 || s[i][0] > 1024 || (s[i][0] & 31) || s[i][1] < 1 || s[i][0] * s[i][1] > 1024 ||
+            (s[i][2] != 1 && s[i][2] != 2))
+            return false;
+    *f = dp::BatchShape{s[0][0], s[0][1], s[0][2]};
+    *b = dp::BatchShape{s[1][0], s[1][1], s[1][2]};
     return true;
 }
 
@@ -277,13 +297,15 @@ dp_status dp_set_inputs_batch(dp_design *D, const float *sp, const float *tr, in
     return DP_OK;
 }
 
-dp_status dp_batch_tuning(const dp_design *D, int32_t *shape4, float *ms2) {
-    if (!D || !shape4) return DP_EINVAL;
+dp_status dp_batch_tuning(const dp_design *D, int32_t *shape6, float *ms2) {
+    if (!D || !shape6) return DP_EINVAL;
     const dp_batch &B = D->batch;
-    shape4[0] = B.fwd_shape.bx;
-    shape4[1] = B.fwd_shape.by;
-    shape4[2] = B.bwd_shape.bx;
-    shape4[3] = B.bwd_shape.by;
+    shape6[0] = B.fwd_shape.bx;
+    shape6[1] = B.fwd_shape.by;
+    shape6[2] = B.fwd_shape.v;
+    shape6[3] = B.bwd_shape.bx;
+    shape6[4] = B.bwd_shape.by;
+    shape6[5] = B.bwd_shape.v;
     if (ms2) {
         ms2[0] = B.tune_ms[0];
         ms2[1] = B.tune_ms[1];

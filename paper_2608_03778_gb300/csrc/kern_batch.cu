@@ -105,6 +105,38 @@ __global__ void k_seedb(float *ks, const double *__restrict__ w, double K, int64
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s < S) ks[s] = (float)(w ? K * w[s] : K);
 }
+// The same level with two consecutive scenarios per thread (S even): each fanin
+// gather is one 16-byte load of both scenarios' P, so a warp keeps twice the
+// bytes in flight; every (cell, scenario) is computed exactly as above.
+__global__ void k_fwdb_level2(const uint4 *__restrict__ fanin, float2 *pq, int32_t c0, int32_t c1, int64_t ns,
+                              int64_t S, OpTable ops) {
+    const int64_t s = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    pdl_trigger();
+    if (s >= S) return;
+    const int64_t step = (int64_t)gridDim.y * blockDim.y;
+    const int64_t cf = c0 + (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
+    uint4 r = cf < c1 ? fanin[cf] : make_uint4(0, 0, 0, 0);   // static: before the wait
+    pdl_wait();
+    for (int64_t c = cf; c < c1; c += step) {
+        if (c != cf) r = fanin[c];
+        const uint32_t op = r.x >> 24;
+        const int k = op_arity(ops, op);
+        const uint32_t tt = op_tt(ops, op);
+        const uint32_t n[4] = {r.x & kMask24, r.y, r.z, r.w};
+        float4 v[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            v[j] = j < k ? *reinterpret_cast<const float4 *>(pq + (int64_t)n[j] * S + s) : make_float4(0.f, 0.f, 0.f, 0.f);
+        pair_ff x[4], y[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            x[j] = pair_get(make_float2(v[j].x, v[j].y));
+            y[j] = pair_get(make_float2(v[j].z, v[j].w));
+        }
+        const float2 a = cell_p(k, tt, x), b = cell_p(k, tt, y);
+        *reinterpret_cast<float4 *>(pq + (ns + c) * S + s) = make_float4(a.x, a.y, b.x, b.y);
+    }
+}
 
 // reverse level: each net's adjoint is its fanout range summed in index order
 // plus its local term d(K_s C 2PQ)/dP = 2 K_s C (Q - P); the cell then writes
@@ -143,6 +175,66 @@ __global__ void k_bwdb_level(const uint4 *__restrict__ fanin, const int32_t *__r
         if (k > 1) gfo[(int64_t)ep.y * S + s] = g * d[1];
         if (k > 2) gfo[(int64_t)ep.z * S + s] = g * d[2];
         if (k > 3) gfo[(int64_t)ep.w * S + s] = g * d[3];
+    }
+}
+
+// The same reverse level with two consecutive scenarios per thread (S even):
+// 16-byte loads of both scenarios' P, 8-byte loads and stores of their edge
+// adjoints; every (cell, scenario) is computed exactly as above.
+__global__ void k_bwdb_level2(const uint4 *__restrict__ fanin, const int32_t *__restrict__ fptr,
+                              const int4 *__restrict__ efpos, const float2 *__restrict__ pq,
+                              const float *__restrict__ cload, const float *__restrict__ dcl,
+                              const float *__restrict__ ks, float *gfo, int32_t c0, int32_t c1, int64_t ns, int64_t S,
+                              OpTable ops) {
+    const int64_t s = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    pdl_trigger();
+    if (s >= S) return;
+    const int64_t step = (int64_t)gridDim.y * blockDim.y;
+    const int64_t cf = c0 + (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
+    uint4 rf = cf < c1 ? fanin[cf] : make_uint4(0, 0, 0, 0);   // static: before the wait
+    pdl_wait();
+    const float2 Ks = *reinterpret_cast<const float2 *>(ks + s);
+    for (int64_t c = cf; c < c1; c += step) {
+        const int64_t n = ns + c;
+        const uint4 r = c == cf ? rf : fanin[c];
+        const int4 ep = efpos[c];
+        const int32_t e0 = fptr[n], e1 = fptr[n + 1];
+        const float4 self = *reinterpret_cast<const float4 *>(pq + n * S + s);
+        float2 cl = make_float2(cload[n], cload[n]);
+        if (dcl) {
+            const float2 dd = *reinterpret_cast<const float2 *>(dcl + n * S + s);
+            cl = make_float2(cload[n] + dd.x, cload[n] + dd.y);
+        }
+        const uint32_t op = r.x >> 24;
+        const int k = op_arity(ops, op);
+        const uint32_t nid[4] = {r.x & kMask24, r.y, r.z, r.w};
+        float4 v[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            v[j] = j < k ? *reinterpret_cast<const float4 *>(pq + (int64_t)nid[j] * S + s) : make_float4(0.f, 0.f, 0.f, 0.f);
+        float2 acc = make_float2(0.f, 0.f);
+        for (int32_t e = e0; e < e1; e++) {
+            const float2 t = *reinterpret_cast<const float2 *>(gfo + (int64_t)e * S + s);
+            acc.x += t.x;
+            acc.y += t.y;
+        }
+        float pa[4], qa[4], pb[4], qb[4], da[4], db[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const pair_ff a = pair_get(make_float2(v[j].x, v[j].y)), b = pair_get(make_float2(v[j].z, v[j].w));
+            pa[j] = a.p.hi + a.p.lo;
+            qa[j] = a.q.hi + a.q.lo;
+            pb[j] = b.p.hi + b.p.lo;
+            qb[j] = b.q.hi + b.q.lo;
+        }
+        const float ga = acc.x + 2.f * Ks.x * cl.x * qmp32(make_float2(self.x, self.y));
+        const float gb = acc.y + 2.f * Ks.y * cl.y * qmp32(make_float2(self.z, self.w));
+        cell_partials(k, op_tt(ops, op), pa, qa, da);
+        cell_partials(k, op_tt(ops, op), pb, qb, db);
+        if (k > 0) *reinterpret_cast<float2 *>(gfo + (int64_t)ep.x * S + s) = make_float2(ga * da[0], gb * db[0]);
+        if (k > 1) *reinterpret_cast<float2 *>(gfo + (int64_t)ep.y * S + s) = make_float2(ga * da[1], gb * db[1]);
+        if (k > 2) *reinterpret_cast<float2 *>(gfo + (int64_t)ep.z * S + s) = make_float2(ga * da[2], gb * db[2]);
+        if (k > 3) *reinterpret_cast<float2 *>(gfo + (int64_t)ep.w * S + s) = make_float2(ga * da[3], gb * db[3]);
     }
 }
 
@@ -358,11 +450,14 @@ void launch_fwdb(const DevDesign &d, const BatchBufs &b, const OpTable &ops, con
     }
     const int64_t S = b.S;
     if (d.n_start) k_fwdb_start<<<(unsigned)cdiv(d.n_start * S, 256), 256, 0, s>>>(b.sp_in, b.pq, d.n_start * S);
-    sh = fit_shape(sh, S);
+    const bool two = sh.v == 2 && S % 2 == 0;   // two scenarios per thread
+    sh = fit_shape(sh, two ? S / 2 : S);
     const dim3 blk((unsigned)sh.bx, (unsigned)sh.by);
     for (int l = 1; l <= d.n_levels; l++) {
         const int32_t c0 = lvl[l - 1], c1 = lvl[l];
-        if (c1 > c0) launch_pdl(k_fwdb_level, bgrid(S, sh, c1 - c0), blk, s, d.fanin, b.pq, c0, c1, d.n_start, S, ops);
+        if (c1 <= c0) continue;
+        if (two) launch_pdl(k_fwdb_level2, bgrid(S / 2, sh, c1 - c0), blk, s, d.fanin, b.pq, c0, c1, d.n_start, S, ops);
+        else launch_pdl(k_fwdb_level, bgrid(S, sh, c1 - c0), blk, s, d.fanin, b.pq, c0, c1, d.n_start, S, ops);
     }
 }
 
@@ -387,17 +482,23 @@ void launch_bwdb(const DevDesign &d, const BatchBufs &b, const OpTable &ops, con
         return;
     }
     const int64_t S = b.S;
-    sh = fit_shape(sh, S);
+    const bool two = sh.v == 2 && S % 2 == 0;   // two scenarios per thread in the cell levels
+    const BatchShape sh1 = fit_shape(sh, S);
+    sh = fit_shape(sh, two ? S / 2 : S);
     const dim3 blk((unsigned)sh.bx, (unsigned)sh.by);
     for (int l = d.n_levels; l >= 1; l--) {
         const int32_t c0 = lvl[l - 1], c1 = lvl[l];
-        if (c1 > c0)
+        if (c1 <= c0) continue;
+        if (two)
+            launch_pdl(k_bwdb_level2, bgrid(S / 2, sh, c1 - c0), blk, s, d.fanin, d.fout_ptr,
+                       (const int4 *)d.edge_fpos, b.pq, d.cload, b.dcl, b.ks, b.gfo, c0, c1, d.n_start, S, ops);
+        else
             launch_pdl(k_bwdb_level, bgrid(S, sh, c1 - c0), blk, s, d.fanin, d.fout_ptr, (const int4 *)d.edge_fpos,
                        b.pq, d.cload, b.dcl, b.ks, b.gfo, c0, c1, d.n_start, S, ops);
     }
     if (d.n_start)
-        launch_pdl(k_bwdb_start, bgrid(S, sh, d.n_start), blk, s, d.fout_ptr, b.pq, d.cload, b.dcl, b.ks, b.gfo, b.gsp,
-                   d.n_start, S, tr_mode);
+        launch_pdl(k_bwdb_start, bgrid(S, sh1, d.n_start), dim3((unsigned)sh1.bx, (unsigned)sh1.by), s, d.fout_ptr,
+                   b.pq, d.cload, b.dcl, b.ks, b.gfo, b.gsp, d.n_start, S, tr_mode);
 }
 
 void launch_gradb(const DevDesign &d, const BatchBufs &b, const OpTable &ops, int tr_mode, bool reduce, float *gtr,

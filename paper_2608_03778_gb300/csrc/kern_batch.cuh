@@ -130,7 +130,7 @@ inline BatchShape fit_shape(BatchShape sh, int64_t S) {
     int bx = 1;
     while (bx < S) bx <<= 1;
     if (bx >= sh.bx) return sh;   // a width that is no power of two (set by hand) and S above its half
-    return BatchShape{bx, sh.bx * sh.by / bx};
+    return BatchShape{bx, sh.bx * sh.by / bx, sh.v};
 }
 
 inline dim3 bgrid(int64_t S, BatchShape sh, int64_t rows) {

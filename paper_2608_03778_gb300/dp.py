@@ -404,11 +404,12 @@ def dp_set_inputs_batch(ctx, d, sp, tr, n_scen: int, on_device: int = 0) -> None
 
 
 def dp_batch_tuning(d):
-    """((fwd_bx, fwd_by), (bwd_bx, bwd_by), (fwd_ms, bwd_ms)) chosen by the autotuner."""
-    sh = np.zeros(4, np.int32)
+    """((fwd_bx, fwd_by, fwd_v), (bwd_bx, bwd_by, bwd_v), (fwd_ms, bwd_ms)) chosen by the autotuner
+    (v: scenarios per thread)."""
+    sh = np.zeros(6, np.int32)
     ms = np.zeros(2, np.float32)
     _check(_lib.dp_batch_tuning(d, sh.ctypes.data, ms.ctypes.data))
-    return (int(sh[0]), int(sh[1])), (int(sh[2]), int(sh[3])), (float(ms[0]), float(ms[1]))
+    return (int(sh[0]), int(sh[1]), int(sh[2])), (int(sh[3]), int(sh[4]), int(sh[5])), (float(ms[0]), float(ms[1]))
 
 
 def dp_backward_weighted(ctx, d, cfg: dp_config, weights=None, cap_reduce: int = 0, grad_sp_in=None,

@@ -130,15 +130,17 @@ def test_shapes_give_identical_bits(dp, ctx, small):
     sp, tr = netgen.scenario_inputs(o.n_start, 3000, S)
     cfg = dp.config(grad_mode=0, tr_mode=0)
     results = []
-    for shape in ["32,4", "64,2,32,8", "128,1", "256,1,64,4"]:
+    # (bx, by) or (bx, by, v) for both passes, or one shape per pass; v = 2 scenarios per thread
+    for shape in ["32,4", "64,2,32,8", "128,1", "256,1,64,4", "64,2,2", "128,1,2,32,8,1", "32,8,1,128,2,2"]:
         os.environ["DP_BATCH_SHAPE"] = shape
         try:
             d = dp.dp_design_load(ctx, text, netgen.library_text())
             try:
                 g = run_batch(dp, ctx, d, sp, tr, cfg)
-                want = [int(x) for x in shape.split(",")]
+                a = [int(x) for x in shape.split(",")]
+                want = {2: a + [1] + a + [1], 3: a + a, 4: a[:2] + [1] + a[2:] + [1], 6: a}[len(a)]
                 fwd, bwd, _ = dp.dp_batch_tuning(d)
-                assert list(fwd) + list(bwd) == (want + want if len(want) == 2 else want)
+                assert list(fwd) + list(bwd) == want
             finally:
                 dp.dp_design_free(d)
         finally:
@@ -179,8 +181,8 @@ def test_autotuner_picks_a_candidate(dp, ctx, small):
         fwd, bwd, ms = dp.dp_batch_tuning(d)
     finally:
         dp.dp_design_free(d)
-    for bx, by in (fwd, bwd):
-        assert bx in (32, 64, 128, 256, 512) and by >= 1 and bx * by <= 1024
+    for bx, by, v in (fwd, bwd):
+        assert bx in (32, 64, 128, 256, 512) and by >= 1 and bx * by <= 1024 and v in (1, 2)
     assert ms[0] > 0 and ms[1] > 0
 
 
