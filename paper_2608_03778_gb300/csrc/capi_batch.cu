@@ -18,10 +18,10 @@ namespace {
 int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 // launch shapes the tuner tries: bx threads over scenarios x by cells per block, v scenarios
-// per thread (two only where S is even)
+// per thread (2 or 4 only where S is a multiple of it)
 const dp::BatchShape kShapes[] = {{32, 4, 1}, {32, 8, 1},  {64, 2, 1},  {64, 4, 1},  {128, 1, 1}, {128, 2, 1},
                                   {256, 1, 1}, {512, 1, 1}, {32, 8, 2},  {64, 2, 2},  {64, 4, 2},  {128, 1, 2},
-                                  {128, 2, 2}, {256, 1, 2}};
+                                  {128, 2, 2}, {256, 1, 2}, {32, 4, 4},  {64, 2, 4},  {128, 1, 4}};
 
 template <class T>
 dp_status balloc(dp_design *D, T **p, size_t count) {
@@ -108,7 +108,7 @@ bool parse_shape_env(dp::BatchShape *f, dp::BatchShape *b) {
     }
     for (int i = 0; i < 2; i++)
         if (s[i][0] < 32 || s[i][0] > 1024 || (s[i][0] & 31) || s[i][1] < 1 || s[i][0] * s[i][1] > 1024 ||
-            (s[i][2] != 1 && s[i][2] != 2))
+            (s[i][2] != 1 && s[i][2] != 2 && s[i][2] != 4))
             return false;
     *f = dp::BatchShape{s[0][0], s[0][1], s[0][2]};
     *b = dp::BatchShape{s[1][0], s[1][1], s[1][2]};

@@ -105,12 +105,14 @@ __global__ void k_seedb(float *ks, const double *__restrict__ w, double K, int64
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s < S) ks[s] = (float)(w ? K * w[s] : K);
 }
-// The same level with two consecutive scenarios per thread (S even): each fanin
-// gather is one 16-byte load of both scenarios' P, so a warp keeps twice the
-// bytes in flight; every (cell, scenario) is computed exactly as above.
-__global__ void k_fwdb_level2(const uint4 *__restrict__ fanin, float2 *pq, int32_t c0, int32_t c1, int64_t ns,
+// The same level with V consecutive scenarios per thread (V = 2 or 4, S a
+// multiple of V): each fanin gather is V / 2 16-byte loads of those scenarios'
+// P, so a warp keeps V times the bytes in flight; every (cell, scenario) is
+// computed exactly as above.
+template <int V>
+__global__ void k_fwdb_levelv(const uint4 *__restrict__ fanin, float2 *pq, int32_t c0, int32_t c1, int64_t ns,
                               int64_t S, OpTable ops) {
-    const int64_t s = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    const int64_t s = V * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
     pdl_trigger();
     if (s >= S) return;
     const int64_t step = (int64_t)gridDim.y * blockDim.y;
@@ -123,18 +125,27 @@ __global__ void k_fwdb_level2(const uint4 *__restrict__ fanin, float2 *pq, int32
         const int k = op_arity(ops, op);
         const uint32_t tt = op_tt(ops, op);
         const uint32_t n[4] = {r.x & kMask24, r.y, r.z, r.w};
-        float4 v[4];
+        float4 v[4][V / 2];
 #pragma unroll
         for (int j = 0; j < 4; j++)
-            v[j] = j < k ? *reinterpret_cast<const float4 *>(pq + (int64_t)n[j] * S + s) : make_float4(0.f, 0.f, 0.f, 0.f);
-        pair_ff x[4], y[4];
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
-            x[j] = pair_get(make_float2(v[j].x, v[j].y));
-            y[j] = pair_get(make_float2(v[j].z, v[j].w));
+            for (int h = 0; h < V / 2; h++)
+                v[j][h] = j < k ? reinterpret_cast<const float4 *>(pq + (int64_t)n[j] * S + s)[h]
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 out[V / 2];
+#pragma unroll
+        for (int h = 0; h < V / 2; h++) {
+            pair_ff x[4], y[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                x[j] = pair_get(make_float2(v[j][h].x, v[j][h].y));
+                y[j] = pair_get(make_float2(v[j][h].z, v[j][h].w));
+            }
+            const float2 a = cell_p(k, tt, x), b = cell_p(k, tt, y);
+            out[h] = make_float4(a.x, a.y, b.x, b.y);
         }
-        const float2 a = cell_p(k, tt, x), b = cell_p(k, tt, y);
-        *reinterpret_cast<float4 *>(pq + (ns + c) * S + s) = make_float4(a.x, a.y, b.x, b.y);
+#pragma unroll
+        for (int h = 0; h < V / 2; h++) reinterpret_cast<float4 *>(pq + (ns + c) * S + s)[h] = out[h];
     }
 }
 
@@ -178,63 +189,92 @@ __global__ void k_bwdb_level(const uint4 *__restrict__ fanin, const int32_t *__r
     }
 }
 
-// The same reverse level with two consecutive scenarios per thread (S even):
-// 16-byte loads of both scenarios' P, 8-byte loads and stores of their edge
-// adjoints; every (cell, scenario) is computed exactly as above.
-__global__ void k_bwdb_level2(const uint4 *__restrict__ fanin, const int32_t *__restrict__ fptr,
+// The same reverse level with V consecutive scenarios per thread (V = 2 or 4,
+// S a multiple of V): 16-byte loads of those scenarios' P, 8- or 16-byte loads
+// and stores of their edge adjoints; every (cell, scenario) is computed
+// exactly as above.
+template <int V>
+__global__ void k_bwdb_levelv(const uint4 *__restrict__ fanin, const int32_t *__restrict__ fptr,
                               const int4 *__restrict__ efpos, const float2 *__restrict__ pq,
                               const float *__restrict__ cload, const float *__restrict__ dcl,
                               const float *__restrict__ ks, float *gfo, int32_t c0, int32_t c1, int64_t ns, int64_t S,
                               OpTable ops) {
-    const int64_t s = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    const int64_t s = V * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
     pdl_trigger();
     if (s >= S) return;
     const int64_t step = (int64_t)gridDim.y * blockDim.y;
     const int64_t cf = c0 + (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
     uint4 rf = cf < c1 ? fanin[cf] : make_uint4(0, 0, 0, 0);   // static: before the wait
     pdl_wait();
-    const float2 Ks = *reinterpret_cast<const float2 *>(ks + s);
+    float Ks[V];
+#pragma unroll
+    for (int i = 0; i < V; i++) Ks[i] = ks[s + i];
     for (int64_t c = cf; c < c1; c += step) {
         const int64_t n = ns + c;
         const uint4 r = c == cf ? rf : fanin[c];
         const int4 ep = efpos[c];
         const int32_t e0 = fptr[n], e1 = fptr[n + 1];
-        const float4 self = *reinterpret_cast<const float4 *>(pq + n * S + s);
-        float2 cl = make_float2(cload[n], cload[n]);
-        if (dcl) {
-            const float2 dd = *reinterpret_cast<const float2 *>(dcl + n * S + s);
-            cl = make_float2(cload[n] + dd.x, cload[n] + dd.y);
+        float2 self[V];
+#pragma unroll
+        for (int h = 0; h < V / 2; h++) {
+            const float4 t = reinterpret_cast<const float4 *>(pq + n * S + s)[h];
+            self[2 * h] = make_float2(t.x, t.y);
+            self[2 * h + 1] = make_float2(t.z, t.w);
         }
+        float cl[V];
+#pragma unroll
+        for (int i = 0; i < V; i++) cl[i] = dcl ? cload[n] + dcl[n * S + s + i] : cload[n];
         const uint32_t op = r.x >> 24;
         const int k = op_arity(ops, op);
+        const uint32_t tt = op_tt(ops, op);
         const uint32_t nid[4] = {r.x & kMask24, r.y, r.z, r.w};
-        float4 v[4];
+        float4 v[4][V / 2];
 #pragma unroll
         for (int j = 0; j < 4; j++)
-            v[j] = j < k ? *reinterpret_cast<const float4 *>(pq + (int64_t)nid[j] * S + s) : make_float4(0.f, 0.f, 0.f, 0.f);
-        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int h = 0; h < V / 2; h++)
+                v[j][h] = j < k ? reinterpret_cast<const float4 *>(pq + (int64_t)nid[j] * S + s)[h]
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+        float acc[V];
+#pragma unroll
+        for (int i = 0; i < V; i++) acc[i] = 0.f;
         for (int32_t e = e0; e < e1; e++) {
-            const float2 t = *reinterpret_cast<const float2 *>(gfo + (int64_t)e * S + s);
-            acc.x += t.x;
-            acc.y += t.y;
+            const float *src = gfo + (int64_t)e * S + s;
+            if (V == 4) {
+                const float4 t = *reinterpret_cast<const float4 *>(src);
+                acc[0] += t.x;
+                acc[1 % V] += t.y;
+                acc[2 % V] += t.z;
+                acc[3 % V] += t.w;
+            } else {
+                const float2 t = *reinterpret_cast<const float2 *>(src);
+                acc[0] += t.x;
+                acc[1 % V] += t.y;
+            }
         }
-        float pa[4], qa[4], pb[4], qb[4], da[4], db[4];
+        float g[V], d[V][4];
+#pragma unroll
+        for (int i = 0; i < V; i++) {
+            float p[4], q[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const float4 &w = v[j][i / 2];
+                const pair_ff a = pair_get((i & 1) ? make_float2(w.z, w.w) : make_float2(w.x, w.y));
+                p[j] = a.p.hi + a.p.lo;
+                q[j] = a.q.hi + a.q.lo;
+            }
+            g[i] = acc[i] + 2.f * Ks[i] * cl[i] * qmp32(self[i]);
+            cell_partials(k, tt, p, q, d[i]);
+        }
+        const int pos[4] = {ep.x, ep.y, ep.z, ep.w};
 #pragma unroll
         for (int j = 0; j < 4; j++) {
-            const pair_ff a = pair_get(make_float2(v[j].x, v[j].y)), b = pair_get(make_float2(v[j].z, v[j].w));
-            pa[j] = a.p.hi + a.p.lo;
-            qa[j] = a.q.hi + a.q.lo;
-            pb[j] = b.p.hi + b.p.lo;
-            qb[j] = b.q.hi + b.q.lo;
+            if (j >= k) break;
+            float *dst = gfo + (int64_t)pos[j] * S + s;
+            if (V == 4) *reinterpret_cast<float4 *>(dst) = make_float4(g[0] * d[0][j], g[1 % V] * d[1 % V][j],
+                                                                       g[2 % V] * d[2 % V][j], g[3 % V] * d[3 % V][j]);
+            else *reinterpret_cast<float2 *>(dst) = make_float2(g[0] * d[0][j], g[1 % V] * d[1 % V][j]);
         }
-        const float ga = acc.x + 2.f * Ks.x * cl.x * qmp32(make_float2(self.x, self.y));
-        const float gb = acc.y + 2.f * Ks.y * cl.y * qmp32(make_float2(self.z, self.w));
-        cell_partials(k, op_tt(ops, op), pa, qa, da);
-        cell_partials(k, op_tt(ops, op), pb, qb, db);
-        if (k > 0) *reinterpret_cast<float2 *>(gfo + (int64_t)ep.x * S + s) = make_float2(ga * da[0], gb * db[0]);
-        if (k > 1) *reinterpret_cast<float2 *>(gfo + (int64_t)ep.y * S + s) = make_float2(ga * da[1], gb * db[1]);
-        if (k > 2) *reinterpret_cast<float2 *>(gfo + (int64_t)ep.z * S + s) = make_float2(ga * da[2], gb * db[2]);
-        if (k > 3) *reinterpret_cast<float2 *>(gfo + (int64_t)ep.w * S + s) = make_float2(ga * da[3], gb * db[3]);
     }
 }
 
@@ -450,14 +490,16 @@ void launch_fwdb(const DevDesign &d, const BatchBufs &b, const OpTable &ops, con
     }
     const int64_t S = b.S;
     if (d.n_start) k_fwdb_start<<<(unsigned)cdiv(d.n_start * S, 256), 256, 0, s>>>(b.sp_in, b.pq, d.n_start * S);
-    const bool two = sh.v == 2 && S % 2 == 0;   // two scenarios per thread
-    sh = fit_shape(sh, two ? S / 2 : S);
+    const int v = scen_per_thread(sh, S);
+    sh = fit_shape(sh, S / v);
     const dim3 blk((unsigned)sh.bx, (unsigned)sh.by);
     for (int l = 1; l <= d.n_levels; l++) {
         const int32_t c0 = lvl[l - 1], c1 = lvl[l];
         if (c1 <= c0) continue;
-        if (two) launch_pdl(k_fwdb_level2, bgrid(S / 2, sh, c1 - c0), blk, s, d.fanin, b.pq, c0, c1, d.n_start, S, ops);
-        else launch_pdl(k_fwdb_level, bgrid(S, sh, c1 - c0), blk, s, d.fanin, b.pq, c0, c1, d.n_start, S, ops);
+        const dim3 g = bgrid(S / v, sh, c1 - c0);
+        if (v == 4) launch_pdl(k_fwdb_levelv<4>, g, blk, s, d.fanin, b.pq, c0, c1, d.n_start, S, ops);
+        else if (v == 2) launch_pdl(k_fwdb_levelv<2>, g, blk, s, d.fanin, b.pq, c0, c1, d.n_start, S, ops);
+        else launch_pdl(k_fwdb_level, g, blk, s, d.fanin, b.pq, c0, c1, d.n_start, S, ops);
     }
 }
 
@@ -482,19 +524,23 @@ void launch_bwdb(const DevDesign &d, const BatchBufs &b, const OpTable &ops, con
         return;
     }
     const int64_t S = b.S;
-    const bool two = sh.v == 2 && S % 2 == 0;   // two scenarios per thread in the cell levels
+    const int v = scen_per_thread(sh, S);   // scenarios per thread in the cell levels
     const BatchShape sh1 = fit_shape(sh, S);
-    sh = fit_shape(sh, two ? S / 2 : S);
+    sh = fit_shape(sh, S / v);
     const dim3 blk((unsigned)sh.bx, (unsigned)sh.by);
     for (int l = d.n_levels; l >= 1; l--) {
         const int32_t c0 = lvl[l - 1], c1 = lvl[l];
         if (c1 <= c0) continue;
-        if (two)
-            launch_pdl(k_bwdb_level2, bgrid(S / 2, sh, c1 - c0), blk, s, d.fanin, d.fout_ptr,
-                       (const int4 *)d.edge_fpos, b.pq, d.cload, b.dcl, b.ks, b.gfo, c0, c1, d.n_start, S, ops);
+        const dim3 g = bgrid(S / v, sh, c1 - c0);
+        if (v == 4)
+            launch_pdl(k_bwdb_levelv<4>, g, blk, s, d.fanin, d.fout_ptr, (const int4 *)d.edge_fpos, b.pq, d.cload,
+                       b.dcl, b.ks, b.gfo, c0, c1, d.n_start, S, ops);
+        else if (v == 2)
+            launch_pdl(k_bwdb_levelv<2>, g, blk, s, d.fanin, d.fout_ptr, (const int4 *)d.edge_fpos, b.pq, d.cload,
+                       b.dcl, b.ks, b.gfo, c0, c1, d.n_start, S, ops);
         else
-            launch_pdl(k_bwdb_level, bgrid(S, sh, c1 - c0), blk, s, d.fanin, d.fout_ptr, (const int4 *)d.edge_fpos,
-                       b.pq, d.cload, b.dcl, b.ks, b.gfo, c0, c1, d.n_start, S, ops);
+            launch_pdl(k_bwdb_level, g, blk, s, d.fanin, d.fout_ptr, (const int4 *)d.edge_fpos, b.pq, d.cload,
+                       b.dcl, b.ks, b.gfo, c0, c1, d.n_start, S, ops);
     }
     if (d.n_start)
         launch_pdl(k_bwdb_start, bgrid(S, sh1, d.n_start), dim3((unsigned)sh1.bx, (unsigned)sh1.by), s, d.fout_ptr,

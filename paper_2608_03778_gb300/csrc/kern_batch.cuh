@@ -133,6 +133,9 @@ inline BatchShape fit_shape(BatchShape sh, int64_t S) {
     return BatchShape{bx, sh.bx * sh.by / bx, sh.v};
 }
 
+// scenarios per thread a shape gets for S scenarios: its v where S is a multiple of it, else 1
+inline int scen_per_thread(BatchShape sh, int64_t S) { return (sh.v == 2 || sh.v == 4) && S % sh.v == 0 ? sh.v : 1; }
+
 inline dim3 bgrid(int64_t S, BatchShape sh, int64_t rows) {
     const int64_t gy = bcdiv(rows > 0 ? rows : 1, sh.by);
     return dim3((unsigned)bcdiv(S, sh.bx), (unsigned)(gy < 65535 ? gy : 65535));

@@ -127,7 +127,7 @@ constexpr int kBatchPowerChunks = 1024;   // fixed split of the nets -> determin
 
 struct BatchShape {
     int bx, by;   // threads over scenarios x cells per block
-    int v = 1;    // scenarios per thread in the forward and reverse cell levels (1, or 2 when S is even)
+    int v = 1;    // scenarios per thread in the forward and reverse cell levels (1, 2 or 4; 1 unless S is a multiple)
 };
 
 void launch_fwdb(const DevDesign &d, const BatchBufs &b, const OpTable &ops, const int32_t *lvl_host, int tr_mode,

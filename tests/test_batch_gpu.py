@@ -124,14 +124,17 @@ def test_weights_and_scenario_sums(dp, ctx, small):
                                rtol=2e-6, atol=1e-6 * np.abs(g["grad_pincap"]).max())
 
 
-def test_shapes_give_identical_bits(dp, ctx, small):
+@pytest.mark.parametrize("S", [70, 72])
+def test_shapes_give_identical_bits(dp, ctx, small, S):
+    """Every launch shape gives the same bits: scenario widths, cells per block, and 1, 2 or 4
+    scenarios per thread (a v that does not divide S falls back to 1)."""
     text, o = small
-    S = 70
     sp, tr = netgen.scenario_inputs(o.n_start, 3000, S)
     cfg = dp.config(grad_mode=0, tr_mode=0)
     results = []
-    # (bx, by) or (bx, by, v) for both passes, or one shape per pass; v = 2 scenarios per thread
-    for shape in ["32,4", "64,2,32,8", "128,1", "256,1,64,4", "64,2,2", "128,1,2,32,8,1", "32,8,1,128,2,2"]:
+    # (bx, by) or (bx, by, v) for both passes, or one shape per pass; v scenarios per thread
+    for shape in ["32,4", "64,2,32,8", "128,1", "256,1,64,4", "64,2,2", "128,1,2,32,8,1", "32,8,1,128,2,2",
+                  "32,4,4", "64,2,4,128,1,2", "128,1,4"]:
         os.environ["DP_BATCH_SHAPE"] = shape
         try:
             d = dp.dp_design_load(ctx, text, netgen.library_text())
@@ -182,7 +185,7 @@ def test_autotuner_picks_a_candidate(dp, ctx, small):
     finally:
         dp.dp_design_free(d)
     for bx, by, v in (fwd, bwd):
-        assert bx in (32, 64, 128, 256, 512) and by >= 1 and bx * by <= 1024 and v in (1, 2)
+        assert bx in (32, 64, 128, 256, 512) and by >= 1 and bx * by <= 1024 and v in (1, 2, 4)
     assert ms[0] > 0 and ms[1] > 0
 
 
