@@ -107,17 +107,17 @@ def batched_algorithmic_bytes(nn: int, ns: int, nc: int, ne: int, S: int) -> int
 TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,lts__t_bytes.sum,... (one launch),
     # 2M-cell step, 4th step (profiles/roofline_step_k_sim_wide_traffic.md)
-    "k_sim_wide": {"bytes": 224_548_608 + 162_620_416, "l2_bytes": 7_807_160_736, "workload": "roofline",
+    "k_sim_wide": {"bytes": 224_364_032 + 162_103_808, "l2_bytes": 7_802_348_064, "workload": "roofline",
                    "files": ["kern_persist.cu", "kern_common.cuh"],
-                   "sha": "f0daa1842f2960d9"},
+                   "sha": "8e07f42ec529d814"},
 }
 
 
 # L2 <-> SM throughput ceiling for the L2 fraction of the dominant kernel: ncu's peak of
 # lts__t_bytes on this part (summarised with the capture under profiles/); None until measured.
-L2_PEAK_GBS = 36_205.0
-L2_PEAK_SOURCE = ("ncu on k_sim_wide, 2M-cell step: lts__t_bytes.sum.per_second 11,466 GB/s at "
-                  "lts__t_bytes.sum.pct_of_peak_sustained_elapsed 31.67 %")
+L2_PEAK_GBS = 36_170.0
+L2_PEAK_SOURCE = ("ncu on k_sim_wide, 2M-cell step: lts__t_bytes.sum.per_second 11,488 GB/s at "
+                  "lts__t_bytes.sum.pct_of_peak_sustained_elapsed 31.76 %")
 
 
 def kernel_l2_bytes(kernel: str, workload: str) -> int | None:
@@ -806,7 +806,6 @@ def main() -> None:
         phases.append(dp.dp_phase_times(ctx, d))   # library events around each phase of this step
     torch.cuda.synchronize()
     barrier(world)
-    clocks = clk.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = max_over_ranks(sum(step_ms) / len(step_ms), world)
     ph = np.median(np.stack(phases), axis=0)
@@ -879,12 +878,13 @@ def main() -> None:
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(kernels) * args.steps,   # kernel nodes of the step graph x timed steps
         "gpu_launches_per_step": int(kernels),
-        "clocks": clocks,
         "device_bytes": int(info.device_bytes),
     }
     # ---- forward + reverse alone (model gradient, no simulation): N_c / (t_fwd + t_bwd)
     fbm = fwd_bwd_record(dp, ctx, d, stream, flush, max(args.steps, 50), pk)
     line["fwd_bwd_model"] = fbm
+    # clocks sampled from the first timed step to here (step, warm-L2 steps, forward + reverse)
+    line["clocks"] = clk.stop()
     # ---- the latency floor of the level-synchronous passes, measured with the library's barrier
     if not args.no_probe:
         lat = dp.dp_probe_latency(ctx, 1000)
