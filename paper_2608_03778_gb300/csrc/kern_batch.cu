@@ -89,6 +89,65 @@ __global__ void k_powerb_partials(const float2 *__restrict__ pq, const float *__
     partials[s * nchunks + blockIdx.y] = (double)acc.hi + (double)acc.lo;
 }
 
+// The same partial sums with four consecutive scenarios per thread (S a
+// multiple of 4): one 32-byte load of their P per net, four accumulators, each
+// scenario's terms added in the same net order as above (bitwise the same).
+__global__ void k_powerb_partials4(const float2 *__restrict__ pq, const float *__restrict__ tr_in,
+                                   const float *__restrict__ cload, const float *__restrict__ dcl, double *partials,
+                                   int64_t nn, int64_t ns, int64_t S, int64_t chunk, int nchunks, int tr_mode) {
+    const int64_t s = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    if (s >= S) return;
+    const int64_t n0 = (int64_t)blockIdx.y * chunk, n1 = n0 + chunk < nn ? n0 + chunk : nn;
+    ff acc[4] = {ff_make(0.f), ff_make(0.f), ff_make(0.f), ff_make(0.f)};
+    for (int64_t n = n0; n < n1; n += 2) {
+        float a[2][4], c[2][4];
+#pragma unroll
+        for (int i = 0; i < 2; i++) {
+            const int64_t m = n + i;
+#pragma unroll
+            for (int v = 0; v < 4; v++) a[i][v] = c[i][v] = 0.f;
+            if (m < n1) {
+                if (tr_mode == 2 || (m < ns && tr_mode == 0)) {
+                    const float4 t = *reinterpret_cast<const float4 *>(tr_in + m * S + s);
+                    a[i][0] = t.x;
+                    a[i][1] = t.y;
+                    a[i][2] = t.z;
+                    a[i][3] = t.w;
+                } else {
+                    const float4 u0 = reinterpret_cast<const float4 *>(pq + m * S + s)[0];
+                    const float4 u1 = reinterpret_cast<const float4 *>(pq + m * S + s)[1];
+                    const float2 w[4] = {make_float2(u0.x, u0.y), make_float2(u0.z, u0.w), make_float2(u1.x, u1.y),
+                                         make_float2(u1.z, u1.w)};
+#pragma unroll
+                    for (int v = 0; v < 4; v++) {
+                        const pair_ff pr = pair_get(w[v]);
+                        a[i][v] = 2.f * (pr.p.hi + pr.p.lo) * (pr.q.hi + pr.q.lo);
+                    }
+                }
+                if (dcl) {
+                    const float4 t = *reinterpret_cast<const float4 *>(dcl + m * S + s);
+                    c[i][0] = cload[m] + t.x;
+                    c[i][1] = cload[m] + t.y;
+                    c[i][2] = cload[m] + t.z;
+                    c[i][3] = cload[m] + t.w;
+                } else {
+#pragma unroll
+                    for (int v = 0; v < 4; v++) c[i][v] = cload[m];
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 2; i++)
+#pragma unroll
+            for (int v = 0; v < 4; v++) {
+                const ff t = two_sum(acc[v].hi, a[i][v] * c[i][v]);
+                acc[v] = fast_two_sum(t.hi, t.lo + acc[v].lo);
+            }
+    }
+#pragma unroll
+    for (int v = 0; v < 4; v++) partials[(s + v) * nchunks + blockIdx.y] = (double)acc[v].hi + (double)acc[v].lo;
+}
+
 // one warp per scenario: lane l sums chunks l, l + 32, ... in order, then a fixed shuffle tree
 __global__ void k_sumb_final(const double *__restrict__ partials, int nchunks, int64_t S, double K, double *out) {
     const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -507,9 +566,14 @@ void launch_powerb(const DevDesign &d, const BatchBufs &b, int tr_mode, double K
     const int64_t S = b.S;
     int64_t chunk = 0;
     const int nch = nchunks_of(d.n_nets, &chunk);
-    k_powerb_partials<<<dim3((unsigned)cdiv(S, 128), (unsigned)nch), 128, 0, s>>>(
-        b.pq, tr_mode == 2 ? b.tq : b.tr_in, d.cload, b.dcl, b.partials, d.n_nets, d.n_start, S, chunk, nch,
-        tr_mode);
+    if (S % 4 == 0)
+        k_powerb_partials4<<<dim3((unsigned)cdiv(S / 4, 128), (unsigned)nch), 128, 0, s>>>(
+            b.pq, tr_mode == 2 ? b.tq : b.tr_in, d.cload, b.dcl, b.partials, d.n_nets, d.n_start, S, chunk, nch,
+            tr_mode);
+    else
+        k_powerb_partials<<<dim3((unsigned)cdiv(S, 128), (unsigned)nch), 128, 0, s>>>(
+            b.pq, tr_mode == 2 ? b.tq : b.tr_in, d.cload, b.dcl, b.partials, d.n_nets, d.n_start, S, chunk, nch,
+            tr_mode);
     k_sumb_final<<<(unsigned)cdiv(S * 32, 256), 256, 0, s>>>(b.partials, nch, S, K, b.power);
 }
 
