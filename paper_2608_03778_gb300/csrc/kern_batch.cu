@@ -29,6 +29,15 @@ __global__ void k_fwdb_start(const float *__restrict__ sp_in, float2 *pq, int64_
     pq[i] = make_float2(sp_in[i], 0.f);
 }
 
+// the same, four values per thread (n a multiple of 4): one 16-byte load, two 16-byte stores
+__global__ void k_fwdb_start4(const float *__restrict__ sp_in, float2 *pq, int64_t n) {
+    const int64_t i = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    if (i >= n) return;
+    const float4 a = *reinterpret_cast<const float4 *>(sp_in + i);
+    reinterpret_cast<float4 *>(pq + i)[0] = make_float4(a.x, 0.f, a.y, 0.f);
+    reinterpret_cast<float4 *>(pq + i)[1] = make_float4(a.z, 0.f, a.w, 0.f);
+}
+
 __global__ void k_fwdb_level(const uint4 *__restrict__ fanin, float2 *pq, int32_t c0, int32_t c1, int64_t ns,
                              int64_t S, OpTable ops) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -358,6 +367,51 @@ __global__ void k_bwdb_start(const int32_t *__restrict__ fptr, const float2 *__r
     }
 }
 
+// The same with four consecutive scenarios per thread (S a multiple of 4): 16-byte
+// loads of the edge adjoints, eight edges' loads in flight before they are added in
+// index order (the same order as above, so bitwise the same).
+__global__ void k_bwdb_start4(const int32_t *__restrict__ fptr, const float2 *__restrict__ pq,
+                              const float *__restrict__ cload, const float *__restrict__ dcl,
+                              const float *__restrict__ ks, const float *__restrict__ gfo, float *gsp, int64_t ns,
+                              int64_t S, int tr_mode) {
+    const int64_t s = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    pdl_trigger();
+    if (s >= S) return;
+    pdl_wait();
+    const float4 Ks = *reinterpret_cast<const float4 *>(ks + s);
+    const int64_t step = (int64_t)gridDim.y * blockDim.y;
+    for (int64_t k = (int64_t)blockIdx.y * blockDim.y + threadIdx.y; k < ns; k += step) {
+        const int32_t e0 = fptr[k], e1 = fptr[k + 1];
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int32_t e = e0; e < e1; e += 8) {
+            float4 t[8];
+#pragma unroll
+            for (int i = 0; i < 8; i++)
+                t[i] = e + i < e1 ? *reinterpret_cast<const float4 *>(gfo + (int64_t)(e + i) * S + s)
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int i = 0; i < 8; i++)
+                if (e + i < e1) {
+                    acc.x += t[i].x;
+                    acc.y += t[i].y;
+                    acc.z += t[i].z;
+                    acc.w += t[i].w;
+                }
+        }
+        float g[4] = {acc.x, acc.y, acc.z, acc.w};
+        if (tr_mode) {
+            const float ksv[4] = {Ks.x, Ks.y, Ks.z, Ks.w};
+            const float4 u0 = reinterpret_cast<const float4 *>(pq + k * S + s)[0];
+            const float4 u1 = reinterpret_cast<const float4 *>(pq + k * S + s)[1];
+            const float2 w[4] = {make_float2(u0.x, u0.y), make_float2(u0.z, u0.w), make_float2(u1.x, u1.y),
+                                 make_float2(u1.z, u1.w)};
+#pragma unroll
+            for (int v = 0; v < 4; v++) g[v] += 2.f * ksv[v] * cl_of(cload, dcl, k, S, s + v) * qmp32(w[v]);
+        }
+        *reinterpret_cast<float4 *>(gsp + k * S + s) = make_float4(g[0], g[1], g[2], g[3]);
+    }
+}
+
 // dP_s/dC_n = K_s alpha_n(s); dP_s/dpincap_c = K_s sum_j alpha_{fanin j}(s)
 // (one pin cap per cell, loading each of its fanin nets); dP_s/dTR_k = K_s C_k
 // at a startpoint in tr_mode 0, else 0
@@ -548,7 +602,10 @@ void launch_fwdb(const DevDesign &d, const BatchBufs &b, const OpTable &ops, con
         return;
     }
     const int64_t S = b.S;
-    if (d.n_start) k_fwdb_start<<<(unsigned)cdiv(d.n_start * S, 256), 256, 0, s>>>(b.sp_in, b.pq, d.n_start * S);
+    if (d.n_start && (d.n_start * S) % 4 == 0)
+        k_fwdb_start4<<<(unsigned)cdiv(d.n_start * S / 4, 256), 256, 0, s>>>(b.sp_in, b.pq, d.n_start * S);
+    else if (d.n_start)
+        k_fwdb_start<<<(unsigned)cdiv(d.n_start * S, 256), 256, 0, s>>>(b.sp_in, b.pq, d.n_start * S);
     const int v = scen_per_thread(sh, S);
     sh = fit_shape(sh, S / v);
     const dim3 blk((unsigned)sh.bx, (unsigned)sh.by);
@@ -606,9 +663,14 @@ void launch_bwdb(const DevDesign &d, const BatchBufs &b, const OpTable &ops, con
             launch_pdl(k_bwdb_level, g, blk, s, d.fanin, d.fout_ptr, (const int4 *)d.edge_fpos, b.pq, d.cload,
                        b.dcl, b.ks, b.gfo, c0, c1, d.n_start, S, ops);
     }
-    if (d.n_start)
+    if (d.n_start && S % 4 == 0) {
+        const BatchShape s4 = fit_shape(BatchShape{128, 1, 4}, S / 4);
+        launch_pdl(k_bwdb_start4, bgrid(S / 4, s4, d.n_start), dim3((unsigned)s4.bx, (unsigned)s4.by), s, d.fout_ptr,
+                   b.pq, d.cload, b.dcl, b.ks, b.gfo, b.gsp, d.n_start, S, tr_mode);
+    } else if (d.n_start) {
         launch_pdl(k_bwdb_start, bgrid(S, sh1, d.n_start), dim3((unsigned)sh1.bx, (unsigned)sh1.by), s, d.fout_ptr,
                    b.pq, d.cload, b.dcl, b.ks, b.gfo, b.gsp, d.n_start, S, tr_mode);
+    }
 }
 
 void launch_gradb(const DevDesign &d, const BatchBufs &b, const OpTable &ops, int tr_mode, bool reduce, float *gtr,
