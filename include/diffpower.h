@@ -93,8 +93,11 @@ typedef struct {
                                is multiplied by its beta (Eq. 6);
                             2: hybrid, exact gradient of sum K beta TR C with beta fixed */
     int32_t sim_words;   /* T, 64-bit words per net: 64*T vectors, 64*(T-1) transitions (Eq. 4); 2..4096 */
-    int32_t schedule;    /* 0 (default) and 2: one cooperative launch per pass with grid-wide
-                               level barriers;
+    int32_t schedule;    /* 0 (default): for a small design (dp_info.block_threads > 0) the
+                               forward and the reverse pass each run in one thread block, with
+                               block barriers between levels and the pairs and edge adjoints
+                               in shared memory; otherwise, and for the simulation, as 2;
+                            2: one cooperative launch per pass with grid-wide level barriers;
                             1: one launch per level;
                             3: dataflow forward pass - warps take cells in topological order and
                                wait only for their own fanins (other passes as 2).
@@ -111,6 +114,9 @@ typedef struct {
     int32_t n_levels;    /* depth: cells sit on levels 1..n_levels (Sec. III-A) */
     int32_t n_ops;       /* distinct cell functions (logic ids) in use */
     size_t device_bytes; /* device memory held by the design, bytes */
+    int32_t block_threads; /* > 0: the design is small enough for the single-block forward and
+                              reverse passes (schedules 0 and 4), run with this many threads;
+                              0: it is not (and always 0 from dp_compiled_info) */
 } dp_info;
 
 /* Fills *cfg with the defaults above. */

@@ -203,6 +203,8 @@ void rec(dp_design *D, int i, cudaStream_t s) {
 bool persistent(const dp_design *D, const dp_config &c, int which) {
     return c.schedule != 1 && D->grid[which] > 0 && D->d.n_levels > 0;
 }
+// the forward and reverse passes of a small design in one block (schedule 0)
+bool small_pass(const dp_design *D, const dp_config &c) { return c.schedule == 0 && D->block_threads > 0; }
 bool dataflow(const dp_design *D, const dp_config &c, int which) {
     return c.schedule == 3 && D->flow_grid[which] > 0 && D->d.n_levels > 0;
 }
@@ -215,6 +217,10 @@ cudaError_t q_forward(dp_design *D, const dp_config &c, cudaStream_t s, cudaEven
     if (dataflow(D, c, 0)) {
         if (ready) cudaEventRecord(ready, s);
         cudaError_t e = dp::launch_fwd_flow(D->d, D->ops, c.tr_mode, D->flow_grid[0], D->flow_sleep, s);
+        if (e != cudaSuccess) return e;
+    } else if (small_pass(D, c)) {
+        if (ready) cudaEventRecord(ready, s);
+        cudaError_t e = dp::launch_fwd_block(D->d, D->ops, c.tr_mode, D->block_threads, s);
         if (e != cudaSuccess) return e;
     } else if (persistent(D, c, 0)) {
         cudaError_t e = dp::launch_fwd_persist(D->d, D->ops, c.tr_mode, D->grid[0], s, ready);
@@ -261,6 +267,8 @@ cudaError_t q_hybrid(dp_design *D, const dp_config &c, cudaStream_t s) {
 
 cudaError_t q_backward(dp_design *D, const dp_config &c, float *gsp, cudaStream_t s) {
     const float K = (float)power_K(c);
+    if (small_pass(D, c))
+        return dp::launch_bwd_block(D->d, D->ops, c.grad_mode, c.tr_mode, K, gsp, D->n_edges, D->block_threads, s);
     if (persistent(D, c, 2)) return dp::launch_bwd_persist(D->d, D->ops, c.grad_mode, c.tr_mode, K, gsp, D->grid[2], s);
     for (int l = D->d.n_levels; l >= 1; l--)
         dp::launch_bwd_level(D->d, D->ops, D->lvl_ptr[l - 1], D->lvl_ptr[l], c.grad_mode, K, s);
@@ -631,6 +639,14 @@ dp_status dp_design_upload(dp_ctx *ctx, const dp_compiled *cp, dp_design **out) 
     if (e == cudaSuccess) e = cudaMemsetAsync(d.pq, 0, sizeof(float4) * nn, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.bar, 0, sizeof(unsigned) * dp::persist_bar_words(cp->n_levels), st);
     for (int w = 0; w < 4; w++) D->grid[w] = dp::persist_grid(w, ctx->sm_count);
+    {
+        int32_t width = 0;
+        for (int l = 1; l <= cp->n_levels; l++) width = std::max(width, cp->lvl_ptr[l] - cp->lvl_ptr[l - 1]);
+        const size_t smem = dp::block_smem(1, cp->n_nets, cp->n_edges, cp->n_levels);
+        if (cp->n_levels > 0 && width <= dp::kBlockMaxWidth && smem <= (size_t)dp::kBlockSmemMax &&
+            dp::block_smem_init())
+            D->block_threads = std::min(dp::kBlockThreads, std::max(256, (width + 31) / 32 * 32));
+    }
     if (const char *v = std::getenv("DP_FLOW_BLOCKS")) D->flow_blocks_per_sm = std::atoi(v);
     if (const char *v = std::getenv("DP_FLOW_SLEEP")) D->flow_sleep = (unsigned)std::atoi(v);
     D->flow_grid[0] = dp::flow_grid(0, ctx->sm_count, D->flow_blocks_per_sm);
@@ -688,6 +704,7 @@ dp_status dp_design_info(const dp_design *D, dp_info *info) {
     info->n_levels = D->d.n_levels;
     info->n_ops = D->n_ops;
     info->device_bytes = D->bytes + D->batch.bytes + D->batch.vbytes;
+    info->block_threads = D->block_threads;
     return DP_OK;
 }
 

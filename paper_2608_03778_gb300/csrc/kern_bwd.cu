@@ -21,9 +21,7 @@ __device__ __forceinline__ float fanout_sum(const int32_t *__restrict__ fptr, co
 
 // grad_mode 0: g = acc + local; 1: g = beta (acc + local) (Eq. 6); 2: g = acc + beta local
 __device__ __forceinline__ float combine(int grad_mode, float acc, float local, const float *beta, int64_t n) {
-    if (grad_mode == 1) return beta[n] * (acc + local);
-    if (grad_mode == 2) return acc + beta[n] * local;
-    return acc + local;
+    return adj_combine(grad_mode, acc, local, grad_mode ? beta[n] : 1.f);
 }
 
 __global__ void k_bwd_level(const uint4 *__restrict__ fanin, const int32_t *__restrict__ fptr,
@@ -35,7 +33,7 @@ __global__ void k_bwd_level(const uint4 *__restrict__ fanin, const int32_t *__re
     const int64_t n = ns + c;
     const float acc = fanout_sum(fptr, gfo, n);
     // local term: d(K C 2P(1-P))/dP = K C (2 - 4P) = 2 K C (Q - P)
-    const float g = combine(grad_mode, acc, 2.f * K * cload[n] * pair_qmp(pq[n]), beta, n);
+    const float g = combine(grad_mode, acc, adj_local(K, cload[n], pair_qmp(pq[n])), beta, n);
     gnet[n] = g;
     const uint4 r = fanin[c];
     const uint32_t op = r.x >> 24;
@@ -57,7 +55,7 @@ __global__ void k_bwd_start(const int32_t *__restrict__ fptr, const float4 *__re
     if (k >= ns) return;
     const float acc = fanout_sum(fptr, gfo, k);
     // a startpoint has a local SP term only when its TR is derived from its SP (tr_mode 1)
-    const float local = tr_mode ? 2.f * K * cload[k] * pair_qmp(pq[k]) : 0.f;
+    const float local = tr_mode ? adj_local(K, cload[k], pair_qmp(pq[k])) : 0.f;
     const float g = combine(grad_mode, acc, local, beta, k);
     gnet[k] = g;
     if (out) out[k] = g;

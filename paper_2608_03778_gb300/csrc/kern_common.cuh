@@ -231,6 +231,20 @@ __device__ __forceinline__ void cell_partials(int k, uint32_t tt, const float (&
     }
 }
 
+// The adjoint's local term 2 K C (Q - P) (the derivative of K C 2PQ with respect to P) and its
+// combination with the fanout sum acc -- grad_mode 0: acc + local; 1: beta (acc + local)
+// (Eq. 6); 2: acc + beta local.  Every operation is rounded on its own (no contraction into
+// an FMA, which the compiler may or may not form depending on the surrounding code), so every
+// schedule gives the same bits.
+__device__ __forceinline__ float adj_local(float K, float cl, float qmp) {
+    return __fmul_rn(__fmul_rn(__fmul_rn(2.f, K), cl), qmp);
+}
+__device__ __forceinline__ float adj_combine(int grad_mode, float acc, float local, float b) {
+    if (grad_mode == 1) return __fmul_rn(b, __fadd_rn(acc, local));
+    if (grad_mode == 2) return __fadd_rn(acc, __fmul_rn(b, local));
+    return __fadd_rn(acc, local);
+}
+
 // Sum of a net's edge adjoints gfo[e0..e1) in index order (the order every
 // schedule uses, so results match bit for bit).  Loads go out in batches of
 // 8 before the additions, so a high-fanout net costs one L2 round trip per

@@ -121,9 +121,7 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd_persist(
 
 // --------------------------------------------------------------- backward
 __device__ __forceinline__ float combine(int grad_mode, float acc, float local, float b) {
-    if (grad_mode == 1) return b * (acc + local);
-    if (grad_mode == 2) return acc + b * local;
-    return acc + local;
+    return adj_combine(grad_mode, acc, local, b);
 }
 
 // everything the adjoint of one cell needs except its fanout contributions
@@ -145,7 +143,7 @@ __device__ __forceinline__ BwdStatic bwd_static(const uint4 *fanin, const int32_
     s.e0 = fptr[n];
     s.e1 = fptr[n + 1];
     // local term: d(K C 2P(1-P))/dP = 2 K C (Q - P)
-    s.local = 2.f * K * cload[n] * pair_qmp(pq[n]);
+    s.local = adj_local(K, cload[n], pair_qmp(pq[n]));
     s.b = grad_mode ? beta[n] : 1.f;
     const uint32_t op = r.x >> 24;
     s.k = op_arity(ops, op);
@@ -200,7 +198,143 @@ __global__ void __launch_bounds__(kPersistThreads) k_bwd_persist(
     if (!level_barrier(bar + 32 * (L - 1), err, gridDim.x, limit)) return;
     for (int64_t k = tid; k < ns; k += T) {
         const float acc = fanout_sum_l2(gfo, fptr[k], fptr[k + 1]);
-        const float local = tr_mode ? 2.f * K * cload[k] * pair_qmp(pq[k]) : 0.f;
+        const float local = tr_mode ? adj_local(K, cload[k], pair_qmp(pq[k])) : 0.f;
+        const float g = combine(grad_mode, acc, local, grad_mode ? beta[k] : 1.f);
+        gnet[k] = g;
+        if (out_gsp) out_gsp[k] = g;
+    }
+}
+
+// ------------------------- forward and reverse of a small design in one block
+// For a design whose levels hold at most kBlockMaxWidth cells and whose state
+// fits in one SM's shared memory: the whole pass in a single block, one cell
+// per thread and level.  The level barrier is a block barrier, and the data a
+// level reads from the levels before it -- the (P, Q) pairs in the forward
+// pass, the pairs and the edge adjoints in the reverse pass -- sit in shared
+// memory, so a level costs a block barrier, shared-memory gathers and the
+// cell's arithmetic instead of a grid-wide barrier through L2 and gathers from
+// L2.  The fanin records of the next level are loaded while the current one
+// computes.  Every value is computed by the same code in the same order as in
+// the grid-wide passes, so the results are bitwise the same.
+//
+// Shared memory, forward: n_nets pairs, then the n_levels + 1 level bounds.
+// Reverse: n_nets pairs, n_edges edge adjoints, the level bounds.
+
+__device__ __forceinline__ void load_bounds(int *slvl, const int32_t *lvl, int L) {
+    for (int i = threadIdx.x; i <= L; i += blockDim.x) slvl[i] = lvl[i];
+}
+
+__global__ void __launch_bounds__(kBlockThreads) k_fwd_block(
+    const uint4 *__restrict__ fanin, float4 *pq, float *tr, const float *__restrict__ sp_in,
+    const float *__restrict__ tr_in, const int32_t *__restrict__ lvl, int L, int64_t ns, int64_t nn, int tr_mode,
+    OpTable ops, const uint32_t *epoch) {
+    extern __shared__ float4 spq[];
+    int *slvl = reinterpret_cast<int *>(spq + nn);
+    const int t = threadIdx.x;
+    const uint32_t par = epoch[0] & 1u;
+    load_bounds(slvl, lvl, L);
+    for (int64_t k = t; k < ns; k += blockDim.x) {
+        const pair_ff a = pair_of(sp_in[k]);
+        const float4 v = pair_store(a, par);
+        pq[k] = v;
+        spq[k] = v;
+        tr[k] = tr_mode ? pair_tr(a) : tr_in[k];
+    }
+    __syncthreads();
+    uint4 r = make_uint4(0, 0, 0, 0);
+    if (L > 0 && slvl[0] + t < slvl[1]) r = fanin[slvl[0] + t];
+    for (int l = 1; l <= L; l++) {
+        const int64_t c = slvl[l - 1] + t;
+        const bool on = c < slvl[l];
+        uint4 rn = make_uint4(0, 0, 0, 0);
+        if (l < L && slvl[l] + t < slvl[l + 1]) rn = fanin[slvl[l] + t];   // the next level's record
+        if (l > 1) __syncthreads();   // the levels below are in shared memory
+        if (on) {
+            const uint32_t op = r.x >> 24;
+            const int k = op_arity(ops, op);
+            pair_ff x[4];
+            gather_ff<false>(spq, r, k, x);
+            const pair_ff o = cell_pair(k, op_tt(ops, op), x);
+            const float4 v = pair_store(o, par);
+            spq[ns + c] = v;
+            pq[ns + c] = v;
+            tr[ns + c] = pair_tr(o);
+        }
+        r = rn;
+    }
+}
+
+// the raw static data of one cell for the reverse pass
+struct BwdRaw {
+    uint4 r;
+    int4 ep;
+    int32_t e0, e1;
+    float cl, b;
+};
+
+__device__ __forceinline__ BwdRaw bwd_raw(const uint4 *fanin, const int32_t *fptr, const int4 *efpos,
+                                          const float *cload, const float *beta, int64_t c, int64_t ns,
+                                          int grad_mode) {
+    BwdRaw w;
+    const int64_t n = ns + c;
+    w.r = fanin[c];
+    w.ep = efpos[c];
+    w.e0 = fptr[n];
+    w.e1 = fptr[n + 1];
+    w.cl = cload[n];
+    w.b = grad_mode ? beta[n] : 1.f;
+    return w;
+}
+
+__global__ void __launch_bounds__(kBlockThreads) k_bwd_block(
+    const uint4 *__restrict__ fanin, const int32_t *__restrict__ fptr, const int4 *__restrict__ efpos,
+    const float4 *__restrict__ pq, const float *__restrict__ cload, const float *__restrict__ beta, float *gnet,
+    const int32_t *__restrict__ lvl, int L, int64_t ns, int64_t nn, int64_t ne, int grad_mode, int tr_mode,
+    float K, float *out_gsp, OpTable ops) {
+    extern __shared__ float4 spq[];
+    float *sgfo = reinterpret_cast<float *>(spq + nn);
+    int *slvl = reinterpret_cast<int *>(sgfo + ne);
+    const int t = threadIdx.x;
+    load_bounds(slvl, lvl, L);
+#pragma unroll 8
+    for (int64_t k = t; k < nn; k += blockDim.x) spq[k] = pq[k];
+    BwdRaw w{};
+    if (L > 0 && lvl[L - 1] + t < lvl[L]) w = bwd_raw(fanin, fptr, efpos, cload, beta, lvl[L - 1] + t, ns, grad_mode);
+    __syncthreads();
+    for (int l = L; l >= 1; l--) {
+        const int64_t c = slvl[l - 1] + t;
+        const bool on = c < slvl[l];
+        // the cell's static part (as in the grid-wide pass), from the pairs in shared memory
+        float local = 0.f, d[4] = {0.f, 0.f, 0.f, 0.f};
+        int k = 0;
+        if (on) {
+            local = adj_local(K, w.cl, pair_qmp(spq[ns + c]));
+            const uint32_t op = w.r.x >> 24;
+            k = op_arity(ops, op);
+            float p[4], q[4];
+            gather_pairs(spq, w.r, k, p, q);
+            cell_partials(k, op_tt(ops, op), p, q, d);
+        }
+        const BwdRaw cur = w;
+        if (l > 1 && slvl[l - 2] + t < slvl[l - 1])   // the next level's raw data
+            w = bwd_raw(fanin, fptr, efpos, cload, beta, slvl[l - 2] + t, ns, grad_mode);
+        if (l < L) __syncthreads();   // the levels above have written their edge adjoints
+        if (on) {
+            float acc = 0.f;
+            for (int32_t e = cur.e0; e < cur.e1; e++) acc += sgfo[e];
+            const float g = combine(grad_mode, acc, local, cur.b);
+            gnet[ns + c] = g;
+            if (k > 0) sgfo[cur.ep.x] = g * d[0];
+            if (k > 1) sgfo[cur.ep.y] = g * d[1];
+            if (k > 2) sgfo[cur.ep.z] = g * d[2];
+            if (k > 3) sgfo[cur.ep.w] = g * d[3];
+        }
+    }
+    __syncthreads();
+    for (int64_t k = t; k < ns; k += blockDim.x) {
+        float acc = 0.f;
+        for (int32_t e = fptr[k]; e < fptr[k + 1]; e++) acc += sgfo[e];
+        const float local = tr_mode ? adj_local(K, cload[k], pair_qmp(spq[k])) : 0.f;
         const float g = combine(grad_mode, acc, local, grad_mode ? beta[k] : 1.f);
         gnet[k] = g;
         if (out_gsp) out_gsp[k] = g;
@@ -528,6 +662,34 @@ cudaError_t launch_bwd_persist(const DevDesign &d, const OpTable &ops, int grad_
     return launch_coop(k_bwd_persist, grid, kPersistThreads, s, d.fanin, d.fout_ptr, (const int4 *)d.edge_fpos,
                        (const float4 *)d.pq, (const float *)d.cload, (const float *)d.beta, d.gnet, d.gfo, d.lvl,
                        d.n_levels, d.n_start, grad_mode, tr_mode, K, out_gsp, ops, bar, d.err, kWaitLimitCycles);
+}
+
+size_t block_smem(int which, int64_t n_nets, int64_t n_edges, int n_levels) {
+    return (size_t)n_nets * sizeof(float4) + (which ? (size_t)n_edges * sizeof(float) : 0) +
+           (size_t)(n_levels + 1) * sizeof(int);
+}
+
+bool block_smem_init() {
+    return cudaFuncSetAttribute(k_fwd_block, cudaFuncAttributeMaxDynamicSharedMemorySize, kBlockSmemMax) ==
+               cudaSuccess &&
+           cudaFuncSetAttribute(k_bwd_block, cudaFuncAttributeMaxDynamicSharedMemorySize, kBlockSmemMax) ==
+               cudaSuccess;
+}
+
+cudaError_t launch_fwd_block(const DevDesign &d, const OpTable &ops, int tr_mode, int threads, cudaStream_t s) {
+    const size_t smem = block_smem(0, d.n_nets, 0, d.n_levels);
+    k_fwd_block<<<1, threads, smem, s>>>(d.fanin, d.pq, d.tr, d.sp_in, d.tr_in, d.lvl, d.n_levels, d.n_start,
+                                         d.n_nets, tr_mode, ops, d.epoch);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bwd_block(const DevDesign &d, const OpTable &ops, int grad_mode, int tr_mode, float K,
+                             float *out_gsp, int64_t n_edges, int threads, cudaStream_t s) {
+    const size_t smem = block_smem(1, d.n_nets, n_edges, d.n_levels);
+    k_bwd_block<<<1, threads, smem, s>>>(d.fanin, d.fout_ptr, (const int4 *)d.edge_fpos, (const float4 *)d.pq,
+                                         d.cload, d.beta, d.gnet, d.lvl, d.n_levels, d.n_start, d.n_nets, n_edges,
+                                         grad_mode, tr_mode, K, out_gsp, ops);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_probe_levels(float *buf, int levels, int gather, int grid, int threads, unsigned *bar, int *err,

@@ -20,6 +20,11 @@ constexpr int kPersistThreads = 512;
 // thread per cell of a 38,912-cell level)
 constexpr int kFwdThreads = 256;
 constexpr int kSimThreads = 512;
+// the single-block passes of small designs: at most kBlockMaxWidth cells per level
+// (one per thread) and state within kBlockSmemMax bytes of shared memory
+constexpr int kBlockThreads = 1024;
+constexpr int kBlockMaxWidth = kBlockThreads;
+constexpr int kBlockSmemMax = 227 * 1024;
 // bounded waits give up after this many SM cycles (about 2 s at 2 GHz)
 constexpr long long kWaitLimitCycles = 4000000000LL;
 
@@ -95,6 +100,14 @@ cudaError_t launch_sim_wide(const DevDesign &d, const OpTable &ops, int T, int g
 size_t persist_bar_words(int n_levels);      // counters needed by the three passes
 // ready (may be null) is recorded on s just before the kernel: a branch forked there becomes
 // ready with it rather than ahead of it
+// the forward and the reverse pass of a small design in one block (kern_persist.cu);
+// block_smem(0 forward, 1 reverse, ...): the dynamic shared memory each needs;
+// block_smem_init: raises the kernels' shared-memory limit to kBlockSmemMax (once)
+size_t block_smem(int which, int64_t n_nets, int64_t n_edges, int n_levels);
+bool block_smem_init();
+cudaError_t launch_fwd_block(const DevDesign &d, const OpTable &ops, int tr_mode, int threads, cudaStream_t s);
+cudaError_t launch_bwd_block(const DevDesign &d, const OpTable &ops, int grad_mode, int tr_mode, float K,
+                             float *out_gsp, int64_t n_edges, int threads, cudaStream_t s);
 cudaError_t launch_fwd_persist(const DevDesign &d, const OpTable &ops, int tr_mode, int grid, cudaStream_t s,
                                cudaEvent_t ready = nullptr);
 cudaError_t launch_sim_persist(const DevDesign &d, const OpTable &ops, int T, int grid, cudaStream_t s);

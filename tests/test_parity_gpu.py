@@ -111,7 +111,7 @@ def check_against_oracle(o, g, sp_in, tr_in, cfg):
     return ref
 
 
-@pytest.mark.parametrize("schedule", [0, 1, 3])
+@pytest.mark.parametrize("schedule", [0, 1, 2, 3])
 @pytest.mark.parametrize("grad_mode", [0, 1, 2])
 @pytest.mark.parametrize("tr_mode", [0, 1])
 def test_small_all_modes(dp, ctx, library_text, grad_mode, tr_mode, schedule):
@@ -229,6 +229,63 @@ def test_step_is_deterministic(dp, ctx, library_text, other_schedule):
     for k in ["sp", "tr", "beta", "toggles", "grad_sp_in", "grad_pincap", "grad_cload", "grad_tr_in"]:
         np.testing.assert_array_equal(a[k], b[k])
     assert a["power_model"] == b["power_model"] and a["power_hybrid"] == b["power_hybrid"]
+
+
+# Single-block passes of small designs (schedule 0): the state a block keeps in shared memory
+# is n_nets pairs (16 B), n_edges edge adjoints (4 B) and n_levels + 1 level bounds (4 B), at
+# most 227 KiB, and a level holds at most 1,024 cells.
+BLOCK_SMEM_MAX = 227 * 1024
+
+
+def block_state_bytes(info):
+    return info.n_nets * 16 + info.n_edges * 4 + (info.n_levels + 1) * 4
+
+
+BLOCK_CASES = {
+    # name: (netlist spec or None for the random 0..4-input netlist, single-block expected)
+    "small": (netgen.WORKLOADS["small"], True),
+    "serve_5000": (netgen.WORKLOADS["serve_5000"], True),
+    "near_limit": (netgen.NetlistSpec(8_800, 64, 512, 30, 16, 7), True),    # 98 % of the limit
+    "just_over": (netgen.NetlistSpec(9_000, 64, 512, 30, 16, 7), False),    # 100.6 %
+    "wide_level": (netgen.NetlistSpec(3_000, 200, 100, 2, 16, 8), False),   # 1,500 cells a level
+    "random_4input": (None, True),
+}
+
+
+@pytest.mark.parametrize("case", list(BLOCK_CASES))
+def test_single_block_passes_match_grid_passes(dp, ctx, library_text, case):
+    """Schedule 0 takes the single-block forward and reverse passes exactly when a design fits
+    them, and gives the same bits as the grid-wide passes (schedule 2) in every gradient mode;
+    the near-limit design is also checked against the oracle."""
+    spec, expect = BLOCK_CASES[case]
+    if spec is None:
+        text, lib = custom_case(np.random.default_rng(77), n_in=12, n_cells=900)
+    else:
+        text, lib = netgen.netlist_text(spec), library_text
+    d = dp.dp_design_load(ctx, text, lib)
+    info = dp.dp_design_info(d)
+    dp.dp_design_free(d)
+    c = dp.dp_compile(text, lib)
+    width = int(np.diff(np.asarray(dp.dp_compiled_view_get(c)["lvl_ptr"])).max())
+    dp.dp_compiled_free(c)
+    fits = block_state_bytes(info) <= BLOCK_SMEM_MAX and width <= 1024
+    assert (info.block_threads > 0) == expect and expect == fits
+    if expect:
+        assert 256 <= info.block_threads <= 1024 and info.block_threads % 32 == 0
+    if case == "near_limit":
+        assert block_state_bytes(info) > 0.97 * BLOCK_SMEM_MAX
+    sp, tr = netgen.scenario_inputs(info.n_start, 1000)
+    for grad_mode, tr_mode in [(0, 1), (1, 0), (2, 1)]:
+        runs = [gpu_run(dp, ctx, text, lib, sp[:, 0], tr[:, 0],
+                        dp.config(grad_mode=grad_mode, tr_mode=tr_mode, schedule=sch)) for sch in (0, 2)]
+        for k in ["sp", "tr", "beta", "tr_hyb", "toggles", "grad_sp_in", "grad_tr_in", "grad_pincap",
+                  "grad_cload"]:
+            np.testing.assert_array_equal(runs[0][k], runs[1][k], err_msg=k)
+        assert runs[0]["power_model"] == runs[1]["power_model"]
+        assert runs[0]["power_hybrid"] == runs[1]["power_hybrid"]
+        if case in ("near_limit", "random_4input"):
+            cfg = dp.config(grad_mode=grad_mode, tr_mode=tr_mode)
+            check_against_oracle(Oracle(text, lib), runs[0], sp[:, 0], tr[:, 0], cfg)
 
 
 # ---------------------------------------------------------------- edge cases

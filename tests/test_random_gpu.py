@@ -56,7 +56,7 @@ def test_random_single_scenario(dp, ctx, seed):
     o = Oracle(text, lib)
     sp, tr = random_inputs(rng, o.n_start)
     cfg = dp.config(tr_mode=int(rng.integers(2)), grad_mode=int(rng.integers(3)),
-                    schedule=int(rng.choice([0, 1, 3])), sim_words=int(rng.choice([4, 16, 20, 64, 100])),
+                    schedule=int(rng.choice([0, 1, 2, 3])), sim_words=int(rng.choice([4, 16, 20, 64, 100])),
                     seed=int(rng.integers(1 << 40)))
     use_step = bool(rng.integers(2))
     on_device = bool(rng.integers(2))
