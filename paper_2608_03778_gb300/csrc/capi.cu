@@ -213,14 +213,17 @@ bool dataflow(const dp_design *D, const dp_config &c, int which) {
 // The forward pass and the model power.  ready (may be null) is recorded on s just before
 // the first forward kernel: a branch forked there becomes ready with that kernel.
 cudaError_t q_forward(dp_design *D, const dp_config &c, cudaStream_t s, cudaEvent_t ready = nullptr) {
+    if (small_pass(D, c)) {   // the kernel advances the pass counter itself
+        if (ready) cudaEventRecord(ready, s);
+        cudaError_t e = dp::launch_fwd_block(D->d, D->ops, c.tr_mode, D->block_threads, s);
+        if (e != cudaSuccess) return e;
+        dp::launch_power(D->d, false, power_K(c), 0, s);
+        return cudaGetLastError();
+    }
     dp::launch_bump(D->d.epoch, s);   // new parity for the stored (P, Q) pairs
     if (dataflow(D, c, 0)) {
         if (ready) cudaEventRecord(ready, s);
         cudaError_t e = dp::launch_fwd_flow(D->d, D->ops, c.tr_mode, D->flow_grid[0], D->flow_sleep, s);
-        if (e != cudaSuccess) return e;
-    } else if (small_pass(D, c)) {
-        if (ready) cudaEventRecord(ready, s);
-        cudaError_t e = dp::launch_fwd_block(D->d, D->ops, c.tr_mode, D->block_threads, s);
         if (e != cudaSuccess) return e;
     } else if (persistent(D, c, 0)) {
         cudaError_t e = dp::launch_fwd_persist(D->d, D->ops, c.tr_mode, D->grid[0], s, ready);
@@ -642,7 +645,7 @@ dp_status dp_design_upload(dp_ctx *ctx, const dp_compiled *cp, dp_design **out) 
     {
         int32_t width = 0;
         for (int l = 1; l <= cp->n_levels; l++) width = std::max(width, cp->lvl_ptr[l] - cp->lvl_ptr[l - 1]);
-        const size_t smem = dp::block_smem(1, cp->n_nets, cp->n_edges, cp->n_levels);
+        const size_t smem = dp::block_smem(1, cp->n_nets, cp->n_edges, cp->n_levels);   // the larger of the two
         if (cp->n_levels > 0 && width <= dp::kBlockMaxWidth && smem <= (size_t)dp::kBlockSmemMax &&
             dp::block_smem_init())
             D->block_threads = std::min(dp::kBlockThreads, std::max(256, (width + 31) / 32 * 32));

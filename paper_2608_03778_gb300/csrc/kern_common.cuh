@@ -231,6 +231,35 @@ __device__ __forceinline__ void cell_partials(int k, uint32_t tt, const float (&
     }
 }
 
+// The gradients that do not go through the adjoint, one element each (alpha: TR_model, or the
+// hybrid TR; K in binary32): d P / d C_load of user net u, d P / d pincap of user cell u (K times
+// the alpha of the cell's input nets), d P / d TR_in of startpoint k (K beta C_load in tr_mode 0).
+__device__ __forceinline__ float grad_cload_of(const float *alpha, const int32_t *net_of_user, float K, int64_t u) {
+    return K * alpha[net_of_user[u]];
+}
+__device__ __forceinline__ float grad_pincap_of(const uint4 *fanin, const float *alpha, const int32_t *cell_of_user,
+                                                float K, int64_t u, const OpTable &ops) {
+    const uint4 r = fanin[cell_of_user[u]];
+    const int k = op_arity(ops, r.x >> 24);
+    const uint32_t n[4] = {r.x & kMask24, r.y, r.z, r.w};
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < 4; j++)
+        if (j < k) s += alpha[n[j]];
+    return K * s;
+}
+__device__ __forceinline__ float grad_tr_in_of(const float *beta, const float *cload, float K, int tr_mode, int64_t k) {
+    return tr_mode ? 0.f : K * (beta ? beta[k] : 1.f) * cload[k];
+}
+
+// butterfly sum of one double per lane over the warp (every lane gets the sum); the power
+// reductions use this one function, so their order is the same wherever they run
+__device__ __forceinline__ double warp_sum_f64(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    return v;
+}
+
 // The adjoint's local term 2 K C (Q - P) (the derivative of K C 2PQ with respect to P) and its
 // combination with the fanout sum acc -- grad_mode 0: acc + local; 1: beta (acc + local)
 // (Eq. 6); 2: acc + beta local.  Every operation is rounded on its own (no contraction into

@@ -51,11 +51,7 @@ __global__ void k_set_pincap(const int32_t *__restrict__ cells, const float *__r
     if (u >= 0 && u < nc) pincap[cell_of_user[u]] = caps[i];
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-    return v;
-}
+__device__ __forceinline__ double warp_sum(double v) { return warp_sum_f64(v); }
 
 // power partials: a fixed grid and a fixed per-thread stride make the FP64
 // summation order independent of timing, so the result is reproducible
@@ -96,37 +92,27 @@ __global__ void __launch_bounds__(kPowerThreads) k_power_final(const double *__r
     }
 }
 
-// d P / d C_load (user net order) = K alpha
-// alpha: TR_model, or the hybrid TR beta * TR_model as k_hybrid stores it (one gather per net)
-__global__ void k_grad_cload(const float *__restrict__ alpha, const int32_t *__restrict__ net_of_user, float K,
-                             float *out, int64_t nn) {
-    int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (u >= nn) return;
-    out[u] = K * alpha[net_of_user[u]];
-}
-
-// d P / d pincap (user cell order) = K * sum over the cell's inputs of alpha
-__global__ void k_grad_pincap(const uint4 *__restrict__ fanin, const float *__restrict__ alpha,
-                              const int32_t *__restrict__ cell_of_user, float K, float *out, int64_t nc,
-                              OpTable ops) {
-    int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (u >= nc) return;
-    const uint4 r = fanin[cell_of_user[u]];
-    const int k = op_arity(ops, r.x >> 24);
-    const uint32_t n[4] = {r.x & kMask24, r.y, r.z, r.w};
-    float s = 0.f;
-#pragma unroll
-    for (int j = 0; j < 4; j++)
-        if (j < k) s += alpha[n[j]];
-    out[u] = K * s;
-}
-
-// d P / d TR_in (startpoint order) = K beta C_load when the startpoint TR is an input (tr_mode 0)
-__global__ void k_grad_tr_in(const float *__restrict__ beta, const float *__restrict__ cload, float K, int tr_mode,
-                             float *out, int64_t ns) {
-    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= ns) return;
-    out[k] = tr_mode ? 0.f : K * (beta ? beta[k] : 1.f) * cload[k];
+// The output gradients that do not go through the adjoint, in one launch: blocks [0, bp) take
+// d P / d pincap (user cell order: K times the alpha of the cell's inputs), the next bc blocks
+// d P / d C_load (user net order: K alpha), the rest d P / d TR_in (startpoint order: K beta
+// C_load when the startpoint TR is an input, tr_mode 0).  alpha: TR_model, or the hybrid TR
+// beta * TR_model as k_hybrid stores it.  The block's role is uniform over the block.
+__global__ void k_cap_grads(const uint4 *__restrict__ fanin, const float *__restrict__ alpha,
+                            const float *__restrict__ beta, const float *__restrict__ cload,
+                            const int32_t *__restrict__ net_of_user, const int32_t *__restrict__ cell_of_user, float K,
+                            int tr_mode, float *gpin, float *gcl, float *gtr, int64_t nc, int64_t nn, int64_t ns,
+                            unsigned bp, unsigned bc, OpTable ops) {
+    const unsigned b = blockIdx.x;
+    if (b < bp) {
+        const int64_t u = (int64_t)b * blockDim.x + threadIdx.x;
+        if (u < nc) gpin[u] = grad_pincap_of(fanin, alpha, cell_of_user, K, u, ops);
+    } else if (b < bp + bc) {
+        const int64_t u = (int64_t)(b - bp) * blockDim.x + threadIdx.x;
+        if (u < nn) gcl[u] = grad_cload_of(alpha, net_of_user, K, u);
+    } else {
+        const int64_t k = (int64_t)(b - bp - bc) * blockDim.x + threadIdx.x;
+        if (k < ns) gtr[k] = grad_tr_in_of(beta, cload, K, tr_mode, k);
+    }
 }
 
 __global__ void k_gather_f32(const float *__restrict__ src, const int32_t *__restrict__ idx, float *dst, int64_t n) {
@@ -191,15 +177,13 @@ void launch_cap_grads(const DevDesign &d, const OpTable &ops, bool hybrid, int t
                           float *grad_cload, float *grad_pincap, float *grad_tr_in, cudaStream_t s) {
     const float *beta = hybrid ? d.beta : nullptr;
     const float *alpha = hybrid ? d.trh : d.tr;   // trh = beta * TR_model, the same binary32 product
-    if (grad_cload && d.n_nets)
-        k_grad_cload<<<(unsigned)cdiv(d.n_nets, 256), 256, 0, s>>>(alpha, d.net_of_user, (float)K, grad_cload,
-                                                                   d.n_nets);
-    if (grad_pincap && d.n_cells)
-        k_grad_pincap<<<(unsigned)cdiv(d.n_cells, 256), 256, 0, s>>>(d.fanin, alpha, d.cell_of_user, (float)K,
-                                                                     grad_pincap, d.n_cells, ops);
-    if (grad_tr_in && d.n_start)
-        k_grad_tr_in<<<(unsigned)cdiv(d.n_start, 256), 256, 0, s>>>(beta, d.cload, (float)K, tr_mode, grad_tr_in,
-                                                                     d.n_start);
+    const unsigned bp = grad_pincap ? (unsigned)cdiv(d.n_cells, 256) : 0u;
+    const unsigned bc = grad_cload ? (unsigned)cdiv(d.n_nets, 256) : 0u;
+    const unsigned bt = grad_tr_in ? (unsigned)cdiv(d.n_start, 256) : 0u;
+    if (bp + bc + bt)
+        k_cap_grads<<<bp + bc + bt, 256, 0, s>>>(d.fanin, alpha, beta, d.cload, d.net_of_user, d.cell_of_user,
+                                                 (float)K, tr_mode, grad_pincap, grad_cload, grad_tr_in, d.n_cells,
+                                                 d.n_nets, d.n_start, bp, bc, ops);
 }
 
 void launch_gather_f32(const float *src, const int32_t *idx, float *dst, int64_t n, cudaStream_t s) {

@@ -217,21 +217,34 @@ __global__ void __launch_bounds__(kPersistThreads) k_bwd_persist(
 // computes.  Every value is computed by the same code in the same order as in
 // the grid-wide passes, so the results are bitwise the same.
 //
-// Shared memory, forward: n_nets pairs, then the n_levels + 1 level bounds.
-// Reverse: n_nets pairs, n_edges edge adjoints, the level bounds.
+// The forward kernel also advances the pass counter (whose parity tags the stored pairs).  All
+// static data a pass reads is prefetched into L2 at its start: the loads a level issues for the
+// next one then wait for L2, not for DRAM.  (The model power stays with the grid-wide
+// reduction kernels: the FP64 sum of a design's terms on one SM's narrow FP64 pipe took longer
+// than those two launches.)
+//
+// Shared memory, forward: n_nets pairs, then the n_levels + 1 level bounds.  Reverse: n_nets
+// pairs, n_edges edge adjoints, the level bounds.
 
 __device__ __forceinline__ void load_bounds(int *slvl, const int32_t *lvl, int L) {
     for (int i = threadIdx.x; i <= L; i += blockDim.x) slvl[i] = lvl[i];
 }
 
+// every 128-byte line of bytes [p, p + n) into L2
+__device__ __forceinline__ void prefetch_all_l2(const void *p, int64_t n) {
+    const char *c = static_cast<const char *>(p);
+    for (int64_t i = (int64_t)threadIdx.x * 128; i < n; i += (int64_t)blockDim.x * 128) prefetch_l2(c + i);
+}
+
 __global__ void __launch_bounds__(kBlockThreads) k_fwd_block(
     const uint4 *__restrict__ fanin, float4 *pq, float *tr, const float *__restrict__ sp_in,
-    const float *__restrict__ tr_in, const int32_t *__restrict__ lvl, int L, int64_t ns, int64_t nn, int tr_mode,
-    OpTable ops, const uint32_t *epoch) {
+    const float *__restrict__ tr_in, const int32_t *__restrict__ lvl, int L, int64_t ns, int64_t nn, int tr_mode, OpTable ops, uint32_t *epoch) {
     extern __shared__ float4 spq[];
     int *slvl = reinterpret_cast<int *>(spq + nn);
     const int t = threadIdx.x;
-    const uint32_t par = epoch[0] & 1u;
+    const uint32_t pass = epoch[0] + 1u;   // this pass's number
+    const uint32_t par = pass & 1u;
+    prefetch_all_l2(fanin, (nn - ns) * (int64_t)sizeof(uint4));
     load_bounds(slvl, lvl, L);
     for (int64_t k = t; k < ns; k += blockDim.x) {
         const pair_ff a = pair_of(sp_in[k]);
@@ -262,6 +275,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_fwd_block(
         }
         r = rn;
     }
+    if (t == 0) epoch[0] = pass;   // every thread read the old value before the level barriers
 }
 
 // the raw static data of one cell for the reverse pass
@@ -295,6 +309,12 @@ __global__ void __launch_bounds__(kBlockThreads) k_bwd_block(
     float *sgfo = reinterpret_cast<float *>(spq + nn);
     int *slvl = reinterpret_cast<int *>(sgfo + ne);
     const int t = threadIdx.x;
+    const int64_t nc = nn - ns;
+    prefetch_all_l2(fanin, nc * (int64_t)sizeof(uint4));
+    prefetch_all_l2(efpos, nc * (int64_t)sizeof(int4));
+    prefetch_all_l2(fptr, (nn + 1) * (int64_t)sizeof(int32_t));
+    prefetch_all_l2(cload, nn * (int64_t)sizeof(float));
+    if (grad_mode) prefetch_all_l2(beta, nn * (int64_t)sizeof(float));
     load_bounds(slvl, lvl, L);
 #pragma unroll 8
     for (int64_t k = t; k < nn; k += blockDim.x) spq[k] = pq[k];

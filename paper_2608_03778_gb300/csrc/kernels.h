@@ -24,7 +24,7 @@ constexpr int kSimThreads = 512;
 // (one per thread) and state within kBlockSmemMax bytes of shared memory
 constexpr int kBlockThreads = 1024;
 constexpr int kBlockMaxWidth = kBlockThreads;
-constexpr int kBlockSmemMax = 227 * 1024;
+constexpr int kBlockSmemMax = 224 * 1024;   // dynamic; the 227 KiB a block may hold less room for static arrays
 // bounded waits give up after this many SM cycles (about 2 s at 2 GHz)
 constexpr long long kWaitLimitCycles = 4000000000LL;
 
@@ -105,6 +105,7 @@ size_t persist_bar_words(int n_levels);      // counters needed by the three pas
 // block_smem_init: raises the kernels' shared-memory limit to kBlockSmemMax (once)
 size_t block_smem(int which, int64_t n_nets, int64_t n_edges, int n_levels);
 bool block_smem_init();
+// (the forward kernel also advances the pass counter)
 cudaError_t launch_fwd_block(const DevDesign &d, const OpTable &ops, int tr_mode, int threads, cudaStream_t s);
 cudaError_t launch_bwd_block(const DevDesign &d, const OpTable &ops, int grad_mode, int tr_mode, float K,
                              float *out_gsp, int64_t n_edges, int threads, cudaStream_t s);
