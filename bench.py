@@ -107,17 +107,17 @@ def batched_algorithmic_bytes(nn: int, ns: int, nc: int, ne: int, S: int) -> int
 TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,lts__t_bytes.sum,... (one launch),
     # 2M-cell step, 4th step (profiles/roofline_step_k_sim_wide_traffic.md)
-    "k_sim_wide": {"bytes": 224_364_032 + 162_103_808, "l2_bytes": 7_802_348_064, "workload": "roofline",
+    "k_sim_wide": {"bytes": 224_431_360 + 162_189_312, "l2_bytes": 7_804_701_728, "workload": "roofline",
                    "files": ["kern_persist.cu", "kern_common.cuh"],
-                   "sha": "8e07f42ec529d814"},
+                   "sha": "37d79a88186f3586"},
 }
 
 
 # L2 <-> SM throughput ceiling for the L2 fraction of the dominant kernel: ncu's peak of
 # lts__t_bytes on this part (summarised with the capture under profiles/); None until measured.
-L2_PEAK_GBS = 36_170.0
-L2_PEAK_SOURCE = ("ncu on k_sim_wide, 2M-cell step: lts__t_bytes.sum.per_second 11,488 GB/s at "
-                  "lts__t_bytes.sum.pct_of_peak_sustained_elapsed 31.76 %")
+L2_PEAK_GBS = 36_230.0
+L2_PEAK_SOURCE = ("ncu on k_sim_wide, 2M-cell step: lts__t_bytes.sum.per_second 11,532 GB/s at "
+                  "lts__t_bytes.sum.pct_of_peak_sustained_elapsed 31.83 %")
 
 
 def kernel_l2_bytes(kernel: str, workload: str) -> int | None:
