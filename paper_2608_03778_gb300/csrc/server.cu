@@ -280,6 +280,9 @@ cudaError_t capture_batch_graph(dp_server *srv, Slot *sl, int64_t Sg, bool grad,
     cudaMemcpyAsync(sl->h_power, B.b.power, sizeof(double) * (size_t)Sg, cudaMemcpyDeviceToHost, st);
     e = cudaStreamEndCapture(st, &g);
     if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+    // upload now: the first launch of an executable graph otherwise uploads it, and the
+    // worker would pay that (milliseconds for a large design's level chain) inside a batch
+    if (e == cudaSuccess) e = cudaGraphUpload(*out, st);
     if (g) cudaGraphDestroy(g);
     return e;
 }
