@@ -454,6 +454,37 @@ def bench_config_passes(dp, torch, dev, name: str, reps: int, pk: dict, with_sim
     return out
 
 
+# The paper's kernel times (Table II: forward "Alg.", bitwise simulation, backward; 1x A100,
+# its three proprietary designs), beside which the same passes are timed on synthetic
+# netlists of the same cell count and depth.  Context only: other hardware, other designs.
+PAPER_TABLE_II_MS = {
+    "paper_small": {"cells": 13_000, "levels": 70, "forward": 13.5, "bitwise": 12.4, "backward": 13.2},
+    "paper_medium": {"cells": 117_000, "levels": 84, "forward": 16.1, "bitwise": 16.0, "backward": 16.5},
+    "paper_large": {"cells": 652_000, "levels": 104, "forward": 28.9, "bitwise": 26.9, "backward": 24.2},
+}
+
+
+def bench_paper_shaped(dp, torch, dev, reps: int, pk: dict) -> dict:
+    """Forward, 4,096-vector simulation and backward on synthetic netlists with the cell count
+    and depth of the paper's three designs, L2 flushed, beside the paper's Table II times."""
+    out = {}
+    for name, paper in PAPER_TABLE_II_MS.items():
+        r = bench_config_passes(dp, torch, dev, name, reps, pk, True)
+        fb, sim = r["fwd_bwd"], r["simulation"]
+        out[name] = {"workload": r["workload"],
+                     "forward_ms": fb["forward_ms"], "backward_ms": fb["backward_ms"],
+                     "fwd_bwd_ms": fb["ms"], "simulation_levels_ms": sim["levels_ms"],
+                     "simulation_ms": sim["median_ms"],
+                     "paper_a100_ms": {k: paper[k] for k in ("forward", "bitwise", "backward")},
+                     "paper_over_this": {"forward": paper["forward"] / fb["forward_ms"],
+                                         "bitwise": paper["bitwise"] / sim["levels_ms"],
+                                         "backward": paper["backward"] / fb["backward_ms"]}}
+    out["note"] = ("context only: the paper's times are its A100 on its proprietary designs; these are "
+                   "synthetic netlists of the same cell count and depth (the generator's fanin mix, "
+                   "about 3.2 pins per cell against the paper's 4), 4,096 simulated vectors")
+    return out
+
+
 def bench_batched(args, dp, torch, dev, pk: dict) -> dict:
     """The 120,000-cell netlist x 512 input-activity scenarios (scenario-innermost SoA, one
     launch per level for all scenarios, launch shapes from the library's autotuner):
@@ -747,7 +778,8 @@ def main() -> None:
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-scenario measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the request-server measurement")
     ap.add_argument("--no-fd", action="store_true", help="skip the adjoint-vs-finite-difference timing")
-    ap.add_argument("--no-configs", action="store_true", help="skip the 2K- and 120K-cell single-scenario timings")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the 2K- and 120K-cell single-scenario timings and the paper-shaped netlists")
     ap.add_argument("--no-probe", action="store_true", help="skip the level-latency probe")
     ap.add_argument("--serving-only", action="store_true", help=argparse.SUPPRESS)   # the child of serving_in_child
     ap.add_argument("--device", type=int, default=0, help=argparse.SUPPRESS)
@@ -913,6 +945,7 @@ def main() -> None:
     if not args.no_configs:
         line["configs"] = {"small": bench_config_passes(dp, torch, dev, "small", max(args.steps, 50), pk, False),
                            "mid": bench_config_passes(dp, torch, dev, "mid", max(args.steps, 50), pk, True)}
+        line["paper_shaped"] = bench_paper_shaped(dp, torch, dev, max(args.steps, 20), pk)
     if not args.no_batched:
         line["batched"] = bench_batched(args, dp, torch, dev, pk)
     if rank == 0 and not args.no_serving:

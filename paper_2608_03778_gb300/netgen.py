@@ -104,6 +104,19 @@ for _i, _n in enumerate([5_000, 20_000, 50_000, 120_000, 300_000, 600_000, 1_000
     WORKLOADS[f"serve_{_n}"] = _serve_spec(_n, _i + 1)
 
 
+def _paper_spec(n_cells: int, depth: int, seed: int) -> NetlistSpec:
+    # the cell count and depth of the paper's three designs (Table II / III); startpoints
+    # as in the serving designs
+    n_start = int(round(n_cells * 0.0737))
+    n_pi = n_start // 9
+    return NetlistSpec(n_cells, n_pi, n_start - n_pi, depth, 32 if n_cells >= 500_000 else 16, seed)
+
+
+WORKLOADS["paper_small"] = _paper_spec(13_000, 70, 11)
+WORKLOADS["paper_medium"] = _paper_spec(117_000, 84, 12)
+WORKLOADS["paper_large"] = _paper_spec(652_000, 104, 13)
+
+
 def library_text() -> str:
     """The synthetic library: 13 functions x X1/X2/X4 (pin cap 0.8/1.6/3.2 fF) and DFF_X1."""
     lib = _load()
