@@ -123,6 +123,17 @@ def test_small_all_modes(dp, ctx, library_text, grad_mode, tr_mode, schedule):
     check_against_oracle(o, g, sp[:, 0], tr[:, 0], cfg)
 
 
+@pytest.mark.parametrize("grad_mode", [0, 1])
+def test_paper_small_shape(dp, ctx, library_text, grad_mode):
+    """The 13,000-cell, 70-level netlist of the paper-shaped timings, against the oracle."""
+    text = netgen.netlist_text(netgen.WORKLOADS["paper_small"])
+    o = Oracle(text, library_text)
+    sp, tr = netgen.scenario_inputs(o.n_start, 1000)
+    cfg = dp.config(grad_mode=grad_mode)
+    g = gpu_run(dp, ctx, text, library_text, sp[:, 0], tr[:, 0], cfg, use_step=grad_mode == 1)
+    check_against_oracle(o, g, sp[:, 0], tr[:, 0], cfg)
+
+
 @pytest.mark.parametrize("use_step,on_device", [(False, True), (True, False), (True, True)])
 def test_mid_paths(dp, ctx, library_text, use_step, on_device):
     text = netgen.netlist_text(netgen.WORKLOADS["mid"])
