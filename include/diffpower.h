@@ -96,7 +96,10 @@ typedef struct {
     int32_t schedule;    /* 0 (default): for a small design (dp_info.block_threads > 0) the
                                forward and the reverse pass each run in one thread block, with
                                block barriers between levels and the pairs and edge adjoints
-                               in shared memory; otherwise, and for the simulation, as 2;
+                               in shared memory; for a mid-size one (dp_info.cluster_threads >
+                               0) in one cluster of 16 blocks, with the cluster barrier between
+                               levels and the pairs and edge adjoints spread over the blocks'
+                               shared memory; otherwise, and for the simulation, as 2;
                             2: one cooperative launch per pass with grid-wide level barriers;
                             1: one launch per level;
                             3: dataflow forward pass - warps take cells in topological order and
@@ -115,8 +118,11 @@ typedef struct {
     int32_t n_ops;       /* distinct cell functions (logic ids) in use */
     size_t device_bytes; /* device memory held by the design, bytes */
     int32_t block_threads; /* > 0: the design is small enough for the single-block forward and
-                              reverse passes (schedules 0 and 4), run with this many threads;
+                              reverse passes (schedule 0), run with this many threads;
                               0: it is not (and always 0 from dp_compiled_info) */
+    int32_t cluster_threads; /* > 0: the design is not, but fits the single-cluster passes
+                                (schedule 0: 16 blocks of this many threads, nets spread over
+                                their shared memory); 0 otherwise and from dp_compiled_info */
 } dp_info;
 
 /* Fills *cfg with the defaults above. */

@@ -205,6 +205,8 @@ bool persistent(const dp_design *D, const dp_config &c, int which) {
 }
 // the forward and reverse passes of a small design in one block (schedule 0)
 bool small_pass(const dp_design *D, const dp_config &c) { return c.schedule == 0 && D->block_threads > 0; }
+// ... and of a mid-size design in one thread-block cluster (schedule 0)
+bool cluster_pass(const dp_design *D, const dp_config &c) { return c.schedule == 0 && D->cl.threads > 0; }
 bool dataflow(const dp_design *D, const dp_config &c, int which) {
     return c.schedule == 3 && D->flow_grid[which] > 0 && D->d.n_levels > 0;
 }
@@ -221,7 +223,11 @@ cudaError_t q_forward(dp_design *D, const dp_config &c, cudaStream_t s, cudaEven
         return cudaGetLastError();
     }
     dp::launch_bump(D->d.epoch, s);   // new parity for the stored (P, Q) pairs
-    if (dataflow(D, c, 0)) {
+    if (cluster_pass(D, c)) {
+        if (ready) cudaEventRecord(ready, s);
+        cudaError_t e = dp::launch_fwd_cluster(D->d, D->ops, D->cl, c.tr_mode, s);
+        if (e != cudaSuccess) return e;
+    } else if (dataflow(D, c, 0)) {
         if (ready) cudaEventRecord(ready, s);
         cudaError_t e = dp::launch_fwd_flow(D->d, D->ops, c.tr_mode, D->flow_grid[0], D->flow_sleep, s);
         if (e != cudaSuccess) return e;
@@ -272,6 +278,8 @@ cudaError_t q_backward(dp_design *D, const dp_config &c, float *gsp, cudaStream_
     const float K = (float)power_K(c);
     if (small_pass(D, c))
         return dp::launch_bwd_block(D->d, D->ops, c.grad_mode, c.tr_mode, K, gsp, D->n_edges, D->block_threads, s);
+    if (cluster_pass(D, c))
+        return dp::launch_bwd_cluster(D->d, D->ops, D->cl, c.grad_mode, c.tr_mode, K, gsp, s);
     if (persistent(D, c, 2)) return dp::launch_bwd_persist(D->d, D->ops, c.grad_mode, c.tr_mode, K, gsp, D->grid[2], s);
     for (int l = D->d.n_levels; l >= 1; l--)
         dp::launch_bwd_level(D->d, D->ops, D->lvl_ptr[l - 1], D->lvl_ptr[l], c.grad_mode, K, s);
@@ -650,6 +658,71 @@ dp_status dp_design_upload(dp_ctx *ctx, const dp_compiled *cp, dp_design **out) 
             dp::block_smem_init())
             D->block_threads = std::min(dp::kBlockThreads, std::max(256, (width + 31) / 32 * 32));
     }
+    if (D->block_threads == 0 && cp->n_levels > 0 && e == cudaSuccess) {
+        // the single-cluster passes: level l (level 0: the startpoints) cut into C contiguous
+        // chunks, block b computing chunk b and holding its nets at consecutive slots
+        const int C = dp::kClusterBlocks, L = cp->n_levels;
+        auto lo_of = [&](int l) { return l ? ns + cp->lvl_ptr[(size_t)l - 1] : (int64_t)0; };
+        auto hi_of = [&](int l) { return l ? ns + cp->lvl_ptr[(size_t)l] : ns; };
+        std::vector<int32_t> chunk((size_t)L + 1);
+        int most = 0;
+        for (int l = 0; l <= L; l++) {
+            chunk[(size_t)l] = (int32_t)((hi_of(l) - lo_of(l) + C - 1) / C);
+            if (l) most = std::max(most, chunk[(size_t)l]);
+        }
+        const int threads = std::max(64, (most + 31) / 32 * 32);
+        std::vector<int32_t> base((size_t)C * (L + 1));
+        std::vector<int64_t> held((size_t)C, 0);
+        for (int l = 0; l <= L; l++)
+            for (int b = 0; b < C; b++) {
+                base[(size_t)b * (L + 1) + l] = (int32_t)held[(size_t)b];
+                held[(size_t)b] += std::min<int64_t>(chunk[(size_t)l],
+                                                     std::max<int64_t>(0, hi_of(l) - lo_of(l) - (int64_t)b * chunk[(size_t)l]));
+            }
+        const int64_t slots = *std::max_element(held.begin(), held.end());
+        if (threads <= dp::kClusterMaxThreads && dp::cluster_smem(0, slots, 0, L) <= (size_t)dp::kBlockSmemMax) {
+            std::vector<int32_t> loc((size_t)nn), lfptr((size_t)nn);
+            for (int l = 0; l <= L; l++)
+                for (int64_t i = 0; i < hi_of(l) - lo_of(l); i++) {
+                    const int64_t b = i / chunk[(size_t)l];
+                    loc[(size_t)(lo_of(l) + i)] =
+                        (int32_t)((b << 24) | (base[(size_t)b * (L + 1) + l] + i % chunk[(size_t)l]));
+                }
+            std::vector<int64_t> fill((size_t)C, 0);
+            for (int64_t n = 0; n < nn; n++) {
+                const size_t b = (size_t)((uint32_t)loc[(size_t)n] >> 24);
+                lfptr[(size_t)n] = (int32_t)fill[b];
+                fill[b] += cp->fout_ptr[(size_t)n + 1] - cp->fout_ptr[(size_t)n];
+            }
+            const int64_t edges = *std::max_element(fill.begin(), fill.end());
+            const size_t sf = dp::cluster_smem(0, slots, 0, L), sb = dp::cluster_smem(1, slots, edges, L);
+            if (sb <= (size_t)dp::kBlockSmemMax && dp::cluster_fits(threads, sf, sb)) {
+                std::vector<int32_t> floc(4 * (size_t)nc, 0), lefpos(4 * (size_t)nc, -1);
+                for (int64_t c = 0; c < nc; c++) {
+                    const uint32_t *r = &cp->fanin[4 * (size_t)c];
+                    const int k = cp->op_arity[r[0] >> 24];
+                    for (int j = 0; j < k; j++) {
+                        const uint32_t m = j == 0 ? (r[0] & dp::kNetMask) : r[j];
+                        floc[4 * (size_t)c + j] = loc[m];
+                        lefpos[4 * (size_t)c + j] = lfptr[m] + (cp->edge_fpos[4 * (size_t)c + j] - cp->fout_ptr[m]);
+                    }
+                }
+                int32_t *dchunk = nullptr, *dbase = nullptr, *dfloc = nullptr, *dlfptr = nullptr, *dlefpos = nullptr;
+                TRY(dalloc(D, &dchunk, chunk.size()));
+                TRY(dalloc(D, &dbase, base.size()));
+                TRY(dalloc(D, &dfloc, floc.size()));
+                TRY(dalloc(D, &dlfptr, lfptr.size()));
+                TRY(dalloc(D, &dlefpos, lefpos.size()));
+                up(dchunk, chunk.data(), sizeof(int32_t) * chunk.size());
+                up(dbase, base.data(), sizeof(int32_t) * base.size());
+                up(dfloc, floc.data(), sizeof(int32_t) * floc.size());
+                up(dlfptr, lfptr.data(), sizeof(int32_t) * lfptr.size());
+                up(dlefpos, lefpos.data(), sizeof(int32_t) * lefpos.size());
+                if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // before the host vectors go
+                D->cl = dp::ClusterMap{threads, slots, edges, dchunk, dbase, dfloc, dlfptr, dlefpos};
+            }
+        }
+    }
     if (const char *v = std::getenv("DP_FLOW_BLOCKS")) D->flow_blocks_per_sm = std::atoi(v);
     if (const char *v = std::getenv("DP_FLOW_SLEEP")) D->flow_sleep = (unsigned)std::atoi(v);
     D->flow_grid[0] = dp::flow_grid(0, ctx->sm_count, D->flow_blocks_per_sm);
@@ -708,6 +781,7 @@ dp_status dp_design_info(const dp_design *D, dp_info *info) {
     info->n_ops = D->n_ops;
     info->device_bytes = D->bytes + D->batch.bytes + D->batch.vbytes;
     info->block_threads = D->block_threads;
+    info->cluster_threads = D->cl.threads;
     return DP_OK;
 }
 

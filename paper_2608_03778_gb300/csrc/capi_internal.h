@@ -88,6 +88,7 @@ struct dp_design {
     int grid[4] = {0, 0, 0, 0};   // persistent grids: forward, simulation, backward, wide simulation
     int flow_grid[2] = {0, 0};     // dataflow grids: forward, simulation
     int block_threads = 0;         // > 0: the design fits the single-block passes, with this many threads
+    dp::ClusterMap cl;             // the single-cluster passes (cl.threads > 0: the design uses them)
     // launch-shape tuning (defaults, overridable by DP_FLOW_BLOCKS / DP_FLOW_SLEEP for sweeps)
     int flow_blocks_per_sm = 2;
     unsigned flow_sleep = 0;

@@ -597,6 +597,7 @@ extern "C" dp_status dp_compiled_info(const dp_compiled *c, dp_info *info) {
     info->n_ops = c->n_ops;
     info->device_bytes = 0;
     info->block_threads = 0;
+    info->cluster_threads = 0;
     return DP_OK;
 }
 

@@ -100,6 +100,31 @@ cudaError_t launch_sim_wide(const DevDesign &d, const OpTable &ops, int T, int g
 size_t persist_bar_words(int n_levels);      // counters needed by the three passes
 // ready (may be null) is recorded on s just before the kernel: a branch forked there becomes
 // ready with it rather than ahead of it
+// the forward and the reverse pass of a mid-size design in one cluster of kClusterBlocks blocks
+// (kern_cluster.cu): every level cut into one contiguous chunk per block, each net kept in the
+// shared memory of the block that computes it, the hardware cluster barrier between levels.
+constexpr int kClusterBlocks = 16;
+constexpr int kClusterMaxThreads = 512;
+struct ClusterMap {
+    int threads = 0;                    // threads per block (0: the design does not use the cluster)
+    int64_t slots = 0;                  // the most nets one block holds
+    int64_t edges = 0;                  // the most edge adjoints one block holds
+    const int32_t *chunk = nullptr;     // [L+1] cells of level l per block (level 0: the startpoints)
+    const int32_t *base = nullptr;      // [C][L+1] first slot of block b's chunk of level l
+    const int32_t *floc = nullptr;      // [4 nc] location of each input net: owner block << 24 | slot
+    const int32_t *lfptr = nullptr;     // [nn] start of net n's fanout range in its owner's copy
+    const int32_t *lefpos = nullptr;    // [4 nc] position of each input edge in its owner's copy
+};
+// cluster_smem(0 forward, 1 reverse, ...): dynamic shared memory per block; cluster_fits:
+// whether one such cluster can run on this device (also sets the kernels' shared-memory and
+// cluster-size attributes)
+size_t cluster_smem(int which, int64_t slots, int64_t n_edges_local, int n_levels);
+bool cluster_fits(int threads, size_t smem_fwd, size_t smem_bwd);
+cudaError_t launch_fwd_cluster(const DevDesign &d, const OpTable &ops, const ClusterMap &m, int tr_mode,
+                               cudaStream_t s);
+cudaError_t launch_bwd_cluster(const DevDesign &d, const OpTable &ops, const ClusterMap &m, int grad_mode,
+                               int tr_mode, float K, float *out_gsp, cudaStream_t s);
+
 // the forward and the reverse pass of a small design in one block (kern_persist.cu);
 // block_smem(0 forward, 1 reverse, ...): the dynamic shared memory each needs;
 // block_smem_init: raises the kernels' shared-memory limit to kBlockSmemMax (once)

@@ -41,7 +41,8 @@ class dp_config(ctypes.Structure):
 class dp_info(ctypes.Structure):
     _fields_ = [("n_nets", ctypes.c_int64), ("n_start", ctypes.c_int64), ("n_cells", ctypes.c_int64),
                 ("n_edges", ctypes.c_int64), ("n_levels", ctypes.c_int32), ("n_ops", ctypes.c_int32),
-                ("device_bytes", ctypes.c_size_t), ("block_threads", ctypes.c_int32)]
+                ("device_bytes", ctypes.c_size_t), ("block_threads", ctypes.c_int32),
+                ("cluster_threads", ctypes.c_int32)]
 
 
 class dp_compiled_view(ctypes.Structure):

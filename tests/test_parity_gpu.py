@@ -242,33 +242,63 @@ def test_step_is_deterministic(dp, ctx, library_text, other_schedule):
     assert a["power_model"] == b["power_model"] and a["power_hybrid"] == b["power_hybrid"]
 
 
-# Single-block passes of small designs (schedule 0): the state the reverse block keeps in
-# shared memory is n_nets pairs (16 B), n_edges edge adjoints (4 B) and n_levels + 1 level
-# bounds (4 B), at most 224 KiB, and a level holds at most 1,024 cells.
-BLOCK_SMEM_MAX = 224 * 1024
+# Schedule 0 picks, per design, the single-block passes, the single-cluster passes or the
+# grid-wide ones.  Single block: the reverse block keeps n_nets pairs (16 B), n_edges edge
+# adjoints (4 B) and n_levels + 1 level bounds (4 B) in at most 224 KiB of shared memory, and a
+# level holds at most 1,024 cells.  Single cluster (otherwise): 16 blocks, each level cut into 16
+# contiguous chunks, each block holding its chunks' pairs and their fanout ranges' edge
+# adjoints in 224 KiB, a chunk at most 512 cells.
+SMEM_MAX = 224 * 1024
+CLUSTER = 16
 
 
 def block_state_bytes(info):
     return info.n_nets * 16 + info.n_edges * 4 + (info.n_levels + 1) * 4
 
 
-BLOCK_CASES = {
-    # name: (netlist spec or None for the random 0..4-input netlist, single-block expected)
-    "small": (netgen.WORKLOADS["small"], True),
-    "serve_5000": (netgen.WORKLOADS["serve_5000"], True),
-    "near_limit": (netgen.NetlistSpec(8_800, 64, 512, 30, 16, 7), True),    # 99.5 % of the limit
-    "just_over": (netgen.NetlistSpec(9_000, 64, 512, 30, 16, 7), False),    # 101.9 %
-    "wide_level": (netgen.NetlistSpec(3_000, 200, 100, 2, 16, 8), False),   # 1,500 cells a level
-    "random_4input": (None, True),
+def cluster_state_bytes(text, lib, info, dp):
+    """Shared memory of the busiest cluster block's reverse pass: every level (level 0: the
+    startpoints) cut into 16 contiguous chunks, block b holding chunk b's pairs and their fanout
+    ranges' edge adjoints, plus three tables of n_levels + 1 entries."""
+    c = dp.dp_compile(text, lib)
+    v = dp.dp_compiled_view_get(c)
+    fptr = np.asarray(v["fout_ptr"]).astype(np.int64)
+    lp = np.asarray(v["lvl_ptr"]).astype(np.int64)
+    dp.dp_compiled_free(c)
+    ns, nn, L = info.n_start, info.n_nets, info.n_levels
+    owner = np.zeros(nn, np.int64)
+    held = np.zeros(CLUSTER, np.int64)
+    for lo, hi in [(0, ns)] + [(ns + lp[l - 1], ns + lp[l]) for l in range(1, L + 1)]:
+        if hi > lo:
+            b = np.arange(hi - lo) // -(-(hi - lo) // CLUSTER)
+            owner[lo:hi] = b
+            held += np.bincount(b, minlength=CLUSTER)
+    edges = np.bincount(owner, weights=np.diff(fptr), minlength=CLUSTER).max()
+    return int(held.max()) * 16 + int(edges) * 4 + 3 * (L + 1) * 4
+
+
+PASS_CASES = {
+    # name: (netlist spec or None for the random 0..4-input netlist, expected passes)
+    "small": (netgen.WORKLOADS["small"], "block"),
+    "serve_5000": (netgen.WORKLOADS["serve_5000"], "block"),
+    "near_limit": (netgen.NetlistSpec(8_800, 64, 512, 30, 16, 7), "block"),    # 99.5 % of the block's room
+    "just_over": (netgen.NetlistSpec(9_000, 64, 512, 30, 16, 7), "cluster"),   # 101.9 %
+    "wide_level": (netgen.NetlistSpec(3_000, 200, 100, 2, 16, 8), "cluster"),  # 1,500 cells a level
+    "random_4input": (None, "block"),
+    "serve_20000": (netgen.WORKLOADS["serve_20000"], "cluster"),
+    "paper_small": (netgen.WORKLOADS["paper_small"], "cluster"),
+    "mid": (netgen.WORKLOADS["mid"], "cluster"),                                # 98 % of a block's room
+    "serve_300000": (netgen.WORKLOADS["serve_300000"], "grid"),
 }
 
 
-@pytest.mark.parametrize("case", list(BLOCK_CASES))
-def test_single_block_passes_match_grid_passes(dp, ctx, library_text, case):
-    """Schedule 0 takes the single-block forward and reverse passes exactly when a design fits
-    them, and gives the same bits as the grid-wide passes (schedule 2) in every gradient mode;
-    the near-limit design is also checked against the oracle."""
-    spec, expect = BLOCK_CASES[case]
+@pytest.mark.parametrize("case", list(PASS_CASES))
+def test_block_and_cluster_passes_match_grid_passes(dp, ctx, library_text, case):
+    """Schedule 0 takes the single-block or single-cluster forward and reverse passes exactly when
+    a design fits them, and gives the same bits as the grid-wide passes (schedule 2) in every
+    gradient mode, through both entry points and both output kinds; some designs are also
+    checked against the oracle."""
+    spec, expect = PASS_CASES[case]
     if spec is None:
         text, lib = custom_case(np.random.default_rng(77), n_in=12, n_cells=900)
     else:
@@ -279,15 +309,24 @@ def test_single_block_passes_match_grid_passes(dp, ctx, library_text, case):
     c = dp.dp_compile(text, lib)
     width = int(np.diff(np.asarray(dp.dp_compiled_view_get(c)["lvl_ptr"])).max())
     dp.dp_compiled_free(c)
-    fits = block_state_bytes(info) <= BLOCK_SMEM_MAX and width <= 1024
-    assert (info.block_threads > 0) == expect and expect == fits
-    if expect:
-        assert 256 <= info.block_threads <= 1024 and info.block_threads % 32 == 0
+    block = block_state_bytes(info) <= SMEM_MAX and width <= 1024
+    cluster = not block and cluster_state_bytes(text, lib, info, dp) <= SMEM_MAX and -(-width // CLUSTER) <= 512
+    got = "block" if info.block_threads > 0 else "cluster" if info.cluster_threads > 0 else "grid"
+    assert got == expect == ("block" if block else "cluster" if cluster else "grid")
+    if got == "block":
+        assert 256 <= info.block_threads <= 1024 and info.block_threads % 32 == 0 and info.cluster_threads == 0
+    if got == "cluster":
+        assert 64 <= info.cluster_threads <= 512 and info.cluster_threads % 32 == 0
+        assert info.cluster_threads >= -(-width // CLUSTER)
     if case == "near_limit":
-        assert block_state_bytes(info) > 0.97 * BLOCK_SMEM_MAX
+        assert block_state_bytes(info) > 0.97 * SMEM_MAX
+    if case == "mid":
+        assert cluster_state_bytes(text, lib, info, dp) > 0.85 * SMEM_MAX
     sp, tr = netgen.scenario_inputs(info.n_start, 1000)
-    for grad_mode, tr_mode, use_step, on_device in [(0, 1, False, False), (1, 0, True, False), (2, 1, False, True),
-                                                     (0, 0, True, True)]:
+    combos = [(0, 1, False, False), (1, 0, True, False), (2, 1, False, True), (0, 0, True, True)]
+    if case in ("mid", "serve_300000"):
+        combos = combos[1:3]
+    for grad_mode, tr_mode, use_step, on_device in combos:
         runs = [gpu_run(dp, ctx, text, lib, sp[:, 0], tr[:, 0],
                         dp.config(grad_mode=grad_mode, tr_mode=tr_mode, schedule=sch), use_step, on_device)
                 for sch in (0, 2)]
@@ -296,7 +335,7 @@ def test_single_block_passes_match_grid_passes(dp, ctx, library_text, case):
             np.testing.assert_array_equal(runs[0][k], runs[1][k], err_msg=k)
         assert runs[0]["power_model"] == runs[1]["power_model"]
         assert runs[0]["power_hybrid"] == runs[1]["power_hybrid"]
-        if case in ("near_limit", "random_4input"):
+        if case in ("near_limit", "random_4input", "just_over", "paper_small"):
             cfg = dp.config(grad_mode=grad_mode, tr_mode=tr_mode)
             check_against_oracle(Oracle(text, lib), runs[0], sp[:, 0], tr[:, 0], cfg)
 
