@@ -285,6 +285,7 @@ PASS_CASES = {
     "just_over": (netgen.NetlistSpec(9_000, 64, 512, 30, 16, 7), "cluster"),   # 101.9 %
     "wide_level": (netgen.NetlistSpec(3_000, 200, 100, 2, 16, 8), "cluster"),  # 1,500 cells a level
     "random_4input": (None, "block"),
+    "random_4input_large": (12_000, "cluster"),                                # 0..4-input cells, constants
     "serve_20000": (netgen.WORKLOADS["serve_20000"], "cluster"),
     "paper_small": (netgen.WORKLOADS["paper_small"], "cluster"),
     "mid": (netgen.WORKLOADS["mid"], "cluster"),                                # 98 % of a block's room
@@ -301,6 +302,8 @@ def test_block_and_cluster_passes_match_grid_passes(dp, ctx, library_text, case)
     spec, expect = PASS_CASES[case]
     if spec is None:
         text, lib = custom_case(np.random.default_rng(77), n_in=12, n_cells=900)
+    elif isinstance(spec, int):
+        text, lib = custom_case(np.random.default_rng(78), n_in=200, n_cells=spec)
     else:
         text, lib = netgen.netlist_text(spec), library_text
     d = dp.dp_design_load(ctx, text, lib)
@@ -335,7 +338,7 @@ def test_block_and_cluster_passes_match_grid_passes(dp, ctx, library_text, case)
             np.testing.assert_array_equal(runs[0][k], runs[1][k], err_msg=k)
         assert runs[0]["power_model"] == runs[1]["power_model"]
         assert runs[0]["power_hybrid"] == runs[1]["power_hybrid"]
-        if case in ("near_limit", "random_4input", "just_over", "paper_small"):
+        if case in ("near_limit", "random_4input", "just_over", "paper_small", "random_4input_large"):
             cfg = dp.config(grad_mode=grad_mode, tr_mode=tr_mode)
             check_against_oracle(Oracle(text, lib), runs[0], sp[:, 0], tr[:, 0], cfg)
 
