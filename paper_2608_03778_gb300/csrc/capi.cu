@@ -274,13 +274,16 @@ cudaError_t q_hybrid(dp_design *D, const dp_config &c, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t q_backward(dp_design *D, const dp_config &c, float *gsp, cudaStream_t s) {
+// beside: other kernels run beside this pass (the step's gradient outputs), so its grid-wide
+// form leaves them room on the SMs
+cudaError_t q_backward(dp_design *D, const dp_config &c, float *gsp, cudaStream_t s, bool beside = false) {
     const float K = (float)power_K(c);
     if (small_pass(D, c))
         return dp::launch_bwd_block(D->d, D->ops, c.grad_mode, c.tr_mode, K, gsp, D->n_edges, D->block_threads, s);
     if (cluster_pass(D, c))
         return dp::launch_bwd_cluster(D->d, D->ops, D->cl, c.grad_mode, c.tr_mode, K, gsp, s);
-    if (persistent(D, c, 2)) return dp::launch_bwd_persist(D->d, D->ops, c.grad_mode, c.tr_mode, K, gsp, D->grid[2], s);
+    if (persistent(D, c, 2))
+        return dp::launch_bwd_persist(D->d, D->ops, c.grad_mode, c.tr_mode, K, gsp, D->grid[2], !beside, s);
     for (int l = D->d.n_levels; l >= 1; l--)
         dp::launch_bwd_level(D->d, D->ops, D->lvl_ptr[l - 1], D->lvl_ptr[l], c.grad_mode, K, s);
     dp::launch_bwd_start(D->d, c.grad_mode, c.tr_mode, K, gsp, s);
@@ -1029,7 +1032,7 @@ dp_status dp_step(dp_design *D, const dp_config *cfg, float *gsp, float *gtr, fl
                              D->st_gtr, D->cap_stream2);
         cudaEventRecordWithFlags(D->ev_grads, D->cap_stream2, cudaEventRecordExternal);
         cudaEventRecord(D->join, D->cap_stream2);
-        if (le == cudaSuccess) le = q_backward(D, *cfg, nullptr, cs);
+        if (le == cudaSuccess) le = q_backward(D, *cfg, nullptr, cs, true);
         cudaStreamWaitEvent(cs, D->join, 0);
         cudaEventRecordWithFlags(D->ev[4], cs, cudaEventRecordExternal);
         e = cudaStreamEndCapture(cs, &graph);

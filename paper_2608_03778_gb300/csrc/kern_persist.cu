@@ -133,12 +133,11 @@ struct BwdStatic {
     int k;
 };
 
-__device__ __forceinline__ BwdStatic bwd_static(const uint4 *fanin, const int32_t *fptr, const int4 *efpos,
-                                                const float4 *pq, const float *cload, const float *beta, int64_t c,
-                                                int64_t ns, int grad_mode, float K, const OpTable &ops) {
+__device__ __forceinline__ BwdStatic bwd_static_r(const uint4 &r, const int32_t *fptr, const int4 *efpos,
+                                                  const float4 *pq, const float *cload, const float *beta, int64_t c,
+                                                  int64_t ns, int grad_mode, float K, const OpTable &ops) {
     BwdStatic s;
     const int64_t n = ns + c;
-    const uint4 r = fanin[c];
     s.ep = efpos[c];
     s.e0 = fptr[n];
     s.e1 = fptr[n + 1];
@@ -153,6 +152,62 @@ __device__ __forceinline__ BwdStatic bwd_static(const uint4 *fanin, const int32_
     return s;
 }
 
+__device__ __forceinline__ BwdStatic bwd_static(const uint4 *fanin, const int32_t *fptr, const int4 *efpos,
+                                                const float4 *pq, const float *cload, const float *beta, int64_t c,
+                                                int64_t ns, int grad_mode, float K, const OpTable &ops) {
+    return bwd_static_r(fanin[c], fptr, efpos, pq, cload, beta, c, ns, grad_mode, K, ops);
+}
+
+// the static data of one cell for the reverse pass, loaded a level before it is used (the
+// fanin pairs as stored; an unused slot as the pair P = 0, Q = 1)
+struct BwdPre {
+    int4 ep;
+    int32_t e0, e1;
+    float cl, b;
+    float4 self, in[4];
+};
+
+__device__ __forceinline__ void bwd_pre(BwdPre &w, const uint4 &r, const int32_t *fptr, const int4 *efpos,
+                                        const float4 *pq, const float *cload, const float *beta, int64_t c,
+                                        int64_t ns, int grad_mode, const OpTable &ops) {
+    const int64_t n = ns + c;
+    w.ep = efpos[c];
+    w.e0 = fptr[n];
+    w.e1 = fptr[n + 1];
+    w.cl = cload[n];
+    w.b = grad_mode ? beta[n] : 1.f;
+    w.self = pq[n];
+    const int k = op_arity(ops, r.x >> 24);
+    const uint32_t nid[4] = {r.x & kMask24, r.y, r.z, r.w};
+#pragma unroll
+    for (int j = 0; j < 4; j++) w.in[j] = j < k ? pq[nid[j]] : make_float4(0.f, 0.f, 1.f, 0.f);
+}
+
+// bwd_static_r from the preloaded data: the same operations on the same values
+__device__ __forceinline__ BwdStatic bwd_static_pre(const BwdPre &w, const uint4 &r, float K, const OpTable &ops) {
+    BwdStatic s;
+    s.ep = w.ep;
+    s.e0 = w.e0;
+    s.e1 = w.e1;
+    s.local = adj_local(K, w.cl, pair_qmp(w.self));
+    s.b = w.b;
+    const uint32_t op = r.x >> 24;
+    s.k = op_arity(ops, op);
+    float p[4], q[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        p[j] = 0.f;
+        q[j] = 1.f;
+        if (j < s.k) {
+            const float4 v = pq_decode(w.in[j]);
+            p[j] = v.x + v.y;
+            q[j] = v.z + v.w;
+        }
+    }
+    cell_partials(s.k, op_tt(ops, op), p, q, s.d);
+    return s;
+}
+
 __device__ __forceinline__ void bwd_finish(const BwdStatic &s, int64_t n, float *gnet, float *gfo, int grad_mode) {
     const float acc = fanout_sum_l2(gfo, s.e0, s.e1);
     const float g = combine(grad_mode, acc, s.local, s.b);
@@ -163,6 +218,13 @@ __device__ __forceinline__ void bwd_finish(const BwdStatic &s, int64_t n, float 
     if (s.k > 3) gfo[s.ep.w] = g * s.d[3];
 }
 
+// PRE: the whole static part of a level's cell (fanout range, edge positions, C_load, beta,
+// its own and its fanins' pairs) is loaded a level ahead and its fanin record two levels ahead,
+// so the window between a block's arrival and its wait only computes (about 120 registers:
+// the block holds its SM's register file).  Without PRE only the record is loaded a level
+// ahead and the rest in the window (64 registers), for the step, whose gradient-output kernel
+// runs beside this pass.
+template <bool PRE>
 __global__ void __launch_bounds__(kPersistThreads) k_bwd_persist(
     const uint4 *__restrict__ fanin, const int32_t *__restrict__ fptr, const int4 *__restrict__ efpos,
     const float4 *__restrict__ pq, const float *__restrict__ cload, const float *__restrict__ beta, float *gnet,
@@ -170,15 +232,34 @@ __global__ void __launch_bounds__(kPersistThreads) k_bwd_persist(
     float *out_gsp, OpTable ops, unsigned *bar, int *err, long long limit) {
     const int64_t tid = spread_tid();
     const int64_t T = (int64_t)gridDim.x * blockDim.x;
+    auto rec = [&](int l) {   // the fanin record of this thread's cell on level l (if any)
+        if (l < 1) return make_uint4(0, 0, 0, 0);
+        const int64_t cl = lvl[l - 1] + tid;
+        return cl < lvl[l] ? fanin[cl] : make_uint4(0, 0, 0, 0);
+    };
+    uint4 r1 = rec(L), r2 = PRE ? rec(L - 1) : make_uint4(0, 0, 0, 0);
+    BwdPre w;
+    if (PRE && L > 0 && lvl[L - 1] + tid < lvl[L])
+        bwd_pre(w, r1, fptr, efpos, pq, cload, beta, lvl[L - 1] + tid, ns, grad_mode, ops);
     for (int l = L; l >= 1; l--) {
         const int32_t c0 = lvl[l - 1], c1 = lvl[l];
         const int64_t c = c0 + tid;
         // the top level has no fanout inside the pass: no barrier before it.  Below it the
-        // block arrives for the level above, then gathers this level's static part (its
-        // loads do not depend on the level above) while the other blocks arrive.
+        // block arrives for the level above, then forms this level's static part (it does not
+        // depend on the level above) and issues the next level's loads while the other blocks
+        // arrive.
         if (l < L) barrier_arrive(bar + 32 * (L - 1 - l));
         BwdStatic s;
-        if (c < c1) s = bwd_static(fanin, fptr, efpos, pq, cload, beta, c, ns, grad_mode, K, ops);
+        if (PRE) {
+            if (c < c1) s = bwd_static_pre(w, r1, K, ops);
+            if (l > 1 && lvl[l - 2] + tid < lvl[l - 1])
+                bwd_pre(w, r2, fptr, efpos, pq, cload, beta, lvl[l - 2] + tid, ns, grad_mode, ops);
+            r1 = r2;
+            r2 = rec(l - 2);
+        } else {
+            if (c < c1) s = bwd_static_r(r1, fptr, efpos, pq, cload, beta, c, ns, grad_mode, K, ops);
+            r1 = rec(l - 1);
+        }
         if (l >= 3) {
             const int64_t cp = lvl[l - 3] + tid;
             if (cp < lvl[l - 2]) {
@@ -638,7 +719,13 @@ int persist_grid(int which, int sm_count) {
     if (which == 3) return wide_grid(sm_count);
     if (which == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fwd_persist, kFwdThreads, 0);
     else if (which == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sim_persist, kSimThreads, 0);
-    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bwd_persist, kPersistThreads, 0);
+    else {   // both forms of the reverse pass run on the same grid: the smaller occupancy
+        int per2 = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bwd_persist<true>, kPersistThreads, 0);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_bwd_persist<false>, kPersistThreads, 0);
+        per = per < per2 ? per : per2;
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -676,10 +763,10 @@ cudaError_t launch_sim_wide(const DevDesign &d, const OpTable &ops, int T, int g
 }
 
 cudaError_t launch_bwd_persist(const DevDesign &d, const OpTable &ops, int grad_mode, int tr_mode, float K,
-                               float *out_gsp, int grid, cudaStream_t s) {
+                               float *out_gsp, int grid, bool pre, cudaStream_t s) {
     unsigned *bar = d.bar + 2 * 32 * ((size_t)d.n_levels + 2);
     cudaMemsetAsync(bar, 0, bar_bytes(d), s);
-    return launch_coop(k_bwd_persist, grid, kPersistThreads, s, d.fanin, d.fout_ptr, (const int4 *)d.edge_fpos,
+    return launch_coop(pre ? k_bwd_persist<true> : k_bwd_persist<false>, grid, kPersistThreads, s, d.fanin, d.fout_ptr, (const int4 *)d.edge_fpos,
                        (const float4 *)d.pq, (const float *)d.cload, (const float *)d.beta, d.gnet, d.gfo, d.lvl,
                        d.n_levels, d.n_start, grad_mode, tr_mode, K, out_gsp, ops, bar, d.err, kWaitLimitCycles);
 }

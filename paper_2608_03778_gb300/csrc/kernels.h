@@ -137,8 +137,10 @@ cudaError_t launch_bwd_block(const DevDesign &d, const OpTable &ops, int grad_mo
 cudaError_t launch_fwd_persist(const DevDesign &d, const OpTable &ops, int tr_mode, int grid, cudaStream_t s,
                                cudaEvent_t ready = nullptr);
 cudaError_t launch_sim_persist(const DevDesign &d, const OpTable &ops, int T, int grid, cudaStream_t s);
+// pre: the form that loads each level's static part a level ahead (about 120 registers: no
+// other kernel fits beside it on an SM); otherwise the 64-register form
 cudaError_t launch_bwd_persist(const DevDesign &d, const OpTable &ops, int grad_mode, int tr_mode, float K,
-                               float *out_gsp, int grid, cudaStream_t s);
+                               float *out_gsp, int grid, bool pre, cudaStream_t s);
 cudaError_t launch_wait_selftest(unsigned *bar, int *err, long long limit, cudaStream_t s);
 // latency probes (buffers owned by the caller; bar zeroed by the caller, 32 words per level)
 cudaError_t launch_probe_levels(float *buf, int levels, int gather, int grid, int threads, unsigned *bar, int *err,
