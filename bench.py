@@ -107,17 +107,17 @@ def batched_algorithmic_bytes(nn: int, ns: int, nc: int, ne: int, S: int) -> int
 TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,lts__t_bytes.sum,... (one launch),
     # 2M-cell step, 4th step (profiles/roofline_step_k_sim_wide_traffic.md)
-    "k_sim_wide": {"bytes": 224_431_360 + 162_189_312, "l2_bytes": 7_804_701_728, "workload": "roofline",
+    "k_sim_wide": {"bytes": 224_526_080 + 162_210_304, "l2_bytes": 7_799_694_112, "workload": "roofline",
                    "files": ["kern_persist.cu", "kern_common.cuh"],
-                   "sha": "37d79a88186f3586"},
+                   "sha": "d68f35c894eb261c"},
 }
 
 
 # L2 <-> SM throughput ceiling for the L2 fraction of the dominant kernel: ncu's peak of
 # lts__t_bytes on this part (summarised with the capture under profiles/); None until measured.
-L2_PEAK_GBS = 36_230.0
-L2_PEAK_SOURCE = ("ncu on k_sim_wide, 2M-cell step: lts__t_bytes.sum.per_second 11,532 GB/s at "
-                  "lts__t_bytes.sum.pct_of_peak_sustained_elapsed 31.83 %")
+L2_PEAK_GBS = 36_130.0
+L2_PEAK_SOURCE = ("ncu on k_sim_wide, 2M-cell step: lts__t_bytes.sum.per_second 11,471 GB/s at "
+                  "lts__t_bytes.sum.pct_of_peak_sustained_elapsed 31.75 %")
 
 
 def kernel_l2_bytes(kernel: str, workload: str) -> int | None:
