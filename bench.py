@@ -565,10 +565,11 @@ def bench_serving(args, dp, torch, dev) -> dict:
     """Served requests on 8 resident netlists (5K, 20K, 50K, 120K, 300K, 600K, 1M and 2M cells,
     generator seeds 1-8): 2,000 requests, each naming a design uniformly and carrying either new
     input SP/TR or a sizing delta (1 % of the design's X1 cells moved to X2 or X4), half of them
-    asking for gradients.  Three runs of the same requests: Poisson arrivals at 5,000 requests/s
-    through the continuous-batching server (latency from submission to completion, p50/p99;
-    one untimed run of the same stream first, three timed ones reported); all
-    2,000 submitted at once (saturated throughput); and the plain loop - one request at a time,
+    asking for gradients.  Three kinds of runs of the same requests: Poisson arrivals at 5,000
+    requests/s through the continuous-batching server (latency from submission to completion,
+    p50/p99; one untimed run of the same stream first, then three timed ones, their medians
+    reported with every run); all 2,000 submitted at once (saturated throughput; three runs, the
+    median one reported with every run); and the plain loop - one request at a time,
     synchronous, the same kernels with one scenario per launch.  The served results must equal the
     plain loop's bit for bit."""
     from paper_2608_03778_gb300 import netgen
@@ -655,13 +656,22 @@ def bench_serving(args, dp, torch, dev) -> dict:
                          "mean_batch": (st1.requests - st0.requests) / max(nb, 1),
                          "host_launch_us_per_batch": 1e6 * (st1.host_launch_s - st0.host_launch_s) / max(nb, 1)})
             served = results()
-        # saturated
-        t0 = time.perf_counter()
-        tickets = [dp.dp_server_submit(srv, j["req"]) for j in jobs]
-        lat_sat = np.array([dp.dp_server_wait(srv, t, 600.0) for t in tickets])
-        t_sat = time.perf_counter() - t0
-        st2 = dp.dp_server_get_stats(srv)
-        saturated = results()
+        # saturated: all requests at once, three times (the median run is reported first)
+        sat_runs = []
+        for _ in range(3):
+            st1 = dp.dp_server_get_stats(srv)
+            t0 = time.perf_counter()
+            tickets = [dp.dp_server_submit(srv, j["req"]) for j in jobs]
+            lat_sat = np.array([dp.dp_server_wait(srv, t, 600.0) for t in tickets])
+            t_sat = time.perf_counter() - t0
+            st2 = dp.dp_server_get_stats(srv)
+            sat_runs.append({"throughput_rps": n_req / t_sat, "seconds": t_sat,
+                             "p50_ms": float(np.percentile(lat_sat, 50)), "p99_ms": float(np.percentile(lat_sat, 99)),
+                             "mean_batch": (st2.requests - st1.requests) / max(st2.batches - st1.batches, 1)})
+            saturated = results()
+            if not all(all(np.array_equal(x, y) for x, y in zip(a, b)) for a, b in zip(saturated, served)):
+                raise RuntimeError("saturated results differ from the Poisson runs'")
+        sat_med = sorted(sat_runs, key=lambda r: r["seconds"])[1]
         # plain loop
         t0 = time.perf_counter()
         lat_plain = np.array([dp.dp_server_wait(plain, dp.dp_server_submit(plain, j["req"]), 600.0) for j in jobs])
@@ -673,13 +683,15 @@ def bench_serving(args, dp, torch, dev) -> dict:
             "workload": "8 resident netlists serve_5000 ... serve_2000000 (seeds 1-8); 2,000 requests, half new "
                         "input SP/TR, half sizing deltas (1 % of X1 cells to X2/X4); gradients on half",
             "max_batch": max_batch,
-            "poisson": {"rate_per_s": rate, **runs[0], "runs": runs},
-            "saturated": {"throughput_rps": n_req / t_sat, "p50_ms": float(np.percentile(lat_sat, 50)),
-                          "p99_ms": float(np.percentile(lat_sat, 99)),
-                          "mean_batch": (st2.requests - st1.requests) / max(st2.batches - st1.batches, 1)},
+            "poisson": {"rate_per_s": rate,
+                        "p50_ms": float(np.median([r["p50_ms"] for r in runs])),
+                        "p99_ms": float(np.median([r["p99_ms"] for r in runs])),
+                        "throughput_rps": float(np.median([r["throughput_rps"] for r in runs])),
+                        "reported": "median over the three runs", "runs": runs},
+            "saturated": {**sat_med, "reported": "the median of three runs", "runs": sat_runs},
             "plain_loop": {"throughput_rps": n_req / t_plain, "p50_ms": float(np.percentile(lat_plain, 50)),
                            "p99_ms": float(np.percentile(lat_plain, 99))},
-            "speedup_saturated_vs_plain": t_plain / t_sat,
+            "speedup_saturated_vs_plain": t_plain / sat_med["seconds"],
             "identical_to_plain_loop": bool(same),
             "device_bytes": int(dp.dp_server_get_stats(srv).device_bytes),
         }
