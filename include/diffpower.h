@@ -496,6 +496,12 @@ dp_status dp_server_design_info(dp_server *srv, int32_t id, dp_info *info);
 /* Queues a request (validated first: DP_EINVAL) and returns its ticket without
  * waiting; thread-safe. */
 dp_status dp_server_submit(dp_server *srv, const dp_request *req, uint64_t *ticket);
+/* Queues n requests at once (reqs[n], their tickets into tickets[n]): all are validated
+ * first, and if one is invalid nothing is queued and its status (DP_EINVAL) is returned
+ * with its index in the message; otherwise they enter their designs' queues in order,
+ * under one lock, before the worker is woken, so a burst forms full batches.  A plain
+ * server runs them one after another.  Thread-safe. */
+dp_status dp_server_submit_many(dp_server *srv, const dp_request *reqs, int32_t n, uint64_t *tickets);
 /* Waits until the request is done (timeout_s > 0: at most that long, then
  * DP_ETIMEOUT and the ticket stays valid), reports its latency from submission
  * to completion in ms and releases the ticket. */

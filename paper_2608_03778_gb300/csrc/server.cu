@@ -836,6 +836,50 @@ dp_status dp_server_submit(dp_server *srv, const dp_request *r, uint64_t *ticket
     return DP_OK;
 }
 
+dp_status dp_server_submit_many(dp_server *srv, const dp_request *reqs, int32_t n, uint64_t *tickets) {
+    if (!srv || n < 0 || (n > 0 && (!reqs || !tickets))) return DP_EINVAL;
+    if (srv->cfg.plain) {
+        for (int32_t i = 0; i < n; i++) {
+            const dp_status st = dp_server_submit(srv, &reqs[i], &tickets[i]);
+            if (st != DP_OK) return st;
+        }
+        return DP_OK;
+    }
+    std::vector<Design *> des((size_t)n, nullptr);
+    for (int32_t i = 0; i < n; i++) {
+        const dp_status st = check_request(srv, &reqs[i], &des[(size_t)i]);
+        if (st != DP_OK) {
+            std::lock_guard<std::mutex> lk(srv->emu);
+            srv->err = "request " + std::to_string(i) + ": " + srv->err;
+            return st;
+        }
+    }
+    std::vector<Req *> qs((size_t)n, nullptr);
+    for (int32_t i = 0; i < n; i++) {
+        qs[(size_t)i] = new (std::nothrow) Req();
+        if (!qs[(size_t)i]) {
+            for (Req *q : qs) delete q;
+            return srv_err(srv, DP_ENOMEM, "out of host memory");
+        }
+    }
+    const double t = now_s();
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        for (int32_t i = 0; i < n; i++) {
+            Req *q = qs[(size_t)i];
+            q->r = reqs[i];
+            q->t_submit = t;
+            q->ticket = srv->next_ticket++;
+            srv->reqs[q->ticket] = q;
+            des[(size_t)i]->queue.push_back(q);
+            tickets[i] = q->ticket;
+        }
+        srv->queued.fetch_add(n, std::memory_order_acq_rel);
+    }
+    srv->cv_work.notify_one();
+    return DP_OK;
+}
+
 dp_status dp_server_wait(dp_server *srv, uint64_t ticket, double timeout_s, double *latency_ms) {
     if (!srv) return DP_EINVAL;
     std::unique_lock<std::mutex> lk(srv->mu);

@@ -125,6 +125,7 @@ _sig("dp_server_add_design", [_P, ctypes.c_char_p, ctypes.c_size_t, ctypes.c_cha
                               ctypes.POINTER(ctypes.c_int32)])
 _sig("dp_server_design_info", [_P, ctypes.c_int32, ctypes.POINTER(dp_info)])
 _sig("dp_server_submit", [_P, ctypes.POINTER(dp_request), ctypes.POINTER(ctypes.c_uint64)])
+_sig("dp_server_submit_many", [_P, ctypes.POINTER(dp_request), ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64)])
 _sig("dp_server_wait", [_P, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(ctypes.c_double)])
 _sig("dp_server_get_stats", [_P, ctypes.POINTER(dp_server_stats)])
 _sig("dp_get_power", [_P, _S, _P, _S])
@@ -148,6 +149,7 @@ EXPORTED = ["dp_config_default", "dp_last_error", "dp_compile", "dp_compiled_fre
             "dp_get_power", "dp_set_inputs_batch", "dp_batch_tuning", "dp_backward_weighted", "dp_ascent_step",
             "dp_virus_eval", "dp_sizing_scores", "dp_server_config_default", "dp_server_create", "dp_server_destroy",
             "dp_server_last_error", "dp_server_add_design", "dp_server_design_info", "dp_server_submit",
+            "dp_server_submit_many",
             "dp_server_wait", "dp_server_get_stats"]
 
 
@@ -490,6 +492,15 @@ def dp_server_submit(srv, req: dp_request) -> int:
     t = ctypes.c_uint64()
     _scheck(_lib.dp_server_submit(srv, ctypes.byref(req), ctypes.byref(t)), srv)
     return t.value
+
+
+def dp_server_submit_many(srv, reqs) -> list:
+    """Queues a list of requests at once; returns their tickets."""
+    n = len(reqs)
+    arr = (dp_request * n)(*reqs)
+    t = (ctypes.c_uint64 * n)()
+    _scheck(_lib.dp_server_submit_many(srv, arr, n, t), srv)
+    return list(t)
 
 
 def dp_server_wait(srv, ticket: int, timeout_s: float = 0.0) -> float:

@@ -148,6 +148,37 @@ def test_alone_equals_in_mix(dp, server):
             np.testing.assert_array_equal(x, y)
 
 
+def test_burst_submission_gives_the_same_bits(dp, server):
+    """dp_server_submit_many queues a burst in one step: the results equal those of the same
+    requests run one at a time, the batches are full, and one invalid request in a burst
+    queues nothing."""
+    srv, ids, infos, refs = server
+    jobs = make_jobs(dp, ids, infos, 60, 21, refs)
+    run(dp, srv, jobs, together=False)
+    alone = [j.result() for j in jobs]
+    for j in jobs:
+        for a in j.result():
+            a[...] = 0
+    st0 = dp.dp_server_get_stats(srv)
+    tickets = dp.dp_server_submit_many(srv, [j.req for j in jobs])
+    assert len(tickets) == len(jobs) and len(set(tickets)) == len(jobs)
+    for t in tickets:
+        dp.dp_server_wait(srv, t, 60.0)
+    st1 = dp.dp_server_get_stats(srv)
+    assert st1.requests - st0.requests == len(jobs)
+    assert (st1.requests - st0.requests) / (st1.batches - st0.batches) > 4   # 60 requests on 3 designs, max 16
+    for j, a in zip(jobs, alone):
+        for x, y in zip(j.result(), a):
+            np.testing.assert_array_equal(x, y)
+    bad = dp.request(99, np.zeros(1))
+    with pytest.raises(dp.DPError) as e:
+        dp.dp_server_submit_many(srv, [jobs[0].req, bad])
+    assert e.value.name == "DP_EINVAL"
+    st2 = dp.dp_server_get_stats(srv)
+    assert st2.requests == st1.requests   # nothing from the rejected burst was queued or run
+    assert dp.dp_server_submit_many(srv, []) == []
+
+
 def test_reference_batches_skip_the_forward_with_the_same_bits(dp, server):
     """A batch of requests that all use the reference inputs starts from the forward state
     cached when the design was added; the same requests with the reference inputs given
