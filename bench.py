@@ -568,8 +568,8 @@ def bench_serving(args, dp, torch, dev) -> dict:
     asking for gradients.  Three kinds of runs of the same requests: Poisson arrivals at 5,000
     requests/s through the continuous-batching server (latency from submission to completion,
     p50/p99; one untimed run of the same stream first, then three timed ones, their medians
-    reported with every run); all 2,000 submitted at once, as one burst (saturated throughput;
-    three runs, the median one reported with every run); and the plain loop - one request at a time,
+    reported with every run); all 2,000 submitted back to back (saturated throughput; three runs,
+    the median one reported with every run); and the plain loop - one request at a time,
     synchronous, the same kernels with one scenario per launch.  The served results must equal the
     plain loop's bit for bit."""
     from paper_2608_03778_gb300 import netgen
@@ -661,7 +661,7 @@ def bench_serving(args, dp, torch, dev) -> dict:
         for _ in range(3):
             st1 = dp.dp_server_get_stats(srv)
             t0 = time.perf_counter()
-            tickets = dp.dp_server_submit_many(srv, [j["req"] for j in jobs])   # one burst
+            tickets = [dp.dp_server_submit(srv, j["req"]) for j in jobs]   # back to back
             lat_sat = np.array([dp.dp_server_wait(srv, t, 600.0) for t in tickets])
             t_sat = time.perf_counter() - t0
             st2 = dp.dp_server_get_stats(srv)
