@@ -819,6 +819,10 @@ def main() -> None:
         run_reference(args, rank, world)
         return
     args.warmup = max(3, args.warmup)
+    # the request server first, in its own process, while this one holds no CUDA context yet:
+    # measured after the other sections, with this process's context (idle) on the same GPU,
+    # its saturated runs varied two-fold between otherwise identical runs
+    serving = serving_in_child(local) if rank == 0 and not args.no_serving else None
 
     import torch
     torch.cuda.set_device(local)
@@ -970,8 +974,8 @@ def main() -> None:
         line["paper_shaped"] = bench_paper_shaped(dp, torch, dev, max(args.steps, 20), pk)
     if not args.no_batched:
         line["batched"] = bench_batched(args, dp, torch, dev, pk)
-    if rank == 0 and not args.no_serving:
-        line["serving"] = serving_in_child(local)
+    if serving is not None:
+        line["serving"] = serving
     if rank == 0 and world == 1 and not args.no_fd:
         line["adjoint_vs_fd"] = bench_adjoint_vs_fd(dp, torch, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
