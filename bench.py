@@ -708,9 +708,9 @@ def bench_serving(args, dp, torch, dev) -> dict:
 
 def serving_in_child(device: int) -> dict:
     """The serving measurement in a fresh interpreter on the same GPU: its own CUDA
-    context, threads and host allocations, so that nothing the earlier measurements
-    leave in this process enters its latencies (repeated in one process, the Poisson
-    latencies grew from run to run)."""
+    context, streams, threads and host allocations, so that nothing the earlier
+    measurements leave in this process enters its latencies (servers created one after
+    another in one process serve Poisson arrivals a little more slowly each time)."""
     drop = {"RANK", "WORLD_SIZE", "LOCAL_RANK", "LOCAL_WORLD_SIZE", "GROUP_RANK", "ROLE_RANK",
             "MASTER_ADDR", "MASTER_PORT", "TORCHELASTIC_RUN_ID"}
     env = {k: v for k, v in os.environ.items() if k not in drop}

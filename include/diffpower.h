@@ -433,7 +433,14 @@ dp_status dp_power_noalloc(int device, const float *tr, const float *beta, const
  * forward state, computed once by dp_server_add_design.  A request's
  * results do not depend on the requests it shares a batch with: they are
  * bitwise the same alone and in any mix.  Model power and model gradient
- * (Eq. 1, Eq. 2, Eq. 7); no simulation. */
+ * (Eq. 1, Eq. 2, Eq. 7); no simulation.
+ *
+ * Each slot holds one CUDA stream.  The device has a fixed number of hardware
+ * work queues (CUDA_DEVICE_MAX_CONNECTIONS, 8 unless the process sets it
+ * before its first CUDA call, at most 32); streams beyond that share queues,
+ * and a batch on a stream that shares a queue with a busy one waits behind
+ * its work.  A process that holds many other streams, or creates servers one
+ * after another, should set it to 32. */
 typedef struct dp_server dp_server;
 
 typedef struct {

@@ -185,6 +185,17 @@ dp_status ensure_words(dp_design *D, int T) {
     return s;
 }
 
+// The step graph's capture and branch streams and the side stream of its output copies,
+// created by the first dp_step.  A design that never steps (a server slot, a batched or
+// per-pass caller) holds no stream of its own: streams beyond the device's hardware work
+// queues share queues, and a stream sharing a queue with a busy one waits behind its work.
+dp_status ensure_step_streams(dp_design *D) {
+    cudaError_t e = cudaSuccess;
+    for (cudaStream_t *p : {&D->cap_stream, &D->cap_stream2, &D->out_stream})
+        if (!*p && e == cudaSuccess) e = cudaStreamCreateWithFlags(p, cudaStreamNonBlocking);
+    return e == cudaSuccess ? DP_OK : cuda_err(D->ctx, e, "step streams");
+}
+
 dp_status ensure_stage(dp_design *D) {
     if (D->st_gsp) return DP_OK;
     dp_status s;
@@ -734,11 +745,8 @@ dp_status dp_design_upload(dp_ctx *ctx, const dp_compiled *cp, dp_design **out) 
     dp::launch_cload(d, st);
     for (auto &ev : D->ev)
         if (e == cudaSuccess) e = cudaEventCreate(&ev);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&D->cap_stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&D->cap_stream2, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&D->fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&D->join, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&D->out_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&D->ev_grads, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&D->ev_copies, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaGetLastError();
@@ -999,6 +1007,7 @@ dp_status dp_step(dp_design *D, const dp_config *cfg, float *gsp, float *gtr, fl
     DeviceGuard g(D->ctx->device);
     if ((s = ensure_words(D, cfg->sim_words)) != DP_OK) return s;
     if ((s = ensure_stage(D)) != DP_OK) return s;
+    if ((s = ensure_step_streams(D)) != DP_OK) return s;
     cudaStream_t st = D->ctx->stream;
     if (!D->graph || std::memcmp(&D->graph_cfg, cfg, sizeof *cfg) != 0) {
         if (D->graph) { cudaGraphExecDestroy(D->graph); D->graph = nullptr; }
