@@ -571,12 +571,13 @@ def bench_serving(args, dp, torch, dev) -> dict:
     reported with every run); all 2,000 submitted back to back (saturated throughput; one untimed
     run, then three, the median one reported with every run); and the plain loop - one request
     at a time,
-    synchronous, the same kernels with one scenario per launch.  The served results must equal the
+    synchronous, the same kernels with one scenario per launch.  The server runs two batch slots per
+    design (one batch's copies beside the next one's kernels).  The served results must equal the
     plain loop's bit for bit."""
     from paper_2608_03778_gb300 import netgen
     names = [f"serve_{n}" for n in (5000, 20000, 50000, 120000, 300000, 600000, 1000000, 2000000)]
     lib = netgen.library_text()
-    n_req, rate, max_batch = 2000, 5000.0, 64
+    n_req, rate, max_batch, slots = 2000, 5000.0, 64, 2
     rng = np.random.default_rng(2026)
     texts = [netgen.netlist_text(netgen.WORKLOADS[n]) for n in names]
     x1 = []
@@ -586,7 +587,7 @@ def bench_serving(args, dp, torch, dev) -> dict:
         dp.dp_compiled_free(c)
         x1.append(np.flatnonzero(v["pincap"][v["cell_of_user"]] == np.float32(0.8)).astype(np.int32))
     pin = lambda n, dt: torch.empty(n, dtype=dt, pin_memory=True).numpy()  # noqa: E731
-    srv = dp.dp_server_create(dp.server_config(device=dev.index or 0, max_batch=max_batch))
+    srv = dp.dp_server_create(dp.server_config(device=dev.index or 0, max_batch=max_batch, slots_per_design=slots))
     plain = dp.dp_server_create(dp.server_config(device=dev.index or 0, plain=1))
     try:
         infos = []
@@ -689,6 +690,8 @@ def bench_serving(args, dp, torch, dev) -> dict:
             "workload": "8 resident netlists serve_5000 ... serve_2000000 (seeds 1-8); 2,000 requests, half new "
                         "input SP/TR, half sizing deltas (1 % of X1 cells to X2/X4); gradients on half",
             "max_batch": max_batch,
+            "slots_per_design": slots,
+            "cuda_device_max_connections": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS", "8 (default)"),
             "poisson": {"rate_per_s": rate,
                         "p50_ms": float(np.median([r["p50_ms"] for r in runs])),
                         "p99_ms": float(np.median([r["p99_ms"] for r in runs])),
@@ -710,10 +713,13 @@ def serving_in_child(device: int) -> dict:
     """The serving measurement in a fresh interpreter on the same GPU: its own CUDA
     context, streams, threads and host allocations, so that nothing the earlier
     measurements leave in this process enters its latencies (servers created one after
-    another in one process serve Poisson arrivals a little more slowly each time)."""
+    another in one process serve Poisson arrivals a little more slowly each time).  The
+    child gets 32 hardware work queues (CUDA_DEVICE_MAX_CONNECTIONS, unless the caller set
+    it): the server's 16 slot streams and the plain loop's 8 then share none."""
     drop = {"RANK", "WORLD_SIZE", "LOCAL_RANK", "LOCAL_WORLD_SIZE", "GROUP_RANK", "ROLE_RANK",
             "MASTER_ADDR", "MASTER_PORT", "TORCHELASTIC_RUN_ID"}
     env = {k: v for k, v in os.environ.items() if k not in drop}
+    env.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     r = subprocess.run([sys.executable, os.path.abspath(__file__), "--serving-only", "--device", str(device)],
                        env=env, capture_output=True, text=True, timeout=1800)
     if r.returncode != 0:
